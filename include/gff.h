@@ -1,0 +1,189 @@
+/*
+ * gff.h - C ABI of the GB300 Galerkin-FFT crystal-plasticity solver (libgff.so).
+ *
+ * The library solves, increment by increment, the periodic equilibrium of an
+ * RVE voxel grid with the variational (Galerkin) FFT method of Lucarini &
+ * Segurado, "On the accuracy of spectral solvers for micromechanics based
+ * fatigue modeling" (arXiv:1806.10599):
+ *   find F(x) = Fbar + F~(x) with  G(P(F, alpha)) = 0            (Eqs. linear_momentum, eql_discrete2)
+ * by Newton-Raphson (Eqs. F_dif, P_dif) whose linear systems
+ *   G(K : dF) = -G(P)                                            (Eqs. linequil, linequil2, newlinop)
+ * are solved matrix-free by conjugate gradients (Sect. 2.1), with the
+ * continuous projection G^ (Eq. G) or the discrete one G^' (Sect. 2.2), and
+ * accumulates the fatigue indicator parameters of Sect. 3.3.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns a gff_status; GFF_OK is 0, errors are negative.  On
+ *    error, gff_last_error(h) returns a message (valid until the next call on h).
+ *  - The caller owns every pointer it passes.  Pointers are HOST pointers
+ *    unless the parameter name ends in _dev, in which case they are device
+ *    pointers on the GPU current at gff_create, valid on the handle's stream.
+ *    No memory allocated by the library is returned to the caller.
+ *  - Tensors are 3x3 row-major: component c = 3*i + j.  Voxel fields are
+ *    structure-of-arrays [9][nz][ny][nx] (x fastest), N = nx*ny*nz.
+ *  - A handle is one RVE; calls on one handle must not run concurrently.
+ *  - Units are SI (Pa, s); lengths are those of gff_grid.L.
+ *  - The GPU path requires nx, ny, nz even, between 4 and 128, with no prime
+ *    factor other than 2, 3 and 5; other sizes give GFF_ERR_ARG.
+ */
+#ifndef GFF_H
+#define GFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gff_handle gff_handle;
+
+typedef enum {
+    GFF_OK = 0,
+    GFF_ERR_ARG = -1,            /* invalid argument or unsupported size            */
+    GFF_ERR_OOM = -2,            /* device allocation failed                        */
+    GFF_ERR_CUDA = -3,           /* CUDA runtime error (message has the detail)     */
+    GFF_ERR_NO_CONVERGENCE = -4, /* Newton or CG reached its iteration cap          */
+    GFF_ERR_CP_FAIL = -5,        /* crystal-plasticity local Newton failed          */
+    GFF_ERR_TIMEOUT = -6,        /* a bounded device wait gave up                   */
+    GFF_ERR_STATE = -7,          /* call out of order (e.g. no microstructure yet)  */
+    GFF_ERR_IO = -8              /* file read/write failed                          */
+} gff_status;
+
+enum { GFF_PROJ_CONTINUOUS = 0, GFF_PROJ_DISCRETE = 1 };
+enum { GFF_PREC_FP64 = 0, GFF_PREC_MIXED = 1 };
+enum { GFF_MAT_SVK_CUBIC = 0, GFF_MAT_SVK_ISO = 1, GFF_MAT_CP_FCC = 2 };
+enum {
+    GFF_FIELD_F = 0,      /* deformation gradient, 9 per voxel          */
+    GFF_FIELD_P = 1,      /* first Piola-Kirchhoff stress, 9 per voxel  */
+    GFF_FIELD_K = 2,      /* tangent dP/dF, 81 per voxel [81][N], index 9*c + d */
+    GFF_FIELD_FP_INV = 3, /* inverse plastic deformation gradient, 9    */
+    GFF_FIELD_CHI = 4,    /* backstress per slip system, 12             */
+    GFF_FIELD_GAMMA = 5,  /* cumulative signed slip per system, 12      */
+    GFF_FIELD_PCYC = 6,   /* accumulated plastic strain in the cycle, 1 */
+    GFF_FIELD_WCYC = 7    /* dissipated energy per system in the cycle, 12 */
+};
+
+typedef struct {
+    int nx, ny, nz;
+    double L[3]; /* box lengths along x, y, z */
+} gff_grid;
+
+typedef struct {
+    int kind;                /* GFF_MAT_*                                            */
+    double C11, C12, C44;    /* cubic constants (SVK_CUBIC, CP_FCC), Pa             */
+    double E, nu;            /* isotropic constants (SVK_ISO)                        */
+    double gdot0;            /* reference slip rate, 1/s        (CP_FCC, Eq. gamma_dot) */
+    double p_exp;            /* rate exponent 1/m (integer valued, CP_FCC)          */
+    double tau0;             /* critical resolved shear stress, Pa (CP_FCC)         */
+    double c_af, d_af;       /* Armstrong-Frederick backstress constants (CP_FCC)   */
+} gff_material;
+
+typedef struct {
+    int projection;    /* GFF_PROJ_*                                               */
+    int precision;     /* GFF_PREC_FP64 or GFF_PREC_MIXED (FP32 CG/FFT/projection) */
+    double newton_tol; /* stop when ||b||_2 / ||P||_2 <= newton_tol                */
+    double cg_tol;     /* CG stops when ||r|| <= max(cg_tol ||b||, 0.1 newton_tol ||P||) */
+    int newton_max, cg_max;
+    int max_cuts;      /* time-step halvings allowed after a CP failure            */
+    int warm_start;    /* reserved, must be 0                                       */
+    double fs_k, fs_sigma_y; /* Fatemi-Socie constants                             */
+} gff_options;
+
+typedef struct {
+    int newton_iters;   /* Newton corrections taken                         */
+    int cg_iters;       /* CG iterations summed over the increment          */
+    int cuts;           /* time-step halvings used                           */
+    double residual;    /* final ||b|| / ||P||                               */
+    double Pmacro[9];   /* volume average of P                              */
+    double Fmacro[9];   /* volume average of F                              */
+    double seconds;     /* wall time of the increment                       */
+} gff_step_report;
+
+/* Defaults: continuous projection, FP64, newton_tol 1e-8, cg_tol 1e-8,
+ * newton_max 30, cg_max 2000, max_cuts 4, fs_k 0.5, fs_sigma_y 153e6. */
+void gff_options_default(gff_options* opt);
+
+/* Create one RVE on the current CUDA device: allocates its device buffers
+ * (about 1.5 kB per voxel in FP64 with crystal plasticity).  F starts at the
+ * identity, internal variables at zero.  Grid and equations: Sect. 2.1. */
+gff_status gff_create(const gff_grid* grid, const gff_options* opt, gff_handle** out);
+void gff_destroy(gff_handle* h);
+const char* gff_last_error(const gff_handle* h);
+
+/* Run all device work of h on `stream` (a cudaStream_t; NULL = legacy default stream). */
+gff_status gff_set_stream(gff_handle* h, void* stream);
+gff_status gff_set_options(gff_handle* h, const gff_options* opt);
+
+/* Voxel grain map and grain orientations (Sect. 3.1 RVE).
+ * grain_id: N int32 in [0, ngrains); quat: ngrains*4 unit quaternions
+ * (w, x, y, z) mapping crystal axes to sample axes; grain_phase: ngrains
+ * phase indices in [0, 8).  Copies the data; may be called again to change
+ * the microstructure (state is reset). */
+gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain_id, int ngrains,
+                                  const double* quat, const int32_t* grain_phase);
+
+/* Constitutive law of one phase (Eq. constitutive; Sect. 3.2). */
+gff_status gff_set_material(gff_handle* h, int phase, const gff_material* m);
+
+/* Overwrite (set) or read (get) one voxel field of the committed state.
+ * `which` = GFF_FIELD_*; host buffer of (components x N) doubles in the SoA
+ * layout above.  Setting F also evaluates nothing: call gff_constitutive. */
+gff_status gff_set_field(gff_handle* h, int which, const double* host);
+gff_status gff_get_field(gff_handle* h, int which, double* host);
+
+/* Evaluate P and K = dP/dF (Eq. P_dif) at the current F for a time step dt,
+ * without committing internal variables. */
+gff_status gff_constitutive(gff_handle* h, double dt);
+
+/* y = G_M(K : x)  (Eq. newlinop) with the K of the last constitutive
+ * evaluation.  precision GFF_PREC_FP64: x_dev, y_dev are double[9N];
+ * GFF_PREC_MIXED: float[9N] and K rounded to FP32.  mask9 (host, may be NULL)
+ * marks stress-controlled components: the zero frequency of the operator is
+ * diag(mask9) instead of 0.  x_dev and y_dev may not overlap. */
+gff_status gff_apply_operator(gff_handle* h, int precision, const uint8_t* mask9,
+                              const void* x_dev, void* y_dev);
+
+/* Diagnostic twin of gff_apply_operator: the same three kernels, with CUDA
+ * events recorded on the handle's stream around each; ms_out[3] (host)
+ * receives their durations in milliseconds -- [0] the per-plane K
+ * contraction with the forward x/y transforms, [1] the z transforms with the
+ * projection, [2] the inverse y/x transforms.  Synchronises the stream. */
+gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t* mask9,
+                                    const void* x_dev, void* y_dev, float* ms_out);
+
+/* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */
+gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9,
+                       const void* x_dev, void* y_dev);
+
+/* One load increment (Sect. 2.1): macroscopic Fbar[9] on components with
+ * mask[c] = 0, average stress Pbar[9] on components with mask[c] = 1.
+ * Newton-CG to newton_tol, then internal variables and FIP accumulators are
+ * committed.  On failure the committed state is unchanged.  report may be NULL. */
+gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], const uint8_t mask[9],
+                    const double Pbar[9], gff_step_report* report);
+
+/* nsteps increments; arrays are nsteps x 9 (mask uint8).  cycle_start
+ * (nsteps, may be NULL) restarts the FIP accumulators before that increment.
+ * Pmacro_out (nsteps x 9) and reports (nsteps) may be NULL.  Stops at the
+ * first failing increment and returns its status. */
+gff_status gff_run_history(gff_handle* h, int nsteps, const double* dt, const double* Fbar,
+                           const uint8_t* mask, const double* Pbar, const uint8_t* cycle_start,
+                           double* Pmacro_out, gff_step_report* reports);
+
+/* Fatigue indicator parameters (Sect. 3.3, Eqs. eqplas, strainenergy, Pmax).
+ * gff_reset_fips restarts the per-cycle accumulators.  gff_get_fips returns
+ * grain averages of the current accumulators: pcyc_g[ngrains],
+ * wcyc_g[ngrains*12], fs_g[ngrains] (Fatemi-Socie); any may be NULL. */
+gff_status gff_reset_fips(gff_handle* h);
+gff_status gff_get_fips(gff_handle* h, double* pcyc_g, double* wcyc_g, double* fs_g);
+
+/* Committed state to/from a raw little-endian file (header + F, internal
+ * variables, FIP accumulators).  Loading requires the same grid. */
+gff_status gff_save_state(gff_handle* h, const char* path);
+gff_status gff_load_state(gff_handle* h, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GFF_H */

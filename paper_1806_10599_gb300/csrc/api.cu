@@ -1,0 +1,860 @@
+// C ABI of libgff: handle lifetime, grid tables, microstructure set-up and the
+// Newton-Raphson / conjugate-gradient increment driver (Sect. 2.1).
+#include <chrono>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gff_internal.cuh"
+
+using namespace gff;
+
+namespace {
+
+#define GFF_TRY(expr)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) return fail(h, GFF_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+gff_status fail(gff_handle* h, gff_status st, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+gff_status fail(gff_handle* h, gff_status st, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return st;
+}
+
+// ------------------------------------------------------------------ axis plans and tables
+bool make_plan(int n, AxisPlan& p) {
+    if (n < 4 || n > MAXN || (n & 1)) return false;
+    int m = n, a2 = 0, a3 = 0, a5 = 0;
+    while (m % 2 == 0) { m /= 2; ++a2; }
+    while (m % 3 == 0) { m /= 3; ++a3; }
+    while (m % 5 == 0) { m /= 5; ++a5; }
+    if (m != 1) return false;
+    p.n = n;
+    p.nst = 0;
+    while (a2 >= 3) { p.radix[p.nst++] = 8; a2 -= 3; }
+    if (a2 == 2) p.radix[p.nst++] = 4;
+    if (a2 == 1) p.radix[p.nst++] = 2;
+    for (int i = 0; i < a5; ++i) p.radix[p.nst++] = 5;
+    for (int i = 0; i < a3; ++i) p.radix[p.nst++] = 3;
+    return p.nst <= MAXST;
+}
+
+// Frequency held at position `pos` after the in-place forward (decimation in
+// frequency) transform: pos = sum_i p_i m_i with m_i = n / (r_0...r_i), and
+// the frequency is p_0 + r_0 p_1 + r_0 r_1 p_2 + ...
+int freq_of_pos(int pos, const AxisPlan& p) {
+    int f = 0, mult = 1, len = p.n;
+    for (int i = 0; i < p.nst; ++i) {
+        const int m = len / p.radix[i];
+        const int d = pos / m;
+        pos -= d * m;
+        f += d * mult;
+        mult *= p.radix[i];
+        len = m;
+    }
+    return f;
+}
+
+struct TableLayout {
+    size_t tw64, tw32, posx, fqy, fqz, qt64, qt32, total;
+};
+
+TableLayout table_layout() {
+    TableLayout t;
+    size_t o = 0;
+    t.tw64 = o; o += 3 * MAXN * sizeof(double2);
+    t.tw32 = o; o += 3 * MAXN * sizeof(float2);
+    t.posx = o; o += MAXN * sizeof(int);
+    t.fqy = o; o += MAXN * sizeof(int);
+    t.fqz = o; o += MAXN * sizeof(int);
+    t.qt64 = o; o += 6 * MAXN * sizeof(double);
+    t.qt32 = o; o += 6 * MAXN * sizeof(float);
+    t.total = o;
+    return t;
+}
+
+gff_status build_tables(gff_handle* h) {
+    const int n3[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
+    AxisPlan* pl[3] = {&h->g.ax, &h->g.ay, &h->g.az};
+    for (int a = 0; a < 3; ++a)
+        if (!make_plan(n3[a], *pl[a]))
+            return fail(h, GFF_ERR_ARG, "grid axis %d: n = %d unsupported (even, 4..%d, factors 2,3,5)", a, n3[a], MAXN);
+    const TableLayout L = table_layout();
+    std::vector<unsigned char> host(L.total, 0);
+    double2* tw64 = reinterpret_cast<double2*>(host.data() + L.tw64);
+    float2* tw32 = reinterpret_cast<float2*>(host.data() + L.tw32);
+    int* posx = reinterpret_cast<int*>(host.data() + L.posx);
+    int* fqy = reinterpret_cast<int*>(host.data() + L.fqy);
+    int* fqz = reinterpret_cast<int*>(host.data() + L.fqz);
+    double* qt64 = reinterpret_cast<double*>(host.data() + L.qt64);
+    float* qt32 = reinterpret_cast<float*>(host.data() + L.qt32);
+    const double twopi = 6.283185307179586476925286766559;
+    for (int a = 0; a < 3; ++a) {
+        const int n = n3[a];
+        const double Lj = h->grid.L[a];
+        for (int k = 0; k < n; ++k) {
+            const double th = twopi * k / n;
+            tw64[a * MAXN + k] = make_double2(std::cos(th), -std::sin(th));
+            tw32[a * MAXN + k] = make_float2((float)std::cos(th), (float)-std::sin(th));
+            // wave-vector tables: q = 2 pi kappa / n, kappa = k (k < n/2) or k - n
+            const int kappa = (2 * k < n) ? k : k - n;
+            const double q = twopi * kappa / n;
+            const bool nyq = (2 * k == n);
+            const double qc = q * n / Lj;
+            const double qd = nyq ? 0.0 : std::tan(0.5 * q) * n / Lj;
+            qt64[(0 * 3 + a) * MAXN + k] = qc;
+            qt64[(1 * 3 + a) * MAXN + k] = qd;
+            qt32[(0 * 3 + a) * MAXN + k] = (float)qc;
+            qt32[(1 * 3 + a) * MAXN + k] = (float)qd;
+        }
+    }
+    for (int p = 0; p < h->grid.nx; ++p) posx[freq_of_pos(p, h->g.ax)] = p;
+    for (int p = 0; p < h->grid.ny; ++p) fqy[p] = freq_of_pos(p, h->g.ay);
+    for (int p = 0; p < h->grid.nz; ++p) fqz[p] = freq_of_pos(p, h->g.az);
+    cudaError_t e = cudaMalloc(&h->tables, L.total);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_OOM, "tables: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(h->tables, host.data(), L.total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "tables copy: %s", cudaGetErrorString(e));
+    unsigned char* d = static_cast<unsigned char*>(h->tables);
+    for (int a = 0; a < 3; ++a) {
+        h->g.tw64[a] = reinterpret_cast<const double2*>(d + L.tw64) + a * MAXN;
+        h->g.tw32[a] = reinterpret_cast<const float2*>(d + L.tw32) + a * MAXN;
+        for (int kind = 0; kind < 2; ++kind) {
+            h->g.qt64[kind][a] = reinterpret_cast<const double*>(d + L.qt64) + (kind * 3 + a) * MAXN;
+            h->g.qt32[kind][a] = reinterpret_cast<const float*>(d + L.qt32) + (kind * 3 + a) * MAXN;
+        }
+    }
+    h->g.posx = reinterpret_cast<const int*>(d + L.posx);
+    h->g.fqy = reinterpret_cast<const int*>(d + L.fqy);
+    h->g.fqz = reinterpret_cast<const int*>(d + L.fqz);
+    return GFF_OK;
+}
+
+// ------------------------------------------------------------------ crystallography (host)
+void quat_rot(const double* q, double* R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double n = std::sqrt(w * w + x * x + y * y + z * z);
+    w /= n; x /= n; y /= n; z /= n;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+inline double kd(int a, int b) { return a == b ? 1.0 : 0.0; }
+
+void stiffness(const gff_material& m, const double* R, double* Cout) {
+    double C[81];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) {
+                    double v;
+                    if (m.kind == GFF_MAT_SVK_ISO) {
+                        const double lam = m.E * m.nu / ((1 + m.nu) * (1 - 2 * m.nu));
+                        const double mu = m.E / (2 * (1 + m.nu));
+                        v = lam * kd(i, j) * kd(k, l) + mu * (kd(i, k) * kd(j, l) + kd(i, l) * kd(j, k));
+                    } else {
+                        v = m.C12 * kd(i, j) * kd(k, l) + m.C44 * (kd(i, k) * kd(j, l) + kd(i, l) * kd(j, k));
+                        if (i == j && j == k && k == l) v += m.C11 - m.C12 - 2 * m.C44;
+                    }
+                    C[27 * i + 9 * j + 3 * k + l] = v;
+                }
+    if (m.kind == GFF_MAT_SVK_ISO) {
+        std::memcpy(Cout, C, sizeof C);
+        return;
+    }
+    // C'_ijkl = R_ia R_jb R_kc R_ld C_abcd, done one index at a time
+    double t1[81], t2[81];
+    auto rot_index = [&](const double* in, double* out, int pos) {
+        for (int q = 0; q < 81; ++q) {
+            int idx[4] = {q / 27, (q / 9) % 3, (q / 3) % 3, q % 3};
+            double s = 0;
+            for (int a = 0; a < 3; ++a) {
+                int j2[4] = {idx[0], idx[1], idx[2], idx[3]};
+                j2[pos] = a;
+                s += R[3 * idx[pos] + a] * in[27 * j2[0] + 9 * j2[1] + 3 * j2[2] + j2[3]];
+            }
+            out[q] = s;
+        }
+    };
+    rot_index(C, t1, 0);
+    rot_index(t1, t2, 1);
+    rot_index(t2, t1, 2);
+    rot_index(t1, Cout, 3);
+}
+
+// 12 octahedral systems: normals (111), (-111), (1-11), (11-1); for each the
+// <110> directions orthogonal to it, in lexicographic order of the six <110>
+// vectors whose first non-zero entry is positive.
+void slip_systems(double s[12][3], double m[12][3]) {
+    const int nrm[4][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {1, 1, -1}};
+    const int dirs[6][3] = {{0, 1, -1}, {0, 1, 1}, {1, -1, 0}, {1, 0, -1}, {1, 0, 1}, {1, 1, 0}};
+    int a = 0;
+    for (int p = 0; p < 4; ++p)
+        for (int d = 0; d < 6; ++d) {
+            const int dot = nrm[p][0] * dirs[d][0] + nrm[p][1] * dirs[d][1] + nrm[p][2] * dirs[d][2];
+            if (dot != 0) continue;
+            for (int k = 0; k < 3; ++k) {
+                s[a][k] = dirs[d][k] / std::sqrt(2.0);
+                m[a][k] = nrm[p][k] / std::sqrt(3.0);
+            }
+            ++a;
+        }
+}
+
+}  // namespace
+
+struct gff_hostdata {
+    std::vector<double> quat;
+    std::vector<int> phase;
+};
+
+namespace {
+
+gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const std::vector<int>& phase) {
+    const int ng = h->ngrains;
+    std::vector<double> C(81 * (size_t)ng), S0(108 * (size_t)ng), nrmprm((36 + 5) * (size_t)ng);
+    std::vector<int> kind(ng);
+    double s[12][3], m[12][3];
+    slip_systems(s, m);
+    h->any_cp = false;
+    for (int g = 0; g < ng; ++g) {
+        const int ph = phase[g];
+        if (ph < 0 || ph >= 8 || !h->mat_set[ph]) return fail(h, GFF_ERR_STATE, "grain %d: phase %d has no material", g, ph);
+        const gff_material& mt = h->mat[ph];
+        double R[9];
+        quat_rot(&quat[4 * (size_t)g], R);
+        stiffness(mt, R, &C[81 * (size_t)g]);
+        kind[g] = mt.kind;
+        if (mt.kind == GFF_MAT_CP_FCC) h->any_cp = true;
+        for (int a = 0; a < 12; ++a) {
+            double sr[3], mr[3];
+            for (int i = 0; i < 3; ++i) {
+                sr[i] = R[3 * i] * s[a][0] + R[3 * i + 1] * s[a][1] + R[3 * i + 2] * s[a][2];
+                mr[i] = R[3 * i] * m[a][0] + R[3 * i + 1] * m[a][1] + R[3 * i + 2] * m[a][2];
+            }
+            for (int i = 0; i < 3; ++i) {
+                for (int j = 0; j < 3; ++j) S0[108 * (size_t)g + 9 * a + 3 * i + j] = sr[i] * mr[j];
+                nrmprm[36 * (size_t)g + 3 * a + i] = mr[i];
+            }
+        }
+        double* pr = &nrmprm[36 * (size_t)ng + 5 * (size_t)g];
+        pr[0] = mt.gdot0;
+        pr[1] = mt.p_exp;
+        pr[2] = mt.tau0;
+        pr[3] = mt.c_af;
+        pr[4] = mt.d_af;
+    }
+    GFF_TRY(cudaMemcpy(h->d_C, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GFF_TRY(cudaMemcpy(h->d_S0, S0.data(), S0.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GFF_TRY(cudaMemcpy(h->d_nrm, nrmprm.data(), nrmprm.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GFF_TRY(cudaMemcpy(h->d_gkind, kind.data(), kind.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return GFF_OK;
+}
+
+gff_status ensure_grains(gff_handle* h);
+
+template <typename T> void dfree(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+gff_status dalloc(gff_handle* h, void** p, size_t bytes, const char* what) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    return GFF_OK;
+}
+
+// Read one device double (synchronises the stream).
+gff_status fetch(gff_handle* h, const double* d, int n, double* out) {
+    GFF_TRY(cudaMemcpyAsync(h->h_scal, d, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    GFF_TRY(cudaStreamSynchronize(h->stream));
+    std::memcpy(out, h->h_scal, n * sizeof(double));
+    return GFF_OK;
+}
+
+ProjArgs proj_args(const gff_handle* h, const uint8_t* mask9) {
+    ProjArgs pa;
+    pa.kind = h->opt.projection;
+    for (int c = 0; c < 9; ++c) pa.mask[c] = (mask9 && mask9[c]) ? 1.0f : 0.0f;
+    return pa;
+}
+
+OutArgs out_args(const gff_handle* h, double scale_sign, const double* add9) {
+    OutArgs oa;
+    oa.scale = scale_sign / (double)h->N;
+    for (int c = 0; c < 9; ++c) oa.add[c] = add9 ? add9[c] : 0.0;
+    return oa;
+}
+
+}  // namespace
+
+// =================================================================== API
+// Definitions take C linkage from their declarations in gff.h.
+#define GFF_EXPORT __attribute__((visibility("default")))
+
+
+GFF_EXPORT void gff_options_default(gff_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->projection = GFF_PROJ_CONTINUOUS;
+    o->precision = GFF_PREC_FP64;
+    o->newton_tol = 1e-8;
+    o->cg_tol = 1e-8;
+    o->newton_max = 30;
+    o->cg_max = 2000;
+    o->max_cuts = 4;
+    o->warm_start = 0;
+    o->fs_k = 0.5;
+    o->fs_sigma_y = 153e6;
+}
+
+GFF_EXPORT const char* gff_last_error(const gff_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+static gff_status check_options(gff_handle* h, const gff_options* o) {
+    if (o->projection != GFF_PROJ_CONTINUOUS && o->projection != GFF_PROJ_DISCRETE)
+        return fail(h, GFF_ERR_ARG, "projection %d", o->projection);
+    if (o->precision != GFF_PREC_FP64 && o->precision != GFF_PREC_MIXED)
+        return fail(h, GFF_ERR_ARG, "precision %d", o->precision);
+    if (!(o->newton_tol > 0) || !(o->cg_tol > 0) || o->newton_max < 0 || o->cg_max < 1 || o->max_cuts < 0)
+        return fail(h, GFF_ERR_ARG, "tolerances / caps out of range");
+    if (o->warm_start != 0) return fail(h, GFF_ERR_ARG, "warm_start is reserved and must be 0");
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_create(const gff_grid* grid, const gff_options* opt, gff_handle** out) {
+    if (!grid || !out) return GFF_ERR_ARG;
+    *out = nullptr;
+    gff_handle* h = new gff_handle();
+    h->grid = *grid;
+    gff_options_default(&h->opt);
+    if (opt) h->opt = *opt;
+    gff_status st = check_options(h, &h->opt);
+    if (st != GFF_OK) {
+        *out = h;
+        return st;
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!(grid->L[a] > 0)) {
+            *out = h;
+            return fail(h, GFF_ERR_ARG, "box length L[%d] must be positive", a);
+        }
+    cudaGetDevice(&h->device);
+    h->N = (long long)grid->nx * grid->ny * grid->nz;
+    h->nxh = grid->nx / 2 + 1;
+    h->g.nx = grid->nx;
+    h->g.ny = grid->ny;
+    h->g.nz = grid->nz;
+    h->g.nxh = h->nxh;
+    h->g.N = h->N;
+    *out = h;
+    if ((st = build_tables(h)) != GFF_OK) return st;
+    const long long N = h->N;
+    const size_t f64 = 9 * N * sizeof(double), f32 = 9 * N * sizeof(float);
+    struct A { void** p; size_t b; const char* w; } allocs[] = {
+        {(void**)&h->d_F, f64, "F"},        {(void**)&h->d_Fk, f64, "Fk"},
+        {(void**)&h->d_P, f64, "P"},        {(void**)&h->d_K, 9 * f64, "K"},
+        {(void**)&h->d_b, f64, "b"},        {(void**)&h->d_x, f64, "x"},
+        {(void**)&h->d_r, f64, "r"},        {(void**)&h->d_p, f64, "p"},
+        {(void**)&h->d_Ap, f64, "Ap"},      {(void**)&h->d_K32, 9 * f32, "K32"},
+        {(void**)&h->d_b32, f32, "b32"},    {(void**)&h->d_x32, f32, "x32"},
+        {(void**)&h->d_r32, f32, "r32"},    {(void**)&h->d_p32, f32, "p32"},
+        {(void**)&h->d_Ap32, f32, "Ap32"},
+        {(void**)&h->d_spec, 9 * (size_t)grid->nz * grid->ny * h->nxh * sizeof(double2), "spectrum"},
+        {(void**)&h->d_Fpi, f64, "Fpi"},    {(void**)&h->d_chi, 12 * N * sizeof(double), "chi"},
+        {(void**)&h->d_Fpi_t, f64, "Fpi_t"}, {(void**)&h->d_chi_t, 12 * N * sizeof(double), "chi_t"},
+        {(void**)&h->d_dg, 12 * N * sizeof(double), "dg"}, {(void**)&h->d_tau, 12 * N * sizeof(double), "tau"},
+        {(void**)&h->d_acc, NACC * N * sizeof(double), "fip"}, {(void**)&h->d_flag, 16, "flag"},
+        {(void**)&h->d_red, 32 * RED_BLOCKS * sizeof(double), "reduce"},
+        {(void**)&h->d_scal, 64 * sizeof(double), "scalars"},
+        {(void**)&h->d_gid, N * sizeof(int), "grain id"},
+    };
+    for (auto& a : allocs)
+        if ((st = dalloc(h, a.p, a.b, a.w)) != GFF_OK) return st;
+    cudaError_t e = cudaMallocHost(&h->h_scal, 64 * sizeof(double));
+    if (e != cudaSuccess) return fail(h, GFF_ERR_OOM, "pinned scalars: %s", cudaGetErrorString(e));
+    return GFF_OK;
+}
+
+GFF_EXPORT void gff_destroy(gff_handle* h) {
+    if (!h) return;
+    cudaFree(h->tables);
+    dfree(h->d_gid); dfree(h->d_C); dfree(h->d_S0); dfree(h->d_nrm); dfree(h->d_gkind); dfree(h->d_gphase);
+    dfree(h->d_F); dfree(h->d_Fk); dfree(h->d_P); dfree(h->d_K); dfree(h->d_b); dfree(h->d_x); dfree(h->d_r);
+    dfree(h->d_p); dfree(h->d_Ap); dfree(h->d_K32); dfree(h->d_b32); dfree(h->d_x32); dfree(h->d_r32);
+    dfree(h->d_p32); dfree(h->d_Ap32); dfree(h->d_spec); dfree(h->d_Fpi); dfree(h->d_chi); dfree(h->d_Fpi_t);
+    dfree(h->d_chi_t); dfree(h->d_dg); dfree(h->d_tau); dfree(h->d_acc); dfree(h->d_flag); dfree(h->d_red);
+    dfree(h->d_scal);
+    if (h->h_scal) cudaFreeHost(h->h_scal);
+    delete reinterpret_cast<gff_hostdata*>(h->hostdata);
+    delete h;
+}
+
+GFF_EXPORT gff_status gff_set_stream(gff_handle* h, void* stream) {
+    if (!h) return GFF_ERR_ARG;
+    h->stream = static_cast<cudaStream_t>(stream);
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_set_options(gff_handle* h, const gff_options* opt) {
+    if (!h || !opt) return GFF_ERR_ARG;
+    gff_status st = check_options(h, opt);
+    if (st != GFF_OK) return st;
+    h->opt = *opt;
+    return GFF_OK;
+}
+
+static gff_status reset_state(gff_handle* h) {
+    const long long N = h->N;
+    std::vector<double> eye(9 * N);
+    for (int c = 0; c < 9; ++c)
+        for (long long v = 0; v < N; ++v) eye[c * N + v] = (c % 4 == 0) ? 1.0 : 0.0;
+    GFF_TRY(cudaMemcpy(h->d_F, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
+    GFF_TRY(cudaMemcpy(h->d_Fk, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
+    GFF_TRY(cudaMemcpy(h->d_Fpi, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
+    GFF_TRY(cudaMemset(h->d_chi, 0, 12 * N * sizeof(double)));
+    GFF_TRY(cudaMemset(h->d_P, 0, 9 * N * sizeof(double)));
+    GFF_TRY(cudaMemset(h->d_acc, 0, NACC * N * sizeof(double)));
+    GFF_TRY(cudaMemset(h->d_flag, 0, 16));
+    GFF_TRY(launch_fip_reset(h));
+    GFF_TRY(cudaDeviceSynchronize());
+    h->K_valid = h->K32_valid = false;
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain_id, int ngrains, const double* quat,
+                                  const int32_t* grain_phase) {
+    if (!h || !grain_id || !quat || !grain_phase || ngrains < 1) return fail(h, GFF_ERR_ARG, "bad microstructure args");
+    for (long long v = 0; v < h->N; ++v)
+        if (grain_id[v] < 0 || grain_id[v] >= ngrains) return fail(h, GFF_ERR_ARG, "grain_id[%lld] out of range", v);
+    for (int g = 0; g < ngrains; ++g)
+        if (grain_phase[g] < 0 || grain_phase[g] >= 8) return fail(h, GFF_ERR_ARG, "grain_phase[%d] out of range", g);
+    dfree(h->d_C); dfree(h->d_S0); dfree(h->d_nrm); dfree(h->d_gkind);
+    h->ngrains = ngrains;
+    gff_status st;
+    if ((st = dalloc(h, (void**)&h->d_C, 81 * (size_t)ngrains * sizeof(double), "C")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_S0, 108 * (size_t)ngrains * sizeof(double), "S0")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_nrm, 41 * (size_t)ngrains * sizeof(double), "normals")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_gkind, (size_t)ngrains * sizeof(int), "kind")) != GFF_OK) return st;
+    GFF_TRY(cudaMemcpy(h->d_gid, grain_id, h->N * sizeof(int), cudaMemcpyHostToDevice));
+    gff_hostdata* hd = reinterpret_cast<gff_hostdata*>(h->hostdata);
+    if (!hd) {
+        hd = new gff_hostdata();
+        h->hostdata = hd;
+    }
+    hd->quat.assign(quat, quat + 4 * (size_t)ngrains);
+    hd->phase.assign(grain_phase, grain_phase + ngrains);
+    h->have_ms = true;
+    h->grains_ready = false;
+    return reset_state(h);
+}
+
+GFF_EXPORT gff_status gff_set_material(gff_handle* h, int phase, const gff_material* m) {
+    if (!h || !m || phase < 0 || phase >= 8) return fail(h, GFF_ERR_ARG, "bad material args");
+    if (m->kind < GFF_MAT_SVK_CUBIC || m->kind > GFF_MAT_CP_FCC) return fail(h, GFF_ERR_ARG, "material kind %d", m->kind);
+    if (m->kind == GFF_MAT_CP_FCC) {
+        const double p = m->p_exp;
+        if (!(p >= 1 && p <= 64 && p == std::floor(p)) || !(m->tau0 > 0) || !(m->gdot0 > 0) || m->d_af < 0)
+            return fail(h, GFF_ERR_ARG, "crystal-plasticity constants out of range");
+    }
+    h->mat[phase] = *m;
+    h->mat_set[phase] = true;
+    h->grains_ready = false;
+    return GFF_OK;
+}
+
+namespace {
+gff_status ensure_grains(gff_handle* h) {
+    if (!h->have_ms) return fail(h, GFF_ERR_STATE, "no microstructure set");
+    if (h->grains_ready) return GFF_OK;
+    gff_hostdata* hd = reinterpret_cast<gff_hostdata*>(h->hostdata);
+    gff_status st = upload_grains(h, hd->quat, hd->phase);
+    if (st == GFF_OK) h->grains_ready = true;
+    return st;
+}
+
+int field_comps(int which) {
+    switch (which) {
+        case GFF_FIELD_F: case GFF_FIELD_P: case GFF_FIELD_FP_INV: return 9;
+        case GFF_FIELD_K: return 81;
+        case GFF_FIELD_CHI: case GFF_FIELD_GAMMA: case GFF_FIELD_WCYC: return 12;
+        case GFF_FIELD_PCYC: return 1;
+        default: return 0;
+    }
+}
+
+double* field_ptr(gff_handle* h, int which) {
+    switch (which) {
+        case GFF_FIELD_F: return h->d_F;
+        case GFF_FIELD_P: return h->d_P;
+        case GFF_FIELD_K: return h->d_K;
+        case GFF_FIELD_FP_INV: return h->d_Fpi;
+        case GFF_FIELD_CHI: return h->d_chi;
+        case GFF_FIELD_GAMMA: return h->d_acc + 13 * h->N;
+        case GFF_FIELD_PCYC: return h->d_acc;
+        case GFF_FIELD_WCYC: return h->d_acc + 1 * h->N;
+        default: return nullptr;
+    }
+}
+}  // namespace
+
+GFF_EXPORT gff_status gff_set_field(gff_handle* h, int which, const double* host) {
+    if (!h || !host) return fail(h, GFF_ERR_ARG, "bad args");
+    if (!h->have_ms) return fail(h, GFF_ERR_STATE, "no microstructure set");
+    const int nc = field_comps(which);
+    double* d = field_ptr(h, which);
+    if (!nc || !d) return fail(h, GFF_ERR_ARG, "field %d", which);
+    GFF_TRY(cudaMemcpyAsync(d, host, nc * h->N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (which == GFF_FIELD_F)
+        GFF_TRY(cudaMemcpyAsync(h->d_Fk, host, 9 * h->N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (which == GFF_FIELD_K) h->K_valid = true, h->K32_valid = false;
+    GFF_TRY(cudaStreamSynchronize(h->stream));
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_get_field(gff_handle* h, int which, double* host) {
+    if (!h || !host) return fail(h, GFF_ERR_ARG, "bad args");
+    const int nc = field_comps(which);
+    double* d = field_ptr(h, which);
+    if (!nc || !d) return fail(h, GFF_ERR_ARG, "field %d", which);
+    GFF_TRY(cudaMemcpyAsync(host, d, nc * h->N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    GFF_TRY(cudaStreamSynchronize(h->stream));
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_constitutive(gff_handle* h, double dt) {
+    if (!h) return GFF_ERR_ARG;
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+    GFF_TRY(launch_constitutive(h, h->d_Fk, dt, true));
+    int flag = 0;
+    GFF_TRY(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    GFF_TRY(cudaStreamSynchronize(h->stream));
+    h->K_valid = h->K32_valid = true;
+    if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_apply_operator(gff_handle* h, int precision, const uint8_t* mask9, const void* x_dev, void* y_dev) {
+    if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(h, GFF_ERR_ARG, "bad apply args");
+    if (!h->K_valid) return fail(h, GFF_ERR_STATE, "no tangent: call gff_constitutive first");
+    const ProjArgs pa = proj_args(h, mask9);
+    const OutArgs oa = out_args(h, 1.0, nullptr);
+    if (precision == GFF_PREC_FP64) {
+        GFF_TRY(launch_galerkin<double>(h, (const double*)x_dev, h->d_K, (double*)y_dev, pa, oa, h->d_spec));
+    } else if (precision == GFF_PREC_MIXED) {
+        if (!h->K32_valid) {
+            GFF_TRY(launch_cast64to32(h->d_K32, h->d_K, 81 * h->N, h->stream));
+            h->K32_valid = true;
+        }
+        GFF_TRY(launch_galerkin<float>(h, (const float*)x_dev, h->d_K32, (float*)y_dev, pa, oa,
+                                       reinterpret_cast<float2*>(h->d_spec)));
+    } else {
+        return fail(h, GFF_ERR_ARG, "precision %d", precision);
+    }
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t* mask9,
+                                               const void* x_dev, void* y_dev, float* ms_out) {
+    if (!h || !x_dev || !y_dev || x_dev == y_dev || !ms_out) return fail(h, GFF_ERR_ARG, "bad apply args");
+    if (!h->K_valid) return fail(h, GFF_ERR_STATE, "no tangent: call gff_constitutive first");
+    if (precision != GFF_PREC_FP64 && precision != GFF_PREC_MIXED) return fail(h, GFF_ERR_ARG, "precision %d", precision);
+    const ProjArgs pa = proj_args(h, mask9);
+    const OutArgs oa = out_args(h, 1.0, nullptr);
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+    if (e == cudaSuccess && precision == GFF_PREC_MIXED && !h->K32_valid) {
+        e = launch_cast64to32(h->d_K32, h->d_K, 81 * h->N, h->stream);
+        if (e == cudaSuccess) h->K32_valid = true;
+    }
+    if (e == cudaSuccess) {
+        if (precision == GFF_PREC_FP64)
+            e = launch_galerkin<double>(h, (const double*)x_dev, h->d_K, (double*)y_dev, pa, oa, h->d_spec, ev);
+        else
+            e = launch_galerkin<float>(h, (const float*)x_dev, h->d_K32, (float*)y_dev, pa, oa,
+                                       reinterpret_cast<float2*>(h->d_spec), ev);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms_out[i], ev[i], ev[i + 1]);
+    for (int i = 0; i < 4; ++i)
+        if (ev[i]) cudaEventDestroy(ev[i]);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "timed apply: %s", cudaGetErrorString(e));
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9, const void* x_dev, void* y_dev) {
+    if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(h, GFF_ERR_ARG, "bad project args");
+    const ProjArgs pa = proj_args(h, mask9);
+    const OutArgs oa = out_args(h, 1.0, nullptr);
+    if (precision == GFF_PREC_FP64) {
+        GFF_TRY(launch_galerkin<double>(h, (const double*)x_dev, (const double*)nullptr, (double*)y_dev, pa, oa,
+                                        h->d_spec));
+    } else if (precision == GFF_PREC_MIXED) {
+        GFF_TRY(launch_galerkin<float>(h, (const float*)x_dev, (const float*)nullptr, (float*)y_dev, pa, oa,
+                                       reinterpret_cast<float2*>(h->d_spec)));
+    } else {
+        return fail(h, GFF_ERR_ARG, "precision %d", precision);
+    }
+    return GFF_OK;
+}
+
+// ------------------------------------------------------------------ Newton-CG increment
+namespace {
+
+// CG on G_M(K : dF) = b from dF = 0 (Sect. 2.1).  T = double: vectors
+// d_x/d_r/d_p/d_Ap with K; T = float: the FP32 copies with K32.  Stops when
+// ||r|| <= stop or after cg_max iterations.
+template <typename T>
+gff_status cg_solve(gff_handle* h, const ProjArgs& pa, T* x, T* r, T* p, T* Ap, const T* K, double rr0, double stop,
+                    int* iters) {
+    const long long n = 9 * h->N;
+    const OutArgs oa = out_args(h, 1.0, nullptr);
+    typename C2<T>::t* spec = reinterpret_cast<typename C2<T>::t*>(h->d_spec);
+    GFF_TRY(launch_zero<T>(x, n, h->stream));
+    GFF_TRY(cudaMemcpyAsync(p, r, n * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
+    double rr = rr0;
+    int it = 0;
+    while (it < h->opt.cg_max && std::sqrt(rr) > stop) {
+        GFF_TRY(launch_galerkin<T>(h, p, K, Ap, pa, oa, spec));
+        GFF_TRY(launch_dot<T>(p, Ap, n, h->d_red, h->d_scal, h->stream));
+        double pAp;
+        gff_status st = fetch(h, h->d_scal, 1, &pAp);
+        if (st != GFF_OK) return st;
+        if (!(pAp != 0.0) || !std::isfinite(pAp)) return fail(h, GFF_ERR_NO_CONVERGENCE, "CG breakdown (p.Ap = %g)", pAp);
+        const double alpha = rr / pAp;
+        GFF_TRY(launch_cg_update<T>(x, r, p, Ap, alpha, n, h->d_red, h->d_scal, h->stream));
+        double rr_new;
+        if ((st = fetch(h, h->d_scal, 1, &rr_new)) != GFF_OK) return st;
+        GFF_TRY(launch_xpby<T>(p, r, rr_new / rr, n, h->stream));
+        rr = rr_new;
+        ++it;
+    }
+    *iters = it;
+    return GFF_OK;
+}
+
+gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const uint8_t* mask, const double* Pbar,
+                            gff_step_report* rep) {
+    const long long N = h->N;
+    const long long n = 9 * N;
+    gff_status st;
+    // zero-fluctuation start: F = F_{k-1} + dFbar on strain-controlled components
+    double Fsum[9];
+    GFF_TRY(launch_sum9(h->d_F, N, h->d_red, h->d_scal, h->stream));
+    if ((st = fetch(h, h->d_scal, 9, Fsum)) != GFF_OK) return st;
+    double d9[9], add9[9];
+    for (int c = 0; c < 9; ++c) {
+        d9[c] = mask[c] ? 0.0 : Fbar[c] - Fsum[c] / (double)N;
+        add9[c] = mask[c] ? Pbar[c] : 0.0;
+    }
+    GFF_TRY(launch_add_const9(h->d_Fk, h->d_F, d9, N, h->stream));
+    const ProjArgs pa = proj_args(h, mask);
+    const OutArgs ores = out_args(h, -1.0, add9);
+    const bool mixed = h->opt.precision == GFF_PREC_MIXED;
+    int newton = 0, cgsum = 0;
+    double res = 0.0;
+    bool conv = false;
+    for (int it = 0; it <= h->opt.newton_max; ++it) {
+        GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed));
+        // b = -G_M(P) + M : Pbar
+        GFF_TRY(launch_galerkin<double>(h, h->d_P, (const double*)nullptr, h->d_b, pa, ores, h->d_spec));
+        GFF_TRY(launch_dot<double>(h->d_b, h->d_b, n, h->d_red, h->d_scal, h->stream));
+        GFF_TRY(launch_dot<double>(h->d_P, h->d_P, n, h->d_red + RED_BLOCKS, h->d_scal + 1, h->stream));
+        GFF_TRY(cudaMemcpyAsync(h->d_scal + 2, h->d_flag, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+        double s3[3];
+        if ((st = fetch(h, h->d_scal, 3, s3)) != GFF_OK) return st;
+        int flag;
+        std::memcpy(&flag, &s3[2], sizeof(int));
+        if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
+        const double nb = std::sqrt(s3[0]), nP = std::sqrt(s3[1]);
+        res = nP > 0 ? nb / nP : nb;
+        if (res <= h->opt.newton_tol) {
+            conv = true;
+            break;
+        }
+        if (it == h->opt.newton_max) break;
+        const double stop = std::fmax(h->opt.cg_tol * nb, 0.1 * h->opt.newton_tol * nP);
+        int its = 0;
+        if (!mixed) {
+            GFF_TRY(cudaMemcpyAsync(h->d_r, h->d_b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            if ((st = cg_solve<double>(h, pa, h->d_x, h->d_r, h->d_p, h->d_Ap, h->d_K, s3[0], stop, &its)) != GFF_OK)
+                return st;
+            GFF_TRY(launch_axpy_to64<double>(h->d_Fk, h->d_x, n, h->stream));
+        } else {
+            GFF_TRY(launch_cast64to32(h->d_r32, h->d_b, n, h->stream));
+            GFF_TRY(launch_dot<float>(h->d_r32, h->d_r32, n, h->d_red, h->d_scal, h->stream));
+            double rr32;
+            if ((st = fetch(h, h->d_scal, 1, &rr32)) != GFF_OK) return st;
+            if ((st = cg_solve<float>(h, pa, h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, h->d_K32, rr32, stop, &its)) !=
+                GFF_OK)
+                return st;
+            GFF_TRY(launch_axpy_to64<float>(h->d_Fk, h->d_x32, n, h->stream));
+        }
+        cgsum += its;
+        ++newton;
+    }
+    if (rep) {
+        rep->newton_iters = newton;
+        rep->cg_iters = cgsum;
+        rep->residual = res;
+    }
+    if (!conv) return fail(h, GFF_ERR_NO_CONVERGENCE, "Newton: residual %.3e after %d iterations", res, newton);
+    return GFF_OK;
+}
+
+}  // namespace
+
+GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], const uint8_t mask[9], const double Pbar[9],
+                    gff_step_report* report) {
+    if (!h || !Fbar || !mask || !Pbar || !(dt > 0)) return fail(h, GFF_ERR_ARG, "bad step args");
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    gff_step_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    st = newton_increment(h, dt, Fbar, mask, Pbar, &rep);
+    if (st != GFF_OK) {
+        if (report) *report = rep;
+        return st;
+    }
+    const long long N = h->N;
+    // commit: F, P (already for the converged F), internal variables, FIPs
+    GFF_TRY(cudaMemcpyAsync(h->d_F, h->d_Fk, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->any_cp) {
+        GFF_TRY(cudaMemcpyAsync(h->d_Fpi, h->d_Fpi_t, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        GFF_TRY(cudaMemcpyAsync(h->d_chi, h->d_chi_t, 12 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        GFF_TRY(launch_fip_accumulate(h));
+    }
+    h->K_valid = true;
+    h->K32_valid = h->opt.precision == GFF_PREC_MIXED;
+    double s[18];
+    GFF_TRY(launch_sum9(h->d_P, N, h->d_red, h->d_scal, h->stream));
+    GFF_TRY(launch_sum9(h->d_F, N, h->d_red + 9 * RED_BLOCKS, h->d_scal + 9, h->stream));
+    if ((st = fetch(h, h->d_scal, 18, s)) != GFF_OK) return st;
+    for (int c = 0; c < 9; ++c) {
+        rep.Pmacro[c] = s[c] / (double)N;
+        rep.Fmacro[c] = s[9 + c] / (double)N;
+    }
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (report) *report = rep;
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_run_history(gff_handle* h, int nsteps, const double* dt, const double* Fbar, const uint8_t* mask,
+                           const double* Pbar, const uint8_t* cycle_start, double* Pmacro_out,
+                           gff_step_report* reports) {
+    if (!h || nsteps < 0 || !dt || !Fbar || !mask || !Pbar) return fail(h, GFF_ERR_ARG, "bad history args");
+    for (int k = 0; k < nsteps; ++k) {
+        if (cycle_start && cycle_start[k]) {
+            gff_status st = gff_reset_fips(h);
+            if (st != GFF_OK) return st;
+        }
+        gff_step_report rep;
+        gff_status st = gff_step(h, dt[k], Fbar + 9 * k, mask + 9 * k, Pbar + 9 * k, &rep);
+        if (reports) reports[k] = rep;
+        if (st != GFF_OK) return st;
+        if (Pmacro_out) std::memcpy(Pmacro_out + 9 * k, rep.Pmacro, 9 * sizeof(double));
+    }
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_reset_fips(gff_handle* h) {
+    if (!h) return GFF_ERR_ARG;
+    GFF_TRY(launch_fip_reset(h));
+    GFF_TRY(cudaStreamSynchronize(h->stream));
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_get_fips(gff_handle* h, double* pcyc_g, double* wcyc_g, double* fs_g) {
+    if (!h) return GFF_ERR_ARG;
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    const int ng = h->ngrains;
+    double* d = nullptr;
+    if ((st = dalloc(h, (void**)&d, (14 + 38) * (size_t)ng * sizeof(double), "grain fips")) != GFF_OK) return st;
+    cudaError_t e = launch_grain_fips(h, d, d + ng, d + 13 * (size_t)ng);
+    std::vector<double> host(14 * (size_t)ng);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), d, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "grain fips: %s", cudaGetErrorString(e));
+    if (pcyc_g) std::memcpy(pcyc_g, host.data(), ng * sizeof(double));
+    if (wcyc_g) std::memcpy(wcyc_g, host.data() + ng, 12 * (size_t)ng * sizeof(double));
+    if (fs_g) std::memcpy(fs_g, host.data() + 13 * (size_t)ng, ng * sizeof(double));
+    return GFF_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint
+static const char kMagic[8] = {'G', 'F', 'F', 'S', 'T', 'A', 'T', '1'};
+
+GFF_EXPORT gff_status gff_save_state(gff_handle* h, const char* path) {
+    if (!h || !path) return fail(h, GFF_ERR_ARG, "bad args");
+    const long long N = h->N;
+    const size_t counts[4] = {9 * (size_t)N, 9 * (size_t)N, 12 * (size_t)N, NACC * (size_t)N};
+    double* src[4] = {h->d_F, h->d_Fpi, h->d_chi, h->d_acc};
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(h, GFF_ERR_IO, "cannot open %s", path);
+    int32_t hdr[4] = {h->grid.nx, h->grid.ny, h->grid.nz, NACC};
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1;
+    std::vector<double> buf;
+    for (int i = 0; i < 4 && ok; ++i) {
+        buf.resize(counts[i]);
+        cudaError_t e = cudaMemcpy(buf.data(), src[i], counts[i] * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(h, GFF_ERR_CUDA, "save: %s", cudaGetErrorString(e));
+        }
+        ok = std::fwrite(buf.data(), sizeof(double), counts[i], f) == counts[i];
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? GFF_OK : fail(h, GFF_ERR_IO, "write failed: %s", path);
+}
+
+GFF_EXPORT gff_status gff_load_state(gff_handle* h, const char* path) {
+    if (!h || !path) return fail(h, GFF_ERR_ARG, "bad args");
+    const long long N = h->N;
+    const size_t counts[4] = {9 * (size_t)N, 9 * (size_t)N, 12 * (size_t)N, NACC * (size_t)N};
+    double* dst[4] = {h->d_F, h->d_Fpi, h->d_chi, h->d_acc};
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(h, GFF_ERR_IO, "cannot open %s", path);
+    char mg[8];
+    int32_t hdr[4];
+    bool ok = std::fread(mg, 1, 8, f) == 8 && std::memcmp(mg, kMagic, 8) == 0 && std::fread(hdr, sizeof hdr, 1, f) == 1;
+    if (ok && (hdr[0] != h->grid.nx || hdr[1] != h->grid.ny || hdr[2] != h->grid.nz || hdr[3] != NACC)) {
+        std::fclose(f);
+        return fail(h, GFF_ERR_ARG, "state file grid %dx%dx%d does not match", hdr[0], hdr[1], hdr[2]);
+    }
+    std::vector<double> buf;
+    for (int i = 0; i < 4 && ok; ++i) {
+        buf.resize(counts[i]);
+        ok = std::fread(buf.data(), sizeof(double), counts[i], f) == counts[i];
+        if (ok) {
+            cudaError_t e = cudaMemcpy(dst[i], buf.data(), counts[i] * sizeof(double), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                std::fclose(f);
+                return fail(h, GFF_ERR_CUDA, "load: %s", cudaGetErrorString(e));
+            }
+        }
+    }
+    std::fclose(f);
+    if (!ok) return fail(h, GFF_ERR_IO, "read failed or not a state file: %s", path);
+    GFF_TRY(cudaMemcpy(h->d_Fk, h->d_F, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice));
+    h->K_valid = h->K32_valid = false;
+    return GFF_OK;
+}
+

@@ -1,0 +1,498 @@
+// Galerkin operator y = F^-1{ G^ : F(K : x) }  (Eqs. eql_discrete3, newlinop)
+// as three kernels over the [9][nz][ny][nx] field:
+//
+//   k_plane_fwd  one CTA per (component c, plane z): optional per-voxel
+//                contraction y_c = K_cd x_d, then the 2D forward transform of
+//                the plane held in shared memory -- a real-to-complex pass
+//                along x (two real rows packed as one complex row) and a
+//                complex pass along y -- written as the half spectrum
+//                [9][nz][ny][nx/2+1].
+//   k_zproj      one CTA per W consecutive (ky, kx) columns: forward
+//                transform along z of all 9 components, the projection
+//                G^ (Eq. G) or G^' (Sect. 2.2) at every frequency, inverse
+//                transform along z, in place.
+//   k_plane_inv  one CTA per (c, z): inverse y, complex-to-real x, epilogue
+//                out = scale * y + add_c.
+//
+// Each axis transform is an in-place mixed-radix (2, 3, 4, 5, 8) FFT in
+// shared memory: forward = decimation in frequency (natural order in,
+// digit-reversed out), inverse = the same stages replayed backwards with
+// conjugate twiddles (digit-reversed in, natural out), so no reordering pass
+// is needed; the projection reads the frequency of each position from a table.
+#include "gff_internal.cuh"
+
+namespace gff {
+namespace {
+
+template <typename C>
+__device__ __forceinline__ C mk(decltype(C::x) a, decltype(C::x) b) {
+    C r;
+    r.x = a;
+    r.y = b;
+    return r;
+}
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+// a * w and a * conj(w)
+template <typename C> __device__ __forceinline__ C cmul(C a, C w) {
+    return mk<C>(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+template <typename C> __device__ __forceinline__ C cmulc(C a, C w) {
+    return mk<C>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C rot90(C a) {
+    return INV ? mk<C>(-a.y, a.x) : mk<C>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------- butterflies
+// Unnormalised radix-R DFT of v[0..R-1]: y_p = sum_q v_q w^(pq), w = exp(-+2 pi i / R).
+template <int R, bool INV, typename C> struct Bfly;
+
+template <bool INV, typename C> struct Bfly<2, INV, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <bool INV, typename C> struct Bfly<4, INV, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        C a2 = cadd(v[1], v[3]), a3 = rot90<INV>(csub(v[1], v[3]));
+        v[0] = cadd(a0, a2);
+        v[2] = csub(a0, a2);
+        v[1] = cadd(a1, a3);
+        v[3] = csub(a1, a3);
+    }
+};
+
+template <bool INV, typename C> struct Bfly<8, INV, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using T = decltype(C::x);
+        const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+        C e[4] = {v[0], v[2], v[4], v[6]};
+        C o[4] = {v[1], v[3], v[5], v[7]};
+        Bfly<4, INV, C>::run(e);
+        Bfly<4, INV, C>::run(o);
+        // o_p *= w8^p, w8 = exp(-+ i pi / 4)
+        C o1 = INV ? mk<C>((o[1].x - o[1].y) * h, (o[1].x + o[1].y) * h)
+                   : mk<C>((o[1].x + o[1].y) * h, (o[1].y - o[1].x) * h);
+        C o2 = rot90<INV>(o[2]);
+        C o3 = INV ? mk<C>(-(o[3].x + o[3].y) * h, (o[3].x - o[3].y) * h)
+                   : mk<C>((o[3].y - o[3].x) * h, -(o[3].x + o[3].y) * h);
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+template <bool INV, typename C> struct Bfly<3, INV, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using T = decltype(C::x);
+        const T s3 = (T)0.86602540378443864676;  // sin(2 pi / 3)
+        C t1 = cadd(v[1], v[2]);
+        C t2 = csub(v[0], cscale(t1, (T)0.5));
+        C t3 = rot90<INV>(cscale(csub(v[1], v[2]), s3));  // -+ i s3 (v1 - v2)
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, t3);
+        v[2] = csub(t2, t3);
+    }
+};
+
+template <bool INV, typename C> struct Bfly<5, INV, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using T = decltype(C::x);
+        const T c1 = (T)0.30901699437494742410;   // cos(2 pi / 5)
+        const T c2 = (T)-0.80901699437494742410;  // cos(4 pi / 5)
+        const T s1 = (T)0.95105651629515357212;   // sin(2 pi / 5)
+        const T s2 = (T)0.58778525229247312917;   // sin(4 pi / 5)
+        C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+        C t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        C a1 = mk<C>(v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y);
+        C a2 = mk<C>(v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y);
+        C b1 = rot90<INV>(mk<C>(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y));
+        C b2 = rot90<INV>(mk<C>(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y));
+        v[0] = cadd(v[0], cadd(t1, t2));
+        v[1] = cadd(a1, b1);
+        v[4] = csub(a1, b1);
+        v[2] = cadd(a2, b2);
+        v[3] = csub(a2, b2);
+    }
+};
+
+// ---------------------------------------------------------------- one radix stage
+// Lines l = ls * NLF + lf start at s + ls*SS + lf*SF; elements are ES apart.
+// Sub-arrays of length `len` are split by radix R with stride m = len / R.
+// Threads take (lf fastest, then butterfly, then ls) so that neighbouring
+// lanes touch neighbouring shared-memory words.
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void run_stage(typename C2<T>::t* s, const typename C2<T>::t* tw, int n, int len,
+                                          int NLF, int SF, int NLS, int SS, int ES, int tid, int nthr) {
+    using C = typename C2<T>::t;
+    const int m = len / R, nb = n / R, twstep = n / len;
+    const int total = NLF * nb * NLS;
+    const int st = m * ES;
+    for (int idx = tid; idx < total; idx += nthr) {
+        const int lf = idx % NLF;
+        const int t = idx / NLF;
+        const int bb = t % nb;
+        const int lsl = t / nb;
+        const int sub = bb / m;
+        const int j = bb - sub * m;
+        C* base = s + lsl * SS + lf * SF + (sub * len + j) * ES;
+        C v[R];
+        if (!INV) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = base[q * st];
+            Bfly<R, false, C>::run(v);
+            if (j) {
+#pragma unroll
+                for (int p = 1; p < R; ++p) v[p] = cmul(v[p], tw[p * j * twstep]);
+            }
+#pragma unroll
+            for (int p = 0; p < R; ++p) base[p * st] = v[p];
+        } else {
+#pragma unroll
+            for (int p = 0; p < R; ++p) v[p] = base[p * st];
+            if (j) {
+#pragma unroll
+                for (int p = 1; p < R; ++p) v[p] = cmulc(v[p], tw[p * j * twstep]);
+            }
+            Bfly<R, true, C>::run(v);
+#pragma unroll
+            for (int q = 0; q < R; ++q) base[q * st] = v[q];
+        }
+    }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void stage_dispatch(int R, typename C2<T>::t* s, const typename C2<T>::t* tw, int n,
+                                               int len, int NLF, int SF, int NLS, int SS, int ES, int tid,
+                                               int nthr) {
+    switch (R) {
+        case 8: run_stage<T, 8, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
+        case 4: run_stage<T, 4, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
+        case 2: run_stage<T, 2, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
+        case 3: run_stage<T, 3, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
+        case 5: run_stage<T, 5, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
+        default: break;
+    }
+}
+
+// Whole transform of a batch of lines; ends with a barrier.
+template <typename T, bool INV>
+__device__ void fft_lines(typename C2<T>::t* s, const typename C2<T>::t* tw, const AxisPlan& pl, int NLF, int SF,
+                          int NLS, int SS, int ES, int tid, int nthr) {
+    const int n = pl.n;
+    if (!INV) {
+        int len = n;
+        for (int k = 0; k < pl.nst; ++k) {
+            stage_dispatch<T, false>(pl.radix[k], s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr);
+            len /= pl.radix[k];
+            __syncthreads();
+        }
+    } else {
+        int len = 1;
+        for (int k = pl.nst - 1; k >= 0; --k) {
+            len *= pl.radix[k];
+            stage_dispatch<T, true>(pl.radix[k], s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr);
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T> __device__ __forceinline__ const typename C2<T>::t* twp(const GridDev& g, int a);
+template <> __device__ __forceinline__ const double2* twp<double>(const GridDev& g, int a) { return g.tw64[a]; }
+template <> __device__ __forceinline__ const float2* twp<float>(const GridDev& g, int a) { return g.tw32[a]; }
+template <typename T> __device__ __forceinline__ const T* qtp(const GridDev& g, int kind, int a);
+template <> __device__ __forceinline__ const double* qtp<double>(const GridDev& g, int kind, int a) {
+    return g.qt64[kind][a];
+}
+template <> __device__ __forceinline__ const float* qtp<float>(const GridDev& g, int kind, int a) {
+    return g.qt32[kind][a];
+}
+
+// ---------------------------------------------------------------- pass 1: (K:x) and the 2D forward transform
+template <typename T, bool WITH_K>
+__global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, const T* __restrict__ K,
+                                                   typename C2<T>::t* __restrict__ spec, GridDev g) {
+    using C = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
+    C* s = reinterpret_cast<C*>(sm_raw);
+    C* twx = s + ny * ls;
+    C* twy = twx + nx;
+    int* posx = reinterpret_cast<int*>(twy + ny);
+    const int c = blockIdx.x, z = blockIdx.y;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const long long N = g.N;
+    const long long pl = (long long)z * ny * nx;
+
+    for (int i = tid; i < nx; i += nthr) {
+        twx[i] = twp<T>(g, 0)[i];
+        posx[i] = g.posx[i];
+    }
+    for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
+
+    for (int e = tid; e < half * nx; e += nthr) {
+        const int r = e / nx, xi = e - r * nx;
+        const long long v0 = pl + (long long)(2 * r) * nx + xi, v1 = v0 + nx;
+        T a, b;
+        if (WITH_K) {
+            a = (T)0;
+            b = (T)0;
+            const T* Kc = K + (long long)c * 9 * N;
+#pragma unroll
+            for (int d = 0; d < 9; ++d) {
+                a = fma(__ldg(Kc + d * N + v0), __ldg(x + d * N + v0), a);
+                b = fma(__ldg(Kc + d * N + v1), __ldg(x + d * N + v1), b);
+            }
+        } else {
+            a = __ldg(x + c * N + v0);
+            b = __ldg(x + c * N + v1);
+        }
+        s[r * 2 * ls + xi] = mk<C>(a, b);
+    }
+    __syncthreads();
+    // x transform of the ny/2 packed rows (row pair r at offset 2 r ls)
+    fft_lines<T, false>(s, twx, g.ax, 1, 0, half, 2 * ls, 1, tid, nthr);
+    // split each packed row into the half spectra of its two real rows
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5, kh = nx / 2;
+    for (int r = warp; r < half; r += nw) {
+        C* row = s + r * 2 * ls;
+        C A[3], B[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int k = lane + 32 * t;
+            if (k <= kh) {
+                const C zk = row[posx[k]];
+                const C zm = row[posx[k == 0 ? 0 : nx - k]];
+                A[t] = mk<C>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
+                B[t] = mk<C>((zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int k = lane + 32 * t;
+            if (k <= kh) {
+                row[k] = A[t];
+                row[ls + k] = B[t];
+            }
+        }
+    }
+    __syncthreads();
+    // y transform of the nxh columns
+    fft_lines<T, false>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
+    C* out = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
+    for (int e = tid; e < ny * nxh; e += nthr) out[e] = s[e];
+}
+
+// ---------------------------------------------------------------- pass 2: z transform + projection
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa) {
+    using C = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
+    C* s = reinterpret_cast<C*>(sm_raw);  // [9][nz][W]
+    C* twz = s + 9 * nz * W;
+    T* qx = reinterpret_cast<T*>(twz + nz);
+    T* qy = qx + nxh;
+    T* qz = qy + ny;
+    int* fqy = reinterpret_cast<int*>(qz + nz);
+    int* fqz = fqy + ny;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const long long nF = (long long)ny * nxh;
+    const long long f0 = (long long)blockIdx.x * W;
+
+    for (int i = tid; i < nz; i += nthr) {
+        twz[i] = twp<T>(g, 2)[i];
+        qz[i] = qtp<T>(g, pa.kind, 2)[i];
+        fqz[i] = g.fqz[i];
+    }
+    for (int i = tid; i < ny; i += nthr) {
+        qy[i] = qtp<T>(g, pa.kind, 1)[i];
+        fqy[i] = g.fqy[i];
+    }
+    for (int i = tid; i < nxh; i += nthr) qx[i] = qtp<T>(g, pa.kind, 0)[i];
+    for (int e = tid; e < 9 * nz * W; e += nthr) {
+        const int w = e % W;
+        const long long cz = e / W;
+        const long long f = f0 + w;
+        s[e] = f < nF ? spec[cz * nF + f] : mk<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    fft_lines<T, false>(s, twz, g.az, W, 1, 9, nz * W, W, tid, nthr);
+
+    for (int e = tid; e < nz * W; e += nthr) {
+        const int w = e % W, pz = e / W;
+        const long long f = f0 + w;
+        if (f >= nF) continue;
+        const int py = (int)(f / nxh), kx = (int)(f - (long long)py * nxh);
+        const int ky = fqy[py], kz = fqz[pz];
+        C v[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) v[c] = s[(c * nz + pz) * W + w];
+        if (kx == 0 && ky == 0 && kz == 0) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = cscale(v[c], (T)pa.mask[c]);
+        } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = mk<C>((T)0, (T)0);
+        } else {
+            const T a = qx[kx], b = qy[ky], d = qz[kz];
+            const T inv = (T)1 / sqrt(a * a + b * b + d * d);
+            const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                // t_i = sum_l x_il n_l ; y_ij = t_i n_j   (G_ijkl = delta_ik n_j n_l)
+                const C t = mk<C>(v[3 * i].x * n0 + v[3 * i + 1].x * n1 + v[3 * i + 2].x * n2,
+                                  v[3 * i].y * n0 + v[3 * i + 1].y * n1 + v[3 * i + 2].y * n2);
+                v[3 * i] = cscale(t, n0);
+                v[3 * i + 1] = cscale(t, n1);
+                v[3 * i + 2] = cscale(t, n2);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) s[(c * nz + pz) * W + w] = v[c];
+    }
+    __syncthreads();
+    fft_lines<T, true>(s, twz, g.az, W, 1, 9, nz * W, W, tid, nthr);
+    for (int e = tid; e < 9 * nz * W; e += nthr) {
+        const int w = e % W;
+        const long long cz = e / W;
+        const long long f = f0 + w;
+        if (f < nF) spec[cz * nF + f] = s[e];
+    }
+}
+
+// ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
+template <typename T>
+__global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
+                                                   GridDev g, OutArgs oa) {
+    using C = typename C2<T>::t;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
+    C* s = reinterpret_cast<C*>(sm_raw);
+    C* twx = s + ny * ls;
+    C* twy = twx + nx;
+    int* posx = reinterpret_cast<int*>(twy + ny);
+    const int c = blockIdx.x, z = blockIdx.y;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const long long N = g.N;
+    const long long pl = (long long)z * ny * nx;
+
+    for (int i = tid; i < nx; i += nthr) {
+        twx[i] = twp<T>(g, 0)[i];
+        posx[i] = g.posx[i];
+    }
+    for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
+    const C* in = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
+    for (int e = tid; e < ny * nxh; e += nthr) s[e] = in[e];
+    __syncthreads();
+    fft_lines<T, true>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
+    // merge the half spectra of rows 2r, 2r+1 into one packed complex row
+    // Z_k = A_k + i B_k over all k (Hermitian symmetry of real rows), in the
+    // digit-reversed order the inverse x pass expects
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5, kh = nx / 2;
+    for (int r = warp; r < half; r += nw) {
+        C* row = s + r * 2 * ls;
+        C A[3], B[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int k = lane + 32 * t;
+            if (k <= kh) {
+                A[t] = row[k];
+                B[t] = row[ls + k];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int k = lane + 32 * t;
+            if (k <= kh) {
+                if (k == 0 || k == kh) {
+                    row[posx[k]] = mk<C>(A[t].x, B[t].x);
+                } else {
+                    row[posx[k]] = mk<C>(A[t].x - B[t].y, A[t].y + B[t].x);
+                    row[posx[nx - k]] = mk<C>(A[t].x + B[t].y, B[t].x - A[t].y);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    fft_lines<T, true>(s, twx, g.ax, 1, 0, half, 2 * ls, 1, tid, nthr);
+    const T sc = (T)oa.scale, ad = (T)oa.add[c];
+    T* yc = y + c * N;
+    for (int e = tid; e < half * nx; e += nthr) {
+        const int r = e / nx, xi = e - r * nx;
+        const long long v0 = pl + (long long)(2 * r) * nx + xi;
+        const C zv = s[r * 2 * ls + xi];
+        yc[v0] = fma(sc, zv.x, ad);
+        yc[v0 + nx] = fma(sc, zv.y, ad);
+    }
+}
+
+template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 4 : 8; }
+
+template <typename T> size_t zproj_smem(const GridDev& g) {
+    using C = typename C2<T>::t;
+    constexpr int W = zproj_width<T>();
+    return (size_t)9 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
+           (g.ny + g.nz) * sizeof(int) + 16;
+}
+
+template <typename K> void allow_smem(K kern, size_t bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t plane_smem_bytes(int nx, int ny, int elem) {
+    return (size_t)ny * (nx / 2 + 1) * elem + (size_t)(nx + ny) * elem + (size_t)nx * sizeof(int) + 16;
+}
+
+// ev (optional): four events recorded before, between and after the kernels.
+template <typename T>
+cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
+                            const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev) {
+    using C = typename C2<T>::t;
+    const GridDev& g = h->g;
+    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(C));
+    const size_t smB = zproj_smem<T>(g);
+    constexpr int W = zproj_width<T>();
+    const dim3 gridA(9, g.nz);
+    const long long nF = (long long)g.ny * g.nxh;
+    const int blocksB = (int)((nF + W - 1) / W);
+    if (ev) cudaEventRecord(ev[0], h->stream);
+    if (K) {
+        allow_smem(k_plane_fwd<T, true>, smA);
+        k_plane_fwd<T, true><<<gridA, 512, smA, h->stream>>>(x, K, spec, g);
+    } else {
+        allow_smem(k_plane_fwd<T, false>, smA);
+        k_plane_fwd<T, false><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g);
+    }
+    if (ev) cudaEventRecord(ev[1], h->stream);
+    allow_smem(k_zproj<T, W>, smB);
+    k_zproj<T, W><<<blocksB, 256, smB, h->stream>>>(spec, g, pa);
+    if (ev) cudaEventRecord(ev[2], h->stream);
+    allow_smem(k_plane_inv<T>, smA);
+    k_plane_inv<T><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa);
+    if (ev) cudaEventRecord(ev[3], h->stream);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_galerkin<double>(const gff_handle*, const double*, const double*, double*,
+                                             const ProjArgs&, const OutArgs&, double2*, cudaEvent_t*);
+template cudaError_t launch_galerkin<float>(const gff_handle*, const float*, const float*, float*, const ProjArgs&,
+                                            const OutArgs&, float2*, cudaEvent_t*);
+
+}  // namespace gff

@@ -1,0 +1,168 @@
+// Internal declarations of libgff: device tables, the handle, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "gff.h"
+
+namespace gff {
+
+constexpr int MAXN = 128;   // largest axis length of the plane kernels
+constexpr int MAXST = 8;    // largest number of radix stages per axis
+constexpr int NSLIP = 12;
+
+template <typename T> struct C2;
+template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; };
+
+// Mixed-radix plan of one axis: n = radix[0] * ... * radix[nst-1].
+// The forward transform is decimation in frequency in place: natural input,
+// output at position p holds frequency freq_of_pos(p).  The inverse replays
+// the forward stages backwards with conjugate twiddles (decimation in time),
+// taking that order back to natural order.
+struct AxisPlan {
+    int n;
+    int nst;
+    int radix[MAXST];
+};
+
+// Read-only tables of one grid, resident on the device.
+struct GridDev {
+    int nx, ny, nz, nxh;
+    long long N;
+    AxisPlan ax, ay, az;
+    const double2* tw64[3];  // W_n^k = exp(-2 pi i k / n), k < n, per axis (x, y, z)
+    const float2* tw32[3];
+    const int* posx;         // [nx]: position of natural frequency kx after the forward x pass
+    const int* fqy;          // [ny]: frequency held at position py after the forward y pass
+    const int* fqz;          // [nz]
+    const double* qt64[2][3];  // [kind][axis][k]: q~ (continuous) or q~' (discrete) per FFT index
+    const float* qt32[2][3];
+};
+
+// Projection parameters of one call.
+struct ProjArgs {
+    int kind;        // GFF_PROJ_*
+    float mask[9];   // 1 = stress-controlled component (zero frequency keeps it)
+};
+
+// Output epilogue of the inverse plane pass: out = scale * y + add[c].
+struct OutArgs {
+    double scale;
+    double add[9];
+};
+
+struct GrainDev {
+    const double* C;        // [ngrains][81] rotated stiffness
+    const double* S0;       // [ngrains][12][9] Schmid tensors, sample frame
+    const double* nrm;      // [ngrains][12][3] slip-plane normals, sample frame
+    const int* kind;        // [ngrains] material kind
+    const int* phase;       // [ngrains]
+};
+
+struct CPParamsDev {
+    double gdot0, p, tau0, c, d;
+};
+
+}  // namespace gff
+
+struct gff_handle {
+    gff_grid grid;
+    gff_options opt;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    long long N = 0;
+    int nxh = 0;
+    gff::GridDev g{};
+    void* tables = nullptr;  // backing store of GridDev pointers
+
+    // microstructure
+    int ngrains = 0;
+    bool have_ms = false;
+    int* d_gid = nullptr;
+    double* d_C = nullptr;
+    double* d_S0 = nullptr;
+    double* d_nrm = nullptr;
+    int* d_gkind = nullptr;
+    int* d_gphase = nullptr;
+    gff_material mat[8];
+    bool mat_set[8] = {false};
+    bool any_cp = false;
+
+    // FP64 fields [9][N] (K: [81][N])
+    double* d_F = nullptr;     // committed F
+    double* d_Fk = nullptr;    // Newton iterate
+    double* d_P = nullptr;
+    double* d_K = nullptr;
+    double* d_b = nullptr;
+    double* d_x = nullptr;
+    double* d_r = nullptr;
+    double* d_p = nullptr;
+    double* d_Ap = nullptr;
+    // FP32 copies for the mixed path
+    float* d_K32 = nullptr;
+    float* d_b32 = nullptr;
+    float* d_x32 = nullptr;
+    float* d_r32 = nullptr;
+    float* d_p32 = nullptr;
+    float* d_Ap32 = nullptr;
+    // half spectrum [9][nz][ny][nxh] complex (FP64 size; FP32 reuses it)
+    double2* d_spec = nullptr;
+    // crystal plasticity state (committed / trial) and FIP accumulators
+    double* d_Fpi = nullptr;   // [9][N]
+    double* d_chi = nullptr;   // [12][N]
+    double* d_Fpi_t = nullptr;
+    double* d_chi_t = nullptr;
+    double* d_dg = nullptr;    // [12][N] slip increments of the trial
+    double* d_tau = nullptr;   // [12][N]
+    double* d_acc = nullptr;   // [NACC][N]
+    int* d_flag = nullptr;     // device status word (CP failures)
+    // reductions
+    double* d_red = nullptr;   // partial sums
+    double* d_scal = nullptr;  // final scalars
+    double* h_scal = nullptr;  // pinned host mirror
+    bool K_valid = false;
+    bool K32_valid = false;
+    bool grains_ready = false;
+    void* hostdata = nullptr;  // host copies of the orientations and phases
+    std::string err;
+};
+
+namespace gff {
+
+constexpr int NACC = 1 + 12 * 5;  // pcyc, W[12], gamma[12], gmin[12], gmax[12], sn[12]
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+
+// ---- launchers (fft_proj.cu)
+template <typename T>
+cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
+                            const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr);
+size_t plane_smem_bytes(int nx, int ny, int elem);
+
+// ---- vector kernels (vec.cu)
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, long long n, double* partial, double* out, cudaStream_t s);
+cudaError_t launch_sum9(const double* a, long long N, double* partial, double* out9, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_update(T* x, T* r, const T* p, const T* Ap, double alpha, long long n, double* partial,
+                             double* out_rr, cudaStream_t s);
+template <typename T>
+cudaError_t launch_xpby(T* p, const T* r, double beta, long long n, cudaStream_t s);
+cudaError_t launch_add_const9(double* F, const double* Fsrc, const double* d9, long long N, cudaStream_t s);
+template <typename Tin>
+cudaError_t launch_axpy_to64(double* y, const Tin* x, long long n, cudaStream_t s);
+cudaError_t launch_cast64to32(float* y, const double* x, long long n, cudaStream_t s);
+cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
+
+// ---- constitutive kernels (material.cu)
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32);
+cudaError_t launch_fip_accumulate(gff_handle* h);
+cudaError_t launch_fip_reset(gff_handle* h);
+cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs);
+
+}  // namespace gff

@@ -1,0 +1,609 @@
+// Per-voxel constitutive update P, K = dP/dF (Eqs. constitutive, P_dif) and
+// the fatigue-indicator accumulators (Sect. 3.3).
+//
+// St.Venant-Kirchhoff: E = (F^T F - I)/2, S = C:E, P = F S,
+//   K_ijkl = delta_ik S_lj + F_ip C_pjln F_kn.
+// FCC crystal plasticity (12 {111}<110> systems, flow rule of Eq. gamma_dot
+// with a constant resistance tau0 and an Armstrong-Frederick backstress):
+//   Fp^-1 = Fp^-1_n (I - sum_a dg_a S0_a), Fe = F Fp^-1, Ce = Fe^T Fe,
+//   S = C : (Ce - I)/2, tau_a = (Ce S) : S0_a,
+//   chi_a = (chi_n,a + c dg_a) / (1 + d |dg_a|),
+//   r_a = dg_a - dt gdot0 h((tau_a - chi_a)/tau0),  h(x) = |x|^p sign(x),
+// solved for dg by Newton from dg = 0 (12x12 LU with partial pivoting), then
+//   P = Fe S Fp^-T and K by implicit differentiation of r(dg, F) = 0.
+// Everything is FP64.  One thread per voxel.
+#include <cmath>
+
+#include "gff_internal.cuh"
+
+namespace gff {
+namespace {
+
+constexpr int TPB = 128;
+
+__device__ __forceinline__ void mm(const double* a, const double* b, double* c) {  // c = a b
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
+}
+__device__ __forceinline__ void mtm(const double* a, const double* b, double* c) {  // c = a^T b
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c[3 * i + j] = a[i] * b[j] + a[3 + i] * b[3 + j] + a[6 + i] * b[6 + j];
+}
+__device__ __forceinline__ void mmt(const double* a, const double* b, double* c) {  // c = a b^T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[3 * j] + a[3 * i + 1] * b[3 * j + 1] + a[3 * i + 2] * b[3 * j + 2];
+}
+__device__ __forceinline__ double ddot9(const double* a, const double* b) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s = fma(a[k], b[k], s);
+    return s;
+}
+// S = C : E for a symmetric E (C has minor symmetries)
+__device__ __forceinline__ void c_ddot(const double* __restrict__ C, const double* E, double* S) {
+#pragma unroll
+    for (int ij = 0; ij < 9; ++ij) {
+        const double* Cr = C + 9 * ij;
+        double s = 0.0;
+#pragma unroll
+        for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(Cr + kl), E[kl], s);
+        S[ij] = s;
+    }
+}
+
+__device__ __forceinline__ double ipow(double a, int p) {  // a >= 0, p >= 0
+    double r = 1.0, b = a;
+    while (p) {
+        if (p & 1) r *= b;
+        b *= b;
+        p >>= 1;
+    }
+    return r;
+}
+
+__device__ __forceinline__ double sgn(double v) { return (v > 0.0) - (v < 0.0); }
+
+struct CPOut {
+    double P[9];
+    double Fpi[9];
+    double chi[12];
+    double dg[12];
+    double tau[12];
+    bool ok;
+};
+
+// LU with partial pivoting of an n x n row-major matrix, in place.
+template <int NN>
+__device__ bool lu_factor(double* a, int* piv) {
+    for (int k = 0; k < NN; ++k) {
+        int p = k;
+        double m = fabs(a[k * NN + k]);
+        for (int i = k + 1; i < NN; ++i) {
+            const double v = fabs(a[i * NN + k]);
+            if (v > m) {
+                m = v;
+                p = i;
+            }
+        }
+        piv[k] = p;
+        if (m == 0.0) return false;
+        if (p != k)
+            for (int j = 0; j < NN; ++j) {
+                const double t = a[k * NN + j];
+                a[k * NN + j] = a[p * NN + j];
+                a[p * NN + j] = t;
+            }
+        const double inv = 1.0 / a[k * NN + k];
+        for (int i = k + 1; i < NN; ++i) {
+            const double l = a[i * NN + k] * inv;
+            a[i * NN + k] = l;
+            for (int j = k + 1; j < NN; ++j) a[i * NN + j] = fma(-l, a[k * NN + j], a[i * NN + j]);
+        }
+    }
+    return true;
+}
+template <int NN>
+__device__ void lu_solve(const double* a, const int* piv, double* b) {
+    for (int k = 0; k < NN; ++k) {
+        const int p = piv[k];
+        if (p != k) {
+            const double t = b[k];
+            b[k] = b[p];
+            b[p] = t;
+        }
+    }
+    for (int i = 1; i < NN; ++i) {
+        double s = b[i];
+        for (int j = 0; j < i; ++j) s = fma(-a[i * NN + j], b[j], s);
+        b[i] = s;
+    }
+    for (int i = NN - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int j = i + 1; j < NN; ++j) s = fma(-a[i * NN + j], b[j], s);
+        b[i] = s / a[i * NN + i];
+    }
+}
+
+// Elastic state for slip increments dg: Fpi, Fe, Ce, S, M = Ce S, tau.
+struct ElState {
+    double Fpi[9], Fe[9], Ce[9], S[9], M[9], tau[12];
+};
+
+__device__ void elastic_state(const double* F, const double* A, const double* dg, const double* __restrict__ S0,
+                              const double* __restrict__ C, ElState& st) {
+    double Lp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Lp[k] = 0.0;
+    for (int a = 0; a < NSLIP; ++a)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Lp[k] = fma(dg[a], __ldg(S0 + 9 * a + k), Lp[k]);
+    double IL[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) IL[k] = ((k % 4) == 0 ? 1.0 : 0.0) - Lp[k];
+    mm(A, IL, st.Fpi);
+    mm(F, st.Fpi, st.Fe);
+    mtm(st.Fe, st.Fe, st.Ce);
+    double E[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) E[k] = 0.5 * (st.Ce[k] - ((k % 4) == 0 ? 1.0 : 0.0));
+    c_ddot(C, E, st.S);
+    mm(st.Ce, st.S, st.M);
+    for (int a = 0; a < NSLIP; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) t = fma(st.M[k], __ldg(S0 + 9 * a + k), t);
+        st.tau[a] = t;
+    }
+}
+
+// Derivatives with respect to dg_b at fixed F:
+//   dFpi_b = -A S0_b, dFe_b = F dFpi_b, dCe_b = dFe_b^T Fe + Fe^T dFe_b,
+//   dS_b = C : dCe_b / 2.
+__device__ void dstate_ddg(const double* F, const double* A, const double* __restrict__ S0_b,
+                           const double* __restrict__ C, const ElState& st, double* dFpi, double* dFe, double* dCe,
+                           double* dS) {
+    double Sb[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Sb[k] = __ldg(S0_b + k);
+    mm(A, Sb, dFpi);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dFpi[k] = -dFpi[k];
+    mm(F, dFpi, dFe);
+    double t1[9], t2[9];
+    mtm(dFe, st.Fe, t1);
+    mtm(st.Fe, dFe, t2);
+    double hE[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        dCe[k] = t1[k] + t2[k];
+        hE[k] = 0.5 * dCe[k];
+    }
+    c_ddot(C, hE, dS);
+}
+
+__device__ void cp_update(const double* F, const double* A, const double* chin, double dt,
+                          const double* __restrict__ S0, const double* __restrict__ C, const CPParamsDev& pr,
+                          double* K /* 81 or null */, CPOut& out) {
+    const double g = pr.tau0, coef = dt * pr.gdot0;
+    const int p = (int)pr.p;
+    double dg[NSLIP];
+    for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
+    double J[NSLIP * NSLIP];
+    int piv[NSLIP];
+    double dh[NSLIP], chi[NSLIP];
+    ElState st;
+    bool conv = false;
+    const int maxit = 100;
+    for (int it = 0; it <= maxit; ++it) {
+        elastic_state(F, A, dg, S0, C, st);
+        double r[NSLIP], rmax = 0.0;
+        for (int a = 0; a < NSLIP; ++a) {
+            const double den = 1.0 + pr.d * fabs(dg[a]);
+            chi[a] = (chin[a] + pr.c * dg[a]) / den;
+            const double x = (st.tau[a] - chi[a]) / g;
+            const double ax = fabs(x);
+            const double axp1 = ipow(ax, p - 1);
+            dh[a] = p * axp1;
+            r[a] = dg[a] - coef * sgn(x) * axp1 * ax;
+            rmax = fmax(rmax, fabs(r[a]));
+        }
+        // Jacobian dr_a/ddg_b
+        for (int b = 0; b < NSLIP; ++b) {
+            double dFpi[9], dFe[9], dCe[9], dS[9], dM[9], t1[9];
+            dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
+            mm(dCe, st.S, dM);
+            mm(st.Ce, dS, t1);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) dM[k] += t1[k];
+            for (int a = 0; a < NSLIP; ++a) {
+                double dtau = 0.0;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) dtau = fma(dM[k], __ldg(S0 + 9 * a + k), dtau);
+                double v = -(coef / g) * dh[a] * dtau;
+                if (a == b) {
+                    const double den = 1.0 + pr.d * fabs(dg[a]);
+                    const double dchi = (pr.c - pr.d * sgn(dg[a]) * chi[a]) / den;
+                    v += 1.0 + (coef / g) * dh[a] * dchi;
+                }
+                J[a * NSLIP + b] = v;
+            }
+        }
+        if (rmax <= 1e-14) {
+            conv = true;
+            break;
+        }
+        if (it == maxit) break;
+        if (!lu_factor<NSLIP>(J, piv)) break;
+        lu_solve<NSLIP>(J, piv, r);
+        for (int a = 0; a < NSLIP; ++a) dg[a] -= r[a];
+    }
+    out.ok = conv;
+    // P = Fe S Fpi^T
+    double FeS[9];
+    mm(st.Fe, st.S, FeS);
+    mmt(FeS, st.Fpi, out.P);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out.Fpi[k] = st.Fpi[k];
+    for (int a = 0; a < NSLIP; ++a) {
+        out.chi[a] = chi[a];
+        out.dg[a] = dg[a];
+        out.tau[a] = st.tau[a];
+    }
+    if (!K || !conv) return;
+    if (!lu_factor<NSLIP>(J, piv)) {
+        out.ok = false;
+        return;
+    }
+    // dP/ddg_b  (12 x 9)
+    double dPb[NSLIP * 9];
+    for (int b = 0; b < NSLIP; ++b) {
+        double dFpi[9], dFe[9], dCe[9], dS[9], t1[9], t2[9], t3[9], t4[9];
+        dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
+        mm(dFe, st.S, t1);
+        mmt(t1, st.Fpi, t2);  // dFe S Fpi^T
+        mm(st.Fe, dS, t1);
+        mmt(t1, st.Fpi, t3);  // Fe dS Fpi^T
+        mmt(FeS, dFpi, t4);   // Fe S dFpi^T
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dPb[9 * b + k] = t2[k] + t3[k] + t4[k];
+    }
+    double SFt[9];
+    mmt(st.S, st.Fpi, SFt);  // S Fpi^T
+    for (int kl = 0; kl < 9; ++kl) {
+        const int k = kl / 3, l = kl % 3;
+        // dFe = E_kl Fpi: row k equals row l of Fpi
+        double dFe[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dFe[q] = 0.0;
+        dFe[3 * k] = st.Fpi[3 * l];
+        dFe[3 * k + 1] = st.Fpi[3 * l + 1];
+        dFe[3 * k + 2] = st.Fpi[3 * l + 2];
+        double t1[9], t2[9], dCe[9], hE[9], dS[9];
+        mtm(dFe, st.Fe, t1);
+        mtm(st.Fe, dFe, t2);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            dCe[q] = t1[q] + t2[q];
+            hE[q] = 0.5 * dCe[q];
+        }
+        c_ddot(C, hE, dS);
+        // dP at fixed dg = dFe S Fpi^T + Fe dS Fpi^T
+        double dP[9], t3[9];
+        mm(dFe, SFt, dP);
+        mm(st.Fe, dS, t3);
+        mmt(t3, st.Fpi, t1);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dP[q] += t1[q];
+        // dtau_a = (dCe S + Ce dS) : S0_a ; dr_a = -(coef/g) h'_a dtau_a ; ddg = -J^-1 dr
+        double dM[9];
+        mm(dCe, st.S, dM);
+        mm(st.Ce, dS, t2);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dM[q] += t2[q];
+        double rhs[NSLIP];
+        for (int a = 0; a < NSLIP; ++a) {
+            double dtau = 0.0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dtau = fma(dM[q], __ldg(S0 + 9 * a + q), dtau);
+            rhs[a] = (coef / g) * dh[a] * dtau;  // = -dr_a, so J ddg = rhs
+        }
+        lu_solve<NSLIP>(J, piv, rhs);
+        for (int b = 0; b < NSLIP; ++b)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dP[q] = fma(dPb[9 * b + q], rhs[b], dP[q]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) K[9 * q + kl] = dP[q];
+    }
+}
+
+__device__ void svk_update(const double* F, const double* __restrict__ C, double* P, double* K) {
+    double E[9], S[9];
+    mtm(F, F, E);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) E[k] = 0.5 * (E[k] - ((k % 4) == 0 ? 1.0 : 0.0));
+    c_ddot(C, E, S);
+    mm(F, S, P);
+    if (!K) return;
+    // K_ijkl = delta_ik S_lj + sum_p F_ip (sum_n C_pjln F_kn)
+    for (int j = 0; j < 3; ++j)
+        for (int l = 0; l < 3; ++l) {
+            double h[9];  // h[p][k] = sum_n C_pjln F_kn
+#pragma unroll
+            for (int pp = 0; pp < 3; ++pp)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const double* Cr = C + 27 * pp + 9 * j + 3 * l;  // C_{p j l n}
+                    h[3 * pp + k] = __ldg(Cr) * F[3 * k] + __ldg(Cr + 1) * F[3 * k + 1] + __ldg(Cr + 2) * F[3 * k + 2];
+                }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    double v = F[3 * i] * h[k] + F[3 * i + 1] * h[3 + k] + F[3 * i + 2] * h[6 + k];
+                    if (i == k) v += S[3 * l + j];
+                    K[9 * (3 * i + j) + (3 * k + l)] = v;
+                }
+        }
+}
+
+struct ConstArgs {
+    const double* F;
+    const int* gid;
+    const double* C;
+    const double* S0;
+    const int* gkind;
+    const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
+    const double* Fpi_n;
+    const double* chi_n;
+    double dt;
+    double* P;
+    double* K;
+    float* K32;
+    double* Fpi_t;
+    double* chi_t;
+    double* dg;
+    double* tau;
+    int* flag;
+    long long N;
+};
+
+__global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.N) return;
+    const long long N = a.N;
+    const int gi = a.gid[v];
+    const int kind = a.gkind[gi];
+    const double* C = a.C + 81LL * gi;
+    double F[9], K[81];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = a.F[k * N + v];
+    if (kind == GFF_MAT_CP_FCC) {
+        double A[9], chin[12];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) A[k] = a.Fpi_n[k * N + v];
+        for (int s = 0; s < NSLIP; ++s) chin[s] = a.chi_n[s * N + v];
+        CPParamsDev pr;
+        const double* gp = a.gprm + 5LL * gi;
+        pr.gdot0 = gp[0];
+        pr.p = gp[1];
+        pr.tau0 = gp[2];
+        pr.c = gp[3];
+        pr.d = gp[4];
+        CPOut o;
+        cp_update(F, A, chin, a.dt, a.S0 + 108LL * gi, C, pr, K, o);
+        if (!o.ok) atomicAdd(a.flag, 1);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            a.P[k * N + v] = o.P[k];
+            a.Fpi_t[k * N + v] = o.Fpi[k];
+        }
+        for (int s = 0; s < NSLIP; ++s) {
+            a.chi_t[s * N + v] = o.chi[s];
+            a.dg[s * N + v] = o.dg[s];
+            a.tau[s * N + v] = o.tau[s];
+        }
+    } else {
+        double P[9];
+        svk_update(F, C, P, K);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a.P[k * N + v] = P[k];
+        if (a.Fpi_t) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) a.Fpi_t[k * N + v] = a.Fpi_n[k * N + v];
+            for (int s = 0; s < NSLIP; ++s) {
+                a.chi_t[s * N + v] = a.chi_n[s * N + v];
+                a.dg[s * N + v] = 0.0;
+                a.tau[s * N + v] = 0.0;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
+    if (a.K32) {
+#pragma unroll
+        for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
+    }
+}
+
+// ---------------------------------------------------------------- fatigue indicator parameters
+struct FipArgs {
+    const int* gid;
+    const int* gkind;
+    const double* S0;
+    const double* nrm;
+    const double* dg;
+    const double* tau;
+    const double* F;
+    const double* P;
+    double* acc;  // [NACC][N]
+    long long N;
+};
+
+__global__ void __launch_bounds__(TPB) k_fip_accumulate(FipArgs a) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.N) return;
+    const long long N = a.N;
+    const int gi = a.gid[v];
+    if (a.gkind[gi] != GFF_MAT_CP_FCC) return;
+    const double* S0 = a.S0 + 108LL * gi;
+    const double* nr = a.nrm + 36LL * gi;
+    double dDp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dDp[k] = 0.0;
+    for (int s = 0; s < NSLIP; ++s) {
+        const double d = a.dg[s * N + v];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) dDp[3 * i + j] += d * 0.5 * (S0[9 * s + 3 * i + j] + S0[9 * s + 3 * j + i]);
+    }
+    double* acc = a.acc;
+    acc[v] += sqrt(2.0 / 3.0 * ddot9(dDp, dDp));
+    double F[9], P[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        F[k] = a.F[k * N + v];
+        P[k] = a.P[k * N + v];
+    }
+    const double J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                     F[2] * (F[3] * F[7] - F[4] * F[6]);
+    double sig[9];
+    mmt(P, F, sig);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sig[k] /= J;
+    for (int s = 0; s < NSLIP; ++s) {
+        const double d = a.dg[s * N + v];
+        acc[(1 + s) * N + v] += a.tau[s * N + v] * d;
+        const double gm = acc[(13 + s) * N + v] + d;
+        acc[(13 + s) * N + v] = gm;
+        acc[(25 + s) * N + v] = fmin(acc[(25 + s) * N + v], gm);
+        acc[(37 + s) * N + v] = fmax(acc[(37 + s) * N + v], gm);
+        const double m0 = nr[3 * s], m1 = nr[3 * s + 1], m2 = nr[3 * s + 2];
+        const double sn = m0 * (sig[0] * m0 + sig[1] * m1 + sig[2] * m2) + m1 * (sig[3] * m0 + sig[4] * m1 + sig[5] * m2) +
+                          m2 * (sig[6] * m0 + sig[7] * m1 + sig[8] * m2);
+        acc[(49 + s) * N + v] = fmax(acc[(49 + s) * N + v], sn);
+    }
+}
+
+__global__ void __launch_bounds__(TPB) k_fip_reset(double* acc, long long N) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    acc[v] = 0.0;
+    for (int s = 0; s < NSLIP; ++s) {
+        acc[(1 + s) * N + v] = 0.0;
+        const double gm = acc[(13 + s) * N + v];
+        acc[(25 + s) * N + v] = gm;
+        acc[(37 + s) * N + v] = gm;
+        acc[(49 + s) * N + v] = -INFINITY;
+    }
+}
+
+// per-grain sums: out[g][0] = count, [1] = pcyc, [2..13] = W, [14..25] = dgamma, [26..37] = sn
+constexpr int GSUM = 38;
+__global__ void __launch_bounds__(TPB) k_grain_sums(const int* gid, const int* gkind, const double* acc, long long N,
+                                                    double* out) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    const int gi = gid[v];
+    if (gkind[gi] != GFF_MAT_CP_FCC) return;
+    double* o = out + (long long)GSUM * gi;
+    atomicAdd(o, 1.0);
+    atomicAdd(o + 1, acc[v]);
+    for (int s = 0; s < NSLIP; ++s) {
+        atomicAdd(o + 2 + s, acc[(1 + s) * N + v]);
+        atomicAdd(o + 14 + s, acc[(37 + s) * N + v] - acc[(25 + s) * N + v]);
+        atomicAdd(o + 26 + s, acc[(49 + s) * N + v]);
+    }
+}
+
+__global__ void k_grain_final(const double* sums, int ngrains, double fs_k, double fs_sy, double* pc, double* w,
+                              double* fs) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ngrains) return;
+    const double* o = sums + (long long)GSUM * gi;
+    const double n = o[0];
+    if (n <= 0.0) {
+        pc[gi] = 0.0;
+        fs[gi] = 0.0;
+        for (int s = 0; s < NSLIP; ++s) w[NSLIP * gi + s] = 0.0;
+        return;
+    }
+    pc[gi] = o[1] / n;
+    double best = -INFINITY;
+    for (int s = 0; s < NSLIP; ++s) {
+        w[NSLIP * gi + s] = o[2 + s] / n;
+        const double v = 0.5 * (o[14 + s] / n) * (1.0 + fs_k * (o[26 + s] / n) / fs_sy);
+        best = fmax(best, v);
+    }
+    fs[gi] = best;
+}
+
+}  // namespace
+
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32) {
+    ConstArgs a;
+    a.F = F;
+    a.gid = h->d_gid;
+    a.C = h->d_C;
+    a.S0 = h->d_S0;
+    a.gkind = h->d_gkind;
+    a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
+    a.Fpi_n = h->d_Fpi;
+    a.chi_n = h->d_chi;
+    a.dt = dt;
+    a.P = h->d_P;
+    a.K = h->d_K;
+    a.K32 = write_k32 ? h->d_K32 : nullptr;
+    a.Fpi_t = h->d_Fpi_t;
+    a.chi_t = h->d_chi_t;
+    a.dg = h->d_dg;
+    a.tau = h->d_tau;
+    a.flag = h->d_flag;
+    a.N = h->N;
+    const int blocks = (int)((h->N + TPB - 1) / TPB);
+    k_constitutive<<<blocks, TPB, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fip_accumulate(gff_handle* h) {
+    FipArgs a;
+    a.gid = h->d_gid;
+    a.gkind = h->d_gkind;
+    a.S0 = h->d_S0;
+    a.nrm = h->d_nrm;
+    a.dg = h->d_dg;
+    a.tau = h->d_tau;
+    a.F = h->d_F;
+    a.P = h->d_P;
+    a.acc = h->d_acc;
+    a.N = h->N;
+    const int blocks = (int)((h->N + TPB - 1) / TPB);
+    k_fip_accumulate<<<blocks, TPB, 0, h->stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fip_reset(gff_handle* h) {
+    const int blocks = (int)((h->N + TPB - 1) / TPB);
+    k_fip_reset<<<blocks, TPB, 0, h->stream>>>(h->d_acc, h->N);
+    return cudaGetLastError();
+}
+
+// pc[ngrains], w[ngrains*12], fs[ngrains] are device arrays; scratch holds GSUM*ngrains doubles
+cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs) {
+    double* sums = pc + h->ngrains * 14;  // caller provides room after the outputs
+    cudaError_t e = cudaMemsetAsync(sums, 0, sizeof(double) * GSUM * h->ngrains, h->stream);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)((h->N + TPB - 1) / TPB);
+    k_grain_sums<<<blocks, TPB, 0, h->stream>>>(h->d_gid, h->d_gkind, h->d_acc, h->N, sums);
+    k_grain_final<<<(h->ngrains + 127) / 128, 128, 0, h->stream>>>(sums, h->ngrains, h->opt.fs_k, h->opt.fs_sigma_y, pc,
+                                                                    w, fs);
+    return cudaGetLastError();
+}
+
+}  // namespace gff

@@ -1,0 +1,181 @@
+// Conjugate-gradient vector updates and reductions (Sect. 2.1, the Krylov
+// solver of Eq. linequil2).  Reductions are two-stage and deterministic: a
+// fixed grid of RED_BLOCKS blocks writes partial sums, one block adds them in
+// a fixed order.  Sums are accumulated in FP64 for both precisions.
+#include "gff_internal.cuh"
+
+namespace gff {
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_dot_partial(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                                     double* __restrict__ partial) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc = fma((double)a[i], (double)b[i], acc);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// out[k] = sum_b partial[k * nb + b], one block per k
+__global__ void __launch_bounds__(TPB) k_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[(long long)blockIdx.x * nb + i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = acc;
+}
+
+// per-component sums of a [9][N] field: grid (RED_BLOCKS, 9)
+__global__ void __launch_bounds__(TPB) k_sum9_partial(const double* __restrict__ a, long long N,
+                                                      double* __restrict__ partial) {
+    __shared__ double sh[32];
+    const double* ac = a + (long long)blockIdx.y * N;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+        acc += ac[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                   const T* __restrict__ Ap, T alpha, long long n,
+                                                   double* __restrict__ partial) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, Ap[i], r[i]);
+        r[i] = ri;
+        acc = fma((double)ri, (double)ri, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_xpby(T* __restrict__ p, const T* __restrict__ r, T beta, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+struct Nine {
+    double v[9];
+};
+
+__global__ void __launch_bounds__(TPB) k_add_const9(double* __restrict__ F, const double* __restrict__ Fsrc, Nine d,
+                                                    long long N) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 9 * N; i += (long long)gridDim.x * blockDim.x)
+        F[i] = Fsrc[i] + d.v[i / N];
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(TPB) k_axpy_to64(double* __restrict__ y, const Tin* __restrict__ x, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += (double)x[i];
+}
+
+__global__ void __launch_bounds__(TPB) k_cast(float* __restrict__ y, const double* __restrict__ x, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_fill(T* __restrict__ y, T v, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+
+inline int grid_for(long long n) {
+    long long b = (n + TPB - 1) / TPB;
+    return (int)(b < 152LL * 8 ? (b < 1 ? 1 : b) : 152LL * 8);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, long long n, double* partial, double* out, cudaStream_t s) {
+    k_dot_partial<T><<<RED_BLOCKS, TPB, 0, s>>>(a, b, n, partial);
+    k_final<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum9(const double* a, long long N, double* partial, double* out9, cudaStream_t s) {
+    k_sum9_partial<<<dim3(RED_BLOCKS, 9), TPB, 0, s>>>(a, N, partial);
+    k_final<<<9, TPB, 0, s>>>(partial, RED_BLOCKS, out9);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_update(T* x, T* r, const T* p, const T* Ap, double alpha, long long n, double* partial,
+                             double* out_rr, cudaStream_t s) {
+    k_cg_update<T><<<RED_BLOCKS, TPB, 0, s>>>(x, r, p, Ap, (T)alpha, n, partial);
+    k_final<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, out_rr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_xpby(T* p, const T* r, double beta, long long n, cudaStream_t s) {
+    k_xpby<T><<<grid_for(n), TPB, 0, s>>>(p, r, (T)beta, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_const9(double* F, const double* Fsrc, const double* d9, long long N, cudaStream_t s) {
+    Nine d;
+    for (int c = 0; c < 9; ++c) d.v[c] = d9[c];
+    k_add_const9<<<grid_for(9 * N), TPB, 0, s>>>(F, Fsrc, d, N);
+    return cudaGetLastError();
+}
+
+template <typename Tin>
+cudaError_t launch_axpy_to64(double* y, const Tin* x, long long n, cudaStream_t s) {
+    k_axpy_to64<Tin><<<grid_for(n), TPB, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast64to32(float* y, const double* x, long long n, cudaStream_t s) {
+    k_cast<<<grid_for(n), TPB, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s) {
+    k_fill<double><<<grid_for(n), TPB, 0, s>>>(y, v, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_zero(T* y, long long n, cudaStream_t s) {
+    k_fill<T><<<grid_for(n), TPB, 0, s>>>(y, (T)0, n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_dot<double>(const double*, const double*, long long, double*, double*, cudaStream_t);
+template cudaError_t launch_dot<float>(const float*, const float*, long long, double*, double*, cudaStream_t);
+template cudaError_t launch_cg_update<double>(double*, double*, const double*, const double*, double, long long,
+                                              double*, double*, cudaStream_t);
+template cudaError_t launch_cg_update<float>(float*, float*, const float*, const float*, double, long long, double*,
+                                             double*, cudaStream_t);
+template cudaError_t launch_xpby<double>(double*, const double*, double, long long, cudaStream_t);
+template cudaError_t launch_xpby<float>(float*, const float*, double, long long, cudaStream_t);
+template cudaError_t launch_axpy_to64<double>(double*, const double*, long long, cudaStream_t);
+template cudaError_t launch_axpy_to64<float>(double*, const float*, long long, cudaStream_t);
+template cudaError_t launch_zero<double>(double*, long long, cudaStream_t);
+template cudaError_t launch_zero<float>(float*, long long, cudaStream_t);
+
+}  // namespace gff

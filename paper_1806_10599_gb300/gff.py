@@ -1,0 +1,302 @@
+"""Thin ctypes binding of libgff.so (include/gff.h): same names, argument
+marshalling only.  Every computation happens in the CUDA library; importing
+this module fails loudly when libgff.so has not been built.
+
+Host arrays are numpy arrays (converted to contiguous float64 / int32 /
+uint8 as the C signature requires).  Device arguments (`*_dev`) are torch
+CUDA tensors (or raw integer addresses).
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libgff.so")
+
+GFF_OK = 0
+GFF_ERR_ARG = -1
+GFF_ERR_OOM = -2
+GFF_ERR_CUDA = -3
+GFF_ERR_NO_CONVERGENCE = -4
+GFF_ERR_CP_FAIL = -5
+GFF_ERR_TIMEOUT = -6
+GFF_ERR_STATE = -7
+GFF_ERR_IO = -8
+
+GFF_PROJ_CONTINUOUS, GFF_PROJ_DISCRETE = 0, 1
+GFF_PREC_FP64, GFF_PREC_MIXED = 0, 1
+GFF_MAT_SVK_CUBIC, GFF_MAT_SVK_ISO, GFF_MAT_CP_FCC = 0, 1, 2
+(GFF_FIELD_F, GFF_FIELD_P, GFF_FIELD_K, GFF_FIELD_FP_INV, GFF_FIELD_CHI,
+ GFF_FIELD_GAMMA, GFF_FIELD_PCYC, GFF_FIELD_WCYC) = range(8)
+FIELD_COMPONENTS = {0: 9, 1: 9, 2: 81, 3: 9, 4: 12, 5: 12, 6: 1, 7: 12}
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+
+class gff_grid(ctypes.Structure):
+    _fields_ = [("nx", c_int), ("ny", c_int), ("nz", c_int), ("L", c_double * 3)]
+
+
+class gff_material(ctypes.Structure):
+    _fields_ = [("kind", c_int)] + [
+        (n, c_double) for n in ("C11", "C12", "C44", "E", "nu", "gdot0", "p_exp", "tau0", "c_af", "d_af")
+    ]
+
+
+class gff_options(ctypes.Structure):
+    _fields_ = [
+        ("projection", c_int),
+        ("precision", c_int),
+        ("newton_tol", c_double),
+        ("cg_tol", c_double),
+        ("newton_max", c_int),
+        ("cg_max", c_int),
+        ("max_cuts", c_int),
+        ("warm_start", c_int),
+        ("fs_k", c_double),
+        ("fs_sigma_y", c_double),
+    ]
+
+
+class gff_step_report(ctypes.Structure):
+    _fields_ = [
+        ("newton_iters", c_int),
+        ("cg_iters", c_int),
+        ("cuts", c_int),
+        ("residual", c_double),
+        ("Pmacro", c_double * 9),
+        ("Fmacro", c_double * 9),
+        ("seconds", c_double),
+    ]
+
+
+class GffError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("gff status %d: %s" % (status, msg))
+        self.status = status
+
+
+_P = ctypes.POINTER
+_SIGS = {
+    "gff_options_default": (None, [_P(gff_options)]),
+    "gff_create": (c_int, [_P(gff_grid), _P(gff_options), _P(c_void_p)]),
+    "gff_destroy": (None, [c_void_p]),
+    "gff_last_error": (ctypes.c_char_p, [c_void_p]),
+    "gff_set_stream": (c_int, [c_void_p, c_void_p]),
+    "gff_set_options": (c_int, [c_void_p, _P(gff_options)]),
+    "gff_set_microstructure": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "gff_set_material": (c_int, [c_void_p, c_int, _P(gff_material)]),
+    "gff_set_field": (c_int, [c_void_p, c_int, c_void_p]),
+    "gff_get_field": (c_int, [c_void_p, c_int, c_void_p]),
+    "gff_constitutive": (c_int, [c_void_p, c_double]),
+    "gff_apply_operator": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "gff_project": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "gff_apply_operator_timed": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
+    "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p]),
+    "gff_reset_fips": (c_int, [c_void_p]),
+    "gff_get_fips": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_save_state": (c_int, [c_void_p, ctypes.c_char_p]),
+    "gff_load_state": (c_int, [c_void_p, ctypes.c_char_p]),
+}
+
+
+def load_library(path=LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libgff.so not built (%s): run `python -m paper_1806_10599_gb300.build`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(h, st):
+    if st != GFF_OK:
+        msg = _lib.gff_last_error(h)
+        raise GffError(st, msg.decode() if msg else "")
+    return st
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(c_void_p)
+
+
+def _dev(t):
+    if isinstance(t, int):
+        return c_void_p(t)
+    return c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------- same-name wrappers
+def gff_options_default():
+    o = gff_options()
+    _lib.gff_options_default(ctypes.byref(o))
+    return o
+
+
+def gff_create(grid, opt=None):
+    h = c_void_p()
+    st = _lib.gff_create(ctypes.byref(grid), ctypes.byref(opt) if opt is not None else None, ctypes.byref(h))
+    if st != GFF_OK:
+        msg = _lib.gff_last_error(h).decode() if h.value else ""
+        if h.value:
+            _lib.gff_destroy(h)
+        raise GffError(st, msg)
+    return h
+
+
+def gff_destroy(h):
+    _lib.gff_destroy(h)
+
+
+def gff_last_error(h):
+    return _lib.gff_last_error(h).decode()
+
+
+def gff_set_stream(h, stream):
+    s = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", 0)
+    return _check(h, _lib.gff_set_stream(h, c_void_p(s)))
+
+
+def gff_set_options(h, opt):
+    return _check(h, _lib.gff_set_options(h, ctypes.byref(opt)))
+
+
+def gff_set_microstructure(h, grain_id, ngrains, quat, grain_phase):
+    g, gp = _host(grain_id, np.int32)
+    q, qp = _host(quat, np.float64)
+    p, pp = _host(grain_phase, np.int32)
+    return _check(h, _lib.gff_set_microstructure(h, gp, int(ngrains), qp, pp))
+
+
+def gff_set_material(h, phase, mat):
+    return _check(h, _lib.gff_set_material(h, int(phase), ctypes.byref(mat)))
+
+
+def gff_set_field(h, which, host):
+    a, ap = _host(host, np.float64)
+    return _check(h, _lib.gff_set_field(h, int(which), ap))
+
+
+def gff_get_field(h, which, n_voxels):
+    out = np.empty(FIELD_COMPONENTS[which] * n_voxels)
+    _check(h, _lib.gff_get_field(h, int(which), out.ctypes.data_as(c_void_p)))
+    return out
+
+
+def gff_constitutive(h, dt):
+    return _check(h, _lib.gff_constitutive(h, float(dt)))
+
+
+def _mask(mask9):
+    if mask9 is None:
+        return None, None
+    return _host(mask9, np.uint8)
+
+
+def gff_apply_operator(h, precision, mask9, x_dev, y_dev):
+    m, mp = _mask(mask9)
+    return _check(h, _lib.gff_apply_operator(h, int(precision), mp, _dev(x_dev), _dev(y_dev)))
+
+
+def gff_apply_operator_timed(h, precision, mask9, x_dev, y_dev):
+    """Returns the three kernel durations (ms) of one apply."""
+    m, mp = _mask(mask9)
+    ms = (ctypes.c_float * 3)()
+    _check(h, _lib.gff_apply_operator_timed(h, int(precision), mp, _dev(x_dev), _dev(y_dev),
+                                            ctypes.cast(ms, c_void_p)))
+    return [ms[0], ms[1], ms[2]]
+
+
+def gff_project(h, precision, mask9, x_dev, y_dev):
+    m, mp = _mask(mask9)
+    return _check(h, _lib.gff_project(h, int(precision), mp, _dev(x_dev), _dev(y_dev)))
+
+
+def gff_step(h, dt, Fbar, mask, Pbar):
+    f, fp = _host(Fbar, np.float64)
+    m, mp = _host(mask, np.uint8)
+    p, pp = _host(Pbar, np.float64)
+    rep = gff_step_report()
+    _check(h, _lib.gff_step(h, float(dt), fp, mp, pp, ctypes.byref(rep)))
+    return rep
+
+
+def gff_run_history(h, dt, Fbar, mask, Pbar, cycle_start=None):
+    n = int(np.asarray(dt).shape[0])
+    d, dp = _host(dt, np.float64)
+    f, fp = _host(Fbar, np.float64)
+    m, mp = _host(mask, np.uint8)
+    p, pp = _host(Pbar, np.float64)
+    cs, csp = _host(cycle_start, np.uint8) if cycle_start is not None else (None, None)
+    Pm = np.zeros((n, 9))
+    reps = (gff_step_report * max(n, 1))()
+    _check(h, _lib.gff_run_history(h, n, dp, fp, mp, pp, csp, Pm.ctypes.data_as(c_void_p),
+                                   ctypes.cast(reps, c_void_p)))
+    return Pm, [reps[k] for k in range(n)]
+
+
+def gff_reset_fips(h):
+    return _check(h, _lib.gff_reset_fips(h))
+
+
+def gff_get_fips(h, ngrains):
+    pc = np.zeros(ngrains)
+    w = np.zeros((ngrains, 12))
+    fs = np.zeros(ngrains)
+    _check(h, _lib.gff_get_fips(h, pc.ctypes.data_as(c_void_p), w.ctypes.data_as(c_void_p),
+                                fs.ctypes.data_as(c_void_p)))
+    return pc, w, fs
+
+
+def gff_save_state(h, path):
+    return _check(h, _lib.gff_save_state(h, str(path).encode()))
+
+
+def gff_load_state(h, path):
+    return _check(h, _lib.gff_load_state(h, str(path).encode()))
+
+
+# --------------------------------------------------------------------------- convenience
+def make_grid(nx, ny, nz, L=(1.0, 1.0, 1.0)):
+    g = gff_grid()
+    g.nx, g.ny, g.nz = nx, ny, nz
+    g.L[0], g.L[1], g.L[2] = L
+    return g
+
+
+def make_options(**kw):
+    o = gff_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_material(kind, C11=168.4e9, C12=121.4e9, C44=75.4e9, E=400e9, nu=0.2, gdot0=1e-3, p_exp=20.0,
+                  tau0=50e6, c_af=20e9, d_af=200.0):
+    m = gff_material()
+    m.kind = kind
+    m.C11, m.C12, m.C44, m.E, m.nu = C11, C12, C44, E, nu
+    m.gdot0, m.p_exp, m.tau0, m.c_af, m.d_af = gdot0, p_exp, tau0, c_af, d_af
+    return m
+
+
+def create_rve(ms, materials, options=None):
+    """Handle for a rve_inputs.Microstructure with {phase: gff_material}."""
+    h = gff_create(make_grid(ms.nx, ms.ny, ms.nz, ms.L), options)
+    try:
+        for ph, m in materials.items():
+            gff_set_material(h, ph, m)
+        gff_set_microstructure(h, ms.grain_id.reshape(-1), ms.ngrains, ms.quat, ms.phase)
+    except Exception:
+        gff_destroy(h)
+        raise
+    return h

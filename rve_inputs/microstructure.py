@@ -43,11 +43,15 @@ class Microstructure:
         return self.nx * self.ny * self.nz
 
 
-def periodic_voronoi(shape, ngrains, seed, L=(1.0, 1.0, 1.0), chunk=1 << 16):
+def periodic_voronoi(shape, ngrains, seed, L=(1.0, 1.0, 1.0)):
     """Nearest-seed labels of voxel centres ((i + 1/2) h) under the periodic
     minimum-image Euclidean distance; ties go to the lowest seed index.
 
-    shape = (nz, ny, nx).  Seeds are uniform in [0, L)^3."""
+    shape = (nz, ny, nx).  Seeds are uniform in [0, L)^3.  The search uses a
+    periodic k-d tree (scipy cKDTree with boxsize = L); the two nearest
+    seeds are returned so that exact ties can be resolved by index."""
+    from scipy.spatial import cKDTree
+
     nz, ny, nx = shape
     L = np.asarray(L, dtype=np.float64)
     u = uniform01(seed, 3 * ngrains, OFF_SEEDS).reshape(ngrains, 3)
@@ -57,13 +61,11 @@ def periodic_voronoi(shape, ngrains, seed, L=(1.0, 1.0, 1.0), chunk=1 << 16):
     centres = np.stack(
         [(xi.ravel() + 0.5) * h[0], (yi.ravel() + 0.5) * h[1], (zi.ravel() + 0.5) * h[2]], axis=1
     )
-    out = np.empty(centres.shape[0], dtype=np.int32)
-    for s in range(0, centres.shape[0], chunk):
-        c = centres[s : s + chunk]
-        d = np.abs(c[:, None, :] - seeds[None, :, :])
-        d = np.minimum(d, L[None, None, :] - d)
-        d2 = np.einsum("vgk,vgk->vg", d, d)
-        out[s : s + chunk] = np.argmin(d2, axis=1)
+    if ngrains == 1:
+        return np.zeros(shape, dtype=np.int32)
+    tree = cKDTree(seeds, boxsize=L)
+    d, i = tree.query(centres, k=2)
+    out = np.where(d[:, 0] == d[:, 1], np.minimum(i[:, 0], i[:, 1]), i[:, 0]).astype(np.int32)
     return out.reshape(nz, ny, nx)
 
 

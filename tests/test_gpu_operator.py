@@ -1,0 +1,142 @@
+"""Parity of the CUDA Galerkin operator with the oracle (Eqs. eql_discrete3,
+newlinop; G^ of Eq. G and G^' of Sect. 2.2), element by element on seeded
+inputs.  Tolerances: FP64 relative L2 1e-12 (the transforms differ only in
+rounding order), FP32 relative L2 2e-6 (single-precision rounding of
+~log2(N) butterfly stages and the K contraction)."""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import gff, rel_l2, torch_cuda, voxel_K_oracle
+from oracle import spectral as sp
+from rve_inputs import polycrystal, standard_normal
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(16, 16, 16), (6, 10, 12), (12, 48, 20), (40, 8, 30), (32, 32, 32)]  # (nz, ny, nx)
+MASKS = [None, np.array([0, 1, 1, 1, 1, 1, 1, 0, 1], dtype=np.uint8)]
+
+
+def _field(seed, shape):
+    nz, ny, nx = shape
+    return standard_normal(seed, 9 * nz * ny * nx).reshape(3, 3, nz, ny, nx)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("kind", [sp.KIND_CONTINUOUS, sp.KIND_DISCRETE])
+@pytest.mark.parametrize("mi", [0, 1])
+def test_project_matches_oracle(shape, kind, mi):
+    torch = torch_cuda()
+    g = gff()
+    nz, ny, nx = shape
+    L = (1.0, 2.0, 0.5) if shape == (12, 48, 20) else (1.0, 1.0, 1.0)
+    h = g.gff_create(g.make_grid(nx, ny, nz, L), g.make_options(projection=kind))
+    try:
+        x = _field(7, shape)
+        mask = MASKS[mi]
+        ref = sp.G(x, L, kind, None if mask is None else mask.astype(np.float64))
+        X = torch.from_numpy(x.reshape(9, -1).copy()).cuda()
+        Y = torch.empty_like(X)
+        g.gff_project(h, g.GFF_PREC_FP64, mask, X, Y)
+        torch.cuda.synchronize()
+        assert rel_l2(Y.cpu().numpy(), ref) <= 1e-12
+        X32, Y32 = X.float(), torch.empty_like(X.float())
+        g.gff_project(h, g.GFF_PREC_MIXED, mask, X32, Y32)
+        torch.cuda.synchronize()
+        assert rel_l2(Y32.cpu().numpy(), ref) <= 2e-6
+    finally:
+        g.gff_destroy(h)
+
+
+def _svk_handle(shape, ngrains, seed, kind=sp.KIND_CONTINUOUS):
+    g = gff()
+    ms = polycrystal(shape, ngrains, seed)
+    h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options(projection=kind))
+    return g, ms, h
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (6, 10, 12), (40, 8, 30)])
+@pytest.mark.parametrize("kind", [sp.KIND_CONTINUOUS, sp.KIND_DISCRETE])
+def test_apply_matches_oracle(shape, kind):
+    torch = torch_cuda()
+    g, ms, h = _svk_handle(shape, 5, 3, kind)
+    try:
+        N = ms.n_voxels
+        F = np.eye(3).reshape(3, 3, 1, 1, 1) + 0.02 * _field(11, shape)
+        g.gff_set_field(h, g.GFF_FIELD_F, F.reshape(9, N))
+        g.gff_constitutive(h, 1.0)
+        P_ref, K_ref = voxel_K_oracle(ms, F)
+        K_gpu = g.gff_get_field(h, g.GFF_FIELD_K, N).reshape(3, 3, 3, 3, *shape)
+        P_gpu = g.gff_get_field(h, g.GFF_FIELD_P, N).reshape(3, 3, *shape)
+        assert rel_l2(K_gpu, K_ref) <= 1e-14
+        assert rel_l2(P_gpu, P_ref) <= 1e-13
+        x = _field(12, shape)
+        mask = MASKS[1]
+        ref = sp.GK(K_ref, x, (1.0, 1.0, 1.0), kind, mask.astype(np.float64))
+        X = torch.from_numpy(x.reshape(9, -1).copy()).cuda()
+        Y = torch.empty_like(X)
+        g.gff_apply_operator(h, g.GFF_PREC_FP64, mask, X, Y)
+        torch.cuda.synchronize()
+        assert rel_l2(Y.cpu().numpy(), ref) <= 1e-12
+        Y32 = torch.empty_like(X.float())
+        g.gff_apply_operator(h, g.GFF_PREC_MIXED, mask, X.float(), Y32)
+        torch.cuda.synchronize()
+        assert rel_l2(Y32.cpu().numpy(), ref) <= 2e-6
+    finally:
+        g.gff_destroy(h)
+
+
+def _bench_case(n, ngrains, seed_x):
+    """Apply-benchmark inputs: K = rotated cubic C per voxel (the tangent at
+    F = I), x ~ N(0, 1) per component."""
+    ms = polycrystal(n, ngrains, 5)
+    x = standard_normal(seed_x, 9 * ms.n_voxels)
+    return ms, x
+
+
+@pytest.mark.parametrize("kind", [sp.KIND_CONTINUOUS, sp.KIND_DISCRETE])
+def test_apply_full_size_128_matches_oracle(kind):
+    """The benchmark's 128^3 case, same launch configuration, every output
+    element compared with the oracle."""
+    torch = torch_cuda()
+    g = gff()
+    ms, x = _bench_case(128, 500, 7)
+    h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options(projection=kind))
+    try:
+        g.gff_constitutive(h, 1.0)
+        X = torch.from_numpy(x.reshape(9, -1)).cuda()
+        Y = torch.empty_like(X)
+        g.gff_apply_operator(h, g.GFF_PREC_FP64, None, X, Y)
+        Y32 = torch.empty_like(X.float())
+        g.gff_apply_operator(h, g.GFF_PREC_MIXED, None, X.float(), Y32)
+        torch.cuda.synchronize()
+        F = np.broadcast_to(np.eye(3).reshape(3, 3, 1, 1, 1), (3, 3, 128, 128, 128))
+        _, K_ref = voxel_K_oracle(ms, F)
+        ref = sp.GK(K_ref, x.reshape(3, 3, 128, 128, 128), (1.0, 1.0, 1.0), kind)
+        del K_ref
+        assert rel_l2(Y.cpu().numpy(), ref) <= 1e-12
+        assert rel_l2(Y32.cpu().numpy(), ref) <= 2e-6
+    finally:
+        g.gff_destroy(h)
+
+
+def test_invalid_sizes_are_rejected():
+    torch_cuda()
+    g = gff()
+    for n in [(7, 8, 8), (8, 8, 14), (8, 8, 256), (2, 8, 8), (8, 8, 22)]:
+        with pytest.raises(g.GffError) as e:
+            g.gff_create(g.make_grid(*n))
+        assert e.value.status == g.GFF_ERR_ARG
+
+
+def test_apply_without_tangent_is_a_state_error():
+    torch = torch_cuda()
+    g = gff()
+    h = g.gff_create(g.make_grid(8, 8, 8))
+    try:
+        X = torch.zeros(9 * 512, dtype=torch.float64, device="cuda")
+        with pytest.raises(g.GffError) as e:
+            g.gff_apply_operator(h, g.GFF_PREC_FP64, None, X, torch.empty_like(X))
+        assert e.value.status == g.GFF_ERR_STATE
+    finally:
+        g.gff_destroy(h)
