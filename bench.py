@@ -43,7 +43,9 @@ def parse():
     p.add_argument("--impl", choices=["gff", "reference"], default="gff")
     p.add_argument("--increments", type=int, default=6, help="CP increments timed per precision (0: skip)")
     p.add_argument("--cpu-applies", type=int, default=3, help="oracle applies in the CPU baseline sample")
-    return p.parse_args()
+    p.add_argument("--grid", type=int, default=N_GRID, help="grid size (smaller grids only for profiling runs)")
+    a = p.parse_args()
+    return a
 
 
 # --------------------------------------------------------------------------- distributed plumbing
@@ -178,14 +180,14 @@ def hbm_peak(peaks):
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_inputs():
+def oracle_inputs(n=N_GRID):
     import numpy as np
 
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from oracle import materials as omat
     from rve_inputs import polycrystal, standard_normal
 
-    ms = polycrystal(N_GRID, N_GRAINS, SEED_MS)
+    ms = polycrystal(n, N_GRAINS, SEED_MS)
     R = omat.quat_to_rot(ms.quat)
     Cc = omat.cubic_stiffness(168.4e9, 121.4e9, 75.4e9)
     Cg = np.stack([omat.rotate4(Cc, R[g]) for g in range(ms.ngrains)])  # tangent at F = I
@@ -194,11 +196,11 @@ def oracle_inputs():
     return K, x
 
 
-def oracle_apply_rate(napplies):
-    """Oracle applies/s at 128^3 on this host (numpy FFT and einsum: 1 thread)."""
+def oracle_apply_rate(napplies, n=N_GRID):
+    """Oracle applies/s on this host (numpy FFT and einsum: 1 thread)."""
     from oracle import spectral as sp
 
-    K, x = oracle_inputs()
+    K, x = oracle_inputs(n)
     sp.GK(K, x)  # warm-up
     t0 = time.perf_counter()
     for _ in range(napplies):
@@ -212,7 +214,7 @@ def run_reference(args, world, rank):
         return
     from oracle import spectral as sp
 
-    K, x = oracle_inputs()
+    K, x = oracle_inputs(args.grid)
     for _ in range(args.warmup):
         sp.GK(K, x)
     t0 = time.perf_counter()
@@ -223,21 +225,22 @@ def run_reference(args, world, rank):
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.grid),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d oracle applies at 128^3 (numpy FP64, one thread)" % args.steps},
+                         "sample": "%d oracle applies at %d^3 (numpy FP64, one thread)" % (args.steps, args.grid)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def workload_config():
+def workload_config(n=N_GRID):
     return {
-        "workload": "Galerkin operator apply y = G(K:x) at 128^3 voxels, FP64, continuous projection; "
+        "workload": "Galerkin operator apply y = G(K:x) at %d^3 voxels, FP64, continuous projection; "
                     "K = rotated cubic C (168.4/121.4/75.4 GPa) per voxel of a 500-grain periodic Voronoi "
-                    "polycrystal (seed 5); x ~ N(0,1) (seed 7)",
-        "grid": [N_GRID] * 3, "grains": N_GRAINS, "projection": "continuous", "precision": "fp64",
-        "l2": "inputs larger than L2 (K alone is 1.36 GB)", "parallelism": "independent replicas",
+                    "polycrystal (seed 5); x ~ N(0,1) (seed 7)" % n,
+        "grid": [n] * 3, "grains": N_GRAINS, "projection": "continuous", "precision": "fp64",
+        "l2": "inputs larger than L2 (K alone is %.2f GB)" % (81 * 8 * n ** 3 / 1e9),
+        "parallelism": "independent replicas",
     }
 
 
@@ -301,7 +304,7 @@ def run_gpu(args, world, rank, local):
     from paper_1806_10599_gb300 import gff as g
     from rve_inputs import polycrystal, standard_normal
 
-    ms = polycrystal(N_GRID, N_GRAINS, SEED_MS)
+    ms = polycrystal(args.grid, N_GRAINS, SEED_MS)
     N = ms.n_voxels
     h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options())
     hd = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options(projection=g.GFF_PROJ_DISCRETE))
@@ -356,9 +359,9 @@ def run_gpu(args, world, rank, local):
     peaks, src = measured_peaks()
     peak = hbm_peak(peaks)
     nvox = N
-    b64 = kernel_bytes_per_voxel(N_GRID, 8)
-    b32 = kernel_bytes_per_voxel(N_GRID, 4)
-    fl = kernel_flops_per_voxel(N_GRID)
+    b64 = kernel_bytes_per_voxel(args.grid, 8)
+    b32 = kernel_bytes_per_voxel(args.grid, 4)
+    fl = kernel_flops_per_voxel(args.grid)
     names = ["k_plane_fwd (K:x + forward x/y transforms)", "k_zproj (z transforms + projection)",
              "k_plane_inv (inverse y/x transforms)"]
     dom = max(range(3), key=lambda i: k64[i])
@@ -384,15 +387,16 @@ def run_gpu(args, world, rank, local):
 
     cpu = None
     if world == 1 and args.cpu_applies > 0:
-        rate, secs = oracle_apply_rate(args.cpu_applies)
+        rate, secs = oracle_apply_rate(args.cpu_applies, args.grid)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d oracle applies at 128^3 (numpy FP64, one thread), %.1f s" % (args.cpu_applies, secs)}
+               "sample": "%d oracle applies at %d^3 (numpy FP64, one thread), %.1f s"
+                         % (args.cpu_applies, args.grid, secs)}
 
     value = world * args.steps / (ms64 * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.grid),
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
                 "d2h_bytes_per_step": int(x.nbytes)},

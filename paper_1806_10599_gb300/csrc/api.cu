@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -617,33 +618,43 @@ namespace {
 
 // CG on G_M(K : dF) = b from dF = 0 (Sect. 2.1).  T = double: vectors
 // d_x/d_r/d_p/d_Ap with K; T = float: the FP32 copies with K32.  Stops when
-// ||r|| <= stop or after cg_max iterations.
+// ||r|| <= stop or after cg_max iterations.  The scalars (r.r, p.Ap, alpha,
+// beta) and the stop test live on the device; the host launches iterations
+// in chunks and reads the stop flag once per chunk.  Once the flag is set,
+// every remaining kernel of the chunk returns at entry.
+constexpr int CG_CHUNK = 8;
+
 template <typename T>
 gff_status cg_solve(gff_handle* h, const ProjArgs& pa, T* x, T* r, T* p, T* Ap, const T* K, double rr0, double stop,
                     int* iters) {
     const long long n = 9 * h->N;
     const OutArgs oa = out_args(h, 1.0, nullptr);
     typename C2<T>::t* spec = reinterpret_cast<typename C2<T>::t*>(h->d_spec);
+    double* cg = h->d_scal + 32;
+    int* flag = reinterpret_cast<int*>(h->d_scal + 48);
     GFF_TRY(launch_zero<T>(x, n, h->stream));
     GFF_TRY(cudaMemcpyAsync(p, r, n * sizeof(T), cudaMemcpyDeviceToDevice, h->stream));
-    double rr = rr0;
-    int it = 0;
-    while (it < h->opt.cg_max && std::sqrt(rr) > stop) {
-        GFF_TRY(launch_galerkin<T>(h, p, K, Ap, pa, oa, spec));
-        GFF_TRY(launch_dot<T>(p, Ap, n, h->d_red, h->d_scal, h->stream));
-        double pAp;
-        gff_status st = fetch(h, h->d_scal, 1, &pAp);
-        if (st != GFF_OK) return st;
-        if (!(pAp != 0.0) || !std::isfinite(pAp)) return fail(h, GFF_ERR_NO_CONVERGENCE, "CG breakdown (p.Ap = %g)", pAp);
-        const double alpha = rr / pAp;
-        GFF_TRY(launch_cg_update<T>(x, r, p, Ap, alpha, n, h->d_red, h->d_scal, h->stream));
-        double rr_new;
-        if ((st = fetch(h, h->d_scal, 1, &rr_new)) != GFF_OK) return st;
-        GFF_TRY(launch_xpby<T>(p, r, rr_new / rr, n, h->stream));
-        rr = rr_new;
-        ++it;
+    GFF_TRY(launch_cg_init(cg, flag, rr0, stop * stop, h->stream));
+    int done = 0;
+    int hflag[2] = {0, 0};
+    while (done < h->opt.cg_max) {
+        const int k = std::min(CG_CHUNK, h->opt.cg_max - done);
+        for (int i = 0; i < k; ++i) {
+            GFF_TRY(launch_galerkin<T>(h, p, K, Ap, pa, oa, spec, nullptr, flag));
+            GFF_TRY(launch_cg_alpha<T>(p, Ap, n, h->d_red, cg, flag, h->stream));
+            GFF_TRY(launch_cg_step<T>(x, r, p, Ap, n, h->d_red, cg, flag, h->stream));
+        }
+        done += k;
+        GFF_TRY(cudaMemcpyAsync(h->h_scal, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        GFF_TRY(cudaStreamSynchronize(h->stream));
+        std::memcpy(hflag, h->h_scal, sizeof hflag);
+        if (hflag[0]) break;
     }
-    *iters = it;
+    double it_d;
+    gff_status st = fetch(h, cg + CG_ITERS, 1, &it_d);
+    if (st != GFF_OK) return st;
+    *iters = (int)it_d;
+    if (hflag[1]) return fail(h, GFF_ERR_NO_CONVERGENCE, "CG breakdown after %d iterations", *iters);
     return GFF_OK;
 }
 

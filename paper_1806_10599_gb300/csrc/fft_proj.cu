@@ -223,8 +223,10 @@ template <> __device__ __forceinline__ const float* qtp<float>(const GridDev& g,
 // ---------------------------------------------------------------- pass 1: (K:x) and the 2D forward transform
 template <typename T, bool WITH_K>
 __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, const T* __restrict__ K,
-                                                   typename C2<T>::t* __restrict__ spec, GridDev g) {
+                                                   typename C2<T>::t* __restrict__ spec, GridDev g,
+                                                   const int* __restrict__ skip) {
     using C = typename C2<T>::t;
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
     C* s = reinterpret_cast<C*>(sm_raw);
@@ -298,8 +300,10 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, cons
 
 // ---------------------------------------------------------------- pass 2: z transform + projection
 template <typename T, int W>
-__global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa) {
+__global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa,
+                                              const int* __restrict__ skip) {
     using C = typename C2<T>::t;
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
     C* s = reinterpret_cast<C*>(sm_raw);  // [9][nz][W]
@@ -377,8 +381,9 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
 // ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
 template <typename T>
 __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
-                                                   GridDev g, OutArgs oa) {
+                                                   GridDev g, OutArgs oa, const int* __restrict__ skip) {
     using C = typename C2<T>::t;
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
     C* s = reinterpret_cast<C*>(sm_raw);
@@ -461,9 +466,10 @@ size_t plane_smem_bytes(int nx, int ny, int elem) {
 }
 
 // ev (optional): four events recorded before, between and after the kernels.
+// skip (optional, device): when *skip != 0 at run time every kernel returns at once.
 template <typename T>
 cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
-                            const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev) {
+                            const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev, const int* skip) {
     using C = typename C2<T>::t;
     const GridDev& g = h->g;
     const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(C));
@@ -475,24 +481,24 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (K) {
         allow_smem(k_plane_fwd<T, true>, smA);
-        k_plane_fwd<T, true><<<gridA, 512, smA, h->stream>>>(x, K, spec, g);
+        k_plane_fwd<T, true><<<gridA, 512, smA, h->stream>>>(x, K, spec, g, skip);
     } else {
         allow_smem(k_plane_fwd<T, false>, smA);
-        k_plane_fwd<T, false><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g);
+        k_plane_fwd<T, false><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g, skip);
     }
     if (ev) cudaEventRecord(ev[1], h->stream);
     allow_smem(k_zproj<T, W>, smB);
-    k_zproj<T, W><<<blocksB, 256, smB, h->stream>>>(spec, g, pa);
+    k_zproj<T, W><<<blocksB, 256, smB, h->stream>>>(spec, g, pa, skip);
     if (ev) cudaEventRecord(ev[2], h->stream);
     allow_smem(k_plane_inv<T>, smA);
-    k_plane_inv<T><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa);
+    k_plane_inv<T><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa, skip);
     if (ev) cudaEventRecord(ev[3], h->stream);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_galerkin<double>(const gff_handle*, const double*, const double*, double*,
-                                             const ProjArgs&, const OutArgs&, double2*, cudaEvent_t*);
+                                             const ProjArgs&, const OutArgs&, double2*, cudaEvent_t*, const int*);
 template cudaError_t launch_galerkin<float>(const gff_handle*, const float*, const float*, float*, const ProjArgs&,
-                                            const OutArgs&, float2*, cudaEvent_t*);
+                                            const OutArgs&, float2*, cudaEvent_t*, const int*);
 
 }  // namespace gff

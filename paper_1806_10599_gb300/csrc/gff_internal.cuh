@@ -139,7 +139,8 @@ constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 // ---- launchers (fft_proj.cu)
 template <typename T>
 cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
-                            const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr);
+                            const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr,
+                            const int* skip = nullptr);
 size_t plane_smem_bytes(int nx, int ny, int elem);
 
 // ---- vector kernels (vec.cu)
@@ -156,6 +157,16 @@ template <typename Tin>
 cudaError_t launch_axpy_to64(double* y, const Tin* x, long long n, cudaStream_t s);
 cudaError_t launch_cast64to32(float* y, const double* x, long long n, cudaStream_t s);
 cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s);
+// Device-resident CG scalars (see vec.cu): cg[CG_RR] = r.r, cg[CG_PAP], cg[CG_ALPHA],
+// cg[CG_BETA], cg[CG_STOP2] = stop^2, cg[CG_ITERS]; flag[0] = stop, flag[1] = breakdown.
+enum { CG_RR = 0, CG_PAP = 1, CG_ALPHA = 2, CG_BETA = 3, CG_STOP2 = 4, CG_ITERS = 5 };
+cudaError_t launch_cg_init(double* cg, int* flag, double rr0, double stop2, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_alpha(const T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,
+                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_step(T* x, T* r, T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,
+                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
 

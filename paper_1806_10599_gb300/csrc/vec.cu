@@ -102,6 +102,100 @@ __global__ void __launch_bounds__(TPB) k_fill(T* __restrict__ y, T v, long long 
         y[i] = v;
 }
 
+// ---- device-resident CG iteration (no host round trip per iteration)
+__global__ void k_cg_init(double* cg, int* flag, double rr0, double stop2) {
+    cg[CG_RR] = rr0;
+    cg[CG_PAP] = 0.0;
+    cg[CG_ALPHA] = 0.0;
+    cg[CG_BETA] = 0.0;
+    cg[CG_STOP2] = stop2;
+    cg[CG_ITERS] = 0.0;
+    flag[0] = rr0 <= stop2 ? 1 : 0;
+    flag[1] = 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_dot_partial_skip(const T* __restrict__ a, const T* __restrict__ b, long long n,
+                                                          double* __restrict__ partial, const int* __restrict__ flag) {
+    if (*flag) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc = fma((double)a[i], (double)b[i], acc);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// alpha = r.r / p.Ap ; a zero or non-finite p.Ap stops the solve with the breakdown flag
+__global__ void __launch_bounds__(TPB) k_final_alpha(const double* __restrict__ partial, int nb, double* cg, int* flag) {
+    if (*flag) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        cg[CG_PAP] = acc;
+        if (acc == 0.0 || !isfinite(acc)) {
+            flag[1] = 1;
+            flag[0] = 1;
+        } else {
+            cg[CG_ALPHA] = cg[CG_RR] / acc;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_cg_update_dev(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                       const T* __restrict__ Ap, long long n, double* __restrict__ partial,
+                                                       const double* __restrict__ cg, const int* __restrict__ flag) {
+    if (*flag) return;
+    __shared__ double sh[32];
+    const T alpha = (T)cg[CG_ALPHA];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, Ap[i], r[i]);
+        r[i] = ri;
+        acc = fma((double)ri, (double)ri, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// beta = r.r(new) / r.r(old), iteration count, convergence test on r.r <= stop^2
+__global__ void __launch_bounds__(TPB) k_final_beta(const double* __restrict__ partial, int nb, double* cg, int* flag) {
+    if (*flag) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        cg[CG_BETA] = acc / cg[CG_RR];
+        cg[CG_RR] = acc;
+        cg[CG_ITERS] += 1.0;
+        if (!isfinite(acc)) {
+            flag[1] = 1;
+            flag[0] = 1;
+        } else if (acc <= cg[CG_STOP2]) {
+            flag[0] = 2;  // converged; the direction update below still runs this once
+        }
+    }
+}
+
+// p = r + beta p (skipped once the solve has stopped before this iteration)
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_xpby_dev(T* __restrict__ p, const T* __restrict__ r, long long n,
+                                                  const double* __restrict__ cg, int* __restrict__ flag) {
+    if (*flag == 1) return;
+    const T beta = (T)cg[CG_BETA];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], r[i]);
+}
+
+__global__ void k_promote_stop(int* flag) {
+    if (flag[0] == 2) flag[0] = 1;
+}
+
 inline int grid_for(long long n) {
     long long b = (n + TPB - 1) / TPB;
     return (int)(b < 152LL * 8 ? (b < 1 ? 1 : b) : 152LL * 8);
@@ -164,6 +258,39 @@ cudaError_t launch_zero(T* y, long long n, cudaStream_t s) {
     k_fill<T><<<grid_for(n), TPB, 0, s>>>(y, (T)0, n);
     return cudaGetLastError();
 }
+
+cudaError_t launch_cg_init(double* cg, int* flag, double rr0, double stop2, cudaStream_t s) {
+    k_cg_init<<<1, 1, 0, s>>>(cg, flag, rr0, stop2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_alpha(const T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,
+                            cudaStream_t s) {
+    k_dot_partial_skip<T><<<RED_BLOCKS, TPB, 0, s>>>(p, Ap, n, partial, flag);
+    k_final_alpha<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+    return cudaGetLastError();
+}
+
+// x += alpha p, r -= alpha Ap, r.r, beta, convergence test, p = r + beta p
+template <typename T>
+cudaError_t launch_cg_step(T* x, T* r, T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,
+                           cudaStream_t s) {
+    k_cg_update_dev<T><<<RED_BLOCKS, TPB, 0, s>>>(x, r, p, Ap, n, partial, cg, flag);
+    k_final_beta<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+    k_xpby_dev<T><<<grid_for(n), TPB, 0, s>>>(p, r, n, cg, flag);
+    k_promote_stop<<<1, 1, 0, s>>>(flag);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_cg_alpha<double>(const double*, const double*, long long, double*, double*, int*,
+                                             cudaStream_t);
+template cudaError_t launch_cg_alpha<float>(const float*, const float*, long long, double*, double*, int*,
+                                            cudaStream_t);
+template cudaError_t launch_cg_step<double>(double*, double*, double*, const double*, long long, double*, double*,
+                                            int*, cudaStream_t);
+template cudaError_t launch_cg_step<float>(float*, float*, float*, const float*, long long, double*, double*, int*,
+                                           cudaStream_t);
 
 template cudaError_t launch_dot<double>(const double*, const double*, long long, double*, double*, cudaStream_t);
 template cudaError_t launch_dot<float>(const float*, const float*, long long, double*, double*, cudaStream_t);

@@ -98,8 +98,9 @@ def test_crystal_plasticity_increments_fp64(kind):
     assert rel_l2(f[g.GFF_FIELD_F], o.F.reshape(9, -1)) <= 1e-8
     assert rel_l2(f[g.GFF_FIELD_P], o.P.reshape(9, -1)) <= 1e-8
     Fpi_ref = o.Fpi.transpose(1, 2, 0).reshape(9, -1)
-    assert rel_l2(f[g.GFF_FIELD_FP_INV] - np.eye(3).reshape(9, 1), Fpi_ref - np.eye(3).reshape(9, 1)) <= 1e-7
-    assert rel_l2(f[g.GFF_FIELD_CHI], o.chi.T) <= 1e-7
+    I9 = np.eye(3).reshape(9, 1)
+    assert rel_l2(f[g.GFF_FIELD_FP_INV].reshape(9, -1) - I9, Fpi_ref - I9) <= 1e-7
+    assert rel_l2(f[g.GFF_FIELD_CHI].reshape(12, -1), o.chi.T) <= 1e-7
     pc, w, fs = o.grain_fips()
     assert rel_l2(fips[0], pc) <= 1e-3
     assert rel_l2(fips[1], w) <= 1e-3
