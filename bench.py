@@ -273,6 +273,13 @@ def per_kernel_ms(g, h, prec, X, Y, reps):
 
 
 def time_increments(g, torch, nsteps, precision):
+    try:
+        return _time_increments(g, torch, nsteps, precision)
+    except Exception as e:  # report, do not lose the apply measurement
+        return {"error": str(e)}
+
+
+def _time_increments(g, torch, nsteps, precision):
     from rve_inputs import cyclic_history, polycrystal
 
     ms = polycrystal(64, 200, 2)
@@ -347,8 +354,8 @@ def run_gpu(args, world, rank, local):
 
     inc = None
     if args.increments > 0 and rank == 0:
-        inc = {"workload": "64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1% cycles, "
-                           "first %d increments (dt 0.05 s), Newton tol 1e-6" % args.increments,
+        inc = {"workload": ("64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1 pct "
+                            "strain cycles, first %d increments (dt 0.05 s), Newton tol 1e-6") % args.increments,
                "fp64": time_increments(g, torch, args.increments, 0),
                "mixed": time_increments(g, torch, args.increments, 1)}
     g.gff_destroy(h)
@@ -356,9 +363,22 @@ def run_gpu(args, world, rank, local):
 
     if rank != 0:
         return
-    peaks, src = measured_peaks()
+    cpu = None
+    if world == 1 and args.cpu_applies > 0:
+        rate, secs = oracle_apply_rate(args.cpu_applies, args.grid)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d oracle applies at %d^3 (numpy FP64, one thread), %.1f s"
+                         % (args.cpu_applies, args.grid, secs)}
+    raw = {"ms64": ms64, "ms32": ms32, "msd": msd, "k64": k64, "k32": k32, "e2e_s": e2e_s,
+           "xbytes": int(x.nbytes), "clocks": clk, "increment": inc, "cpu": cpu}
+    print(json.dumps(build_line(args, world, raw, *measured_peaks())), flush=True)
+
+
+def build_line(args, world, raw, peaks, src):
+    """The benchmark's JSON line from the measured numbers (pure function)."""
     peak = hbm_peak(peaks)
-    nvox = N
+    nvox = args.grid ** 3
+    k64, k32 = raw["k64"], raw["k32"]
     b64 = kernel_bytes_per_voxel(args.grid, 8)
     b32 = kernel_bytes_per_voxel(args.grid, 4)
     fl = kernel_flops_per_voxel(args.grid)
@@ -382,33 +402,26 @@ def run_gpu(args, world, rank, local):
     dom32 = max(range(3), key=lambda i: k32[i])
     gbs32 = [b32[i] * nvox / (k32[i] * 1e-3) / 1e9 for i in range(3)]
     roof32 = {"bound": "hbm", "kernel": names[dom32], "achieved": gbs32[dom32], "peak": peak, "unit": "GB/s",
-              "frac": gbs32[dom32] / peak, "peak_source": src, "kernel_ms": k32,
-              "all_kernels_gbs": gbs32, "apply_gbs": sum(b32) * nvox / (sum(k32) * 1e-3) / 1e9}
-
-    cpu = None
-    if world == 1 and args.cpu_applies > 0:
-        rate, secs = oracle_apply_rate(args.cpu_applies, args.grid)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d oracle applies at %d^3 (numpy FP64, one thread), %.1f s"
-                         % (args.cpu_applies, args.grid, secs)}
-
-    value = world * args.steps / (ms64 * 1e-3)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms64 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args.grid),
-        "roofline": roof, "cpu_baseline": cpu,
-        "e2e": {"value": world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
-                "d2h_bytes_per_step": int(x.nbytes)},
-        "gpu_launches": 3 * args.steps, "clocks": clk,
+              "frac": gbs32[dom32] / peak, "peak_source": src, "kernel_ms": k32, "all_kernels_gbs": gbs32,
+              "apply_gbs": sum(b32) * nvox / (sum(k32) * 1e-3) / 1e9, "traffic": None,
+              "algorithmic_bytes_per_launch": b32[dom32] * nvox}
+    steps = args.steps
+    return {
+        "metric": METRIC, "value": world * steps / (raw["ms64"] * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": raw["ms64"] / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.grid), "roofline": roof, "cpu_baseline": raw["cpu"],
+        "e2e": {"value": world * steps / raw["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": raw["xbytes"],
+                "d2h_bytes_per_step": raw["xbytes"]},
+        "gpu_launches": 3 * steps, "clocks": raw["clocks"],
         "variants": {
-            "fp32_apply": {"value": world * args.steps / (ms32 * 1e-3), "unit": UNIT, "dtype": "f32",
+            "fp32_apply": {"value": world * steps / (raw["ms32"] * 1e-3), "unit": UNIT, "dtype": "f32",
                            "roofline": roof32},
-            "discrete_projection_fp64": {"value": world * args.steps / (msd * 1e-3), "unit": UNIT, "dtype": "f64"},
+            "discrete_projection_fp64": {"value": world * steps / (raw["msd"] * 1e-3), "unit": UNIT,
+                                         "dtype": "f64"},
         },
-        "increment": inc,
+        "increment": raw["increment"],
     }
-    print(json.dumps(line), flush=True)
 
 
 def main():
