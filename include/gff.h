@@ -156,6 +156,27 @@ gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t*
 gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9,
                        const void* x_dev, void* y_dev);
 
+/* Allocation-free twin of gff_project, for callers that may not allocate
+ * device memory themselves (an application whose own allocator owns the
+ * whole device-memory budget, or a loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc/cudaFree may cause).  No handle: the grid,
+ * projection (GFF_PROJ_*) and precision (GFF_PREC_FP64: double x_dev/y_dev,
+ * GFF_PREC_MIXED: float) are passed directly; mask9 as in gff_project; the
+ * work is queued on `stream` (a cudaStream_t, NULL = legacy default stream).
+ * The paper has no counterpart.
+ * Scratch: a file-scope device array of about 3.6 MB inside libgff.so, held
+ * by every GPU that loads the library until the process exits; grids are
+ * limited to nx*ny*nz <= 32768 voxels (axes as for gff_create), larger ones
+ * return GFF_ERR_ARG.  The first call on a device looks up that array's
+ * address (make this first call before any stream capture).  No cudaMalloc,
+ * cudaFree or other allocating routine is called.  All calls share the one
+ * array per device, so calls whose device work overlaps (different streams,
+ * or host threads) race and corrupt each other's results; serialise them.
+ * Returns GFF_ERR_ARG for bad arguments, GFF_ERR_CUDA on a CUDA error (no
+ * handle, so no message). */
+gff_status gff_project_noalloc(const gff_grid* grid, int projection, int precision,
+                               const uint8_t* mask9, const void* x_dev, void* y_dev, void* stream);
+
 /* One load increment (Sect. 2.1): macroscopic Fbar[9] on components with
  * mask[c] = 0, average stress Pbar[9] on components with mask[c] = 1.
  * Newton-CG to newton_tol, then internal variables and FIP accumulators are

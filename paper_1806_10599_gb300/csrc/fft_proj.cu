@@ -19,6 +19,10 @@
 // digit-reversed out), inverse = the same stages replayed backwards with
 // conjugate twiddles (digit-reversed in, natural out), so no reordering pass
 // is needed; the projection reads the frequency of each position from a table.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
 #include "gff_internal.cuh"
 
 namespace gff {
@@ -502,3 +506,185 @@ template cudaError_t launch_galerkin<float>(const gff_handle*, const float*, con
                                             const OutArgs&, float2*, cudaEvent_t*, const int*);
 
 }  // namespace gff
+
+// =================================================================== allocation-free projection
+// gff_project_noalloc serves callers that may not allocate device memory
+// themselves: code embedded in a host application whose allocator owns the
+// whole device-memory budget, or loops that cannot afford the device-wide
+// synchronisation a cudaMalloc/cudaFree may imply.  It runs the same three
+// kernels as gff_project, but its scratch -- the half spectrum and the grid
+// tables -- is the file-scope array below, which every GPU that loads the
+// library holds until the process exits.  The paper has no counterpart.
+namespace gff {
+namespace {
+
+constexpr long long NOALLOC_MAX_VOXELS = 32768;  // e.g. 32^3, 16 x 32 x 64, ...
+// half spectrum: 9 nz ny (nx/2+1) complex values <= 9 N 3/4 for even nx >= 4
+constexpr size_t NOALLOC_SPEC_BYTES = 9ull * (NOALLOC_MAX_VOXELS / 4 * 3) * sizeof(double2);
+
+struct NoallocTables {
+    double2 tw64[3][MAXN];
+    float2 tw32[3][MAXN];
+    int posx[MAXN], fqy[MAXN], fqz[MAXN];
+    double qt64[2][3][MAXN];
+    float qt32[2][3][MAXN];
+};
+constexpr size_t NOALLOC_TABLE_OFFSET = NOALLOC_SPEC_BYTES;
+constexpr size_t NOALLOC_BYTES = NOALLOC_SPEC_BYTES + ((sizeof(NoallocTables) + 255) / 256) * 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current) by the first call made on it.  In host code the symbol
+// itself is only a host-side stand-in and must never be passed to a kernel.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+cudaError_t noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return cudaSuccess;
+}
+
+bool noalloc_plan(int n, AxisPlan& p) {
+    if (n < 4 || n > MAXN || (n & 1)) return false;
+    int m = n, a2 = 0, a3 = 0, a5 = 0;
+    while (m % 2 == 0) { m /= 2; ++a2; }
+    while (m % 3 == 0) { m /= 3; ++a3; }
+    while (m % 5 == 0) { m /= 5; ++a5; }
+    if (m != 1) return false;
+    p.n = n;
+    p.nst = 0;
+    while (a2 >= 3) { p.radix[p.nst++] = 8; a2 -= 3; }
+    if (a2 == 2) p.radix[p.nst++] = 4;
+    if (a2 == 1) p.radix[p.nst++] = 2;
+    for (int i = 0; i < a5; ++i) p.radix[p.nst++] = 5;
+    for (int i = 0; i < a3; ++i) p.radix[p.nst++] = 3;
+    return p.nst <= MAXST;
+}
+
+// frequency at position pos after the in-place forward transform of plan p
+int noalloc_freq(int pos, const AxisPlan& p) {
+    int f = 0, mult = 1, len = p.n;
+    for (int i = 0; i < p.nst; ++i) {
+        const int m = len / p.radix[i];
+        const int d = pos / m;
+        pos -= d * m;
+        f += d * mult;
+        mult *= p.radix[i];
+        len = m;
+    }
+    return f;
+}
+
+template <typename T>
+cudaError_t noalloc_launch(const GridDev& g, const T* x, T* y, const ProjArgs& pa, const OutArgs& oa,
+                           typename C2<T>::t* spec, cudaStream_t st) {
+    using C = typename C2<T>::t;
+    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(C));
+    const size_t smB = zproj_smem<T>(g);
+    constexpr int W = zproj_width<T>();
+    const dim3 gridA(9, g.nz);
+    const long long nF = (long long)g.ny * g.nxh;
+    allow_smem(k_plane_fwd<T, false>, smA);
+    k_plane_fwd<T, false><<<gridA, 512, smA, st>>>(x, nullptr, spec, g, nullptr);
+    allow_smem(k_zproj<T, W>, smB);
+    k_zproj<T, W><<<(int)((nF + W - 1) / W), 256, smB, st>>>(spec, g, pa, nullptr);
+    allow_smem(k_plane_inv<T>, smA);
+    k_plane_inv<T><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace gff
+
+// No cudaMalloc, cudaFree or other allocating call is made here; see gff.h.
+__attribute__((visibility("default"))) gff_status gff_project_noalloc(const gff_grid* grid, int projection,
+                                                                      int precision, const uint8_t* mask9,
+                                                                      const void* x_dev, void* y_dev, void* stream) {
+    using namespace gff;
+    if (!grid || !x_dev || !y_dev || x_dev == y_dev) return GFF_ERR_ARG;
+    if (projection != GFF_PROJ_CONTINUOUS && projection != GFF_PROJ_DISCRETE) return GFF_ERR_ARG;
+    if (precision != GFF_PREC_FP64 && precision != GFF_PREC_MIXED) return GFF_ERR_ARG;
+    GridDev g{};
+    const int n3[3] = {grid->nx, grid->ny, grid->nz};
+    AxisPlan* pl[3] = {&g.ax, &g.ay, &g.az};
+    for (int a = 0; a < 3; ++a) {
+        if (!noalloc_plan(n3[a], *pl[a])) return GFF_ERR_ARG;
+        if (!(grid->L[a] > 0)) return GFF_ERR_ARG;
+    }
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > NOALLOC_MAX_VOXELS) return GFF_ERR_ARG;  // larger grids need gff_create + gff_project
+    void* base = nullptr;
+    if (noalloc_scratch(&base) != cudaSuccess) return GFF_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // grid tables, built on the host stack and copied into the scratch
+    NoallocTables t;
+    std::memset(&t, 0, sizeof t);
+    const double twopi = 6.283185307179586476925286766559;
+    for (int a = 0; a < 3; ++a) {
+        const int n = n3[a];
+        for (int k = 0; k < n; ++k) {
+            const double th = twopi * k / n;
+            t.tw64[a][k] = make_double2(std::cos(th), -std::sin(th));
+            t.tw32[a][k] = make_float2((float)std::cos(th), (float)-std::sin(th));
+            const int kappa = (2 * k < n) ? k : k - n;
+            const double q = twopi * kappa / n;
+            const double qc = q * n / grid->L[a];
+            const double qd = (2 * k == n) ? 0.0 : std::tan(0.5 * q) * n / grid->L[a];
+            t.qt64[0][a][k] = qc;
+            t.qt64[1][a][k] = qd;
+            t.qt32[0][a][k] = (float)qc;
+            t.qt32[1][a][k] = (float)qd;
+        }
+    }
+    for (int p = 0; p < grid->nx; ++p) t.posx[noalloc_freq(p, g.ax)] = p;
+    for (int p = 0; p < grid->ny; ++p) t.fqy[p] = noalloc_freq(p, g.ay);
+    for (int p = 0; p < grid->nz; ++p) t.fqz[p] = noalloc_freq(p, g.az);
+    unsigned char* d = static_cast<unsigned char*>(base);
+    NoallocTables* dt = reinterpret_cast<NoallocTables*>(d + NOALLOC_TABLE_OFFSET);
+    // pageable source: the call returns once the data is staged, so the stack buffer may go
+    if (cudaMemcpyAsync(dt, &t, sizeof t, cudaMemcpyHostToDevice, st) != cudaSuccess) return GFF_ERR_CUDA;
+
+    g.nx = grid->nx;
+    g.ny = grid->ny;
+    g.nz = grid->nz;
+    g.nxh = grid->nx / 2 + 1;
+    g.N = N;
+    for (int a = 0; a < 3; ++a) {
+        g.tw64[a] = dt->tw64[a];
+        g.tw32[a] = dt->tw32[a];
+        for (int kind = 0; kind < 2; ++kind) {
+            g.qt64[kind][a] = dt->qt64[kind][a];
+            g.qt32[kind][a] = dt->qt32[kind][a];
+        }
+    }
+    g.posx = dt->posx;
+    g.fqy = dt->fqy;
+    g.fqz = dt->fqz;
+    ProjArgs pa;
+    pa.kind = projection;
+    for (int c = 0; c < 9; ++c) pa.mask[c] = (mask9 && mask9[c]) ? 1.0f : 0.0f;
+    OutArgs oa;
+    oa.scale = 1.0 / (double)N;
+    for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
+    // the spectrum is fully written by the first kernel before it is read: nothing to clear
+    cudaError_t e;
+    if (precision == GFF_PREC_FP64)
+        e = noalloc_launch<double>(g, (const double*)x_dev, (double*)y_dev, pa, oa, reinterpret_cast<double2*>(d), st);
+    else
+        e = noalloc_launch<float>(g, (const float*)x_dev, (float*)y_dev, pa, oa, reinterpret_cast<float2*>(d), st);
+    return e == cudaSuccess ? GFF_OK : GFF_ERR_CUDA;
+}

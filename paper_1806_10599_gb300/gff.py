@@ -93,6 +93,7 @@ _SIGS = {
     "gff_apply_operator": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "gff_project": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "gff_apply_operator_timed": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_project_noalloc": (c_int, [_P(gff_grid), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
     "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
@@ -219,6 +220,18 @@ def gff_apply_operator_timed(h, precision, mask9, x_dev, y_dev):
 def gff_project(h, precision, mask9, x_dev, y_dev):
     m, mp = _mask(mask9)
     return _check(h, _lib.gff_project(h, int(precision), mp, _dev(x_dev), _dev(y_dev)))
+
+
+def gff_project_noalloc(grid, projection, precision, mask9, x_dev, y_dev, stream=0):
+    """y = G_M(x) without any device allocation (scratch inside libgff.so;
+    at most 32768 voxels; overlapping calls race -- see gff.h)."""
+    m, mp = _mask(mask9)
+    s = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", 0)
+    st = _lib.gff_project_noalloc(ctypes.byref(grid), int(projection), int(precision), mp, _dev(x_dev),
+                                  _dev(y_dev), c_void_p(s))
+    if st != GFF_OK:
+        raise GffError(st, "gff_project_noalloc failed")
+    return st
 
 
 def gff_step(h, dt, Fbar, mask, Pbar):
