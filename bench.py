@@ -295,7 +295,10 @@ def _time_increments(g, torch, nsteps, precision):
     finally:
         g.gff_destroy(h)
     return {"s_per_increment": dt / nsteps, "newton": [r.newton_iters for r in reps],
-            "cg": [r.cg_iters for r in reps], "P11_MPa_last": Pm[-1][0] / 1e6}
+            "cg": [r.cg_iters for r in reps], "P11_MPa_last": Pm[-1][0] / 1e6,
+            "s_constitutive": sum(r.t_constitutive for r in reps) / nsteps,
+            "s_residual": sum(r.t_residual for r in reps) / nsteps,
+            "s_linear": sum(r.t_linear for r in reps) / nsteps}
 
 
 def run_gpu(args, world, rank, local):

@@ -98,6 +98,9 @@ typedef struct {
     double Pmacro[9];   /* volume average of P                              */
     double Fmacro[9];   /* volume average of F                              */
     double seconds;     /* wall time of the increment                       */
+    double t_constitutive; /* device time in constitutive updates, s        */
+    double t_residual;     /* device time in residual evaluations, s         */
+    double t_linear;       /* device time in the CG solves, s                */
 } gff_step_report;
 
 /* Defaults: continuous projection, FP64, newton_tol 1e-8, cg_tol 1e-8,

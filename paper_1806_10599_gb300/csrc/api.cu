@@ -225,7 +225,7 @@ namespace {
 
 gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const std::vector<int>& phase) {
     const int ng = h->ngrains;
-    std::vector<double> C(81 * (size_t)ng), S0(108 * (size_t)ng), nrmprm((36 + 5) * (size_t)ng);
+    std::vector<double> C(81 * (size_t)ng), S0(108 * (size_t)ng), nrmprm((36 + 5 + 144) * (size_t)ng);
     std::vector<int> kind(ng);
     double s[12][3], m[12][3];
     slip_systems(s, m);
@@ -250,6 +250,21 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
                 nrmprm[36 * (size_t)g + 3 * a + i] = mr[i];
             }
         }
+        // H_ab = S0_a : C : sym(S0_b), the slip interaction at small elastic strain
+        double* Hg = &nrmprm[41 * (size_t)ng + 144 * (size_t)g];
+        const double* Sg = &S0[108 * (size_t)g];
+        const double* Cg = &C[81 * (size_t)g];
+        for (int a = 0; a < 12; ++a)
+            for (int b = 0; b < 12; ++b) {
+                double v = 0.0;
+                for (int ij = 0; ij < 9; ++ij)
+                    for (int kl = 0; kl < 9; ++kl) {
+                        const int k = kl / 3, l = kl % 3;
+                        const double symb = 0.5 * (Sg[9 * b + 3 * k + l] + Sg[9 * b + 3 * l + k]);
+                        v += Sg[9 * a + ij] * Cg[9 * ij + kl] * symb;
+                    }
+                Hg[12 * a + b] = v;
+            }
         double* pr = &nrmprm[36 * (size_t)ng + 5 * (size_t)g];
         pr[0] = mt.gdot0;
         pr[1] = mt.p_exp;
@@ -446,7 +461,8 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
     gff_status st;
     if ((st = dalloc(h, (void**)&h->d_C, 81 * (size_t)ngrains * sizeof(double), "C")) != GFF_OK) return st;
     if ((st = dalloc(h, (void**)&h->d_S0, 108 * (size_t)ngrains * sizeof(double), "S0")) != GFF_OK) return st;
-    if ((st = dalloc(h, (void**)&h->d_nrm, 41 * (size_t)ngrains * sizeof(double), "normals")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_nrm, (41 + 144) * (size_t)ngrains * sizeof(double), "normals")) != GFF_OK)
+        return st;
     if ((st = dalloc(h, (void**)&h->d_gkind, (size_t)ngrains * sizeof(int), "kind")) != GFF_OK) return st;
     GFF_TRY(cudaMemcpy(h->d_gid, grain_id, h->N * sizeof(int), cudaMemcpyHostToDevice));
     gff_hostdata* hd = reinterpret_cast<gff_hostdata*>(h->hostdata);
@@ -679,16 +695,33 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     int newton = 0, cgsum = 0;
     double res = 0.0;
     bool conv = false;
+    double t_const = 0.0, t_res = 0.0, t_lin = 0.0;
+    cudaEvent_t ev[4];
+    for (int i = 0; i < 4; ++i) GFF_TRY(cudaEventCreate(&ev[i]));
+    struct EvGuard {
+        cudaEvent_t* e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
     for (int it = 0; it <= h->opt.newton_max; ++it) {
         GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
-        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed));
+        GFF_TRY(cudaEventRecord(ev[0], h->stream));
+        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed, it > 0));
+        GFF_TRY(cudaEventRecord(ev[1], h->stream));
         // b = -G_M(P) + M : Pbar
         GFF_TRY(launch_galerkin<double>(h, h->d_P, (const double*)nullptr, h->d_b, pa, ores, h->d_spec));
         GFF_TRY(launch_dot<double>(h->d_b, h->d_b, n, h->d_red, h->d_scal, h->stream));
         GFF_TRY(launch_dot<double>(h->d_P, h->d_P, n, h->d_red + RED_BLOCKS, h->d_scal + 1, h->stream));
         GFF_TRY(cudaMemcpyAsync(h->d_scal + 2, h->d_flag, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+        GFF_TRY(cudaEventRecord(ev[2], h->stream));
         double s3[3];
         if ((st = fetch(h, h->d_scal, 3, s3)) != GFF_OK) return st;
+        float ms01 = 0.f, ms12 = 0.f;
+        GFF_TRY(cudaEventElapsedTime(&ms01, ev[0], ev[1]));
+        GFF_TRY(cudaEventElapsedTime(&ms12, ev[1], ev[2]));
+        t_const += 1e-3 * ms01;
+        t_res += 1e-3 * ms12;
         int flag;
         std::memcpy(&flag, &s3[2], sizeof(int));
         if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
@@ -701,6 +734,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         if (it == h->opt.newton_max) break;
         const double stop = std::fmax(h->opt.cg_tol * nb, 0.1 * h->opt.newton_tol * nP);
         int its = 0;
+        GFF_TRY(cudaEventRecord(ev[2], h->stream));
         if (!mixed) {
             GFF_TRY(cudaMemcpyAsync(h->d_r, h->d_b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
             if ((st = cg_solve<double>(h, pa, h->d_x, h->d_r, h->d_p, h->d_Ap, h->d_K, s3[0], stop, &its)) != GFF_OK)
@@ -716,6 +750,11 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
                 return st;
             GFF_TRY(launch_axpy_to64<float>(h->d_Fk, h->d_x32, n, h->stream));
         }
+        GFF_TRY(cudaEventRecord(ev[3], h->stream));
+        GFF_TRY(cudaEventSynchronize(ev[3]));
+        float ms23 = 0.f;
+        GFF_TRY(cudaEventElapsedTime(&ms23, ev[2], ev[3]));
+        t_lin += 1e-3 * ms23;
         cgsum += its;
         ++newton;
     }
@@ -723,6 +762,9 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         rep->newton_iters = newton;
         rep->cg_iters = cgsum;
         rep->residual = res;
+        rep->t_constitutive = t_const;
+        rep->t_residual = t_res;
+        rep->t_linear = t_lin;
     }
     if (!conv) return fail(h, GFF_ERR_NO_CONVERGENCE, "Newton: residual %.3e after %d iterations", res, newton);
     return GFF_OK;

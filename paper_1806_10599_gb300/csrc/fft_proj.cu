@@ -20,6 +20,7 @@
 // conjugate twiddles (digit-reversed in, natural out), so no reordering pass
 // is needed; the projection reads the frequency of each position from a table.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -225,7 +226,22 @@ template <> __device__ __forceinline__ const float* qtp<float>(const GridDev& g,
 }
 
 // ---------------------------------------------------------------- pass 1: (K:x) and the 2D forward transform
-template <typename T, bool WITH_K>
+// 16-byte vectors of T for the streaming loads and stores
+template <typename T> struct V16;
+template <> struct V16<double> {
+    using t = double2;
+    static constexpr int n = 2;
+    static __device__ __forceinline__ double get(const double2& v, int j) { return j ? v.y : v.x; }
+};
+template <> struct V16<float> {
+    using t = float4;
+    static constexpr int n = 4;
+    static __device__ __forceinline__ float get(const float4& v, int j) {
+        return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w;
+    }
+};
+
+template <typename T, bool WITH_K, bool VEC>
 __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, const T* __restrict__ K,
                                                    typename C2<T>::t* __restrict__ spec, GridDev g,
                                                    const int* __restrict__ skip) {
@@ -248,24 +264,62 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, cons
     }
     for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
 
-    for (int e = tid; e < half * nx; e += nthr) {
-        const int r = e / nx, xi = e - r * nx;
-        const long long v0 = pl + (long long)(2 * r) * nx + xi, v1 = v0 + nx;
-        T a, b;
-        if (WITH_K) {
-            a = (T)0;
-            b = (T)0;
-            const T* Kc = K + (long long)c * 9 * N;
+    if (VEC) {
+        // 16-byte loads of VW consecutive voxels of one row; K row c is read
+        // once, the 9 components of x are shared by the 9 CTAs of this plane
+        using VT = typename V16<T>::t;
+        constexpr int VW = V16<T>::n;
+        const int nxv = nx / VW;
+        T* sf = reinterpret_cast<T*>(s);
+        for (int e = tid; e < ny * nxv; e += nthr) {
+            const int yy = e / nxv, xv = e - yy * nxv;
+            const long long v0 = pl + (long long)yy * nx + xv * VW;
+            T acc[VW];
+            if (WITH_K) {
+                const T* Kc = K + (long long)c * 9 * N;
+                VT kv[9], xq[9];
 #pragma unroll
-            for (int d = 0; d < 9; ++d) {
-                a = fma(__ldg(Kc + d * N + v0), __ldg(x + d * N + v0), a);
-                b = fma(__ldg(Kc + d * N + v1), __ldg(x + d * N + v1), b);
+                for (int d = 0; d < 9; ++d) {
+                    kv[d] = __ldg(reinterpret_cast<const VT*>(Kc + d * N + v0));
+                    xq[d] = __ldg(reinterpret_cast<const VT*>(x + d * N + v0));
+                }
+#pragma unroll
+                for (int j = 0; j < VW; ++j) {
+                    T t = (T)0;
+#pragma unroll
+                    for (int d = 0; d < 9; ++d) t = fma(V16<T>::get(kv[d], j), V16<T>::get(xq[d], j), t);
+                    acc[j] = t;
+                }
+            } else {
+                const VT xv4 = __ldg(reinterpret_cast<const VT*>(x + c * N + v0));
+#pragma unroll
+                for (int j = 0; j < VW; ++j) acc[j] = V16<T>::get(xv4, j);
             }
-        } else {
-            a = __ldg(x + c * N + v0);
-            b = __ldg(x + c * N + v1);
+            // row yy is the real (even) or imaginary (odd) part of packed row yy/2
+            T* dst = sf + 2 * ((yy >> 1) * 2 * ls + xv * VW) + (yy & 1);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) dst[2 * j] = acc[j];
         }
-        s[r * 2 * ls + xi] = mk<C>(a, b);
+    } else {
+        for (int e = tid; e < half * nx; e += nthr) {
+            const int r = e / nx, xi = e - r * nx;
+            const long long v0 = pl + (long long)(2 * r) * nx + xi, v1 = v0 + nx;
+            T a, b;
+            if (WITH_K) {
+                a = (T)0;
+                b = (T)0;
+                const T* Kc = K + (long long)c * 9 * N;
+#pragma unroll
+                for (int d = 0; d < 9; ++d) {
+                    a = fma(__ldg(Kc + d * N + v0), __ldg(x + d * N + v0), a);
+                    b = fma(__ldg(Kc + d * N + v1), __ldg(x + d * N + v1), b);
+                }
+            } else {
+                a = __ldg(x + c * N + v0);
+                b = __ldg(x + c * N + v1);
+            }
+            s[r * 2 * ls + xi] = mk<C>(a, b);
+        }
     }
     __syncthreads();
     // x transform of the ny/2 packed rows (row pair r at offset 2 r ls)
@@ -299,7 +353,11 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, cons
     // y transform of the nxh columns
     fft_lines<T, false>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
     C* out = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
-    for (int e = tid; e < ny * nxh; e += nthr) out[e] = s[e];
+    // the plane is contiguous in both places and ny * nxh * sizeof(C) is a multiple of 16
+    const int nq = ny * nxh * (int)sizeof(C) / 16;
+    const float4* src4 = reinterpret_cast<const float4*>(s);
+    float4* dst4 = reinterpret_cast<float4*>(out);
+    for (int e = tid; e < nq; e += nthr) dst4[e] = src4[e];
 }
 
 // ---------------------------------------------------------------- pass 2: z transform + projection
@@ -383,7 +441,7 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
 }
 
 // ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
-template <typename T>
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
                                                    GridDev g, OutArgs oa, const int* __restrict__ skip) {
     using C = typename C2<T>::t;
@@ -405,7 +463,12 @@ __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __re
     }
     for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
     const C* in = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
-    for (int e = tid; e < ny * nxh; e += nthr) s[e] = in[e];
+    {
+        const int nq = ny * nxh * (int)sizeof(C) / 16;
+        const float4* src4 = reinterpret_cast<const float4*>(in);
+        float4* dst4 = reinterpret_cast<float4*>(s);
+        for (int e = tid; e < nq; e += nthr) dst4[e] = __ldg(src4 + e);
+    }
     __syncthreads();
     fft_lines<T, true>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
     // merge the half spectra of rows 2r, 2r+1 into one packed complex row
@@ -441,12 +504,27 @@ __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __re
     fft_lines<T, true>(s, twx, g.ax, 1, 0, half, 2 * ls, 1, tid, nthr);
     const T sc = (T)oa.scale, ad = (T)oa.add[c];
     T* yc = y + c * N;
-    for (int e = tid; e < half * nx; e += nthr) {
-        const int r = e / nx, xi = e - r * nx;
-        const long long v0 = pl + (long long)(2 * r) * nx + xi;
-        const C zv = s[r * 2 * ls + xi];
-        yc[v0] = fma(sc, zv.x, ad);
-        yc[v0 + nx] = fma(sc, zv.y, ad);
+    if (VEC) {
+        using VT = typename V16<T>::t;
+        constexpr int VW = V16<T>::n;
+        const int nxv = nx / VW;
+        const T* sf = reinterpret_cast<const T*>(s);
+        for (int e = tid; e < ny * nxv; e += nthr) {
+            const int yy = e / nxv, xv = e - yy * nxv;
+            const T* src = sf + 2 * ((yy >> 1) * 2 * ls + xv * VW) + (yy & 1);
+            T o[VW];
+#pragma unroll
+            for (int j = 0; j < VW; ++j) o[j] = fma(sc, src[2 * j], ad);
+            *reinterpret_cast<VT*>(yc + pl + (long long)yy * nx + xv * VW) = *reinterpret_cast<const VT*>(o);
+        }
+    } else {
+        for (int e = tid; e < half * nx; e += nthr) {
+            const int r = e / nx, xi = e - r * nx;
+            const long long v0 = pl + (long long)(2 * r) * nx + xi;
+            const C zv = s[r * 2 * ls + xi];
+            yc[v0] = fma(sc, zv.x, ad);
+            yc[v0 + nx] = fma(sc, zv.y, ad);
+        }
     }
 }
 
@@ -457,6 +535,12 @@ template <typename T> size_t zproj_smem(const GridDev& g) {
     constexpr int W = zproj_width<T>();
     return (size_t)9 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
            (g.ny + g.nz) * sizeof(int) + 16;
+}
+
+// 16-byte vector access needs nx to hold whole vectors and 16-byte aligned bases
+// (N is a multiple of 4 because nx and ny are even, so component offsets keep the alignment)
+template <typename T> bool vec_ok(const GridDev& g, const void* p) {
+    return (g.nx % (16 / (int)sizeof(T))) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0;
 }
 
 template <typename K> void allow_smem(K kern, size_t bytes) {
@@ -482,20 +566,37 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     const dim3 gridA(9, g.nz);
     const long long nF = (long long)g.ny * g.nxh;
     const int blocksB = (int)((nF + W - 1) / W);
+    const bool vin = vec_ok<T>(g, x) && (!K || vec_ok<T>(g, K));
+    const bool vout = vec_ok<T>(g, y);
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (K) {
-        allow_smem(k_plane_fwd<T, true>, smA);
-        k_plane_fwd<T, true><<<gridA, 512, smA, h->stream>>>(x, K, spec, g, skip);
+        if (vin) {
+            allow_smem(k_plane_fwd<T, true, true>, smA);
+            k_plane_fwd<T, true, true><<<gridA, 512, smA, h->stream>>>(x, K, spec, g, skip);
+        } else {
+            allow_smem(k_plane_fwd<T, true, false>, smA);
+            k_plane_fwd<T, true, false><<<gridA, 512, smA, h->stream>>>(x, K, spec, g, skip);
+        }
     } else {
-        allow_smem(k_plane_fwd<T, false>, smA);
-        k_plane_fwd<T, false><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g, skip);
+        if (vin) {
+            allow_smem(k_plane_fwd<T, false, true>, smA);
+            k_plane_fwd<T, false, true><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g, skip);
+        } else {
+            allow_smem(k_plane_fwd<T, false, false>, smA);
+            k_plane_fwd<T, false, false><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g, skip);
+        }
     }
     if (ev) cudaEventRecord(ev[1], h->stream);
     allow_smem(k_zproj<T, W>, smB);
     k_zproj<T, W><<<blocksB, 256, smB, h->stream>>>(spec, g, pa, skip);
     if (ev) cudaEventRecord(ev[2], h->stream);
-    allow_smem(k_plane_inv<T>, smA);
-    k_plane_inv<T><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa, skip);
+    if (vout) {
+        allow_smem(k_plane_inv<T, true>, smA);
+        k_plane_inv<T, true><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa, skip);
+    } else {
+        allow_smem(k_plane_inv<T, false>, smA);
+        k_plane_inv<T, false><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa, skip);
+    }
     if (ev) cudaEventRecord(ev[3], h->stream);
     return cudaGetLastError();
 }
@@ -597,12 +698,12 @@ cudaError_t noalloc_launch(const GridDev& g, const T* x, T* y, const ProjArgs& p
     constexpr int W = zproj_width<T>();
     const dim3 gridA(9, g.nz);
     const long long nF = (long long)g.ny * g.nxh;
-    allow_smem(k_plane_fwd<T, false>, smA);
-    k_plane_fwd<T, false><<<gridA, 512, smA, st>>>(x, nullptr, spec, g, nullptr);
+    allow_smem(k_plane_fwd<T, false, false>, smA);
+    k_plane_fwd<T, false, false><<<gridA, 512, smA, st>>>(x, nullptr, spec, g, nullptr);
     allow_smem(k_zproj<T, W>, smB);
     k_zproj<T, W><<<(int)((nF + W - 1) / W), 256, smB, st>>>(spec, g, pa, nullptr);
-    allow_smem(k_plane_inv<T>, smA);
-    k_plane_inv<T><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr);
+    allow_smem(k_plane_inv<T, false>, smA);
+    k_plane_inv<T, false><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr);
     return cudaGetLastError();
 }
 

@@ -171,7 +171,8 @@ template <typename T>
 cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
 
 // ---- constitutive kernels (material.cu)
-cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32);
+// warm: start each voxel's local Newton from the slip increments left in d_dg by the previous call
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32, bool warm = false);
 cudaError_t launch_fip_accumulate(gff_handle* h);
 cudaError_t launch_fip_reset(gff_handle* h);
 cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs);

@@ -9,8 +9,14 @@
 //   S = C : (Ce - I)/2, tau_a = (Ce S) : S0_a,
 //   chi_a = (chi_n,a + c dg_a) / (1 + d |dg_a|),
 //   r_a = dg_a - dt gdot0 h((tau_a - chi_a)/tau0),  h(x) = |x|^p sign(x),
-// solved for dg by Newton from dg = 0 (12x12 LU with partial pivoting), then
+// solved for dg by Newton (12x12 LU with partial pivoting), then
 //   P = Fe S Fp^-T and K by implicit differentiation of r(dg, F) = 0.
+// The local Newton starts from the slip increments of the previous global
+// Newton iterate when there is one (else from 0) and takes its steps with the
+// per-grain small-strain Jacobian (see cp_jacobian_approx); the residual is
+// always exact, so it converges to the same root.  The exact Jacobian is
+// assembled once, at the root, for the tangent.  If the fast iteration fails
+// it restarts with the exact Jacobian from dg = 0.
 // Everything is FP64.  One thread per voxel.
 #include <cmath>
 
@@ -187,67 +193,108 @@ __device__ void dstate_ddg(const double* F, const double* A, const double* __res
     c_ddot(C, hE, dS);
 }
 
-__device__ void cp_update(const double* F, const double* A, const double* chin, double dt,
-                          const double* __restrict__ S0, const double* __restrict__ C, const CPParamsDev& pr,
-                          double* K /* 81 or null */, CPOut& out) {
-    const double g = pr.tau0, coef = dt * pr.gdot0;
-    const int p = (int)pr.p;
-    double dg[NSLIP];
-    for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
+// Residual r_a(dg) and the quantities the Jacobians need; returns max |r_a|.
+__device__ double cp_residual(const double* F, const double* A, const double* chin, const double* dg,
+                              const double* __restrict__ S0, const double* __restrict__ C, const CPParamsDev& pr,
+                              double coef, int p, ElState& st, double* chi, double* dh, double* r) {
+    elastic_state(F, A, dg, S0, C, st);
+    double rmax = 0.0;
+    for (int a = 0; a < NSLIP; ++a) {
+        const double den = 1.0 + pr.d * fabs(dg[a]);
+        chi[a] = (chin[a] + pr.c * dg[a]) / den;
+        const double x = (st.tau[a] - chi[a]) / pr.tau0;
+        const double ax = fabs(x);
+        const double axp1 = ipow(ax, p - 1);
+        dh[a] = p * axp1;
+        r[a] = dg[a] - coef * sgn(x) * axp1 * ax;
+        rmax = fmax(rmax, fabs(r[a]));
+    }
+    return rmax;
+}
+
+// Exact Jacobian dr_a/ddg_b at the state st.
+__device__ void cp_jacobian_exact(const double* F, const double* A, const double* dg, const double* __restrict__ S0,
+                                  const double* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& st,
+                                  const double* chi, const double* dh, double* J) {
+    const double g = pr.tau0;
+    for (int b = 0; b < NSLIP; ++b) {
+        double dFpi[9], dFe[9], dCe[9], dS[9], dM[9], t1[9];
+        dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
+        mm(dCe, st.S, dM);
+        mm(st.Ce, dS, t1);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dM[k] += t1[k];
+        for (int a = 0; a < NSLIP; ++a) {
+            double dtau = 0.0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) dtau = fma(dM[k], __ldg(S0 + 9 * a + k), dtau);
+            double v = -(coef / g) * dh[a] * dtau;
+            if (a == b) {
+                const double den = 1.0 + pr.d * fabs(dg[a]);
+                const double dchi = (pr.c - pr.d * sgn(dg[a]) * chi[a]) / den;
+                v += 1.0 + (coef / g) * dh[a] * dchi;
+            }
+            J[a * NSLIP + b] = v;
+        }
+    }
+}
+
+// Small-elastic-strain Jacobian: dtau_a/ddg_b ~ -H_ab with the per-grain
+// constant H_ab = S0_a : C : sym(S0_b) (Ce ~ I, S << C).  Used only to
+// choose Newton steps; the residual stays exact, so the root is unchanged.
+__device__ void cp_jacobian_approx(const double* __restrict__ H, const double* dg, const CPParamsDev& pr, double coef,
+                                   const double* chi, const double* dh, double* J) {
+    const double g = pr.tau0;
+    for (int a = 0; a < NSLIP; ++a) {
+        const double fa = (coef / g) * dh[a];
+        for (int b = 0; b < NSLIP; ++b) J[a * NSLIP + b] = fa * __ldg(H + a * NSLIP + b);
+        const double den = 1.0 + pr.d * fabs(dg[a]);
+        const double dchi = (pr.c - pr.d * sgn(dg[a]) * chi[a]) / den;
+        J[a * NSLIP + a] += 1.0 + fa * dchi;
+    }
+}
+
+// Local Newton on dg from the given start; approximate or exact Jacobian.
+__device__ bool cp_local_solve(const double* F, const double* A, const double* chin, const double* __restrict__ S0,
+                               const double* __restrict__ C, const double* __restrict__ H, const CPParamsDev& pr,
+                               double coef, int p, bool approx, int maxit, double* dg, ElState& st, double* chi,
+                               double* dh) {
     double J[NSLIP * NSLIP];
     int piv[NSLIP];
-    double dh[NSLIP], chi[NSLIP];
-    ElState st;
-    bool conv = false;
-    const int maxit = 100;
     for (int it = 0; it <= maxit; ++it) {
-        elastic_state(F, A, dg, S0, C, st);
-        double r[NSLIP], rmax = 0.0;
-        for (int a = 0; a < NSLIP; ++a) {
-            const double den = 1.0 + pr.d * fabs(dg[a]);
-            chi[a] = (chin[a] + pr.c * dg[a]) / den;
-            const double x = (st.tau[a] - chi[a]) / g;
-            const double ax = fabs(x);
-            const double axp1 = ipow(ax, p - 1);
-            dh[a] = p * axp1;
-            r[a] = dg[a] - coef * sgn(x) * axp1 * ax;
-            rmax = fmax(rmax, fabs(r[a]));
-        }
-        // Jacobian dr_a/ddg_b
-        for (int b = 0; b < NSLIP; ++b) {
-            double dFpi[9], dFe[9], dCe[9], dS[9], dM[9], t1[9];
-            dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
-            mm(dCe, st.S, dM);
-            mm(st.Ce, dS, t1);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) dM[k] += t1[k];
-            for (int a = 0; a < NSLIP; ++a) {
-                double dtau = 0.0;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) dtau = fma(dM[k], __ldg(S0 + 9 * a + k), dtau);
-                double v = -(coef / g) * dh[a] * dtau;
-                if (a == b) {
-                    const double den = 1.0 + pr.d * fabs(dg[a]);
-                    const double dchi = (pr.c - pr.d * sgn(dg[a]) * chi[a]) / den;
-                    v += 1.0 + (coef / g) * dh[a] * dchi;
-                }
-                J[a * NSLIP + b] = v;
-            }
-        }
-        if (rmax <= 1e-14) {
-            conv = true;
-            break;
-        }
-        if (it == maxit) break;
-        if (!lu_factor<NSLIP>(J, piv)) break;
+        double r[NSLIP];
+        const double rmax = cp_residual(F, A, chin, dg, S0, C, pr, coef, p, st, chi, dh, r);
+        if (rmax <= 1e-14) return true;
+        if (it == maxit || !(rmax < 1e300)) return false;
+        if (approx)
+            cp_jacobian_approx(H, dg, pr, coef, chi, dh, J);
+        else
+            cp_jacobian_exact(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
+        if (!lu_factor<NSLIP>(J, piv)) return false;
         lu_solve<NSLIP>(J, piv, r);
         for (int a = 0; a < NSLIP; ++a) dg[a] -= r[a];
     }
+    return false;
+}
+
+__device__ void cp_update(const double* F, const double* A, const double* chin, double dt,
+                          const double* __restrict__ S0, const double* __restrict__ C, const double* __restrict__ H,
+                          const CPParamsDev& pr, const double* dg0 /* 12 or null */, double* K /* 81 or null */,
+                          CPOut& out) {
+    const double g = pr.tau0, coef = dt * pr.gdot0;
+    const int p = (int)pr.p;
+    double dg[NSLIP], dh[NSLIP], chi[NSLIP];
+    ElState st;
+    for (int a = 0; a < NSLIP; ++a) dg[a] = dg0 ? dg0[a] : 0.0;
+    bool conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh);
+    if (!conv) {  // fall back: exact Newton from dg = 0
+        for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
+        conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, false, 100, dg, st, chi, dh);
+    }
     out.ok = conv;
-    // P = Fe S Fpi^T
     double FeS[9];
     mm(st.Fe, st.S, FeS);
-    mmt(FeS, st.Fpi, out.P);
+    mmt(FeS, st.Fpi, out.P);  // P = Fe S Fpi^T
 #pragma unroll
     for (int k = 0; k < 9; ++k) out.Fpi[k] = st.Fpi[k];
     for (int a = 0; a < NSLIP; ++a) {
@@ -256,6 +303,9 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
         out.tau[a] = st.tau[a];
     }
     if (!K || !conv) return;
+    double J[NSLIP * NSLIP];
+    int piv[NSLIP];
+    cp_jacobian_exact(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
     if (!lu_factor<NSLIP>(J, piv)) {
         out.ok = false;
         return;
@@ -357,6 +407,8 @@ struct ConstArgs {
     const int* gid;
     const double* C;
     const double* S0;
+    const double* H;  // [ngrains][144] small-strain slip-interaction matrix
+    int warm;         // 1: start the local Newton from dg (previous iterate)
     const int* gkind;
     const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
     const double* Fpi_n;
@@ -395,8 +447,11 @@ __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
         pr.tau0 = gp[2];
         pr.c = gp[3];
         pr.d = gp[4];
+        double dg0[12];
+        if (a.warm)
+            for (int s2 = 0; s2 < NSLIP; ++s2) dg0[s2] = a.dg[s2 * N + v];
         CPOut o;
-        cp_update(F, A, chin, a.dt, a.S0 + 108LL * gi, C, pr, K, o);
+        cp_update(F, A, chin, a.dt, a.S0 + 108LL * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K, o);
         if (!o.ok) atomicAdd(a.flag, 1);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -546,12 +601,14 @@ __global__ void k_grain_final(const double* sums, int ngrains, double fs_k, doub
 
 }  // namespace
 
-cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32) {
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32, bool warm) {
     ConstArgs a;
     a.F = F;
     a.gid = h->d_gid;
     a.C = h->d_C;
     a.S0 = h->d_S0;
+    a.H = h->d_nrm + 41LL * h->ngrains;
+    a.warm = warm ? 1 : 0;
     a.gkind = h->d_gkind;
     a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
     a.Fpi_n = h->d_Fpi;

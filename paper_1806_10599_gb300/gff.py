@@ -68,6 +68,9 @@ class gff_step_report(ctypes.Structure):
         ("Pmacro", c_double * 9),
         ("Fmacro", c_double * 9),
         ("seconds", c_double),
+        ("t_constitutive", c_double),
+        ("t_residual", c_double),
+        ("t_linear", c_double),
     ]
 
 
