@@ -38,7 +38,7 @@ FP64_PEAK_NOMINAL_GFLOPS = 1250.0  # GB300 FP64 (vector and tensor), nominal
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gff", "reference"], default="gff")
     p.add_argument("--increments", type=int, default=6, help="CP increments timed per precision (0: skip)")
@@ -87,7 +87,7 @@ def max_over_ranks(v, world):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -104,7 +104,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
@@ -318,6 +318,8 @@ def run_gpu(args, world, rank, local):
     N = ms.n_voxels
     h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options())
     hd = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options(projection=g.GFF_PROJ_DISCRETE))
+    tiles = g.gff_autotune(h)
+    g.gff_autotune(hd)
     g.gff_constitutive(h, 1.0)
     g.gff_constitutive(hd, 1.0)
     x = standard_normal(SEED_X, 9 * N).reshape(9, N)
@@ -373,7 +375,7 @@ def run_gpu(args, world, rank, local):
                "sample": "%d oracle applies at %d^3 (numpy FP64, one thread), %.1f s"
                          % (args.cpu_applies, args.grid, secs)}
     raw = {"ms64": ms64, "ms32": ms32, "msd": msd, "k64": k64, "k32": k32, "e2e_s": e2e_s,
-           "xbytes": int(x.nbytes), "clocks": clk, "increment": inc, "cpu": cpu}
+           "xbytes": int(x.nbytes), "clocks": clk, "increment": inc, "cpu": cpu, "tiles": tiles}
     print(json.dumps(build_line(args, world, raw, *measured_peaks())), flush=True)
 
 
@@ -424,6 +426,7 @@ def build_line(args, world, raw, peaks, src):
                                          "dtype": "f64"},
         },
         "increment": raw["increment"],
+        "autotuned_tiles": raw.get("tiles"),
     }
 
 

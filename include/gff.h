@@ -155,6 +155,15 @@ gff_status gff_apply_operator(gff_handle* h, int precision, const uint8_t* mask9
 gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t* mask9,
                                     const void* x_dev, void* y_dev, float* ms_out);
 
+/* Choose the launch shapes of the three apply kernels (threads of the plane
+ * kernels, columns per block and threads of the z kernel) by timing every
+ * candidate on this grid; results are bitwise the same for every choice.
+ * gff_step runs it once per handle if it has not been run.  Uses the handle's
+ * work buffers (call it before setting up an apply by hand, or call
+ * gff_constitutive again afterwards).  tiles_out (host, 8 ints, may be NULL):
+ * {fwd threads, z columns, z threads, inv threads} for FP64 then FP32. */
+gff_status gff_autotune(gff_handle* h, int* tiles_out);
+
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */
 gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9,
                        const void* x_dev, void* y_dev);

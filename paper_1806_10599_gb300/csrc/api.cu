@@ -613,6 +613,19 @@ GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, con
     return GFF_OK;
 }
 
+GFF_EXPORT gff_status gff_autotune(gff_handle* h, int* tiles_out) {
+    if (!h) return GFF_ERR_ARG;
+    GFF_TRY(autotune_galerkin(h));
+    if (tiles_out)
+        for (int p = 0; p < 2; ++p) {
+            tiles_out[4 * p + 0] = h->tune[p].t_fwd;
+            tiles_out[4 * p + 1] = h->tune[p].wz;
+            tiles_out[4 * p + 2] = h->tune[p].t_z;
+            tiles_out[4 * p + 3] = h->tune[p].t_inv;
+        }
+    return GFF_OK;
+}
+
 GFF_EXPORT gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9, const void* x_dev, void* y_dev) {
     if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(h, GFF_ERR_ARG, "bad project args");
     const ProjArgs pa = proj_args(h, mask9);
@@ -780,6 +793,7 @@ GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], c
     const auto t0 = std::chrono::steady_clock::now();
     gff_step_report rep;
     std::memset(&rep, 0, sizeof rep);
+    if (!h->tuned) GFF_TRY(autotune_galerkin(h));
     st = newton_increment(h, dt, Fbar, mask, Pbar, &rep);
     if (st != GFF_OK) {
         if (report) *report = rep;

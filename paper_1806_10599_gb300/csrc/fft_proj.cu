@@ -530,12 +530,13 @@ __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __re
 
 template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 4 : 8; }
 
-template <typename T> size_t zproj_smem(const GridDev& g) {
+template <typename T> size_t zproj_smem(const GridDev& g, int W = zproj_width<T>()) {
     using C = typename C2<T>::t;
-    constexpr int W = zproj_width<T>();
     return (size_t)9 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
            (g.ny + g.nz) * sizeof(int) + 16;
 }
+
+constexpr size_t SMEM_MAX = 227 * 1024;
 
 // 16-byte vector access needs nx to hold whole vectors and 16-byte aligned bases
 // (N is a multiple of 4 because nx and ny are even, so component offsets keep the alignment)
@@ -553,52 +554,175 @@ size_t plane_smem_bytes(int nx, int ny, int elem) {
     return (size_t)ny * (nx / 2 + 1) * elem + (size_t)(nx + ny) * elem + (size_t)nx * sizeof(int) + 16;
 }
 
+namespace {
+
+template <typename T>
+cudaError_t launch_fwd(const GridDev& g, int threads, const T* x, const T* K, typename C2<T>::t* spec,
+                       const int* skip, cudaStream_t st, bool vin) {
+    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
+    const dim3 gridA(9, g.nz);
+    if (K) {
+        if (vin) {
+            allow_smem(k_plane_fwd<T, true, true>, smA);
+            k_plane_fwd<T, true, true><<<gridA, threads, smA, st>>>(x, K, spec, g, skip);
+        } else {
+            allow_smem(k_plane_fwd<T, true, false>, smA);
+            k_plane_fwd<T, true, false><<<gridA, threads, smA, st>>>(x, K, spec, g, skip);
+        }
+    } else {
+        if (vin) {
+            allow_smem(k_plane_fwd<T, false, true>, smA);
+            k_plane_fwd<T, false, true><<<gridA, threads, smA, st>>>(x, nullptr, spec, g, skip);
+        } else {
+            allow_smem(k_plane_fwd<T, false, false>, smA);
+            k_plane_fwd<T, false, false><<<gridA, threads, smA, st>>>(x, nullptr, spec, g, skip);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int W>
+cudaError_t launch_z_w(const GridDev& g, int threads, typename C2<T>::t* spec, const ProjArgs& pa, const int* skip,
+                       cudaStream_t st) {
+    const size_t smB = zproj_smem<T>(g, W);
+    const long long nF = (long long)g.ny * g.nxh;
+    allow_smem(k_zproj<T, W>, smB);
+    k_zproj<T, W><<<(int)((nF + W - 1) / W), threads, smB, st>>>(spec, g, pa, skip);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_z(const GridDev& g, int W, int threads, typename C2<T>::t* spec, const ProjArgs& pa,
+                     const int* skip, cudaStream_t st) {
+    switch (W) {
+        case 2: return launch_z_w<T, 2>(g, threads, spec, pa, skip, st);
+        case 4: return launch_z_w<T, 4>(g, threads, spec, pa, skip, st);
+        case 8: return launch_z_w<T, 8>(g, threads, spec, pa, skip, st);
+        case 16: return launch_z_w<T, 16>(g, threads, spec, pa, skip, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t launch_inv(const GridDev& g, int threads, const typename C2<T>::t* spec, T* y, const OutArgs& oa,
+                       const int* skip, cudaStream_t st, bool vout) {
+    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
+    const dim3 gridA(9, g.nz);
+    if (vout) {
+        allow_smem(k_plane_inv<T, true>, smA);
+        k_plane_inv<T, true><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip);
+    } else {
+        allow_smem(k_plane_inv<T, false>, smA);
+        k_plane_inv<T, false><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T> int tune_index() { return sizeof(T) == 8 ? 0 : 1; }
+
+// fastest candidate of one kernel: run(i) launches candidate i `reps` times
+template <typename F>
+cudaError_t pick_fastest(int ncand, const bool* valid, int reps, cudaStream_t st, F run, int* best) {
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float bestms = 1e30f;
+    *best = -1;
+    for (int i = 0; i < ncand && e == cudaSuccess; ++i) {
+        if (!valid[i]) continue;
+        e = run(i);  // warm-up (also sets the shared-memory attribute)
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run(i);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < bestms) {
+            bestms = ms;
+            *best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+template <typename T>
+cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
+    using C = typename C2<T>::t;
+    const GridDev& g = h->g;
+    C* spec = reinterpret_cast<C*>(h->d_spec);
+    cudaStream_t st = h->stream;
+    const int reps = 3;
+    Tune& tn = h->tune[tune_index<T>()];
+    const bool vin = vec_ok<T>(g, x) && vec_ok<T>(g, K);
+    const int tp[2] = {256, 512};
+    const bool tv[2] = {true, true};
+    int b = -1;
+    cudaError_t e = pick_fastest(2, tv, reps, st, [&](int i) { return launch_fwd<T>(g, tp[i], x, K, spec, nullptr, st, vin); }, &b);
+    if (e != cudaSuccess) return e;
+    tn.t_fwd = tp[b];
+    const int wz[4] = {2, 4, 8, 16};
+    const int tz[2] = {128, 256};
+    bool zv[8];
+    for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i / 2]) <= SMEM_MAX;
+    ProjArgs pa;
+    pa.kind = GFF_PROJ_CONTINUOUS;
+    for (int c = 0; c < 9; ++c) pa.mask[c] = 0.f;
+    e = pick_fastest(8, zv, reps, st, [&](int i) { return launch_z<T>(g, wz[i / 2], tz[i % 2], spec, pa, nullptr, st); }, &b);
+    if (e != cudaSuccess) return e;
+    tn.wz = wz[b / 2];
+    tn.t_z = tz[b % 2];
+    OutArgs oa;
+    oa.scale = 1.0;
+    for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
+    e = pick_fastest(2, tv, reps, st, [&](int i) { return launch_inv<T>(g, tp[i], spec, y, oa, nullptr, st, vec_ok<T>(g, y)); }, &b);
+    if (e != cudaSuccess) return e;
+    tn.t_inv = tp[b];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t autotune_galerkin(gff_handle* h) {
+    // the kernels' cost does not depend on the values: the handle's vectors serve as inputs
+    cudaError_t e = cudaMemsetAsync(h->d_x, 0, 9 * h->N * sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_x32, 0, 9 * h->N * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_K32, 0, 81 * h->N * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_Ap, 0, 9 * h->N * sizeof(double), h->stream);
+    // K: the tangent buffer is only read (its contents do not matter for timing)
+    if (e == cudaSuccess) e = autotune_prec<double>(h, h->d_x, h->d_Ap, h->d_K);
+    if (e == cudaSuccess) e = autotune_prec<float>(h, h->d_x32, h->d_Ap32, h->d_K32);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) h->tuned = true;
+    h->K32_valid = false;  // the FP32 tangent buffer was used as scratch
+    return e;
+}
+
 // ev (optional): four events recorded before, between and after the kernels.
 // skip (optional, device): when *skip != 0 at run time every kernel returns at once.
 template <typename T>
 cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
                             const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev, const int* skip) {
-    using C = typename C2<T>::t;
     const GridDev& g = h->g;
-    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(C));
-    const size_t smB = zproj_smem<T>(g);
-    constexpr int W = zproj_width<T>();
-    const dim3 gridA(9, g.nz);
-    const long long nF = (long long)g.ny * g.nxh;
-    const int blocksB = (int)((nF + W - 1) / W);
+    const Tune& tn = h->tune[tune_index<T>()];
     const bool vin = vec_ok<T>(g, x) && (!K || vec_ok<T>(g, K));
     const bool vout = vec_ok<T>(g, y);
     if (ev) cudaEventRecord(ev[0], h->stream);
-    if (K) {
-        if (vin) {
-            allow_smem(k_plane_fwd<T, true, true>, smA);
-            k_plane_fwd<T, true, true><<<gridA, 512, smA, h->stream>>>(x, K, spec, g, skip);
-        } else {
-            allow_smem(k_plane_fwd<T, true, false>, smA);
-            k_plane_fwd<T, true, false><<<gridA, 512, smA, h->stream>>>(x, K, spec, g, skip);
-        }
-    } else {
-        if (vin) {
-            allow_smem(k_plane_fwd<T, false, true>, smA);
-            k_plane_fwd<T, false, true><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g, skip);
-        } else {
-            allow_smem(k_plane_fwd<T, false, false>, smA);
-            k_plane_fwd<T, false, false><<<gridA, 512, smA, h->stream>>>(x, nullptr, spec, g, skip);
-        }
-    }
+    cudaError_t e = launch_fwd<T>(g, tn.t_fwd, x, K, spec, skip, h->stream, vin);
+    if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], h->stream);
-    allow_smem(k_zproj<T, W>, smB);
-    k_zproj<T, W><<<blocksB, 256, smB, h->stream>>>(spec, g, pa, skip);
+    e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, skip, h->stream);
+    if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], h->stream);
-    if (vout) {
-        allow_smem(k_plane_inv<T, true>, smA);
-        k_plane_inv<T, true><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa, skip);
-    } else {
-        allow_smem(k_plane_inv<T, false>, smA);
-        k_plane_inv<T, false><<<gridA, 512, smA, h->stream>>>(spec, y, g, oa, skip);
-    }
+    e = launch_inv<T>(g, tn.t_inv, spec, y, oa, skip, h->stream, vout);
     if (ev) cudaEventRecord(ev[3], h->stream);
-    return cudaGetLastError();
+    return e;
 }
 
 template cudaError_t launch_galerkin<double>(const gff_handle*, const double*, const double*, double*,

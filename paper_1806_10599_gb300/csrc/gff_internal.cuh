@@ -63,6 +63,14 @@ struct GrainDev {
     const int* phase;       // [ngrains]
 };
 
+// Launch shapes of the three apply kernels (chosen by the autotuner).
+struct Tune {
+    int t_fwd;  // threads of k_plane_fwd
+    int wz;     // (ky, kx) columns per k_zproj block
+    int t_z;    // threads of k_zproj
+    int t_inv;  // threads of k_plane_inv
+};
+
 struct CPParamsDev {
     double gdot0, p, tau0, c, d;
 };
@@ -128,6 +136,8 @@ struct gff_handle {
     bool K32_valid = false;
     bool grains_ready = false;
     void* hostdata = nullptr;  // host copies of the orientations and phases
+    gff::Tune tune[2] = {{512, 4, 256, 512}, {512, 8, 256, 512}};  // [0] FP64, [1] FP32
+    bool tuned = false;
     std::string err;
 };
 
@@ -142,6 +152,9 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
                             const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr,
                             const int* skip = nullptr);
 size_t plane_smem_bytes(int nx, int ny, int elem);
+// Times every candidate launch shape of the three kernels on the handle's own
+// buffers and stores the fastest in h->tune (results do not depend on it).
+cudaError_t autotune_galerkin(gff_handle* h);
 
 // ---- vector kernels (vec.cu)
 template <typename T>

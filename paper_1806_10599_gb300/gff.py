@@ -96,6 +96,7 @@ _SIGS = {
     "gff_apply_operator": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "gff_project": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "gff_apply_operator_timed": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_autotune": (c_int, [c_void_p, c_void_p]),
     "gff_project_noalloc": (c_int, [_P(gff_grid), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
     "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -218,6 +219,13 @@ def gff_apply_operator_timed(h, precision, mask9, x_dev, y_dev):
     _check(h, _lib.gff_apply_operator_timed(h, int(precision), mp, _dev(x_dev), _dev(y_dev),
                                             ctypes.cast(ms, c_void_p)))
     return [ms[0], ms[1], ms[2]]
+
+
+def gff_autotune(h):
+    """Returns {fwd threads, z columns, z threads, inv threads} for FP64 and FP32."""
+    t = (ctypes.c_int * 8)()
+    _check(h, _lib.gff_autotune(h, ctypes.cast(t, c_void_p)))
+    return {"fp64": list(t[0:4]), "fp32": list(t[4:8])}
 
 
 def gff_project(h, precision, mask9, x_dev, y_dev):
