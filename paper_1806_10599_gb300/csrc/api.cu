@@ -555,7 +555,7 @@ GFF_EXPORT gff_status gff_constitutive(gff_handle* h, double dt) {
     gff_status st = ensure_grains(h);
     if (st != GFF_OK) return st;
     GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
-    GFF_TRY(launch_constitutive(h, h->d_Fk, dt, true));
+    GFF_TRY(launch_constitutive(h, h->d_Fk, dt, TANGENT_F64_AND_F32));
     int flag = 0;
     GFF_TRY(cudaMemcpyAsync(&flag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     GFF_TRY(cudaStreamSynchronize(h->stream));
@@ -564,9 +564,14 @@ GFF_EXPORT gff_status gff_constitutive(gff_handle* h, double dt) {
     return GFF_OK;
 }
 
+// FP64 applies need the FP64 tangent; FP32 applies take K32 or round the FP64 one.
+static bool tangent_ready(const gff_handle* h, int precision) {
+    return precision == GFF_PREC_FP64 ? h->K_valid : (h->K32_valid || h->K_valid);
+}
+
 GFF_EXPORT gff_status gff_apply_operator(gff_handle* h, int precision, const uint8_t* mask9, const void* x_dev, void* y_dev) {
     if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(h, GFF_ERR_ARG, "bad apply args");
-    if (!h->K_valid) return fail(h, GFF_ERR_STATE, "no tangent: call gff_constitutive first");
+    if (!tangent_ready(h, precision)) return fail(h, GFF_ERR_STATE, "no tangent for this precision: call gff_constitutive");
     const ProjArgs pa = proj_args(h, mask9);
     const OutArgs oa = out_args(h, 1.0, nullptr);
     if (precision == GFF_PREC_FP64) {
@@ -587,7 +592,7 @@ GFF_EXPORT gff_status gff_apply_operator(gff_handle* h, int precision, const uin
 GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t* mask9,
                                                const void* x_dev, void* y_dev, float* ms_out) {
     if (!h || !x_dev || !y_dev || x_dev == y_dev || !ms_out) return fail(h, GFF_ERR_ARG, "bad apply args");
-    if (!h->K_valid) return fail(h, GFF_ERR_STATE, "no tangent: call gff_constitutive first");
+    if (!tangent_ready(h, precision)) return fail(h, GFF_ERR_STATE, "no tangent for this precision: call gff_constitutive");
     if (precision != GFF_PREC_FP64 && precision != GFF_PREC_MIXED) return fail(h, GFF_ERR_ARG, "precision %d", precision);
     const ProjArgs pa = proj_args(h, mask9);
     const OutArgs oa = out_args(h, 1.0, nullptr);
@@ -720,7 +725,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     for (int it = 0; it <= h->opt.newton_max; ++it) {
         GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
         GFF_TRY(cudaEventRecord(ev[0], h->stream));
-        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed, it > 0));
+        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, it > 0));
         GFF_TRY(cudaEventRecord(ev[1], h->stream));
         // b = -G_M(P) + M : Pbar
         GFF_TRY(launch_galerkin<double>(h, h->d_P, (const double*)nullptr, h->d_b, pa, ores, h->d_spec));
@@ -807,7 +812,8 @@ GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], c
         GFF_TRY(cudaMemcpyAsync(h->d_chi, h->d_chi_t, 12 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         GFF_TRY(launch_fip_accumulate(h));
     }
-    h->K_valid = true;
+    // mixed precision leaves only the FP32 tangent of the last Newton iterate
+    h->K_valid = h->opt.precision != GFF_PREC_MIXED;
     h->K32_valid = h->opt.precision == GFF_PREC_MIXED;
     double s[18];
     GFF_TRY(launch_sum9(h->d_P, N, h->d_red, h->d_scal, h->stream));

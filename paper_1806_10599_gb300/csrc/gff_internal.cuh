@@ -184,8 +184,11 @@ template <typename T>
 cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
 
 // ---- constitutive kernels (material.cu)
-// warm: start each voxel's local Newton from the slip increments left in d_dg by the previous call
-cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32, bool warm = false);
+// tangent: TANGENT_F64 writes the FP64 K; TANGENT_F64_AND_F32 also rounds it into K32;
+// TANGENT_F32 computes the crystal-plasticity tangent in FP32 and writes only K32.
+// warm: start each voxel's local Newton from the slip increments left in d_dg by the previous call.
+enum { TANGENT_F64 = 0, TANGENT_F64_AND_F32 = 1, TANGENT_F32 = 2 };
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm = false);
 cudaError_t launch_fip_accumulate(gff_handle* h);
 cudaError_t launch_fip_reset(gff_handle* h);
 cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs);

@@ -27,23 +27,25 @@ namespace {
 
 constexpr int TPB = 128;
 
-__device__ __forceinline__ void mm(const double* a, const double* b, double* c) {  // c = a b
+// ---------------------------------------------------------------- small dense helpers (row-major 3x3)
+template <typename T> __device__ __forceinline__ void mm(const T* a, const T* b, T* c) {  // c = a b
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[j] + a[3 * i + 1] * b[3 + j] + a[3 * i + 2] * b[6 + j];
 }
-__device__ __forceinline__ void mtm(const double* a, const double* b, double* c) {  // c = a^T b
+template <typename T> __device__ __forceinline__ void mtm(const T* a, const T* b, T* c) {  // c = a^T b
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) c[3 * i + j] = a[i] * b[j] + a[3 + i] * b[3 + j] + a[6 + i] * b[6 + j];
 }
-__device__ __forceinline__ void mmt(const double* a, const double* b, double* c) {  // c = a b^T
+template <typename T> __device__ __forceinline__ void mmt(const T* a, const T* b, T* c) {  // c = a b^T
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) c[3 * i + j] = a[3 * i] * b[3 * j] + a[3 * i + 1] * b[3 * j + 1] + a[3 * i + 2] * b[3 * j + 2];
+        for (int j = 0; j < 3; ++j)
+            c[3 * i + j] = a[3 * i] * b[3 * j] + a[3 * i + 1] * b[3 * j + 1] + a[3 * i + 2] * b[3 * j + 2];
 }
 __device__ __forceinline__ double ddot9(const double* a, const double* b) {
     double s = 0.0;
@@ -51,14 +53,14 @@ __device__ __forceinline__ double ddot9(const double* a, const double* b) {
     for (int k = 0; k < 9; ++k) s = fma(a[k], b[k], s);
     return s;
 }
-// S = C : E for a symmetric E (C has minor symmetries)
-__device__ __forceinline__ void c_ddot(const double* __restrict__ C, const double* E, double* S) {
+// S = C : E (C has minor symmetries; stored in FP64, used in T)
+template <typename T> __device__ __forceinline__ void c_ddot(const double* __restrict__ C, const T* E, T* S) {
 #pragma unroll
     for (int ij = 0; ij < 9; ++ij) {
         const double* Cr = C + 9 * ij;
-        double s = 0.0;
+        T s = (T)0;
 #pragma unroll
-        for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(Cr + kl), E[kl], s);
+        for (int kl = 0; kl < 9; ++kl) s = fma((T)__ldg(Cr + kl), E[kl], s);
         S[ij] = s;
     }
 }
@@ -73,7 +75,7 @@ __device__ __forceinline__ double ipow(double a, int p) {  // a >= 0, p >= 0
     return r;
 }
 
-__device__ __forceinline__ double sgn(double v) { return (v > 0.0) - (v < 0.0); }
+template <typename T> __device__ __forceinline__ T sgn(T v) { return (T)((v > (T)0) - (v < (T)0)); }
 
 struct CPOut {
     double P[9];
@@ -84,62 +86,63 @@ struct CPOut {
     bool ok;
 };
 
-// LU with partial pivoting of an n x n row-major matrix, in place.
-template <int NN>
-__device__ bool lu_factor(double* a, int* piv) {
+// LU with partial pivoting of an NN x NN row-major matrix, in place.
+template <int NN, typename T>
+__device__ bool lu_factor(T* a, int* piv) {
     for (int k = 0; k < NN; ++k) {
         int p = k;
-        double m = fabs(a[k * NN + k]);
+        T m = fabs(a[k * NN + k]);
         for (int i = k + 1; i < NN; ++i) {
-            const double v = fabs(a[i * NN + k]);
+            const T v = fabs(a[i * NN + k]);
             if (v > m) {
                 m = v;
                 p = i;
             }
         }
         piv[k] = p;
-        if (m == 0.0) return false;
+        if (m == (T)0) return false;
         if (p != k)
             for (int j = 0; j < NN; ++j) {
-                const double t = a[k * NN + j];
+                const T t = a[k * NN + j];
                 a[k * NN + j] = a[p * NN + j];
                 a[p * NN + j] = t;
             }
-        const double inv = 1.0 / a[k * NN + k];
+        const T inv = (T)1 / a[k * NN + k];
         for (int i = k + 1; i < NN; ++i) {
-            const double l = a[i * NN + k] * inv;
+            const T l = a[i * NN + k] * inv;
             a[i * NN + k] = l;
             for (int j = k + 1; j < NN; ++j) a[i * NN + j] = fma(-l, a[k * NN + j], a[i * NN + j]);
         }
     }
     return true;
 }
-template <int NN>
-__device__ void lu_solve(const double* a, const int* piv, double* b) {
+template <int NN, typename T>
+__device__ void lu_solve(const T* a, const int* piv, T* b) {
     for (int k = 0; k < NN; ++k) {
         const int p = piv[k];
         if (p != k) {
-            const double t = b[k];
+            const T t = b[k];
             b[k] = b[p];
             b[p] = t;
         }
     }
     for (int i = 1; i < NN; ++i) {
-        double s = b[i];
+        T s = b[i];
         for (int j = 0; j < i; ++j) s = fma(-a[i * NN + j], b[j], s);
         b[i] = s;
     }
     for (int i = NN - 1; i >= 0; --i) {
-        double s = b[i];
+        T s = b[i];
         for (int j = i + 1; j < NN; ++j) s = fma(-a[i * NN + j], b[j], s);
         b[i] = s / a[i * NN + i];
     }
 }
 
 // Elastic state for slip increments dg: Fpi, Fe, Ce, S, M = Ce S, tau.
-struct ElState {
-    double Fpi[9], Fe[9], Ce[9], S[9], M[9], tau[12];
+template <typename T> struct ElStateT {
+    T Fpi[9], Fe[9], Ce[9], S[9], M[9], tau[12];
 };
+using ElState = ElStateT<double>;
 
 __device__ void elastic_state(const double* F, const double* A, const double* dg, const double* __restrict__ S0,
                               const double* __restrict__ C, ElState& st) {
@@ -171,25 +174,26 @@ __device__ void elastic_state(const double* F, const double* A, const double* dg
 // Derivatives with respect to dg_b at fixed F:
 //   dFpi_b = -A S0_b, dFe_b = F dFpi_b, dCe_b = dFe_b^T Fe + Fe^T dFe_b,
 //   dS_b = C : dCe_b / 2.
-__device__ void dstate_ddg(const double* F, const double* A, const double* __restrict__ S0_b,
-                           const double* __restrict__ C, const ElState& st, double* dFpi, double* dFe, double* dCe,
-                           double* dS) {
-    double Sb[9];
+template <typename T>
+__device__ void dstate_ddg(const T* F, const T* A, const double* __restrict__ S0_b, const double* __restrict__ C,
+                           const ElStateT<T>& st, T* dFpi, T* dFe, T* dCe, T* dS) {
+    T Sb[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Sb[k] = __ldg(S0_b + k);
+    for (int k = 0; k < 9; ++k) Sb[k] = (T)__ldg(S0_b + k);
     mm(A, Sb, dFpi);
 #pragma unroll
     for (int k = 0; k < 9; ++k) dFpi[k] = -dFpi[k];
     mm(F, dFpi, dFe);
-    double t1[9], t2[9];
+    T t1[9];
     mtm(dFe, st.Fe, t1);
-    mtm(st.Fe, dFe, t2);
-    double hE[9];
+    T hE[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        dCe[k] = t1[k] + t2[k];
-        hE[k] = 0.5 * dCe[k];
-    }
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            dCe[3 * i + j] = t1[3 * i + j] + t1[3 * j + i];  // Fe^T dFe = (dFe^T Fe)^T
+            hE[3 * i + j] = (T)0.5 * dCe[3 * i + j];
+        }
     c_ddot(C, hE, dS);
 }
 
@@ -212,27 +216,28 @@ __device__ double cp_residual(const double* F, const double* A, const double* ch
     return rmax;
 }
 
-// Exact Jacobian dr_a/ddg_b at the state st.
-__device__ void cp_jacobian_exact(const double* F, const double* A, const double* dg, const double* __restrict__ S0,
-                                  const double* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& st,
-                                  const double* chi, const double* dh, double* J) {
-    const double g = pr.tau0;
+// Exact Jacobian dr_a/ddg_b at the state st, in precision T.
+template <typename T>
+__device__ void cp_jacobian_exact(const T* F, const T* A, const T* dg, const double* __restrict__ S0,
+                                  const double* __restrict__ C, const CPParamsDev& pr, double coef,
+                                  const ElStateT<T>& st, const T* chi, const T* dh, T* J) {
+    const T cg = (T)(coef / pr.tau0), c = (T)pr.c, d = (T)pr.d;
     for (int b = 0; b < NSLIP; ++b) {
-        double dFpi[9], dFe[9], dCe[9], dS[9], dM[9], t1[9];
+        T dFpi[9], dFe[9], dCe[9], dS[9], dM[9], t1[9];
         dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
         mm(dCe, st.S, dM);
         mm(st.Ce, dS, t1);
 #pragma unroll
         for (int k = 0; k < 9; ++k) dM[k] += t1[k];
         for (int a = 0; a < NSLIP; ++a) {
-            double dtau = 0.0;
+            T dtau = (T)0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) dtau = fma(dM[k], __ldg(S0 + 9 * a + k), dtau);
-            double v = -(coef / g) * dh[a] * dtau;
+            for (int k = 0; k < 9; ++k) dtau = fma(dM[k], (T)__ldg(S0 + 9 * a + k), dtau);
+            T v = -cg * dh[a] * dtau;
             if (a == b) {
-                const double den = 1.0 + pr.d * fabs(dg[a]);
-                const double dchi = (pr.c - pr.d * sgn(dg[a]) * chi[a]) / den;
-                v += 1.0 + (coef / g) * dh[a] * dchi;
+                const T den = (T)1 + d * fabs(dg[a]);
+                const T dchi = (c - d * sgn(dg[a]) * chi[a]) / den;
+                v += (T)1 + cg * dh[a] * dchi;
             }
             J[a * NSLIP + b] = v;
         }
@@ -254,7 +259,7 @@ __device__ void cp_jacobian_approx(const double* __restrict__ H, const double* d
     }
 }
 
-// Local Newton on dg from the given start; approximate or exact Jacobian.
+// Local Newton on dg from the given start; approximate or exact Jacobian (FP64).
 __device__ bool cp_local_solve(const double* F, const double* A, const double* chin, const double* __restrict__ S0,
                                const double* __restrict__ C, const double* __restrict__ H, const CPParamsDev& pr,
                                double coef, int p, bool approx, int maxit, double* dg, ElState& st, double* chi,
@@ -269,7 +274,7 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
         if (approx)
             cp_jacobian_approx(H, dg, pr, coef, chi, dh, J);
         else
-            cp_jacobian_exact(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
+            cp_jacobian_exact<double>(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
         if (!lu_factor<NSLIP>(J, piv)) return false;
         lu_solve<NSLIP>(J, piv, r);
         for (int a = 0; a < NSLIP; ++a) dg[a] -= r[a];
@@ -277,11 +282,108 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
     return false;
 }
 
+// Consistent tangent K = dP/dF at the converged return map, in precision T:
+//   K = dP/dF|_dg + (dP/ddg) (ddg/dF),  J ddg/dF = (coef/g) h' dtau/dF|_dg.
+template <typename T>
+__device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd, const double* __restrict__ S0,
+                           const double* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& sd,
+                           const double* chid, const double* dhd, T* K) {
+    T F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
+    ElStateT<T> st;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        F[k] = (T)Fd[k];
+        A[k] = (T)Ad[k];
+        st.Fpi[k] = (T)sd.Fpi[k];
+        st.Fe[k] = (T)sd.Fe[k];
+        st.Ce[k] = (T)sd.Ce[k];
+        st.S[k] = (T)sd.S[k];
+        st.M[k] = (T)sd.M[k];
+    }
+    for (int a = 0; a < NSLIP; ++a) {
+        dg[a] = (T)dgd[a];
+        chi[a] = (T)chid[a];
+        dh[a] = (T)dhd[a];
+        st.tau[a] = (T)sd.tau[a];
+    }
+    T J[NSLIP * NSLIP];
+    int piv[NSLIP];
+    cp_jacobian_exact<T>(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
+    if (!lu_factor<NSLIP>(J, piv)) return false;
+    const T cg = (T)(coef / pr.tau0);
+    T FeS[9];
+    mm(st.Fe, st.S, FeS);
+    // dP/ddg_b  (12 x 9)
+    T dPb[NSLIP * 9];
+    for (int b = 0; b < NSLIP; ++b) {
+        T dFpi[9], dFe[9], dCe[9], dS[9], t1[9], t2[9], t3[9], t4[9];
+        dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
+        mm(dFe, st.S, t1);
+        mmt(t1, st.Fpi, t2);  // dFe S Fpi^T
+        mm(st.Fe, dS, t1);
+        mmt(t1, st.Fpi, t3);  // Fe dS Fpi^T
+        mmt(FeS, dFpi, t4);   // Fe S dFpi^T
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dPb[9 * b + k] = t2[k] + t3[k] + t4[k];
+    }
+    T SFt[9];
+    mmt(st.S, st.Fpi, SFt);  // S Fpi^T
+    for (int kl = 0; kl < 9; ++kl) {
+        const int k = kl / 3, l = kl % 3;
+        // dFe = E_kl Fpi: row k equals row l of Fpi
+        T dFe[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dFe[q] = (T)0;
+        dFe[3 * k] = st.Fpi[3 * l];
+        dFe[3 * k + 1] = st.Fpi[3 * l + 1];
+        dFe[3 * k + 2] = st.Fpi[3 * l + 2];
+        T t1[9], t2[9], dCe[9], hE[9], dS[9];
+        mtm(dFe, st.Fe, t1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                dCe[3 * i + j] = t1[3 * i + j] + t1[3 * j + i];
+                hE[3 * i + j] = (T)0.5 * dCe[3 * i + j];
+            }
+        c_ddot(C, hE, dS);
+        // dP at fixed dg = dFe S Fpi^T + Fe dS Fpi^T
+        T dP[9], t3[9];
+        mm(dFe, SFt, dP);
+        mm(st.Fe, dS, t3);
+        mmt(t3, st.Fpi, t1);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dP[q] += t1[q];
+        // dtau_a = (dCe S + Ce dS) : S0_a ; J ddg = (coef/g) h'_a dtau_a
+        T dM[9];
+        mm(dCe, st.S, dM);
+        mm(st.Ce, dS, t2);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dM[q] += t2[q];
+        T rhs[NSLIP];
+        for (int a = 0; a < NSLIP; ++a) {
+            T dtau = (T)0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dtau = fma(dM[q], (T)__ldg(S0 + 9 * a + q), dtau);
+            rhs[a] = cg * dh[a] * dtau;
+        }
+        lu_solve<NSLIP>(J, piv, rhs);
+        for (int b = 0; b < NSLIP; ++b)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dP[q] = fma(dPb[9 * b + q], rhs[b], dP[q]);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) K[9 * q + kl] = dP[q];
+    }
+    return true;
+}
+
+// Return map (FP64) and, when K is not null, the tangent in precision T.
+template <typename T>
 __device__ void cp_update(const double* F, const double* A, const double* chin, double dt,
                           const double* __restrict__ S0, const double* __restrict__ C, const double* __restrict__ H,
-                          const CPParamsDev& pr, const double* dg0 /* 12 or null */, double* K /* 81 or null */,
+                          const CPParamsDev& pr, const double* dg0 /* 12 or null */, T* K /* 81 or null */,
                           CPOut& out) {
-    const double g = pr.tau0, coef = dt * pr.gdot0;
+    const double coef = dt * pr.gdot0;
     const int p = (int)pr.p;
     double dg[NSLIP], dh[NSLIP], chi[NSLIP];
     ElState st;
@@ -302,74 +404,7 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
         out.dg[a] = dg[a];
         out.tau[a] = st.tau[a];
     }
-    if (!K || !conv) return;
-    double J[NSLIP * NSLIP];
-    int piv[NSLIP];
-    cp_jacobian_exact(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
-    if (!lu_factor<NSLIP>(J, piv)) {
-        out.ok = false;
-        return;
-    }
-    // dP/ddg_b  (12 x 9)
-    double dPb[NSLIP * 9];
-    for (int b = 0; b < NSLIP; ++b) {
-        double dFpi[9], dFe[9], dCe[9], dS[9], t1[9], t2[9], t3[9], t4[9];
-        dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
-        mm(dFe, st.S, t1);
-        mmt(t1, st.Fpi, t2);  // dFe S Fpi^T
-        mm(st.Fe, dS, t1);
-        mmt(t1, st.Fpi, t3);  // Fe dS Fpi^T
-        mmt(FeS, dFpi, t4);   // Fe S dFpi^T
-#pragma unroll
-        for (int k = 0; k < 9; ++k) dPb[9 * b + k] = t2[k] + t3[k] + t4[k];
-    }
-    double SFt[9];
-    mmt(st.S, st.Fpi, SFt);  // S Fpi^T
-    for (int kl = 0; kl < 9; ++kl) {
-        const int k = kl / 3, l = kl % 3;
-        // dFe = E_kl Fpi: row k equals row l of Fpi
-        double dFe[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) dFe[q] = 0.0;
-        dFe[3 * k] = st.Fpi[3 * l];
-        dFe[3 * k + 1] = st.Fpi[3 * l + 1];
-        dFe[3 * k + 2] = st.Fpi[3 * l + 2];
-        double t1[9], t2[9], dCe[9], hE[9], dS[9];
-        mtm(dFe, st.Fe, t1);
-        mtm(st.Fe, dFe, t2);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            dCe[q] = t1[q] + t2[q];
-            hE[q] = 0.5 * dCe[q];
-        }
-        c_ddot(C, hE, dS);
-        // dP at fixed dg = dFe S Fpi^T + Fe dS Fpi^T
-        double dP[9], t3[9];
-        mm(dFe, SFt, dP);
-        mm(st.Fe, dS, t3);
-        mmt(t3, st.Fpi, t1);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) dP[q] += t1[q];
-        // dtau_a = (dCe S + Ce dS) : S0_a ; dr_a = -(coef/g) h'_a dtau_a ; ddg = -J^-1 dr
-        double dM[9];
-        mm(dCe, st.S, dM);
-        mm(st.Ce, dS, t2);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) dM[q] += t2[q];
-        double rhs[NSLIP];
-        for (int a = 0; a < NSLIP; ++a) {
-            double dtau = 0.0;
-#pragma unroll
-            for (int q = 0; q < 9; ++q) dtau = fma(dM[q], __ldg(S0 + 9 * a + q), dtau);
-            rhs[a] = (coef / g) * dh[a] * dtau;  // = -dr_a, so J ddg = rhs
-        }
-        lu_solve<NSLIP>(J, piv, rhs);
-        for (int b = 0; b < NSLIP; ++b)
-#pragma unroll
-            for (int q = 0; q < 9; ++q) dP[q] = fma(dPb[9 * b + q], rhs[b], dP[q]);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) K[9 * q + kl] = dP[q];
-    }
+    if (K && conv) out.ok = cp_tangent<T>(F, A, dg, S0, C, pr, coef, st, chi, dh, K);
 }
 
 __device__ void svk_update(const double* F, const double* __restrict__ C, double* P, double* K) {
@@ -415,8 +450,8 @@ struct ConstArgs {
     const double* chi_n;
     double dt;
     double* P;
-    double* K;
-    float* K32;
+    double* K;    // FP64 tangent (null: not written)
+    float* K32;   // FP32 tangent (null: not written)
     double* Fpi_t;
     double* chi_t;
     double* dg;
@@ -425,6 +460,10 @@ struct ConstArgs {
     long long N;
 };
 
+// F32T: the crystal-plasticity tangent is computed in FP32 and only K32 is
+// written (mixed precision); otherwise the tangent is FP64, written to K and,
+// when K32 is set, also rounded into K32.
+template <bool F32T>
 __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.N) return;
@@ -432,7 +471,7 @@ __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
     const int gi = a.gid[v];
     const int kind = a.gkind[gi];
     const double* C = a.C + 81LL * gi;
-    double F[9], K[81];
+    double F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = a.F[k * N + v];
     if (kind == GFF_MAT_CP_FCC) {
@@ -451,7 +490,22 @@ __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
         if (a.warm)
             for (int s2 = 0; s2 < NSLIP; ++s2) dg0[s2] = a.dg[s2 * N + v];
         CPOut o;
-        cp_update(F, A, chin, a.dt, a.S0 + 108LL * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K, o);
+        if (F32T) {
+            float K[81];
+            cp_update<float>(F, A, chin, a.dt, a.S0 + 108LL * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K, o);
+#pragma unroll
+            for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
+        } else {
+            double K[81];
+            cp_update<double>(F, A, chin, a.dt, a.S0 + 108LL * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K,
+                              o);
+#pragma unroll
+            for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
+            if (a.K32) {
+#pragma unroll
+                for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
+            }
+        }
         if (!o.ok) atomicAdd(a.flag, 1);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -464,25 +518,25 @@ __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
             a.tau[s * N + v] = o.tau[s];
         }
     } else {
-        double P[9];
+        double P[9], K[81];
         svk_update(F, C, P, K);
 #pragma unroll
         for (int k = 0; k < 9; ++k) a.P[k * N + v] = P[k];
-        if (a.Fpi_t) {
+        if (!F32T) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) a.Fpi_t[k * N + v] = a.Fpi_n[k * N + v];
-            for (int s = 0; s < NSLIP; ++s) {
-                a.chi_t[s * N + v] = a.chi_n[s * N + v];
-                a.dg[s * N + v] = 0.0;
-                a.tau[s * N + v] = 0.0;
-            }
+            for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
         }
-    }
+        if (a.K32) {
 #pragma unroll
-    for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
-    if (a.K32) {
+            for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
+        }
 #pragma unroll
-        for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
+        for (int k = 0; k < 9; ++k) a.Fpi_t[k * N + v] = a.Fpi_n[k * N + v];
+        for (int s = 0; s < NSLIP; ++s) {
+            a.chi_t[s * N + v] = a.chi_n[s * N + v];
+            a.dg[s * N + v] = 0.0;
+            a.tau[s * N + v] = 0.0;
+        }
     }
 }
 
@@ -601,7 +655,7 @@ __global__ void k_grain_final(const double* sums, int ngrains, double fs_k, doub
 
 }  // namespace
 
-cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool write_k32, bool warm) {
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm) {
     ConstArgs a;
     a.F = F;
     a.gid = h->d_gid;
@@ -615,8 +669,8 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool 
     a.chi_n = h->d_chi;
     a.dt = dt;
     a.P = h->d_P;
-    a.K = h->d_K;
-    a.K32 = write_k32 ? h->d_K32 : nullptr;
+    a.K = tangent == TANGENT_F32 ? nullptr : h->d_K;
+    a.K32 = tangent == TANGENT_F64 ? nullptr : h->d_K32;
     a.Fpi_t = h->d_Fpi_t;
     a.chi_t = h->d_chi_t;
     a.dg = h->d_dg;
@@ -624,7 +678,10 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, bool 
     a.flag = h->d_flag;
     a.N = h->N;
     const int blocks = (int)((h->N + TPB - 1) / TPB);
-    k_constitutive<<<blocks, TPB, 0, h->stream>>>(a);
+    if (tangent == TANGENT_F32)
+        k_constitutive<true><<<blocks, TPB, 0, h->stream>>>(a);
+    else
+        k_constitutive<false><<<blocks, TPB, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
 
