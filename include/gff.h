@@ -206,6 +206,23 @@ gff_status gff_run_history(gff_handle* h, int nsteps, const double* dt, const do
                            const uint8_t* mask, const double* Pbar, const uint8_t* cycle_start,
                            double* Pmacro_out, gff_step_report* reports);
 
+/* Several RVEs through one loading history together (the statistical
+ * volume element of Sect. 4.3 needs tens of RVEs; sizes may differ).
+ * hs: n distinct handles (1 <= n <= 64) on one device with identical
+ * precision, projection, tolerances and caps, each with microstructure and
+ * materials set.  dt, Fbar, mask, Pbar, cycle_start: as in gff_run_history
+ * (one history for all).  Every Newton/CG step of all RVEs runs as one launch
+ * per kernel; the CG iterations are replayed from a captured CUDA graph.
+ * Each RVE's results are bitwise those of gff_run_history on its own handle.
+ * Pmacro_out (n x nsteps x 9), reports (n x nsteps), per_rve (n): may be NULL.
+ * An RVE whose increment fails keeps its last committed state, gets its
+ * status in per_rve and leaves the batch; the others go on.  Returns GFF_OK
+ * when all RVEs finished, else the first failing RVE's status.  The handles'
+ * streams are synchronised before and after the call. */
+gff_status gff_batch_run(int n, gff_handle* const* hs, int nsteps, const double* dt, const double* Fbar,
+                         const uint8_t* mask, const double* Pbar, const uint8_t* cycle_start,
+                         double* Pmacro_out, gff_step_report* reports, gff_status* per_rve);
+
 /* Fatigue indicator parameters (Sect. 3.3, Eqs. eqplas, strainenergy, Pmax).
  * gff_reset_fips restarts the per-cycle accumulators.  gff_get_fips returns
  * grain averages of the current accumulators: pcyc_g[ngrains],

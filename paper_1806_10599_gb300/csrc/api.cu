@@ -790,6 +790,20 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
 
 }  // namespace
 
+namespace gff {
+// Grain tables uploaded and launch shapes tuned: what gff_step does before its first increment.
+gff_status prepare_for_increments(gff_handle* h) {
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    if (!h->tuned) {
+        cudaError_t e = autotune_galerkin(h);
+        if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    }
+    return GFF_OK;
+}
+void set_error(gff_handle* h, const char* msg) { h->err = msg; }
+}  // namespace gff
+
 GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], const uint8_t mask[9], const double Pbar[9],
                     gff_step_report* report) {
     if (!h || !Fbar || !mask || !Pbar || !(dt > 0)) return fail(h, GFF_ERR_ARG, "bad step args");

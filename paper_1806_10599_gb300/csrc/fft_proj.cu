@@ -242,18 +242,15 @@ template <> struct V16<float> {
 };
 
 template <typename T, bool WITH_K, bool VEC>
-__global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, const T* __restrict__ K,
-                                                   typename C2<T>::t* __restrict__ spec, GridDev g,
-                                                   const int* __restrict__ skip) {
+__device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T* __restrict__ K,
+                                               typename C2<T>::t* __restrict__ spec, const GridDev& g, const int c,
+                                               const int z, unsigned char* sm_raw) {
     using C = typename C2<T>::t;
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
     const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
     C* s = reinterpret_cast<C*>(sm_raw);
     C* twx = s + ny * ls;
     C* twy = twx + nx;
     int* posx = reinterpret_cast<int*>(twy + ny);
-    const int c = blockIdx.x, z = blockIdx.y;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
@@ -360,13 +357,20 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, cons
     for (int e = tid; e < nq; e += nthr) dst4[e] = src4[e];
 }
 
-// ---------------------------------------------------------------- pass 2: z transform + projection
-template <typename T, int W>
-__global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa,
-                                              const int* __restrict__ skip) {
-    using C = typename C2<T>::t;
+template <typename T, bool WITH_K, bool VEC>
+__global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, const T* __restrict__ K,
+                                                   typename C2<T>::t* __restrict__ spec, GridDev g,
+                                                   const int* __restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    plane_fwd_body<T, WITH_K, VEC>(x, K, spec, g, blockIdx.x, blockIdx.y, sm_raw);
+}
+
+// ---------------------------------------------------------------- pass 2: z transform + projection
+template <typename T, int W>
+__device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec, const GridDev& g,
+                                           const ProjArgs& pa, const int blk, unsigned char* sm_raw) {
+    using C = typename C2<T>::t;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
     C* s = reinterpret_cast<C*>(sm_raw);  // [9][nz][W]
     C* twz = s + 9 * nz * W;
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
     int* fqz = fqy + ny;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long nF = (long long)ny * nxh;
-    const long long f0 = (long long)blockIdx.x * W;
+    const long long f0 = (long long)blk * W;
 
     for (int i = tid; i < nz; i += nthr) {
         twz[i] = twp<T>(g, 2)[i];
@@ -440,19 +444,25 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
     }
 }
 
-// ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
-template <typename T, bool VEC>
-__global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
-                                                   GridDev g, OutArgs oa, const int* __restrict__ skip) {
-    using C = typename C2<T>::t;
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa,
+                                              const int* __restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
+    zproj_body<T, W>(spec, g, pa, blockIdx.x, sm_raw);
+}
+
+// ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
+template <typename T, bool VEC>
+__device__ __forceinline__ void plane_inv_body(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
+                                               const GridDev& g, const OutArgs& oa, const int c, const int z,
+                                               unsigned char* sm_raw) {
+    using C = typename C2<T>::t;
     const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
     C* s = reinterpret_cast<C*>(sm_raw);
     C* twx = s + ny * ls;
     C* twy = twx + nx;
     int* posx = reinterpret_cast<int*>(twy + ny);
-    const int c = blockIdx.x, z = blockIdx.y;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
@@ -526,6 +536,14 @@ __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __re
             yc[v0 + nx] = fma(sc, zv.y, ad);
         }
     }
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
+                                                   GridDev g, OutArgs oa, const int* __restrict__ skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    plane_inv_body<T, VEC>(spec, y, g, oa, blockIdx.x, blockIdx.y, sm_raw);
 }
 
 template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 4 : 8; }
@@ -703,6 +721,106 @@ cudaError_t autotune_galerkin(gff_handle* h) {
     h->K32_valid = false;  // the FP32 tangent buffer was used as scratch
     return e;
 }
+
+// ---------------------------------------------------------------- batched launches
+namespace {
+
+__device__ __forceinline__ int find_rve(const int* __restrict__ start, int n, int b) {
+    int r = 0;
+    while (r + 1 < n && __ldg(start + r + 1) <= b) ++r;
+    return r;
+}
+
+template <typename T, bool WITH_K, bool VEC>
+__global__ void __launch_bounds__(512) k_plane_fwd_batch(const RveApply* __restrict__ rv, const int* __restrict__ start,
+                                                         int n) {
+    const int r = find_rve(start, n, blockIdx.x);
+    const RveApply& a = rv[r];
+    if (a.skip && *a.skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int local = blockIdx.x - start[r];
+    plane_fwd_body<T, WITH_K, VEC>(static_cast<const T*>(a.x), static_cast<const T*>(a.K),
+                                   static_cast<typename C2<T>::t*>(a.spec), a.g, local % 9, local / 9, sm_raw);
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_zproj_batch(const RveApply* __restrict__ rv, const int* __restrict__ start,
+                                                    int n, ProjArgs pa) {
+    const int r = find_rve(start, n, blockIdx.x);
+    const RveApply& a = rv[r];
+    if (a.skip && *a.skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    zproj_body<T, W>(static_cast<typename C2<T>::t*>(a.spec), a.g, pa, blockIdx.x - start[r], sm_raw);
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(512) k_plane_inv_batch(const RveApply* __restrict__ rv, const int* __restrict__ start,
+                                                         int n) {
+    const int r = find_rve(start, n, blockIdx.x);
+    const RveApply& a = rv[r];
+    if (a.skip && *a.skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int local = blockIdx.x - start[r];
+    plane_inv_body<T, VEC>(static_cast<const typename C2<T>::t*>(a.spec), static_cast<T*>(a.y), a.g, a.oa,
+                           local % 9, local / 9, sm_raw);
+}
+
+template <typename T, int W>
+cudaError_t launch_zb(const BatchLaunch& bl, const ProjArgs& pa, cudaStream_t st) {
+    allow_smem(k_zproj_batch<T, W>, bl.smem_z);
+    k_zproj_batch<T, W><<<bl.blocks_z, bl.tn.t_z, bl.smem_z, st>>>(bl.rv, bl.start_z, bl.n, pa);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_galerkin_batch(const BatchLaunch& bl, const ProjArgs& pa, cudaStream_t st) {
+    if (bl.withK) {
+        if (bl.vin) {
+            allow_smem(k_plane_fwd_batch<T, true, true>, bl.smem_plane);
+            k_plane_fwd_batch<T, true, true><<<bl.blocks_plane, bl.tn.t_fwd, bl.smem_plane, st>>>(bl.rv, bl.start_plane, bl.n);
+        } else {
+            allow_smem(k_plane_fwd_batch<T, true, false>, bl.smem_plane);
+            k_plane_fwd_batch<T, true, false><<<bl.blocks_plane, bl.tn.t_fwd, bl.smem_plane, st>>>(bl.rv, bl.start_plane, bl.n);
+        }
+    } else {
+        if (bl.vin) {
+            allow_smem(k_plane_fwd_batch<T, false, true>, bl.smem_plane);
+            k_plane_fwd_batch<T, false, true><<<bl.blocks_plane, bl.tn.t_fwd, bl.smem_plane, st>>>(bl.rv, bl.start_plane, bl.n);
+        } else {
+            allow_smem(k_plane_fwd_batch<T, false, false>, bl.smem_plane);
+            k_plane_fwd_batch<T, false, false><<<bl.blocks_plane, bl.tn.t_fwd, bl.smem_plane, st>>>(bl.rv, bl.start_plane, bl.n);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    switch (bl.tn.wz) {
+        case 2: e = launch_zb<T, 2>(bl, pa, st); break;
+        case 4: e = launch_zb<T, 4>(bl, pa, st); break;
+        case 8: e = launch_zb<T, 8>(bl, pa, st); break;
+        case 16: e = launch_zb<T, 16>(bl, pa, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    if (bl.vout) {
+        allow_smem(k_plane_inv_batch<T, true>, bl.smem_plane);
+        k_plane_inv_batch<T, true><<<bl.blocks_plane, bl.tn.t_inv, bl.smem_plane, st>>>(bl.rv, bl.start_plane, bl.n);
+    } else {
+        allow_smem(k_plane_inv_batch<T, false>, bl.smem_plane);
+        k_plane_inv_batch<T, false><<<bl.blocks_plane, bl.tn.t_inv, bl.smem_plane, st>>>(bl.rv, bl.start_plane, bl.n);
+    }
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_galerkin_batch<double>(const BatchLaunch&, const ProjArgs&, cudaStream_t);
+template cudaError_t launch_galerkin_batch<float>(const BatchLaunch&, const ProjArgs&, cudaStream_t);
+
+// Shared-memory bytes of the batched kernels (largest RVE) and the z-blocks of one RVE.
+size_t batch_plane_smem(int nx, int ny, int elem) { return plane_smem_bytes(nx, ny, elem); }
+template <typename T> size_t batch_z_smem(const GridDev& g, int W) { return zproj_smem<T>(g, W); }
+template size_t batch_z_smem<double>(const GridDev&, int);
+template size_t batch_z_smem<float>(const GridDev&, int);
 
 // ev (optional): four events recorded before, between and after the kernels.
 // skip (optional, device): when *skip != 0 at run time every kernel returns at once.

@@ -55,6 +55,30 @@ struct OutArgs {
     double add[9];
 };
 
+// ---- batched launches: one launch serves several RVEs of different sizes.
+// Each RVE owns the block range [start[r], start[r+1]) of the launch.
+constexpr int MAX_BATCH = 64;
+
+// One RVE's operands of a batched Galerkin apply.
+struct RveApply {
+    GridDev g;
+    const void* x;
+    const void* K;   // null: projection only
+    void* y;
+    void* spec;
+    OutArgs oa;
+    const int* skip;  // RVE stop flag, may be null
+};
+
+// One RVE's CG vectors (length n) in a batched CG launch.
+struct RveVec {
+    void* x;
+    void* r;
+    void* p;
+    void* Ap;
+    long long n;
+};
+
 struct GrainDev {
     const double* C;        // [ngrains][81] rotated stiffness
     const double* S0;       // [ngrains][12][9] Schmid tensors, sample frame
@@ -146,6 +170,10 @@ namespace gff {
 constexpr int NACC = 1 + 12 * 5;  // pcyc, W[12], gamma[12], gmin[12], gmax[12], sn[12]
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 
+// ---- host helpers (api.cu)
+gff_status prepare_for_increments(gff_handle* h);
+void set_error(gff_handle* h, const char* msg);
+
 // ---- launchers (fft_proj.cu)
 template <typename T>
 cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
@@ -155,6 +183,22 @@ size_t plane_smem_bytes(int nx, int ny, int elem);
 // Times every candidate launch shape of the three kernels on the handle's own
 // buffers and stores the fastest in h->tune (results do not depend on it).
 cudaError_t autotune_galerkin(gff_handle* h);
+
+// Batched apply: rv (device, n entries), start arrays (device) for the plane
+// kernels (9 nz blocks per RVE) and the z kernel (ceil(ny nxh / wz) blocks).
+struct BatchLaunch {
+    int n;
+    const RveApply* rv;
+    const int* start_plane;
+    const int* start_z;
+    int blocks_plane, blocks_z;
+    size_t smem_plane, smem_z;
+    Tune tn;
+    bool vin, vout, withK;
+};
+template <typename T>
+cudaError_t launch_galerkin_batch(const BatchLaunch& bl, const ProjArgs& pa, cudaStream_t st);
+template <typename T> size_t batch_z_smem(const GridDev& g, int W);
 
 // ---- vector kernels (vec.cu)
 template <typename T>
@@ -183,6 +227,17 @@ cudaError_t launch_cg_step(T* x, T* r, T* p, const T* Ap, long long n, double* p
 template <typename T>
 cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
 
+// batched CG (per-RVE scalars cg[r * 8 + CG_*], flags[2 r], flags[2 r + 1])
+cudaError_t launch_cg_init_batch(int n, double* cg, int* flag, const double* rr0_stop2_dev, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_alpha_batch(int n, const RveVec* v, double* partial, double* cg, int* flag, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cg_step_batch(int n, const RveVec* v, double* partial, double* cg, int* flag, cudaStream_t s);
+// out[r] = a_r . b_r for the n pairs (a_r, b_r) = (v[r].x, v[r].r); partial holds n * RED_BLOCKS
+template <typename T>
+cudaError_t launch_dot_batch(int n, const RveVec* v, double* partial, double* out, cudaStream_t s);
+size_t batch_plane_smem(int nx, int ny, int elem);
+
 // ---- constitutive kernels (material.cu)
 // tangent: TANGENT_F64 writes the FP64 K; TANGENT_F64_AND_F32 also rounds it into K32;
 // TANGENT_F32 computes the crystal-plasticity tangent in FP32 and writes only K32.
@@ -190,6 +245,11 @@ cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
 enum { TANGENT_F64 = 0, TANGENT_F64_AND_F32 = 1, TANGENT_F32 = 2 };
 cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm = false);
 cudaError_t launch_fip_accumulate(gff_handle* h);
+// Batched constitutive update of the RVEs hs[0..n) (skip[r] != 0: RVE r is left alone);
+// cpflag[r] counts return-map failures of RVE r.
+cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, bool warm,
+                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st);
+size_t constitutive_batch_scratch_bytes();
 cudaError_t launch_fip_reset(gff_handle* h);
 cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs);
 

@@ -458,15 +458,14 @@ struct ConstArgs {
     double* tau;
     int* flag;
     long long N;
+    const int* skip;  // batched launches: RVE left alone when *skip != 0
 };
 
 // F32T: the crystal-plasticity tangent is computed in FP32 and only K32 is
 // written (mixed precision); otherwise the tangent is FP64, written to K and,
 // when K32 is set, also rounded into K32.
 template <bool F32T>
-__global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
-    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= a.N) return;
+__device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const long long v) {
     const long long N = a.N;
     const int gi = a.gid[v];
     const int kind = a.gkind[gi];
@@ -538,6 +537,26 @@ __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
             a.tau[s * N + v] = 0.0;
         }
     }
+}
+
+template <bool F32T>
+__global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.N) return;
+    constitutive_voxel<F32T>(a, v);
+}
+
+// one launch over the voxels of several RVEs: RVE r owns blocks [start[r], start[r+1])
+template <bool F32T>
+__global__ void __launch_bounds__(TPB) k_constitutive_batch(const ConstArgs* __restrict__ args,
+                                                            const int* __restrict__ start, int n) {
+    int r = 0;
+    while (r + 1 < n && __ldg(start + r + 1) <= (int)blockIdx.x) ++r;
+    const ConstArgs& a = args[r];
+    if (a.skip && *a.skip) return;
+    const long long v = (long long)(blockIdx.x - start[r]) * blockDim.x + threadIdx.x;
+    if (v >= a.N) return;
+    constitutive_voxel<F32T>(a, v);
 }
 
 // ---------------------------------------------------------------- fatigue indicator parameters
@@ -677,6 +696,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.tau = h->d_tau;
     a.flag = h->d_flag;
     a.N = h->N;
+    a.skip = nullptr;
     const int blocks = (int)((h->N + TPB - 1) / TPB);
     if (tangent == TANGENT_F32)
         k_constitutive<true><<<blocks, TPB, 0, h->stream>>>(a);
@@ -684,6 +704,52 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
         k_constitutive<false><<<blocks, TPB, 0, h->stream>>>(a);
     return cudaGetLastError();
 }
+
+cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, bool warm,
+                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st) {
+    ConstArgs args[MAX_BATCH];
+    int start[MAX_BATCH + 1];
+    start[0] = 0;
+    for (int r = 0; r < n; ++r) {
+        gff_handle* h = hs[r];
+        ConstArgs& a = args[r];
+        a.F = h->d_Fk;
+        a.gid = h->d_gid;
+        a.C = h->d_C;
+        a.S0 = h->d_S0;
+        a.H = h->d_nrm + 41LL * h->ngrains;
+        a.warm = warm ? 1 : 0;
+        a.gkind = h->d_gkind;
+        a.gprm = h->d_nrm + 36LL * h->ngrains;
+        a.Fpi_n = h->d_Fpi;
+        a.chi_n = h->d_chi;
+        a.dt = dt;
+        a.P = h->d_P;
+        a.K = tangent == TANGENT_F32 ? nullptr : h->d_K;
+        a.K32 = tangent == TANGENT_F64 ? nullptr : h->d_K32;
+        a.Fpi_t = h->d_Fpi_t;
+        a.chi_t = h->d_chi_t;
+        a.dg = h->d_dg;
+        a.tau = h->d_tau;
+        a.flag = cpflag_dev + r;
+        a.N = h->N;
+        a.skip = skip_dev + 2 * r;
+        start[r + 1] = start[r] + (int)((h->N + TPB - 1) / TPB);
+    }
+    unsigned char* d = static_cast<unsigned char*>(scratch_dev);
+    ConstArgs* dargs = reinterpret_cast<ConstArgs*>(d);
+    int* dstart = reinterpret_cast<int*>(d + sizeof(ConstArgs) * MAX_BATCH);
+    cudaError_t e = cudaMemcpyAsync(dargs, args, sizeof(ConstArgs) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dstart, start, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (tangent == TANGENT_F32)
+        k_constitutive_batch<true><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+    else
+        k_constitutive_batch<false><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+    return cudaGetLastError();
+}
+
+size_t constitutive_batch_scratch_bytes() { return sizeof(ConstArgs) * MAX_BATCH + sizeof(int) * (MAX_BATCH + 1); }
 
 cudaError_t launch_fip_accumulate(gff_handle* h) {
     FipArgs a;

@@ -196,6 +196,123 @@ __global__ void k_promote_stop(int* flag) {
     if (flag[0] == 2) flag[0] = 1;
 }
 
+// ---- batched CG: blockIdx.y = RVE; each RVE uses the same RED_BLOCKS x TPB
+// grid-stride pattern as the single-RVE kernels, so its sums are bitwise equal
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_dot_partial_batch(const RveVec* __restrict__ v, int which,
+                                                           double* __restrict__ partial, const int* __restrict__ flag) {
+    const int r = blockIdx.y;
+    if (flag && flag[2 * r]) return;
+    __shared__ double sh[32];
+    const T* a = static_cast<const T*>(which == 0 ? v[r].p : v[r].x);
+    const T* b = static_cast<const T*>(which == 0 ? v[r].Ap : v[r].r);
+    const long long n = v[r].n;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc = fma((double)a[i], (double)b[i], acc);
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(TPB) k_final_alpha_batch(const double* __restrict__ partial, int nb, double* cg,
+                                                           int* flag) {
+    const int r = blockIdx.x;
+    if (flag[2 * r]) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[(long long)r * nb + i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        double* c = cg + 8 * r;
+        c[CG_PAP] = acc;
+        if (acc == 0.0 || !isfinite(acc)) {
+            flag[2 * r + 1] = 1;
+            flag[2 * r] = 1;
+        } else {
+            c[CG_ALPHA] = c[CG_RR] / acc;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_cg_update_batch(const RveVec* __restrict__ v, double* __restrict__ partial,
+                                                         const double* __restrict__ cg, const int* __restrict__ flag) {
+    const int r = blockIdx.y;
+    if (flag[2 * r]) return;
+    __shared__ double sh[32];
+    T* x = static_cast<T*>(v[r].x);
+    T* rr = static_cast<T*>(v[r].r);
+    const T* p = static_cast<const T*>(v[r].p);
+    const T* Ap = static_cast<const T*>(v[r].Ap);
+    const long long n = v[r].n;
+    const T alpha = (T)cg[8 * r + CG_ALPHA];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        x[i] = fma(alpha, p[i], x[i]);
+        const T ri = fma(-alpha, Ap[i], rr[i]);
+        rr[i] = ri;
+        acc = fma((double)ri, (double)ri, acc);
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(TPB) k_final_beta_batch(const double* __restrict__ partial, int nb, double* cg,
+                                                          int* flag) {
+    const int r = blockIdx.x;
+    if (flag[2 * r]) return;
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[(long long)r * nb + i];
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        double* c = cg + 8 * r;
+        c[CG_BETA] = acc / c[CG_RR];
+        c[CG_RR] = acc;
+        c[CG_ITERS] += 1.0;
+        if (!isfinite(acc)) {
+            flag[2 * r + 1] = 1;
+            flag[2 * r] = 1;
+        } else if (acc <= c[CG_STOP2]) {
+            flag[2 * r] = 2;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_xpby_batch(const RveVec* __restrict__ v, const double* __restrict__ cg,
+                                                    const int* __restrict__ flag) {
+    const int r = blockIdx.y;
+    if (flag[2 * r] == 1) return;
+    T* p = static_cast<T*>(v[r].p);
+    const T* rr = static_cast<const T*>(v[r].r);
+    const long long n = v[r].n;
+    const T beta = (T)cg[8 * r + CG_BETA];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = fma(beta, p[i], rr[i]);
+}
+
+__global__ void k_promote_stop_batch(int* flag, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n && flag[2 * r] == 2) flag[2 * r] = 1;
+}
+
+// rr0_stop2[2 r] = r.r of RVE r, [2 r + 1] = stop^2; rr0 < 0 marks an RVE that does not solve
+__global__ void k_cg_init_batch(int n, double* cg, int* flag, const double* rr0_stop2) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double rr0 = rr0_stop2[2 * r], s2 = rr0_stop2[2 * r + 1];
+    double* c = cg + 8 * r;
+    c[CG_RR] = rr0;
+    c[CG_PAP] = 0.0;
+    c[CG_ALPHA] = 0.0;
+    c[CG_BETA] = 0.0;
+    c[CG_STOP2] = s2;
+    c[CG_ITERS] = 0.0;
+    flag[2 * r] = (rr0 < 0.0 || rr0 <= s2) ? 1 : 0;
+    flag[2 * r + 1] = 0;
+}
+
 inline int grid_for(long long n) {
     long long b = (n + TPB - 1) / TPB;
     return (int)(b < 152LL * 8 ? (b < 1 ? 1 : b) : 152LL * 8);
@@ -291,6 +408,41 @@ template cudaError_t launch_cg_step<double>(double*, double*, double*, const dou
                                             int*, cudaStream_t);
 template cudaError_t launch_cg_step<float>(float*, float*, float*, const float*, long long, double*, double*, int*,
                                            cudaStream_t);
+
+cudaError_t launch_cg_init_batch(int n, double* cg, int* flag, const double* rr0_stop2_dev, cudaStream_t s) {
+    k_cg_init_batch<<<(n + 63) / 64, 64, 0, s>>>(n, cg, flag, rr0_stop2_dev);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_alpha_batch(int n, const RveVec* v, double* partial, double* cg, int* flag, cudaStream_t s) {
+    k_dot_partial_batch<T><<<dim3(RED_BLOCKS, n), TPB, 0, s>>>(v, 0, partial, flag);
+    k_final_alpha_batch<<<n, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_step_batch(int n, const RveVec* v, double* partial, double* cg, int* flag, cudaStream_t s) {
+    k_cg_update_batch<T><<<dim3(RED_BLOCKS, n), TPB, 0, s>>>(v, partial, cg, flag);
+    k_final_beta_batch<<<n, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+    k_xpby_batch<T><<<dim3(RED_BLOCKS, n), TPB, 0, s>>>(v, cg, flag);
+    k_promote_stop_batch<<<(n + 63) / 64, 64, 0, s>>>(flag, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dot_batch(int n, const RveVec* v, double* partial, double* out, cudaStream_t s) {
+    k_dot_partial_batch<T><<<dim3(RED_BLOCKS, n), TPB, 0, s>>>(v, 1, partial, nullptr);
+    k_final<<<n, TPB, 0, s>>>(partial, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_cg_alpha_batch<double>(int, const RveVec*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_cg_alpha_batch<float>(int, const RveVec*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_cg_step_batch<double>(int, const RveVec*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_cg_step_batch<float>(int, const RveVec*, double*, double*, int*, cudaStream_t);
+template cudaError_t launch_dot_batch<double>(int, const RveVec*, double*, double*, cudaStream_t);
+template cudaError_t launch_dot_batch<float>(int, const RveVec*, double*, double*, cudaStream_t);
 
 template cudaError_t launch_dot<double>(const double*, const double*, long long, double*, double*, cudaStream_t);
 template cudaError_t launch_dot<float>(const float*, const float*, long long, double*, double*, cudaStream_t);

@@ -101,6 +101,8 @@ _SIGS = {
     "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
     "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
+    "gff_batch_run": (c_int, [c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                              c_void_p, c_void_p]),
     "gff_reset_fips": (c_int, [c_void_p]),
     "gff_get_fips": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_save_state": (c_int, [c_void_p, ctypes.c_char_p]),
@@ -266,6 +268,27 @@ def gff_run_history(h, dt, Fbar, mask, Pbar, cycle_start=None):
     _check(h, _lib.gff_run_history(h, n, dp, fp, mp, pp, csp, Pm.ctypes.data_as(c_void_p),
                                    ctypes.cast(reps, c_void_p)))
     return Pm, [reps[k] for k in range(n)]
+
+
+def gff_batch_run(handles, dt, Fbar, mask, Pbar, cycle_start=None, raise_on_error=True):
+    """Runs all handles through one history together.  Returns (Pmacro
+    [n][nsteps][9], reports [n][nsteps], per-RVE status array)."""
+    n = len(handles)
+    hs = (c_void_p * n)(*[h.value for h in handles])
+    ns = int(np.asarray(dt).shape[0])
+    d, dp = _host(dt, np.float64)
+    f, fp = _host(Fbar, np.float64)
+    m, mp = _host(mask, np.uint8)
+    p, pp = _host(Pbar, np.float64)
+    cs, csp = _host(cycle_start, np.uint8) if cycle_start is not None else (None, None)
+    Pm = np.zeros((n, ns, 9))
+    reps = (gff_step_report * max(n * ns, 1))()
+    stat = np.zeros(n, dtype=np.int32)
+    st = _lib.gff_batch_run(n, ctypes.cast(hs, c_void_p), ns, dp, fp, mp, pp, csp, Pm.ctypes.data_as(c_void_p),
+                            ctypes.cast(reps, c_void_p), stat.ctypes.data_as(c_void_p))
+    if st != GFF_OK and raise_on_error:
+        raise GffError(st, "gff_batch_run: per-RVE status %s; %s" % (stat.tolist(), gff_last_error(handles[0])))
+    return Pm, [[reps[r * ns + k] for k in range(ns)] for r in range(n)], stat
 
 
 def gff_reset_fips(h):

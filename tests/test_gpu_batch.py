@@ -1,0 +1,72 @@
+"""Batched RVEs of uneven sizes (gff_batch_run): every RVE's result must be
+bitwise the result of running its handle alone (the batched launches keep
+each RVE's arithmetic and reduction order), in FP64 and in mixed precision,
+with crystal plasticity and with a stiff second phase."""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import gff, gpu_materials, torch_cuda
+from oracle.solver import CP_FCC, SVK_ISO
+from rve_inputs import cyclic_history, polycrystal, polycrystal_with_particles
+
+pytestmark = pytest.mark.gpu
+
+
+def _rves():
+    return [
+        (polycrystal((8, 8, 8), 4, 21), {0: CP_FCC}),
+        (polycrystal((12, 8, 16), 6, 22), {0: CP_FCC}),
+        (polycrystal_with_particles(16, 5, 23, radius=3, frac=0.05), {0: CP_FCC, 1: SVK_ISO}),
+        (polycrystal((6, 10, 20), 3, 24), {0: CP_FCC}),
+    ]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_equals_one_by_one_bitwise(precision):
+    torch_cuda()
+    g = gff()
+    hist = cyclic_history(0.01, 1).head(7)
+    opts = dict(precision=precision, newton_tol=1e-9 if precision == 0 else 1e-7, cg_tol=1e-6)
+    rves = _rves()
+    singles, batch = [], []
+    try:
+        for ms, kinds in rves:
+            singles.append(g.create_rve(ms, gpu_materials(kinds), g.make_options(**opts)))
+            batch.append(g.create_rve(ms, gpu_materials(kinds), g.make_options(**opts)))
+        ref = [g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start) for h in singles]
+        Pm, reps, stat = g.gff_batch_run(batch, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+        assert (stat == 0).all()
+        for r, (ms, kinds) in enumerate(rves):
+            assert np.array_equal(Pm[r], ref[r][0]), r
+            assert [x.newton_iters for x in reps[r]] == [x.newton_iters for x in ref[r][1]]
+            assert [x.cg_iters for x in reps[r]] == [x.cg_iters for x in ref[r][1]]
+            for w in (g.GFF_FIELD_F, g.GFF_FIELD_P, g.GFF_FIELD_FP_INV, g.GFF_FIELD_CHI):
+                a = g.gff_get_field(batch[r], w, ms.n_voxels)
+                b = g.gff_get_field(singles[r], w, ms.n_voxels)
+                assert np.array_equal(a, b), (r, w)
+            fa = g.gff_get_fips(batch[r], ms.ngrains)
+            fb = g.gff_get_fips(singles[r], ms.ngrains)
+            for x, y in zip(fa, fb):
+                assert np.allclose(x, y, rtol=1e-12, atol=0)
+    finally:
+        for h in singles + batch:
+            g.gff_destroy(h)
+
+
+def test_batch_rejects_mismatched_options():
+    torch_cuda()
+    g = gff()
+    ms = polycrystal(8, 3, 1)
+    a = g.create_rve(ms, gpu_materials({0: CP_FCC}), g.make_options(precision=0))
+    b = g.create_rve(ms, gpu_materials({0: CP_FCC}), g.make_options(precision=1))
+    try:
+        hist = cyclic_history(0.01, 1).head(1)
+        with pytest.raises(g.GffError) as e:
+            g.gff_batch_run([a, b], hist.dt, hist.Fbar, hist.mask, hist.Pbar)
+        assert e.value.status == g.GFF_ERR_ARG
+        with pytest.raises(g.GffError):
+            g.gff_batch_run([a, a], hist.dt, hist.Fbar, hist.mask, hist.Pbar)
+    finally:
+        g.gff_destroy(a)
+        g.gff_destroy(b)
