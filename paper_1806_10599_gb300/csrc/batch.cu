@@ -53,8 +53,8 @@ struct Batch {
     int* d_cgflag = nullptr;     // [n][2]
     int* d_inactive = nullptr;   // [n][2] (stride 2 like the CG flags)
     int* d_cpflag = nullptr;     // [n]
-    double* d_partial = nullptr; // [n][RED_BLOCKS]
-    double* d_out = nullptr;     // [4 n + 9 n]
+    double* d_partial = nullptr; // [max(n, 9)][RED_BLOCKS]
+    double* d_out = nullptr;     // [18 n]
     double* d_rr0 = nullptr;     // [n][2]
     void* d_cscratch = nullptr;
     // pinned host mirror
@@ -203,7 +203,9 @@ gff_status setup(Batch& B) {
     const size_t o_szc = take(sizeof(int) * (n + 1));
     const size_t o_cg = take(sizeof(double) * 8 * n), o_cgf = take(sizeof(int) * 2 * n);
     const size_t o_ina = take(sizeof(int) * 2 * n), o_cpf = take(sizeof(int) * n);
-    const size_t o_part = take(sizeof(double) * RED_BLOCKS * n), o_out = take(sizeof(double) * 16 * n);
+    // partial sums: n RVEs x RED_BLOCKS (batched dots) or 9 x RED_BLOCKS (per-component sums)
+    const size_t o_part = take(sizeof(double) * RED_BLOCKS * std::max(n, 9));
+    const size_t o_out = take(sizeof(double) * 18 * n);
     const size_t o_rr0 = take(sizeof(double) * 2 * n), o_cs = take(constitutive_batch_scratch_bytes());
     BTRY(cudaMalloc(&B.arena.p, off));
     unsigned char* d = static_cast<unsigned char*>(B.arena.p);
