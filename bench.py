@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--impl", choices=["gff", "reference"], default="gff")
     p.add_argument("--increments", type=int, default=6, help="CP increments timed per precision (0: skip)")
     p.add_argument("--cpu-applies", type=int, default=3, help="oracle applies in the CPU baseline sample")
+    p.add_argument("--batch-increments", type=int, default=2,
+                   help="increments of the 32-RVE batch, batched and one by one (0: skip)")
     p.add_argument("--grid", type=int, default=N_GRID, help="grid size (smaller grids only for profiling runs)")
     a = p.parse_args()
     return a
@@ -301,6 +303,44 @@ def _time_increments(g, torch, nsteps, precision):
             "s_linear": sum(r.t_linear for r in reps) / nsteps}
 
 
+def time_batch(g, torch, nsteps, precision):
+    """32 RVEs of 32^3 ... 96^3 voxels (10,956,800 in all), crystal plasticity,
+    first `nsteps` increments of a +-1 % cycle: gff_batch_run against running
+    the same RVEs one handle after the other."""
+    try:
+        from rve_inputs import batch_rves, cyclic_history, polycrystal
+
+        specs = batch_rves()
+        hist = cyclic_history(0.01, 1).head(nsteps)
+        opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3)
+        out = {"rves": len(specs), "voxels": int(sum(n ** 3 for n, _, _ in specs)), "increments": nsteps}
+        for mode in ("batched", "one_by_one"):
+            hs = [g.create_rve(polycrystal(n, ng, seed), {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts)
+                  for n, ng, seed in specs]
+            try:
+                for h in hs:
+                    g.gff_autotune(h)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if mode == "batched":
+                    Pm, reps, stat = g.gff_batch_run(hs, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+                    newton = [r[-1].newton_iters for r in reps]
+                else:
+                    newton = []
+                    for h in hs:
+                        _, rp = g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+                        newton.append(rp[-1].newton_iters)
+                torch.cuda.synchronize()
+                out["s_per_increment_" + mode] = (time.perf_counter() - t0) / nsteps
+                out["newton_last_" + mode] = newton
+            finally:
+                for h in hs:
+                    g.gff_destroy(h)
+        return out
+    except Exception as e:  # report, do not lose the apply measurement
+        return {"error": str(e)}
+
+
 def run_gpu(args, world, rank, local):
     import numpy as np
     import torch
@@ -365,6 +405,11 @@ def run_gpu(args, world, rank, local):
                "mixed": time_increments(g, torch, args.increments, 1)}
     g.gff_destroy(h)
     g.gff_destroy(hd)
+    batch = None
+    if args.batch_increments > 0 and rank == 0:
+        batch = {"workload": "32 RVEs (7x32^3, 7x48^3, 6x64^3, 6x80^3, 6x96^3; 50-300 grains, seeds 4000+i), FCC "
+                             "crystal plasticity, +-1 pct cycle, mixed precision, Newton tol 1e-6",
+                 "mixed": time_batch(g, torch, args.batch_increments, 1)}
 
     if rank != 0:
         return
@@ -375,7 +420,8 @@ def run_gpu(args, world, rank, local):
                "sample": "%d oracle applies at %d^3 (numpy FP64, one thread), %.1f s"
                          % (args.cpu_applies, args.grid, secs)}
     raw = {"ms64": ms64, "ms32": ms32, "msd": msd, "k64": k64, "k32": k32, "e2e_s": e2e_s,
-           "xbytes": int(x.nbytes), "clocks": clk, "increment": inc, "cpu": cpu, "tiles": tiles}
+           "xbytes": int(x.nbytes), "clocks": clk, "increment": inc, "cpu": cpu, "tiles": tiles,
+           "batch": batch}
     print(json.dumps(build_line(args, world, raw, *measured_peaks())), flush=True)
 
 
@@ -427,6 +473,7 @@ def build_line(args, world, raw, peaks, src):
         },
         "increment": raw["increment"],
         "autotuned_tiles": raw.get("tiles"),
+        "batch": raw.get("batch"),
     }
 
 

@@ -11,6 +11,7 @@ Arm hosts.
 
 from .rng import splitmix64, uniform01, standard_normal
 from .microstructure import (
+    batch_rves,
     periodic_voronoi,
     random_quaternions,
     place_spheres,
@@ -34,6 +35,7 @@ __all__ = [
     "Microstructure",
     "polycrystal",
     "polycrystal_with_particles",
+    "batch_rves",
     "cyclic_history",
     "ramp_history",
     "LoadHistory",

@@ -22,6 +22,7 @@ from .rng import uniform01
 OFF_SEEDS = 0
 OFF_QUATS = 1 << 40
 OFF_SPHERES = 1 << 41
+OFF_COUNT = 1 << 43
 
 
 @dataclass
@@ -139,3 +140,15 @@ def polycrystal_with_particles(n, ngrains, seed, radius=3, frac=0.05, L=(1.0, 1.
     q = np.vstack([m.quat, [[1.0, 0.0, 0.0, 0.0]]])
     ph = np.concatenate([m.phase, [1]]).astype(np.int32)
     return Microstructure(m.nx, m.ny, m.nz, m.L, gid, q, ph)
+
+
+def batch_rves(count=32, base_seed=4000, sizes=(32, 48, 64, 80, 96), min_grains=50, span=251):
+    """Uneven RVE set: RVE i has n = sizes[i mod len(sizes)] voxels per axis,
+    seed base_seed + i and min_grains + floor(span u_i) grains (u_i uniform
+    from its own seed).  Returns a list of (n, ngrains, seed)."""
+    out = []
+    for i in range(count):
+        seed = base_seed + i
+        u = uniform01(seed, 1, OFF_COUNT)[0]
+        out.append((sizes[i % len(sizes)], min_grains + int(np.floor(span * u)), seed))
+    return out
