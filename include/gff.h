@@ -86,7 +86,8 @@ typedef struct {
     double cg_tol;     /* CG stops when ||r|| <= max(cg_tol ||b||, 0.1 newton_tol ||P||) */
     int newton_max, cg_max;
     int max_cuts;      /* time-step halvings allowed after a CP failure            */
-    int warm_start;    /* reserved, must be 0                                       */
+    int warm_start;    /* learned initial guess (gff_set_warm_start): 0 off, 1 used
+                          only if its residual beats the zero start's, 2 always  */
     double fs_k, fs_sigma_y; /* Fatemi-Socie constants                             */
 } gff_options;
 
@@ -101,7 +102,11 @@ typedef struct {
     double t_constitutive; /* device time in constitutive updates, s        */
     double t_residual;     /* device time in residual evaluations, s         */
     double t_linear;       /* device time in the CG solves, s                */
+    int warm_start_used;   /* 1: the Newton iteration started from the network's guess */
+    double residual_first; /* ||b|| / ||P|| at the start the Newton iteration used     */
 } gff_step_report;
+
+typedef struct gff_unet gff_unet;
 
 /* Defaults: continuous projection, FP64, newton_tol 1e-8, cg_tol 1e-8,
  * newton_max 30, cg_max 2000, max_cuts 4, fs_k 0.5, fs_sigma_y 153e6. */
@@ -222,6 +227,45 @@ gff_status gff_run_history(gff_handle* h, int nsteps, const double* dt, const do
 gff_status gff_batch_run(int n, gff_handle* const* hs, int nsteps, const double* dt, const double* Fbar,
                          const uint8_t* mask, const double* Pbar, const uint8_t* cycle_start,
                          double* Pmacro_out, gff_step_report* reports, gff_status* per_rve);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper; Sect. 2.1 leaves the Newton initial
+ * guess open).  A 4-level periodic 3D U-Net (channels 16, 32, 64, 64) maps,
+ * per voxel, the grain orientation quaternion (4), the phase (1) and the
+ * macroscopic increment direction dFbar/|dFbar| (9) to the fluctuation
+ * increment (F_k - F_{k-1} - dFbar)/|dFbar| (9).  The guess is projected
+ * with G^ (compatible, zero mean) and added to the zero-fluctuation start.
+ * bfloat16 weights/activations, FP32 accumulation on the tensor cores, FP32
+ * master weights and Adam.  Grids must be cubic with n divisible by 8.
+ * ------------------------------------------------------------------------ */
+gff_status gff_unet_create(uint64_t seed, gff_unet** out); /* He-uniform init from SplitMix64(seed) */
+void gff_unet_destroy(gff_unet* u);
+const char* gff_unet_last_error(const gff_unet* u);
+size_t gff_unet_num_params(const gff_unet* u);
+/* Parameters as FP32 host arrays, order: for the 14 convolutions e1a e1b e2a
+ * e2b e3a e3b e4a e4b d3a d3b d2a d2b d1a d1b: W[27][cout][cin] then
+ * b[cout] (tap t = 9(dz+1) + 3(dy+1) + (dx+1)); then the head W[9][16], b[9]. */
+gff_status gff_unet_get_params(gff_unet* u, float* host);
+gff_status gff_unet_set_params(gff_unet* u, const float* host);
+gff_status gff_unet_save(gff_unet* u, const char* path);
+gff_status gff_unet_load(gff_unet* u, const char* path);
+/* Network output y [V][9] for host inputs x [V][14] on an n^3 grid; with a
+ * target [V][9] also the mean-squared-error loss and all parameter gradients
+ * (order of gff_unet_get_params).  target, loss, grads may be NULL. */
+gff_status gff_unet_eval_host(gff_unet* u, int n, const float* x, const float* target, float* y,
+                              double* loss, float* grads);
+/* Keep the last completed increment of h (inputs, fluctuation-increment
+ * target) as a training sample on the device; all samples share one grid. */
+gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h);
+int gff_unet_num_samples(const gff_unet* u);
+/* `steps` Adam steps (lr, betas 0.9/0.999), one sample per step, shuffled
+ * epochs; losses (host, steps, may be NULL) receives each step's loss. */
+gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* losses);
+/* Use u for the initial guess of h's increments: mode 0 off, 1 keep the
+ * guess only when its first residual is below the zero start's (costs one
+ * more constitutive evaluation per increment), 2 always.  gff_batch_run
+ * does not use the warm start. */
+gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode);
 
 /* Fatigue indicator parameters (Sect. 3.3, Eqs. eqplas, strainenergy, Pmax).
  * gff_reset_fips restarts the per-cycle accumulators.  gff_get_fips returns

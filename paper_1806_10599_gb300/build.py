@@ -14,7 +14,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgff.so")
-SOURCES = ["api.cu", "fft_proj.cu", "vec.cu", "material.cu", "batch.cu"]
+SOURCES = ["api.cu", "fft_proj.cu", "vec.cu", "material.cu", "batch.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -276,6 +276,15 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
     GFF_TRY(cudaMemcpy(h->d_S0, S0.data(), S0.size() * sizeof(double), cudaMemcpyHostToDevice));
     GFF_TRY(cudaMemcpy(h->d_nrm, nrmprm.data(), nrmprm.size() * sizeof(double), cudaMemcpyHostToDevice));
     GFF_TRY(cudaMemcpy(h->d_gkind, kind.data(), kind.size() * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<float> gq(5 * (size_t)ng);
+    for (int g = 0; g < ng; ++g) {
+        const double* q = &quat[4 * (size_t)g];
+        const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        const double sgn = q[0] < 0 ? -1.0 : 1.0;  // q and -q are one rotation: keep w >= 0
+        for (int c = 0; c < 4; ++c) gq[5 * (size_t)g + c] = (float)(sgn * q[c] / qn);
+        gq[5 * (size_t)g + 4] = (float)phase[g];
+    }
+    GFF_TRY(cudaMemcpy(h->d_gq, gq.data(), gq.size() * sizeof(float), cudaMemcpyHostToDevice));
     return GFF_OK;
 }
 
@@ -345,7 +354,7 @@ static gff_status check_options(gff_handle* h, const gff_options* o) {
         return fail(h, GFF_ERR_ARG, "precision %d", o->precision);
     if (!(o->newton_tol > 0) || !(o->cg_tol > 0) || o->newton_max < 0 || o->cg_max < 1 || o->max_cuts < 0)
         return fail(h, GFF_ERR_ARG, "tolerances / caps out of range");
-    if (o->warm_start != 0) return fail(h, GFF_ERR_ARG, "warm_start is reserved and must be 0");
+    if (o->warm_start < 0 || o->warm_start > 2) return fail(h, GFF_ERR_ARG, "warm_start must be 0, 1 or 2");
     return GFF_OK;
 }
 
@@ -395,6 +404,7 @@ GFF_EXPORT gff_status gff_create(const gff_grid* grid, const gff_options* opt, g
         {(void**)&h->d_red, 32 * RED_BLOCKS * sizeof(double), "reduce"},
         {(void**)&h->d_scal, 64 * sizeof(double), "scalars"},
         {(void**)&h->d_gid, N * sizeof(int), "grain id"},
+        {(void**)&h->d_Fprev, f64, "F of the previous increment"},
     };
     for (auto& a : allocs)
         if ((st = dalloc(h, a.p, a.b, a.w)) != GFF_OK) return st;
@@ -411,7 +421,7 @@ GFF_EXPORT void gff_destroy(gff_handle* h) {
     dfree(h->d_p); dfree(h->d_Ap); dfree(h->d_K32); dfree(h->d_b32); dfree(h->d_x32); dfree(h->d_r32);
     dfree(h->d_p32); dfree(h->d_Ap32); dfree(h->d_spec); dfree(h->d_Fpi); dfree(h->d_chi); dfree(h->d_Fpi_t);
     dfree(h->d_chi_t); dfree(h->d_dg); dfree(h->d_tau); dfree(h->d_acc); dfree(h->d_flag); dfree(h->d_red);
-    dfree(h->d_scal);
+    dfree(h->d_scal); dfree(h->d_gq); dfree(h->d_Fprev);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete reinterpret_cast<gff_hostdata*>(h->hostdata);
     delete h;
@@ -456,7 +466,7 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
         if (grain_id[v] < 0 || grain_id[v] >= ngrains) return fail(h, GFF_ERR_ARG, "grain_id[%lld] out of range", v);
     for (int g = 0; g < ngrains; ++g)
         if (grain_phase[g] < 0 || grain_phase[g] >= 8) return fail(h, GFF_ERR_ARG, "grain_phase[%d] out of range", g);
-    dfree(h->d_C); dfree(h->d_S0); dfree(h->d_nrm); dfree(h->d_gkind);
+    dfree(h->d_C); dfree(h->d_S0); dfree(h->d_nrm); dfree(h->d_gkind); dfree(h->d_gq);
     h->ngrains = ngrains;
     gff_status st;
     if ((st = dalloc(h, (void**)&h->d_C, 81 * (size_t)ngrains * sizeof(double), "C")) != GFF_OK) return st;
@@ -464,6 +474,8 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
     if ((st = dalloc(h, (void**)&h->d_nrm, (41 + 144) * (size_t)ngrains * sizeof(double), "normals")) != GFF_OK)
         return st;
     if ((st = dalloc(h, (void**)&h->d_gkind, (size_t)ngrains * sizeof(int), "kind")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_gq, 5 * (size_t)ngrains * sizeof(float), "grain quaternions")) != GFF_OK)
+        return st;
     GFF_TRY(cudaMemcpy(h->d_gid, grain_id, h->N * sizeof(int), cudaMemcpyHostToDevice));
     gff_hostdata* hd = reinterpret_cast<gff_hostdata*>(h->hostdata);
     if (!hd) {
@@ -618,6 +630,15 @@ GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, con
     return GFF_OK;
 }
 
+GFF_EXPORT gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode) {
+    if (!h || mode < 0 || mode > 2 || (mode && !u)) return fail(h, GFF_ERR_ARG, "bad warm-start args");
+    if (mode && (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz || h->grid.nx % 8))
+        return fail(h, GFF_ERR_ARG, "the warm-start network needs a cubic grid with n divisible by 8");
+    h->unet = mode ? u : nullptr;
+    h->opt.warm_start = mode;
+    return GFF_OK;
+}
+
 GFF_EXPORT gff_status gff_autotune(gff_handle* h, int* tiles_out) {
     if (!h) return GFF_ERR_ARG;
     GFF_TRY(autotune_galerkin(h));
@@ -711,7 +732,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     const OutArgs ores = out_args(h, -1.0, add9);
     const bool mixed = h->opt.precision == GFF_PREC_MIXED;
     int newton = 0, cgsum = 0;
-    double res = 0.0;
+    double res = 0.0, nb = 0.0, nP = 0.0, rr_b = 0.0;
     bool conv = false;
     double t_const = 0.0, t_res = 0.0, t_lin = 0.0;
     cudaEvent_t ev[4];
@@ -722,19 +743,21 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
         }
     } evg{ev};
-    for (int it = 0; it <= h->opt.newton_max; ++it) {
+
+    // P, K at d_Fk and the residual b = -G_M(P) + M : Pbar with its norms
+    auto evaluate = [&](bool warm_dg) -> gff_status {
         GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
         GFF_TRY(cudaEventRecord(ev[0], h->stream));
-        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, it > 0));
+        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, warm_dg));
         GFF_TRY(cudaEventRecord(ev[1], h->stream));
-        // b = -G_M(P) + M : Pbar
         GFF_TRY(launch_galerkin<double>(h, h->d_P, (const double*)nullptr, h->d_b, pa, ores, h->d_spec));
         GFF_TRY(launch_dot<double>(h->d_b, h->d_b, n, h->d_red, h->d_scal, h->stream));
         GFF_TRY(launch_dot<double>(h->d_P, h->d_P, n, h->d_red + RED_BLOCKS, h->d_scal + 1, h->stream));
         GFF_TRY(cudaMemcpyAsync(h->d_scal + 2, h->d_flag, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
         GFF_TRY(cudaEventRecord(ev[2], h->stream));
         double s3[3];
-        if ((st = fetch(h, h->d_scal, 3, s3)) != GFF_OK) return st;
+        gff_status st2 = fetch(h, h->d_scal, 3, s3);
+        if (st2 != GFF_OK) return st2;
         float ms01 = 0.f, ms12 = 0.f;
         GFF_TRY(cudaEventElapsedTime(&ms01, ev[0], ev[1]));
         GFF_TRY(cudaEventElapsedTime(&ms12, ev[1], ev[2]));
@@ -743,8 +766,38 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         int flag;
         std::memcpy(&flag, &s3[2], sizeof(int));
         if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
-        const double nb = std::sqrt(s3[0]), nP = std::sqrt(s3[1]);
+        rr_b = s3[0];
+        nb = std::sqrt(s3[0]);
+        nP = std::sqrt(s3[1]);
         res = nP > 0 ? nb / nP : nb;
+        return GFF_OK;
+    };
+
+    // learned warm start: mode 1 keeps it only if its residual beats the zero start's, mode 2 always
+    int warm_used = 0;
+    double res_first = 0.0;
+    const int wmode = h->unet ? h->opt.warm_start : 0;
+    if (wmode) {
+        double res_zero = -1.0;
+        if (wmode == 1) {
+            if ((st = evaluate(false)) != GFF_OK) return st;
+            res_zero = res;
+        }
+        cudaError_t e = unet_warm_start(h->unet, h, d9);
+        if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "warm start: %s", cudaGetErrorString(e));
+        if ((st = evaluate(false)) != GFF_OK) return st;
+        warm_used = 1;
+        if (wmode == 1 && !(res < res_zero)) {
+            GFF_TRY(launch_add_const9(h->d_Fk, h->d_F, d9, N, h->stream));
+            if ((st = evaluate(false)) != GFF_OK) return st;
+            warm_used = 0;
+        }
+    } else {
+        if ((st = evaluate(false)) != GFF_OK) return st;
+    }
+    res_first = res;
+    for (int it = 0; it <= h->opt.newton_max; ++it) {
+        if (it > 0 && (st = evaluate(true)) != GFF_OK) return st;
         if (res <= h->opt.newton_tol) {
             conv = true;
             break;
@@ -755,7 +808,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         GFF_TRY(cudaEventRecord(ev[2], h->stream));
         if (!mixed) {
             GFF_TRY(cudaMemcpyAsync(h->d_r, h->d_b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-            if ((st = cg_solve<double>(h, pa, h->d_x, h->d_r, h->d_p, h->d_Ap, h->d_K, s3[0], stop, &its)) != GFF_OK)
+            if ((st = cg_solve<double>(h, pa, h->d_x, h->d_r, h->d_p, h->d_Ap, h->d_K, rr_b, stop, &its)) != GFF_OK)
                 return st;
             GFF_TRY(launch_axpy_to64<double>(h->d_Fk, h->d_x, n, h->stream));
         } else {
@@ -783,6 +836,8 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         rep->t_constitutive = t_const;
         rep->t_residual = t_res;
         rep->t_linear = t_lin;
+        rep->warm_start_used = warm_used;
+        rep->residual_first = res_first;
     }
     if (!conv) return fail(h, GFF_ERR_NO_CONVERGENCE, "Newton: residual %.3e after %d iterations", res, newton);
     return GFF_OK;
@@ -819,7 +874,10 @@ GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], c
         return st;
     }
     const long long N = h->N;
-    // commit: F, P (already for the converged F), internal variables, FIPs
+    // commit: F, P (already for the converged F), internal variables, FIPs;
+    // the previous F is kept for training samples of the warm-start network
+    GFF_TRY(launch_sum9(h->d_F, N, h->d_red, h->d_scal + 18, h->stream));
+    GFF_TRY(cudaMemcpyAsync(h->d_Fprev, h->d_F, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     GFF_TRY(cudaMemcpyAsync(h->d_F, h->d_Fk, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (h->any_cp) {
         GFF_TRY(cudaMemcpyAsync(h->d_Fpi, h->d_Fpi_t, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -829,14 +887,16 @@ GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], c
     // mixed precision leaves only the FP32 tangent of the last Newton iterate
     h->K_valid = h->opt.precision != GFF_PREC_MIXED;
     h->K32_valid = h->opt.precision == GFF_PREC_MIXED;
-    double s[18];
+    double s[27];
     GFF_TRY(launch_sum9(h->d_P, N, h->d_red, h->d_scal, h->stream));
     GFF_TRY(launch_sum9(h->d_F, N, h->d_red + 9 * RED_BLOCKS, h->d_scal + 9, h->stream));
-    if ((st = fetch(h, h->d_scal, 18, s)) != GFF_OK) return st;
+    if ((st = fetch(h, h->d_scal, 27, s)) != GFF_OK) return st;
     for (int c = 0; c < 9; ++c) {
         rep.Pmacro[c] = s[c] / (double)N;
         rep.Fmacro[c] = s[9 + c] / (double)N;
+        h->prev_dFbar[c] = (s[9 + c] - s[18 + c]) / (double)N;
     }
+    h->have_prev = true;
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (report) *report = rep;
     return GFF_OK;

@@ -95,6 +95,10 @@ struct Tune {
     int t_inv;  // threads of k_plane_inv
 };
 
+struct Nine9 {
+    double v[9];
+};
+
 struct CPParamsDev {
     double gdot0, p, tau0, c, d;
 };
@@ -162,6 +166,12 @@ struct gff_handle {
     void* hostdata = nullptr;  // host copies of the orientations and phases
     gff::Tune tune[2] = {{512, 4, 256, 512}, {512, 8, 256, 512}};  // [0] FP64, [1] FP32
     bool tuned = false;
+    // learned warm start
+    float* d_gq = nullptr;       // [ngrains][5]: orientation quaternion (w, x, y, z) and phase
+    double* d_Fprev = nullptr;   // F before the last completed increment
+    bool have_prev = false;
+    double prev_dFbar[9] = {0};  // average F change of the last completed increment
+    struct gff_unet* unet = nullptr;
     std::string err;
 };
 
@@ -169,6 +179,9 @@ namespace gff {
 
 constexpr int NACC = 1 + 12 * 5;  // pcyc, W[12], gamma[12], gmin[12], gmax[12], sn[12]
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+
+// ---- learned warm start (unet.cu): adds G^(network guess) to h->d_Fk
+cudaError_t unet_warm_start(struct gff_unet* u, gff_handle* h, const double* dFbar);
 
 // ---- host helpers (api.cu)
 gff_status prepare_for_increments(gff_handle* h);

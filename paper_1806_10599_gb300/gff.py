@@ -71,6 +71,8 @@ class gff_step_report(ctypes.Structure):
         ("t_constitutive", c_double),
         ("t_residual", c_double),
         ("t_linear", c_double),
+        ("warm_start_used", c_int),
+        ("residual_first", c_double),
     ]
 
 
@@ -103,6 +105,19 @@ _SIGS = {
                                 c_void_p]),
     "gff_batch_run": (c_int, [c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p]),
+    "gff_unet_create": (c_int, [ctypes.c_uint64, _P(c_void_p)]),
+    "gff_unet_destroy": (None, [c_void_p]),
+    "gff_unet_last_error": (ctypes.c_char_p, [c_void_p]),
+    "gff_unet_num_params": (ctypes.c_size_t, [c_void_p]),
+    "gff_unet_get_params": (c_int, [c_void_p, c_void_p]),
+    "gff_unet_set_params": (c_int, [c_void_p, c_void_p]),
+    "gff_unet_save": (c_int, [c_void_p, ctypes.c_char_p]),
+    "gff_unet_load": (c_int, [c_void_p, ctypes.c_char_p]),
+    "gff_unet_eval_host": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_unet_add_sample": (c_int, [c_void_p, c_void_p]),
+    "gff_unet_num_samples": (c_int, [c_void_p]),
+    "gff_unet_train": (c_int, [c_void_p, c_int, c_double, c_void_p]),
+    "gff_set_warm_start": (c_int, [c_void_p, c_void_p, c_int]),
     "gff_reset_fips": (c_int, [c_void_p]),
     "gff_get_fips": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_save_state": (c_int, [c_void_p, ctypes.c_char_p]),
@@ -289,6 +304,89 @@ def gff_batch_run(handles, dt, Fbar, mask, Pbar, cycle_start=None, raise_on_erro
     if st != GFF_OK and raise_on_error:
         raise GffError(st, "gff_batch_run: per-RVE status %s; %s" % (stat.tolist(), gff_last_error(handles[0])))
     return Pm, [[reps[r * ns + k] for k in range(ns)] for r in range(n)], stat
+
+
+def _ucheck(u, st):
+    if st != GFF_OK:
+        msg = _lib.gff_unet_last_error(u)
+        raise GffError(st, msg.decode() if msg else "")
+    return st
+
+
+def gff_unet_create(seed=0):
+    u = c_void_p()
+    st = _lib.gff_unet_create(ctypes.c_uint64(seed), ctypes.byref(u))
+    if st != GFF_OK:
+        msg = _lib.gff_unet_last_error(u).decode() if u.value else ""
+        if u.value:
+            _lib.gff_unet_destroy(u)
+        raise GffError(st, msg)
+    return u
+
+
+def gff_unet_destroy(u):
+    _lib.gff_unet_destroy(u)
+
+
+def gff_unet_last_error(u):
+    return _lib.gff_unet_last_error(u).decode()
+
+
+def gff_unet_num_params(u):
+    return int(_lib.gff_unet_num_params(u))
+
+
+def gff_unet_get_params(u):
+    w = np.empty(gff_unet_num_params(u), dtype=np.float32)
+    _ucheck(u, _lib.gff_unet_get_params(u, w.ctypes.data_as(c_void_p)))
+    return w
+
+
+def gff_unet_set_params(u, w):
+    a, ap = _host(w, np.float32)
+    return _ucheck(u, _lib.gff_unet_set_params(u, ap))
+
+
+def gff_unet_save(u, path):
+    return _ucheck(u, _lib.gff_unet_save(u, str(path).encode()))
+
+
+def gff_unet_load(u, path):
+    return _ucheck(u, _lib.gff_unet_load(u, str(path).encode()))
+
+
+def gff_unet_eval_host(u, n, x, target=None):
+    """x [V][14] -> y [V][9]; with a target also (loss, grads)."""
+    V = n ** 3
+    xa, xp = _host(np.asarray(x).reshape(V, 14), np.float32)
+    y = np.empty((V, 9), dtype=np.float32)
+    if target is None:
+        _ucheck(u, _lib.gff_unet_eval_host(u, n, xp, None, y.ctypes.data_as(c_void_p), None, None))
+        return y
+    ta, tp = _host(np.asarray(target).reshape(V, 9), np.float32)
+    loss = c_double()
+    grads = np.empty(gff_unet_num_params(u), dtype=np.float32)
+    _ucheck(u, _lib.gff_unet_eval_host(u, n, xp, tp, y.ctypes.data_as(c_void_p), ctypes.byref(loss),
+                                       grads.ctypes.data_as(c_void_p)))
+    return y, loss.value, grads
+
+
+def gff_unet_add_sample(u, h):
+    return _ucheck(u, _lib.gff_unet_add_sample(u, h))
+
+
+def gff_unet_num_samples(u):
+    return int(_lib.gff_unet_num_samples(u))
+
+
+def gff_unet_train(u, steps, lr):
+    losses = np.zeros(max(steps, 1))
+    _ucheck(u, _lib.gff_unet_train(u, int(steps), float(lr), losses.ctypes.data_as(c_void_p)))
+    return losses[:steps]
+
+
+def gff_set_warm_start(h, u, mode):
+    return _check(h, _lib.gff_set_warm_start(h, u, int(mode)))
 
 
 def gff_reset_fips(h):

@@ -1,0 +1,124 @@
+"""Warm-start network on the GPU against the FP64 oracle (oracle/unet.py)
+with the same bfloat16 rounding points: forward output, loss and every
+parameter gradient; training lowers the loss; the solver reaches the same
+solution from the learned start as from the zero-fluctuation start.
+
+Tolerances: the GPU accumulates in FP32 where the oracle uses FP64, and a
+bfloat16 rounding can land on the other side of a tie, so outputs and
+gradients agree to relative L2 2e-2 / 5e-2, not to the last bit."""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import gff, gpu_materials, rel_l2, torch_cuda
+from oracle import unet as U
+from oracle.solver import CP_FCC
+from rve_inputs import cyclic_history, polycrystal
+
+pytestmark = pytest.mark.gpu
+
+
+def flat(p):
+    parts = []
+    for name, ci, co in U.LAYERS:
+        W, b = p[name]
+        parts += [W.ravel(), b]
+    W, b = p["head"]
+    parts += [W.ravel(), b]
+    return np.concatenate(parts)
+
+
+def unflat(w):
+    p, k = {}, 0
+    for name, ci, co in U.LAYERS + [U.HEAD]:
+        shape = (27, co, ci) if name != "head" else (co, ci)
+        m = int(np.prod(shape))
+        p[name] = (w[k:k + m].reshape(shape), w[k + m:k + m + co])
+        k += m + co
+    return p
+
+
+def test_forward_and_gradients_match_oracle():
+    torch_cuda()
+    g = gff()
+    n = 8
+    V = n ** 3
+    p = U.init_params(5)
+    rng = np.random.default_rng(6)
+    for name in p:  # non-zero biases exercise the bias paths
+        p[name] = (p[name][0], 0.1 * rng.standard_normal(p[name][1].shape))
+    x = rng.standard_normal((14, n, n, n))
+    t = 0.5 * rng.standard_normal((9, n, n, n))
+    u = g.gff_unet_create(1)
+    try:
+        assert g.gff_unet_num_params(u) == flat(p).size
+        g.gff_unet_set_params(u, flat(p).astype(np.float32))
+        assert np.array_equal(g.gff_unet_get_params(u), flat(p).astype(np.float32))
+        p32 = unflat(flat(p).astype(np.float32).astype(np.float64))
+        y, loss, grads = g.gff_unet_eval_host(u, n, x.reshape(14, V).T, t.reshape(9, V).T)
+        yo, cache = U.forward(p32, x, round_bf16=True)
+        lo, dy = U.mse(yo, t)
+        go = U.backward(p32, cache, dy, round_bf16=True)
+        assert rel_l2(y.T.reshape(9, n, n, n), yo) <= 2e-2
+        assert abs(loss - lo) <= 2e-2 * lo
+        gg = unflat(grads.astype(np.float64))
+        for name, _, _ in U.LAYERS + [U.HEAD]:
+            assert rel_l2(gg[name][0], go[name][0]) <= 5e-2, name
+            assert rel_l2(gg[name][1], go[name][1]) <= 5e-2, name
+    finally:
+        g.gff_unet_destroy(u)
+
+
+def _solve(g, ms, hist, u=None, mode=0, tol=1e-10):
+    h = g.create_rve(ms, gpu_materials({0: CP_FCC}), g.make_options(newton_tol=tol, cg_tol=1e-8))
+    if u is not None:
+        g.gff_set_warm_start(h, u, mode)
+    return h, g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+
+
+def test_training_lowers_the_loss_and_warm_start_keeps_the_solution(tmp_path):
+    torch_cuda()
+    g = gff()
+    hist = cyclic_history(0.01, 1).head(6)
+    u = g.gff_unet_create(3)
+    hs = []
+    try:
+        # training samples from the solver's own increments (two 16^3 RVEs)
+        for seed in (31, 32):
+            h = g.create_rve(polycrystal(16, 6, seed), gpu_materials({0: CP_FCC}), g.make_options(newton_tol=1e-8))
+            hs.append(h)
+            for k in range(hist.nsteps):
+                g.gff_step(h, hist.dt[k], hist.Fbar[k], hist.mask[k], hist.Pbar[k])
+                g.gff_unet_add_sample(u, h)
+        assert g.gff_unet_num_samples(u) == 12
+        losses = g.gff_unet_train(u, 120, 1e-3)
+        assert np.isfinite(losses).all()
+        assert losses[-12:].mean() < 0.5 * losses[:12].mean()
+        path = tmp_path / "w.bin"
+        g.gff_unet_save(u, path)
+        u2 = g.gff_unet_create(99)
+        g.gff_unet_load(u2, path)
+        assert np.array_equal(g.gff_unet_get_params(u2), g.gff_unet_get_params(u))
+        g.gff_unet_destroy(u2)
+
+        ms = polycrystal(16, 6, 33)  # held-out RVE
+        h0, (P0, r0) = _solve(g, ms, hist)
+        h2, (P2, r2) = _solve(g, ms, hist, u, mode=2)
+        h1, (P1, r1) = _solve(g, ms, hist, u, mode=1)
+        hs += [h0, h2, h1]
+        assert all(r.warm_start_used == 1 for r in r2)
+        # same increments solved to tolerance: same solution
+        for k in range(hist.nsteps):
+            assert np.linalg.norm(P2[k] - P0[k]) <= 1e-7 * np.linalg.norm(P0[k])
+        F0 = g.gff_get_field(h0, g.GFF_FIELD_F, ms.n_voxels)
+        F2 = g.gff_get_field(h2, g.GFF_FIELD_F, ms.n_voxels)
+        assert rel_l2(F2 - 1.0 * (np.arange(F2.size) % 1), F0) <= 1e-7
+        # mode 1: where the guess was not kept, the increment is the plain one, bit for bit
+        for k in range(hist.nsteps):
+            if r1[k].warm_start_used == 0 and all(r.warm_start_used == 0 for r in r1[:k]):
+                assert np.array_equal(P1[k], P0[k])
+            assert r1[k].residual_first <= r0[k].residual_first * (1 + 1e-12) or r1[k].warm_start_used == 0
+    finally:
+        for h in hs:
+            g.gff_destroy(h)
+        g.gff_unet_destroy(u)
