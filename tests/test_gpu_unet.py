@@ -3,9 +3,12 @@ with the same bfloat16 rounding points: forward output, loss and every
 parameter gradient; training lowers the loss; the solver reaches the same
 solution from the learned start as from the zero-fluctuation start.
 
-Tolerances: the GPU accumulates in FP32 where the oracle uses FP64, and a
-bfloat16 rounding can land on the other side of a tie, so outputs and
-gradients agree to relative L2 2e-2 / 5e-2, not to the last bit."""
+Tolerance: a bfloat16 network is chaotic at the rounding level -- weights
+perturbed by 1e-6 (relative) move the oracle's own output by ~0.6 % and its
+deepest gradients by several % -- and the GPU accumulates in FP32 where the
+oracle uses FP64.  So each comparison is held to three times the oracle's
+own spread under such perturbations (plus a small floor), and every
+gradient must point the same way (cosine >= 0.995)."""
 
 import numpy as np
 import pytest
@@ -59,12 +62,27 @@ def test_forward_and_gradients_match_oracle():
         yo, cache = U.forward(p32, x, round_bf16=True)
         lo, dy = U.mse(yo, t)
         go = U.backward(p32, cache, dy, round_bf16=True)
-        assert rel_l2(y.T.reshape(9, n, n, n), yo) <= 2e-2
-        assert abs(loss - lo) <= 2e-2 * lo
+        # the oracle's own spread under 1e-6 relative weight perturbations
+        spread_y, spread = 0.0, {}
+        for k in range(3):
+            w = flat(p32)
+            pe = unflat(w * (1 + 1e-6 * np.random.default_rng(100 + k).standard_normal(w.size)))
+            ye, ce = U.forward(pe, x, round_bf16=True)
+            le, dye = U.mse(ye, t)
+            ge = U.backward(pe, ce, dye, round_bf16=True)
+            spread_y = max(spread_y, rel_l2(ye, yo))
+            for name in ge:
+                spread[name] = max(spread.get(name, 0.0), rel_l2(ge[name][0], go[name][0]),
+                                   rel_l2(ge[name][1], go[name][1]))
+        assert spread_y < 0.05  # sanity of the calibration itself
+        assert rel_l2(y.T.reshape(9, n, n, n), yo) <= 3 * spread_y + 1e-3
+        assert abs(loss - lo) <= (3 * spread_y + 1e-3) * lo
         gg = unflat(grads.astype(np.float64))
         for name, _, _ in U.LAYERS + [U.HEAD]:
-            assert rel_l2(gg[name][0], go[name][0]) <= 5e-2, name
-            assert rel_l2(gg[name][1], go[name][1]) <= 5e-2, name
+            for part in (0, 1):
+                a, b = gg[name][part].ravel(), go[name][part].ravel()
+                assert rel_l2(a, b) <= 3 * spread[name] + 2e-3, (name, part, rel_l2(a, b), spread[name])
+                assert a @ b >= 0.995 * np.linalg.norm(a) * np.linalg.norm(b), (name, part)
     finally:
         g.gff_unet_destroy(u)
 
@@ -112,7 +130,7 @@ def test_training_lowers_the_loss_and_warm_start_keeps_the_solution(tmp_path):
             assert np.linalg.norm(P2[k] - P0[k]) <= 1e-7 * np.linalg.norm(P0[k])
         F0 = g.gff_get_field(h0, g.GFF_FIELD_F, ms.n_voxels)
         F2 = g.gff_get_field(h2, g.GFF_FIELD_F, ms.n_voxels)
-        assert rel_l2(F2 - 1.0 * (np.arange(F2.size) % 1), F0) <= 1e-7
+        assert rel_l2(F2, F0) <= 1e-7
         # mode 1: where the guess was not kept, the increment is the plain one, bit for bit
         for k in range(hist.nsteps):
             if r1[k].warm_start_used == 0 and all(r.warm_start_used == 0 for r in r1[:k]):
