@@ -199,7 +199,10 @@ gff_status gff_project_noalloc(const gff_grid* grid, int projection, int precisi
 /* One load increment (Sect. 2.1): macroscopic Fbar[9] on components with
  * mask[c] = 0, average stress Pbar[9] on components with mask[c] = 1.
  * Newton-CG to newton_tol, then internal variables and FIP accumulators are
- * committed.  On failure the committed state is unchanged.  report may be NULL. */
+ * committed.  If Newton or a return map fails, the increment is halved (dt/2,
+ * macroscopic targets interpolated from the committed state) and retried, up
+ * to opt.max_cuts levels (report->cuts counts the halvings); on final failure
+ * the committed state is unchanged.  report may be NULL. */
 gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], const uint8_t mask[9],
                     const double Pbar[9], gff_step_report* report);
 

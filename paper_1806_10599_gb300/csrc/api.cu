@@ -743,6 +743,25 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
         }
     } evg{ev};
+    int warm_used = 0;
+    double res_first = 0.0;
+    // the report is written on every exit, failed attempts included (cut-back adds them up)
+    struct RepGuard {
+        gff_step_report* r;
+        const int &newton, &cgsum, &warm_used;
+        const double &res, &t_const, &t_res, &t_lin, &res_first;
+        ~RepGuard() {
+            if (!r) return;
+            r->newton_iters = newton;
+            r->cg_iters = cgsum;
+            r->residual = res;
+            r->t_constitutive = t_const;
+            r->t_residual = t_res;
+            r->t_linear = t_lin;
+            r->warm_start_used = warm_used;
+            r->residual_first = res_first;
+        }
+    } repg{rep, newton, cgsum, warm_used, res, t_const, t_res, t_lin, res_first};
 
     // P, K at d_Fk and the residual b = -G_M(P) + M : Pbar with its norms
     auto evaluate = [&](bool warm_dg) -> gff_status {
@@ -774,8 +793,6 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     };
 
     // learned warm start: mode 1 keeps it only if its residual beats the zero start's, mode 2 always
-    int warm_used = 0;
-    double res_first = 0.0;
     const int wmode = h->unet ? h->opt.warm_start : 0;
     if (wmode) {
         double res_zero = -1.0;
@@ -829,16 +846,6 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         cgsum += its;
         ++newton;
     }
-    if (rep) {
-        rep->newton_iters = newton;
-        rep->cg_iters = cgsum;
-        rep->residual = res;
-        rep->t_constitutive = t_const;
-        rep->t_residual = t_res;
-        rep->t_linear = t_lin;
-        rep->warm_start_used = warm_used;
-        rep->residual_first = res_first;
-    }
     if (!conv) return fail(h, GFF_ERR_NO_CONVERGENCE, "Newton: residual %.3e after %d iterations", res, newton);
     return GFF_OK;
 }
@@ -859,23 +866,13 @@ gff_status prepare_for_increments(gff_handle* h) {
 void set_error(gff_handle* h, const char* msg) { h->err = msg; }
 }  // namespace gff
 
-GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], const uint8_t mask[9], const double Pbar[9],
-                    gff_step_report* report) {
-    if (!h || !Fbar || !mask || !Pbar || !(dt > 0)) return fail(h, GFF_ERR_ARG, "bad step args");
-    gff_status st = ensure_grains(h);
-    if (st != GFF_OK) return st;
-    const auto t0 = std::chrono::steady_clock::now();
-    gff_step_report rep;
-    std::memset(&rep, 0, sizeof rep);
-    if (!h->tuned) GFF_TRY(autotune_galerkin(h));
-    st = newton_increment(h, dt, Fbar, mask, Pbar, &rep);
-    if (st != GFF_OK) {
-        if (report) *report = rep;
-        return st;
-    }
+namespace {
+
+// Commit the converged iterate: F, internal variables, FIP accumulators; the
+// previous F is kept for training samples of the warm-start network.
+gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
     const long long N = h->N;
-    // commit: F, P (already for the converged F), internal variables, FIPs;
-    // the previous F is kept for training samples of the warm-start network
+    gff_status st;
     GFF_TRY(launch_sum9(h->d_F, N, h->d_red, h->d_scal + 18, h->stream));
     GFF_TRY(cudaMemcpyAsync(h->d_Fprev, h->d_F, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     GFF_TRY(cudaMemcpyAsync(h->d_F, h->d_Fk, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -892,14 +889,66 @@ GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], c
     GFF_TRY(launch_sum9(h->d_F, N, h->d_red + 9 * RED_BLOCKS, h->d_scal + 9, h->stream));
     if ((st = fetch(h, h->d_scal, 27, s)) != GFF_OK) return st;
     for (int c = 0; c < 9; ++c) {
-        rep.Pmacro[c] = s[c] / (double)N;
-        rep.Fmacro[c] = s[9 + c] / (double)N;
+        rep->Pmacro[c] = s[c] / (double)N;
+        rep->Fmacro[c] = s[9 + c] / (double)N;
         h->prev_dFbar[c] = (s[9 + c] - s[18 + c]) / (double)N;
+        h->Pmacro_committed[c] = rep->Pmacro[c];
     }
     h->have_prev = true;
+    return GFF_OK;
+}
+
+// One increment; when Newton or a return map fails, the increment is split
+// into two halves (dt/2; macroscopic F and P interpolated from the last
+// committed state) and retried, down to max_cuts levels.  Nothing is
+// committed by a failed attempt, so each retry starts from the same state.
+gff_status step_with_cuts(gff_handle* h, double dt, const double* Fbar, const uint8_t* mask, const double* Pbar,
+                          int depth, gff_step_report* acc) {
+    gff_step_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    gff_status st = newton_increment(h, dt, Fbar, mask, Pbar, &rep);
+    acc->newton_iters += rep.newton_iters;
+    acc->cg_iters += rep.cg_iters;
+    acc->t_constitutive += rep.t_constitutive;
+    acc->t_residual += rep.t_residual;
+    acc->t_linear += rep.t_linear;
+    acc->residual = rep.residual;
+    if (depth == 0) {
+        acc->warm_start_used = rep.warm_start_used;
+        acc->residual_first = rep.residual_first;
+    }
+    if (st == GFF_OK) return commit_increment(h, acc);
+    if ((st != GFF_ERR_CP_FAIL && st != GFF_ERR_NO_CONVERGENCE) || depth >= h->opt.max_cuts) return st;
+    // macroscopic state of the last commit
+    double Fsum[9];
+    GFF_TRY(launch_sum9(h->d_F, h->N, h->d_red, h->d_scal, h->stream));
+    if ((st = fetch(h, h->d_scal, 9, Fsum)) != GFF_OK) return st;
+    double Fmid[9], Pmid[9];
+    for (int c = 0; c < 9; ++c) {
+        Fmid[c] = 0.5 * (Fsum[c] / (double)h->N + Fbar[c]);
+        Pmid[c] = 0.5 * (h->Pmacro_committed[c] + Pbar[c]);
+    }
+    ++acc->cuts;
+    h->err.clear();
+    if ((st = step_with_cuts(h, 0.5 * dt, Fmid, mask, Pmid, depth + 1, acc)) != GFF_OK) return st;
+    return step_with_cuts(h, 0.5 * dt, Fbar, mask, Pbar, depth + 1, acc);
+}
+
+}  // namespace
+
+GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], const uint8_t mask[9], const double Pbar[9],
+                    gff_step_report* report) {
+    if (!h || !Fbar || !mask || !Pbar || !(dt > 0)) return fail(h, GFF_ERR_ARG, "bad step args");
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    gff_step_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    if (!h->tuned) GFF_TRY(autotune_galerkin(h));
+    st = step_with_cuts(h, dt, Fbar, mask, Pbar, 0, &rep);
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (report) *report = rep;
-    return GFF_OK;
+    return st;
 }
 
 GFF_EXPORT gff_status gff_run_history(gff_handle* h, int nsteps, const double* dt, const double* Fbar, const uint8_t* mask,

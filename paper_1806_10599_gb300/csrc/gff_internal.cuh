@@ -171,6 +171,7 @@ struct gff_handle {
     double* d_Fprev = nullptr;   // F before the last completed increment
     bool have_prev = false;
     double prev_dFbar[9] = {0};  // average F change of the last completed increment
+    double Pmacro_committed[9] = {0};  // average P of the committed state
     struct gff_unet* unet = nullptr;
     std::string err;
 };

@@ -391,7 +391,7 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
     bool conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh);
     if (!conv) {  // fall back: exact Newton from dg = 0
         for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
-        conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, false, 100, dg, st, chi, dh);
+        conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, false, 300, dg, st, chi, dh);
     }
     out.ok = conv;
     double FeS[9];

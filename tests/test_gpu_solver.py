@@ -156,3 +156,48 @@ def test_save_load_resume_is_bitwise(tmp_path):
     finally:
         g.gff_destroy(h1)
         g.gff_destroy(h2)
+
+
+def test_cut_back_reaches_the_uncut_solution():
+    """A hyperelastic increment too large for a small Newton budget is split
+    into halves; the elastic solution does not depend on the path, so the cut
+    step must end where one generous uncut step ends.  Without cuts the same
+    step fails and leaves the committed state unchanged."""
+    torch_cuda()
+    g = gff()
+    ms = polycrystal(16, 6, 41)
+    mats = gpu_materials({0: SVK_CUBIC})
+    N = ms.n_voxels
+    Fbar = np.eye(3).ravel().copy()
+    Fbar[0] += 0.08
+    Fbar[4] -= 0.03
+    mask = np.zeros(9, np.uint8)
+    Pbar = np.zeros(9)
+
+    def run(newton_max, max_cuts):
+        h = g.create_rve(ms, mats, g.make_options(newton_tol=1e-10, cg_tol=1e-4, newton_max=newton_max,
+                                                  max_cuts=max_cuts))
+        try:
+            try:
+                rep = g.gff_step(h, 1.0, Fbar, mask, Pbar)
+            except g.GffError as e:
+                return e.status, None, g.gff_get_field(h, g.GFF_FIELD_F, N)
+            return 0, rep, g.gff_get_field(h, g.GFF_FIELD_F, N)
+        finally:
+            g.gff_destroy(h)
+
+    st, ref, F_ref = run(60, 0)
+    assert st == 0 and ref.cuts == 0
+    for m in range(ref.newton_iters - 1, 0, -1):
+        st0, _, F0 = run(m, 0)
+        assert st0 == g.GFF_ERR_NO_CONVERGENCE
+        assert np.array_equal(F0, np.tile(np.eye(3).reshape(9, 1), (1, N)).ravel())  # nothing committed
+        st, rep, F = run(m, 4)
+        if st == 0:
+            assert rep.cuts >= 1
+            assert np.allclose(rep.Fmacro, Fbar, rtol=0, atol=1e-12)
+            assert rel_l2(F, F_ref) <= 1e-8
+            assert np.linalg.norm(np.array(rep.Pmacro) - ref.Pmacro) <= 1e-8 * np.linalg.norm(ref.Pmacro)
+            break
+    else:
+        pytest.fail("no Newton budget below %d iterations was rescued by cut-back" % ref.newton_iters)
