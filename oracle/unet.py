@@ -10,8 +10,9 @@ t = 9 (dz+1) + 3 (dy+1) + (dx+1), d_t = (dz, dy, dx) in {-1, 0, 1}^3.
 `bf16` rounds a tensor to bfloat16 (round to nearest even), used to mirror
 the points where the GPU stores bfloat16.
 
-Architecture (4 levels, channels 16, 32, 64, 64; ReLU after every 3x3x3
-conv; 2x2x2 average pooling down, nearest-neighbour upsampling up, skip
+Architecture (4 levels, channels 16, 32, 64, 64; leaky ReLU with slope
+1/8 on the negative side after every 3x3x3 conv (plain ReLU let whole layers
+die in training; the power of two keeps slope * bfloat16 exact); 2x2x2 average pooling down, nearest-neighbour upsampling up, skip
 connections by channel concatenation; a 1x1x1 head to 9 outputs):
   e1 = c(c(x, 14->16), 16->16)          at n
   e2 = c(c(pool e1, 16->32), 32->32)    at n/2
@@ -37,6 +38,7 @@ LAYERS = [  # (name, cin, cout)
     ("d1a", 48, 16), ("d1b", 16, 16),
 ]
 HEAD = ("head", 16, 9)
+SLOPE = 0.125  # leaky ReLU slope for z <= 0
 
 
 def bf16(a):
@@ -119,7 +121,7 @@ def forward(p, x, round_bf16=False):
     def cr(name, a):
         W, b = p[name]
         z = conv(a, R(W), b)
-        out = R(np.maximum(z, 0.0))
+        out = R(np.where(z > 0, z, SLOPE * z))
         cache[name] = (a, out)
         return out
 
@@ -150,7 +152,7 @@ def backward(p, cache, dy, round_bf16=False):
     def cb(name, da_out):
         a_in, out = cache[name]
         W, b = p[name]
-        dz = da_out * (out > 0)
+        dz = da_out * np.where(out > 0, 1.0, SLOPE)
         g[name] = (conv_grad_weight(a_in, dz), dz.sum(axis=(1, 2, 3)))
         return R(conv_grad_input(dz, R(W)))
 

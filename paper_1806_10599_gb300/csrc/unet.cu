@@ -164,7 +164,7 @@ gff_status ensure_buffers(gff_unet* u, int n) {
 
 View slice(View v, int c0) { return View{v.p + c0, v.s}; }
 
-// forward conv of layer l: in (cinp channels) -> out (cout channels), ReLU
+// forward conv of layer l: in (cinp channels) -> out (cout channels), leaky ReLU
 cudaError_t conv_fwd(gff_unet* u, int l, View in, View out, Dims d, cudaStream_t st) {
     const int cinp = pad16(kL[l].cin), cout = kL[l].cout;
     const bf16* W = u->d_wf + u->off_w[l];
@@ -237,7 +237,7 @@ gff_status forward(gff_unet* u, View X, cudaStream_t st) {
     return GFF_OK;
 }
 
-// one conv-ReLU backward: dz = da (.) (out > 0); weight/bias grads; din (if wanted)
+// one conv-activation backward: dz = da (.) (out > 0 ? 1 : LEAK); weight/bias grads; din (if wanted)
 gff_status back_layer(gff_unet* u, int l, View in, View out, View da, View* din, Dims d, cudaStream_t st) {
     const int cout = kL[l].cout;
     View dz{u->DZ.p, cout};

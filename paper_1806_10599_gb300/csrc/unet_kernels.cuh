@@ -40,6 +40,9 @@ __device__ __forceinline__ long long neighbour(const Dims& d, long long v, int t
     return ((long long)z * d.ny + y) * d.nx + x;
 }
 
+// negative-side slope of the activation: plain ReLU let whole layers die in training
+constexpr float LEAK = 0.125f;
+
 __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -50,7 +53,8 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
 
 // out[v, co] = act(bias[co] + sum_{t, ci} W[t][co][ci] in[nb(v, t), ci])
 // in: cin channels (multiple of 16) at stride sin; W: [27][NT*8][cin] bf16;
-// out: NT*8 channels at stride sout.  RELU: max(., 0).  Block = 4 warps = 64 voxels.
+// out: NT*8 channels at stride sout.  RELU: leaky ReLU (slope LEAK for z <= 0).
+// Block = 4 warps = 64 voxels.
 template <int NT, bool RELU>
 __global__ void __launch_bounds__(128) k_conv3(const bf16* __restrict__ in, int sin, int cin,
                                                const bf16* __restrict__ W, const float* __restrict__ bias,
@@ -93,17 +97,17 @@ __global__ void __launch_bounds__(128) k_conv3(const bf16* __restrict__ in, int 
         const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
         float r0 = acc[j][0] + b0, r1 = acc[j][1] + b1, r2 = acc[j][2] + b0, r3 = acc[j][3] + b1;
         if (RELU) {
-            r0 = fmaxf(r0, 0.f);
-            r1 = fmaxf(r1, 0.f);
-            r2 = fmaxf(r2, 0.f);
-            r3 = fmaxf(r3, 0.f);
+            r0 = r0 > 0.f ? r0 : LEAK * r0;
+            r1 = r1 > 0.f ? r1 : LEAK * r1;
+            r2 = r2 > 0.f ? r2 : LEAK * r2;
+            r3 = r3 > 0.f ? r3 : LEAK * r3;
         }
         if (oka) *reinterpret_cast<__nv_bfloat162*>(out + va * sout + co) = __floats2bfloat162_rn(r0, r1);
         if (okb) *reinterpret_cast<__nv_bfloat162*>(out + vb * sout + co) = __floats2bfloat162_rn(r2, r3);
     }
 }
 
-// dz = da * (act > 0), C channels
+// dz = da * (act > 0 ? 1 : LEAK), C channels (exact in bfloat16: LEAK is a power of two)
 __global__ void k_relu_mask(const bf16* __restrict__ da, int sda, const bf16* __restrict__ act, int sact,
                             bf16* __restrict__ dz, int sdz, int C, long long V) {
     const long long n = V * C;
@@ -111,7 +115,7 @@ __global__ void k_relu_mask(const bf16* __restrict__ da, int sda, const bf16* __
         const long long v = i / C;
         const int c = (int)(i - v * C);
         const float a = __bfloat162float(act[v * sact + c]);
-        dz[v * sdz + c] = a > 0.f ? da[v * sda + c] : __float2bfloat16(0.f);
+        dz[v * sdz + c] = a > 0.f ? da[v * sda + c] : __float2bfloat16(LEAK * __bfloat162float(da[v * sda + c]));
     }
 }
 

@@ -96,6 +96,7 @@ def main():
         print(json.dumps({
             "samples": g.gff_unet_num_samples(u), "data_s": t1 - t0, "train_s": t2 - t1,
             "train_steps": a.steps, "loss_first": float(np.mean(losses[:50])), "loss_last": float(np.mean(losses[-50:])),
+            "loss_curve": [float(np.mean(c)) for c in np.array_split(losses, 10)],
             "eval": ev,
         }))
     finally:

@@ -125,6 +125,8 @@ def test_training_lowers_the_loss_and_warm_start_keeps_the_solution(tmp_path):
         h1, (P1, r1) = _solve(g, ms, hist, u, mode=1)
         hs += [h0, h2, h1]
         assert all(r.warm_start_used == 1 for r in r2)
+        # the trained network proposes a non-trivial (non-constant) fluctuation: the first residual moves
+        assert all(a.residual_first != b.residual_first for a, b in zip(r2, r0))
         # same increments solved to tolerance: same solution
         for k in range(hist.nsteps):
             assert np.linalg.norm(P2[k] - P0[k]) <= 1e-7 * np.linalg.norm(P0[k])
