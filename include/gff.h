@@ -85,9 +85,10 @@ typedef struct {
     double newton_tol; /* stop when ||b||_2 / ||P||_2 <= newton_tol                */
     double cg_tol;     /* CG stops when ||r|| <= max(cg_tol ||b||, 0.1 newton_tol ||P||) */
     int newton_max, cg_max;
-    int max_cuts;      /* time-step halvings allowed after a CP failure            */
+    int max_cuts;      /* increment halvings allowed after a CP or Newton failure   */
     int warm_start;    /* learned initial guess (gff_set_warm_start): 0 off, 1 used
-                          only if its residual beats the zero start's, 2 always  */
+                          only if its residual beats the zero start's, 2 always
+                          (both drop a guess the return map cannot take)      */
     double fs_k, fs_sigma_y; /* Fatemi-Socie constants                             */
 } gff_options;
 
@@ -266,8 +267,9 @@ int gff_unet_num_samples(const gff_unet* u);
 gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* losses);
 /* Use u for the initial guess of h's increments: mode 0 off, 1 keep the
  * guess only when its first residual is below the zero start's (costs one
- * more constitutive evaluation per increment), 2 always.  gff_batch_run
- * does not use the warm start. */
+ * more constitutive evaluation per increment), 2 always.  In both modes a
+ * guess at which a return map fails, or whose residual is not finite, is
+ * replaced by the zero start.  gff_batch_run does not use the warm start. */
 gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode);
 
 /* Fatigue indicator parameters (Sect. 3.3, Eqs. eqplas, strainenergy, Pmax).

@@ -726,6 +726,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     for (int c = 0; c < 9; ++c) {
         d9[c] = mask[c] ? 0.0 : Fbar[c] - Fsum[c] / (double)N;
         add9[c] = mask[c] ? Pbar[c] : 0.0;
+        h->cur_d9[c] = d9[c];
     }
     GFF_TRY(launch_add_const9(h->d_Fk, h->d_F, d9, N, h->stream));
     const ProjArgs pa = proj_args(h, mask);
@@ -802,9 +803,13 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         }
         cudaError_t e = unet_warm_start(h->unet, h, d9);
         if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "warm start: %s", cudaGetErrorString(e));
-        if ((st = evaluate(false)) != GFF_OK) return st;
+        st = evaluate(false);
+        if (st != GFF_OK && st != GFF_ERR_CP_FAIL) return st;
         warm_used = 1;
-        if (wmode == 1 && !(res < res_zero)) {
+        // a guess the return map cannot take, or one with a non-finite residual, is dropped in
+        // either mode; mode 1 also drops a guess that does not beat the zero start
+        if (st == GFF_ERR_CP_FAIL || !std::isfinite(res) || (wmode == 1 && !(res < res_zero))) {
+            h->err.clear();
             GFF_TRY(launch_add_const9(h->d_Fk, h->d_F, d9, N, h->stream));
             if ((st = evaluate(false)) != GFF_OK) return st;
             warm_used = 0;
@@ -893,6 +898,7 @@ gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
         rep->Fmacro[c] = s[9 + c] / (double)N;
         h->prev_dFbar[c] = (s[9 + c] - s[18 + c]) / (double)N;
         h->Pmacro_committed[c] = rep->Pmacro[c];
+        h->prev_d9[c] = h->cur_d9[c];
     }
     h->have_prev = true;
     return GFF_OK;

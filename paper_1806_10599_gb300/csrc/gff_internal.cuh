@@ -172,6 +172,8 @@ struct gff_handle {
     bool have_prev = false;
     double prev_dFbar[9] = {0};  // average F change of the last completed increment
     double Pmacro_committed[9] = {0};  // average P of the committed state
+    double cur_d9[9] = {0};   // prescribed average F change of the increment being solved
+    double prev_d9[9] = {0};  // the same for the last completed increment
     struct gff_unet* unet = nullptr;
     std::string err;
 };

@@ -4,8 +4,9 @@
 // guess open, Sect. 2.1; this network is not in the paper).
 //
 // Input per voxel (14 channels): the grain's orientation quaternion (4), its
-// phase (1) and the macroscopic increment dFbar / |dFbar| (9).  Output (9):
-// (F_k - F_{k-1} - dFbar) / |dFbar|.  bfloat16 weights and activations, FP32
+// phase (1) and the prescribed macroscopic increment d / |d| (9; d is dFbar
+// on the strain-controlled components, 0 on the stress-controlled ones).
+// Output (9): the fluctuation increment (F_k - F_{k-1} - dFbar) / |d|.  bfloat16 weights and activations, FP32
 // accumulation on the tensor cores (unet_kernels.cuh), FP32 master weights
 // updated by Adam.  The whole network is periodic (wrapping 3x3x3 taps,
 // 2x2x2 pooling, nearest upsampling), so one set of weights serves any grid
@@ -298,7 +299,7 @@ __global__ void k_unet_input(const int* __restrict__ gid, const float* __restric
     }
 }
 
-// target[v][c] = (F[c][v] - Fprev[c][v] - dFbar[c]) / |dFbar|
+// target[v][c] = (F[c][v] - Fprev[c][v] - dFbar[c]) / |d|
 __global__ void k_unet_target(const double* __restrict__ F, const double* __restrict__ Fp, Nine9 dF, double inv,
                               float* __restrict__ t, long long V) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
@@ -505,10 +506,11 @@ UEXPORT gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h) {
     if (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz || h->grid.nx % 8)
         return ufail(u, GFF_ERR_ARG, "samples need cubic grids with n divisible by 8");
     if (u->sample_n && u->sample_n != h->grid.nx) return ufail(u, GFF_ERR_ARG, "all samples must share one grid");
+    // the network sees the prescribed (strain-controlled) increment, as in gff::unet_warm_start
     double nrm = 0.0;
-    for (int c = 0; c < 9; ++c) nrm += h->prev_dFbar[c] * h->prev_dFbar[c];
+    for (int c = 0; c < 9; ++c) nrm += h->prev_d9[c] * h->prev_d9[c];
     nrm = std::sqrt(nrm);
-    if (!(nrm > 0)) return ufail(u, GFF_ERR_ARG, "zero macroscopic increment");
+    if (!(nrm > 0)) return ufail(u, GFF_ERR_ARG, "no prescribed strain increment");
     const long long V = h->N;
     bf16* x = nullptr;
     float* t = nullptr;
@@ -520,7 +522,7 @@ UEXPORT gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h) {
     }
     Nine9 dfn, dF;
     for (int c = 0; c < 9; ++c) {
-        dfn.v[c] = h->prev_dFbar[c] / nrm;
+        dfn.v[c] = h->prev_d9[c] / nrm;
         dF.v[c] = h->prev_dFbar[c];
     }
     k_unet_input<<<grid_of(V), 256, 0, h->stream>>>(h->d_gid, h->d_gq, dfn, x, V);

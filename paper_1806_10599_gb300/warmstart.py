@@ -50,24 +50,33 @@ def evaluate(u, n=128, ngrains=500, seed=5, increments=20, eps=0.01, modes=(0, 1
     out = {}
     for mode in modes:
         h = _rve(n, ngrains, seed)
+        reps, Pm = [], []
         try:
             if mode:
                 g.gff_set_warm_start(h, u, mode)
             g.gff_autotune(h)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            Pm, reps = g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+            for k in range(hist.nsteps):
+                reps.append(g.gff_step(h, hist.dt[k], hist.Fbar[k], hist.mask[k], hist.Pbar[k]))
+                Pm.append(np.array(reps[-1].Pmacro))
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
+        except g.GffError as e:
+            out["mode%d" % mode] = {"failed_at": len(reps), "error": str(e)}
+            continue
         finally:
             g.gff_destroy(h)
         out["mode%d" % mode] = {
             "s_per_increment": dt / hist.nsteps,
             "newton_mean": float(np.mean([r.newton_iters for r in reps])),
             "cg_mean": float(np.mean([r.cg_iters for r in reps])),
+            "cuts": int(sum(r.cuts for r in reps)),
             "residual_first_mean": float(np.mean([r.residual_first for r in reps])),
             "warm_used": int(sum(r.warm_start_used for r in reps)),
             "P11_MPa_last": float(Pm[-1][0] / 1e6),
+            "newton_per_increment": [r.newton_iters for r in reps],
+            "residual_first": [r.residual_first for r in reps],
         }
     return out
 
@@ -92,6 +101,8 @@ def main():
         t2 = time.perf_counter()
         if a.weights:
             g.gff_unet_save(u, a.weights)
+        print(json.dumps({"samples": g.gff_unet_num_samples(u), "data_s": t1 - t0, "train_s": t2 - t1,
+                          "loss_curve": [float(np.mean(c)) for c in np.array_split(losses, 10)]}), flush=True)
         ev = evaluate(u, a.eval_n, a.eval_grains, increments=a.eval_increments)
         print(json.dumps({
             "samples": g.gff_unet_num_samples(u), "data_s": t1 - t0, "train_s": t2 - t1,

@@ -41,10 +41,10 @@ def unflat(w):
     return p
 
 
-def test_forward_and_gradients_match_oracle():
+@pytest.mark.parametrize("n", [8, 32])  # 32^3: several voxel chunks per weight-gradient tap
+def test_forward_and_gradients_match_oracle(n):
     torch_cuda()
     g = gff()
-    n = 8
     V = n ** 3
     p = U.init_params(5)
     rng = np.random.default_rng(6)
