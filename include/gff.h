@@ -52,6 +52,7 @@ typedef enum {
 
 enum { GFF_PROJ_CONTINUOUS = 0, GFF_PROJ_DISCRETE = 1 };
 enum { GFF_PREC_FP64 = 0, GFF_PREC_MIXED = 1 };
+enum { GFF_WARM_OFF = 0, GFF_WARM_NET_IF_BETTER = 1, GFF_WARM_NET = 2, GFF_WARM_EXTRAPOLATE = 3 };
 enum { GFF_MAT_SVK_CUBIC = 0, GFF_MAT_SVK_ISO = 1, GFF_MAT_CP_FCC = 2 };
 enum {
     GFF_FIELD_F = 0,      /* deformation gradient, 9 per voxel          */
@@ -86,9 +87,9 @@ typedef struct {
     double cg_tol;     /* CG stops when ||r|| <= max(cg_tol ||b||, 0.1 newton_tol ||P||) */
     int newton_max, cg_max;
     int max_cuts;      /* increment halvings allowed after a CP or Newton failure   */
-    int warm_start;    /* learned initial guess (gff_set_warm_start): 0 off, 1 used
-                          only if its residual beats the zero start's, 2 always
-                          (both drop a guess the return map cannot take)      */
+    int warm_start;    /* initial guess (gff_set_warm_start): 0 zero start, 1
+                          network if its residual beats the zero start's, 2
+                          network, 3 extrapolation of the last increment     */
     double fs_k, fs_sigma_y; /* Fatemi-Socie constants                             */
 } gff_options;
 
@@ -103,7 +104,7 @@ typedef struct {
     double t_constitutive; /* device time in constitutive updates, s        */
     double t_residual;     /* device time in residual evaluations, s         */
     double t_linear;       /* device time in the CG solves, s                */
-    int warm_start_used;   /* 1: the Newton iteration started from the network's guess */
+    int warm_start_used;   /* 1: the Newton iteration started from the warm-start guess */
     double residual_first; /* ||b|| / ||P|| at the start the Newton iteration used     */
 } gff_step_report;
 
@@ -233,16 +234,23 @@ gff_status gff_batch_run(int n, gff_handle* const* hs, int nsteps, const double*
                          double* Pmacro_out, gff_step_report* reports, gff_status* per_rve);
 
 /* ------------------------------------------------------------------------
- * Learned warm start (not in the paper; Sect. 2.1 leaves the Newton initial
- * guess open).  A 4-level periodic 3D U-Net (channels 16, 32, 64, 64) maps,
- * per voxel, the grain orientation quaternion (4), the phase (1) and the
- * macroscopic increment direction dFbar/|dFbar| (9) to the fluctuation
- * increment (F_k - F_{k-1} - dFbar)/|dFbar| (9).  The guess is projected
- * with G^ (compatible, zero mean) and added to the zero-fluctuation start.
- * bfloat16 weights/activations, FP32 accumulation on the tensor cores, FP32
- * master weights and Adam.  Grids must be cubic with n divisible by 8.
+ * Warm starts (not in the paper; Sect. 2.1 leaves the Newton initial guess
+ * open).  With d_k the prescribed macroscopic increment of increment k (dFbar
+ * on strain-controlled components, 0 on stress-controlled ones) and
+ * y_k = (F_k - F_{k-1} - dFbar_k) / |d_k| its normalised fluctuation
+ * increment, the guess for increment k is F_{k-1} + d_k + G^(|d_k| y~) with
+ *   extrapolation (mode 3):  y~ = s y_{k-1},  s = (d_k . d_{k-1}) / (|d_k| |d_{k-1}|)
+ *   network (modes 1, 2):    y~ = s y_{k-1} + U(x),
+ * G^ projecting onto compatible zero-mean fields.  U is a 4-level periodic
+ * 3D U-Net (channels 16, 32, 64, 64; leaky ReLU) whose 32 input channels per
+ * voxel are the grain orientation quaternion (4), the phase (1), d_k/|d_k|
+ * (9), y_{k-1} (9) and d_{k-1}/|d_{k-1}| (9) (zeros without history); it is
+ * trained on y_k - s y_{k-1}.  bfloat16 weights/activations, FP32
+ * accumulation on the tensor cores, FP32 master weights and Adam.  Grids
+ * must be cubic with n divisible by 8.
  * ------------------------------------------------------------------------ */
-gff_status gff_unet_create(uint64_t seed, gff_unet** out); /* He-uniform init from SplitMix64(seed) */
+/* He-uniform convolution weights from SplitMix64(seed); zero biases and head */
+gff_status gff_unet_create(uint64_t seed, gff_unet** out);
 void gff_unet_destroy(gff_unet* u);
 const char* gff_unet_last_error(const gff_unet* u);
 size_t gff_unet_num_params(const gff_unet* u);
@@ -253,23 +261,28 @@ gff_status gff_unet_get_params(gff_unet* u, float* host);
 gff_status gff_unet_set_params(gff_unet* u, const float* host);
 gff_status gff_unet_save(gff_unet* u, const char* path);
 gff_status gff_unet_load(gff_unet* u, const char* path);
-/* Network output y [V][9] for host inputs x [V][14] on an n^3 grid; with a
+/* Network output y [V][9] for host inputs x [V][32] on an n^3 grid; with a
  * target [V][9] also the mean-squared-error loss and all parameter gradients
  * (order of gff_unet_get_params).  target, loss, grads may be NULL. */
 gff_status gff_unet_eval_host(gff_unet* u, int n, const float* x, const float* target, float* y,
                               double* loss, float* grads);
-/* Keep the last completed increment of h (inputs, fluctuation-increment
- * target) as a training sample on the device; all samples share one grid. */
+/* Keep the last completed increment k of h (inputs from d_k, y_{k-1},
+ * d_{k-1}; target y_k - s y_{k-1}) as a training sample on the device; all
+ * samples share one grid.  The increment must have a prescribed strain
+ * increment (|d_k| > 0). */
 gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h);
 int gff_unet_num_samples(const gff_unet* u);
-/* `steps` Adam steps (lr, betas 0.9/0.999), one sample per step, shuffled
- * epochs; losses (host, steps, may be NULL) receives each step's loss. */
+/* `steps` Adam steps (peak lr with a cosine decay to 0 over the steps, betas
+ * 0.9/0.999, gradients clipped to global norm 1), one sample per step,
+ * shuffled epochs; losses (host, steps, may be NULL) receives each step's
+ * loss. */
 gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* losses);
-/* Use u for the initial guess of h's increments: mode 0 off, 1 keep the
- * guess only when its first residual is below the zero start's (costs one
- * more constitutive evaluation per increment), 2 always.  In both modes a
- * guess at which a return map fails, or whose residual is not finite, is
- * replaced by the zero start.  gff_batch_run does not use the warm start. */
+/* Initial guess of h's increments: mode 0 zero-fluctuation start; 1 network
+ * guess, kept only when its first residual is below the zero start's (costs
+ * one more constitutive evaluation per increment); 2 network guess always;
+ * 3 extrapolation (u may be NULL).  In every mode a guess at which a return
+ * map fails, or whose residual is not finite, is replaced by the zero start.
+ * gff_batch_run does not use warm starts. */
 gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode);
 
 /* Fatigue indicator parameters (Sect. 3.3, Eqs. eqplas, strainenergy, Pmax).

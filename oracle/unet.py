@@ -4,6 +4,12 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Not in the paper: the
 network proposes the fluctuation-strain increment that starts the Newton
 iteration of an increment (Sect. 2.1 leaves the initial guess open).
 
+Input (IN_CH = 32 channels per voxel): the grain's orientation quaternion
+(4), its phase (1), the prescribed macroscopic increment direction (9), the
+previous increment's normalised fluctuation increment (9) and that
+increment's direction (9).  The network itself is generic in these
+channels; what they hold matters only to the solver.
+
 Tensors are (C, nz, ny, nx).  A convolution is periodic (indices wrap) with
 3x3x3 taps: y[o, p] = b[o] + sum_{t, i} W[t, o, i] x[i, p + d_t], tap
 t = 9 (dz+1) + 3 (dy+1) + (dx+1), d_t = (dz, dy, dx) in {-1, 0, 1}^3.
@@ -14,7 +20,7 @@ Architecture (4 levels, channels 16, 32, 64, 64; leaky ReLU with slope
 1/8 on the negative side after every 3x3x3 conv (plain ReLU let whole layers
 die in training; the power of two keeps slope * bfloat16 exact); 2x2x2 average pooling down, nearest-neighbour upsampling up, skip
 connections by channel concatenation; a 1x1x1 head to 9 outputs):
-  e1 = c(c(x, 14->16), 16->16)          at n
+  e1 = c(c(x, 32->16), 16->16)          at n
   e2 = c(c(pool e1, 16->32), 32->32)    at n/2
   e3 = c(c(pool e2, 32->64), 64->64)    at n/4
   e4 = c(c(pool e3, 64->64), 64->64)    at n/8
@@ -29,7 +35,7 @@ import numpy as np
 TAPS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
 
 LAYERS = [  # (name, cin, cout)
-    ("e1a", 14, 16), ("e1b", 16, 16),
+    ("e1a", 32, 16), ("e1b", 16, 16),
     ("e2a", 16, 32), ("e2b", 32, 32),
     ("e3a", 32, 64), ("e3b", 64, 64),
     ("e4a", 64, 64), ("e4b", 64, 64),
@@ -38,6 +44,7 @@ LAYERS = [  # (name, cin, cout)
     ("d1a", 48, 16), ("d1b", 16, 16),
 ]
 HEAD = ("head", 16, 9)
+IN_CH = LAYERS[0][1]
 SLOPE = 0.125  # leaky ReLU slope for z <= 0
 
 

@@ -354,7 +354,8 @@ static gff_status check_options(gff_handle* h, const gff_options* o) {
         return fail(h, GFF_ERR_ARG, "precision %d", o->precision);
     if (!(o->newton_tol > 0) || !(o->cg_tol > 0) || o->newton_max < 0 || o->cg_max < 1 || o->max_cuts < 0)
         return fail(h, GFF_ERR_ARG, "tolerances / caps out of range");
-    if (o->warm_start < 0 || o->warm_start > 2) return fail(h, GFF_ERR_ARG, "warm_start must be 0, 1 or 2");
+    if (o->warm_start < GFF_WARM_OFF || o->warm_start > GFF_WARM_EXTRAPOLATE)
+        return fail(h, GFF_ERR_ARG, "warm_start must be 0, 1, 2 or 3");
     return GFF_OK;
 }
 
@@ -404,7 +405,7 @@ GFF_EXPORT gff_status gff_create(const gff_grid* grid, const gff_options* opt, g
         {(void**)&h->d_red, 32 * RED_BLOCKS * sizeof(double), "reduce"},
         {(void**)&h->d_scal, 64 * sizeof(double), "scalars"},
         {(void**)&h->d_gid, N * sizeof(int), "grain id"},
-        {(void**)&h->d_Fprev, f64, "F of the previous increment"},
+        {(void**)&h->d_yhist, 2 * f32, "increment history"},
     };
     for (auto& a : allocs)
         if ((st = dalloc(h, a.p, a.b, a.w)) != GFF_OK) return st;
@@ -421,7 +422,7 @@ GFF_EXPORT void gff_destroy(gff_handle* h) {
     dfree(h->d_p); dfree(h->d_Ap); dfree(h->d_K32); dfree(h->d_b32); dfree(h->d_x32); dfree(h->d_r32);
     dfree(h->d_p32); dfree(h->d_Ap32); dfree(h->d_spec); dfree(h->d_Fpi); dfree(h->d_chi); dfree(h->d_Fpi_t);
     dfree(h->d_chi_t); dfree(h->d_dg); dfree(h->d_tau); dfree(h->d_acc); dfree(h->d_flag); dfree(h->d_red);
-    dfree(h->d_scal); dfree(h->d_gq); dfree(h->d_Fprev);
+    dfree(h->d_scal); dfree(h->d_gq); dfree(h->d_yhist);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete reinterpret_cast<gff_hostdata*>(h->hostdata);
     delete h;
@@ -456,6 +457,7 @@ static gff_status reset_state(gff_handle* h) {
     GFF_TRY(launch_fip_reset(h));
     GFF_TRY(cudaDeviceSynchronize());
     h->K_valid = h->K32_valid = false;
+    h->nhist = 0;
     return GFF_OK;
 }
 
@@ -631,10 +633,12 @@ GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, con
 }
 
 GFF_EXPORT gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode) {
-    if (!h || mode < 0 || mode > 2 || (mode && !u)) return fail(h, GFF_ERR_ARG, "bad warm-start args");
-    if (mode && (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz || h->grid.nx % 8))
+    const bool net = mode == GFF_WARM_NET_IF_BETTER || mode == GFF_WARM_NET;
+    if (!h || mode < GFF_WARM_OFF || mode > GFF_WARM_EXTRAPOLATE || (net && !u))
+        return fail(h, GFF_ERR_ARG, "bad warm-start args");
+    if (net && (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz || h->grid.nx % 8))
         return fail(h, GFF_ERR_ARG, "the warm-start network needs a cubic grid with n divisible by 8");
-    h->unet = mode ? u : nullptr;
+    h->unet = net ? u : nullptr;
     h->opt.warm_start = mode;
     return GFF_OK;
 }
@@ -793,22 +797,28 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         return GFF_OK;
     };
 
-    // learned warm start: mode 1 keeps it only if its residual beats the zero start's, mode 2 always
-    const int wmode = h->unet ? h->opt.warm_start : 0;
+    // warm starts: mode 1 keeps the network's guess only if its residual beats the zero
+    // start's, mode 2 always, mode 3 extrapolates the last increment without a network
+    int wmode = h->opt.warm_start;
+    if ((wmode == GFF_WARM_NET_IF_BETTER || wmode == GFF_WARM_NET) && !h->unet) wmode = GFF_WARM_OFF;
     if (wmode) {
         double res_zero = -1.0;
-        if (wmode == 1) {
+        if (wmode == GFF_WARM_NET_IF_BETTER) {
             if ((st = evaluate(false)) != GFF_OK) return st;
             res_zero = res;
         }
-        cudaError_t e = unet_warm_start(h->unet, h, d9);
+        int applied = 0;
+        cudaError_t e = warm_guess(wmode == GFF_WARM_EXTRAPOLATE ? nullptr : h->unet, h, d9, &applied);
         if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "warm start: %s", cudaGetErrorString(e));
-        st = evaluate(false);
+        st = applied ? evaluate(false) : GFF_OK;
         if (st != GFF_OK && st != GFF_ERR_CP_FAIL) return st;
-        warm_used = 1;
+        warm_used = applied;
         // a guess the return map cannot take, or one with a non-finite residual, is dropped in
-        // either mode; mode 1 also drops a guess that does not beat the zero start
-        if (st == GFF_ERR_CP_FAIL || !std::isfinite(res) || (wmode == 1 && !(res < res_zero))) {
+        // every mode; mode 1 also drops a guess that does not beat the zero start
+        if (!applied) {
+            if (wmode != GFF_WARM_NET_IF_BETTER && (st = evaluate(false)) != GFF_OK) return st;
+        } else if (st == GFF_ERR_CP_FAIL || !std::isfinite(res) ||
+                   (wmode == GFF_WARM_NET_IF_BETTER && !(res < res_zero))) {
             h->err.clear();
             GFF_TRY(launch_add_const9(h->d_Fk, h->d_F, d9, N, h->stream));
             if ((st = evaluate(false)) != GFF_OK) return st;
@@ -873,13 +883,32 @@ void set_error(gff_handle* h, const char* msg) { h->err = msg; }
 
 namespace {
 
-// Commit the converged iterate: F, internal variables, FIP accumulators; the
-// previous F is kept for training samples of the warm-start network.
+// Commit the converged iterate: F, internal variables, FIP accumulators, and
+// the increment history the warm starts use.
 gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
     const long long N = h->N;
     gff_status st;
-    GFF_TRY(launch_sum9(h->d_F, N, h->d_red, h->d_scal + 18, h->stream));
-    GFF_TRY(cudaMemcpyAsync(h->d_Fprev, h->d_F, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    double s[27];
+    GFF_TRY(launch_sum9(h->d_P, N, h->d_red, h->d_scal, h->stream));
+    GFF_TRY(launch_sum9(h->d_Fk, N, h->d_red + 9 * RED_BLOCKS, h->d_scal + 9, h->stream));
+    GFF_TRY(launch_sum9(h->d_F, N, h->d_red + 18 * RED_BLOCKS, h->d_scal + 18, h->stream));
+    if ((st = fetch(h, h->d_scal, 27, s)) != GFF_OK) return st;
+    double dF[9], dn = 0.0;
+    for (int c = 0; c < 9; ++c) {
+        rep->Pmacro[c] = s[c] / (double)N;
+        rep->Fmacro[c] = s[9 + c] / (double)N;
+        dF[c] = (s[9 + c] - s[18 + c]) / (double)N;
+        dn += h->cur_d9[c] * h->cur_d9[c];
+    }
+    dn = std::sqrt(dn);
+    if (dn > 0) {
+        const int slot = h->ycur ^ 1;
+        GFF_TRY(launch_fluct_incr(h->d_yhist + (size_t)slot * 9 * N, h->d_Fk, h->d_F, dF, 1.0 / dn, N, h->stream));
+        h->ycur = slot;
+        h->nhist = h->nhist < 2 ? h->nhist + 1 : 2;
+    } else {
+        h->nhist = 0;  // a purely stress-controlled increment has no direction: history restarts
+    }
     GFF_TRY(cudaMemcpyAsync(h->d_F, h->d_Fk, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (h->any_cp) {
         GFF_TRY(cudaMemcpyAsync(h->d_Fpi, h->d_Fpi_t, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -889,18 +918,13 @@ gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
     // mixed precision leaves only the FP32 tangent of the last Newton iterate
     h->K_valid = h->opt.precision != GFF_PREC_MIXED;
     h->K32_valid = h->opt.precision == GFF_PREC_MIXED;
-    double s[27];
-    GFF_TRY(launch_sum9(h->d_P, N, h->d_red, h->d_scal, h->stream));
-    GFF_TRY(launch_sum9(h->d_F, N, h->d_red + 9 * RED_BLOCKS, h->d_scal + 9, h->stream));
-    if ((st = fetch(h, h->d_scal, 27, s)) != GFF_OK) return st;
     for (int c = 0; c < 9; ++c) {
-        rep->Pmacro[c] = s[c] / (double)N;
-        rep->Fmacro[c] = s[9 + c] / (double)N;
-        h->prev_dFbar[c] = (s[9 + c] - s[18 + c]) / (double)N;
+        h->prev_dFbar[c] = dF[c];
         h->Pmacro_committed[c] = rep->Pmacro[c];
+        h->prev2_d9[c] = h->prev_d9[c];
         h->prev_d9[c] = h->cur_d9[c];
     }
-    h->have_prev = true;
+    GFF_TRY(cudaStreamSynchronize(h->stream));
     return GFF_OK;
 }
 
@@ -1057,6 +1081,7 @@ GFF_EXPORT gff_status gff_load_state(gff_handle* h, const char* path) {
     if (!ok) return fail(h, GFF_ERR_IO, "read failed or not a state file: %s", path);
     GFF_TRY(cudaMemcpy(h->d_Fk, h->d_F, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice));
     h->K_valid = h->K32_valid = false;
+    h->nhist = 0;  // the increment history is not part of the state file
     return GFF_OK;
 }
 

@@ -166,14 +166,18 @@ struct gff_handle {
     void* hostdata = nullptr;  // host copies of the orientations and phases
     gff::Tune tune[2] = {{512, 4, 256, 512}, {512, 8, 256, 512}};  // [0] FP64, [1] FP32
     bool tuned = false;
-    // learned warm start
+    // warm starts: history of the completed increments.  d is an increment's
+    // prescribed average F change (0 on stress-controlled components) and
+    // y = (F_k - F_{k-1} - dFbar_k) / |d_k| its normalised fluctuation increment.
     float* d_gq = nullptr;       // [ngrains][5]: orientation quaternion (w, x, y, z) and phase
-    double* d_Fprev = nullptr;   // F before the last completed increment
-    bool have_prev = false;
+    float* d_yhist = nullptr;    // [2][9][N]: y of the last two completed increments
+    int ycur = 0;                // slot of the last completed increment's y
+    int nhist = 0;               // consecutive completed increments with |d| > 0 on record (0..2)
     double prev_dFbar[9] = {0};  // average F change of the last completed increment
     double Pmacro_committed[9] = {0};  // average P of the committed state
-    double cur_d9[9] = {0};   // prescribed average F change of the increment being solved
-    double prev_d9[9] = {0};  // the same for the last completed increment
+    double cur_d9[9] = {0};      // d of the increment being solved
+    double prev_d9[9] = {0};     // d of the last completed increment
+    double prev2_d9[9] = {0};    // d of the one before
     struct gff_unet* unet = nullptr;
     std::string err;
 };
@@ -183,8 +187,10 @@ namespace gff {
 constexpr int NACC = 1 + 12 * 5;  // pcyc, W[12], gamma[12], gmin[12], gmax[12], sn[12]
 constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 
-// ---- learned warm start (unet.cu): adds G^(network guess) to h->d_Fk
-cudaError_t unet_warm_start(struct gff_unet* u, gff_handle* h, const double* dFbar);
+// ---- warm starts (unet.cu): add G^(|d| y~) to h->d_Fk for the prescribed increment d9,
+// y~ = s y_{k-1} (+ the network's correction when u is given).  *applied = 0 when there
+// is nothing to add (|d| = 0, or extrapolation without history).
+cudaError_t warm_guess(struct gff_unet* u, gff_handle* h, const double* d9, int* applied);
 
 // ---- host helpers (api.cu)
 gff_status prepare_for_increments(gff_handle* h);
@@ -229,6 +235,9 @@ cudaError_t launch_add_const9(double* F, const double* Fsrc, const double* d9, l
 template <typename Tin>
 cudaError_t launch_axpy_to64(double* y, const Tin* x, long long n, cudaStream_t s);
 cudaError_t launch_cast64to32(float* y, const double* x, long long n, cudaStream_t s);
+// y[c][v] = (Fk[c][v] - F[c][v] - dF9[c]) * inv   (normalised fluctuation increment, FP32)
+cudaError_t launch_fluct_incr(float* y, const double* Fk, const double* F, const double* dF9, double inv, long long N,
+                              cudaStream_t s);
 cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s);
 // Device-resident CG scalars (see vec.cu): cg[CG_RR] = r.r, cg[CG_PAP], cg[CG_ALPHA],
 // cg[CG_BETA], cg[CG_STOP2] = stop^2, cg[CG_ITERS]; flag[0] = stop, flag[1] = breakdown.

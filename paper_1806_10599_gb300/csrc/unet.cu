@@ -3,14 +3,18 @@
 // increment that starts the Newton iteration (the paper leaves the initial
 // guess open, Sect. 2.1; this network is not in the paper).
 //
-// Input per voxel (14 channels): the grain's orientation quaternion (4), its
-// phase (1) and the prescribed macroscopic increment d / |d| (9; d is dFbar
-// on the strain-controlled components, 0 on the stress-controlled ones).
-// Output (9): the fluctuation increment (F_k - F_{k-1} - dFbar) / |d|.  bfloat16 weights and activations, FP32
-// accumulation on the tensor cores (unet_kernels.cuh), FP32 master weights
-// updated by Adam.  The whole network is periodic (wrapping 3x3x3 taps,
-// 2x2x2 pooling, nearest upsampling), so one set of weights serves any grid
-// whose sizes are multiples of 8.
+// Input per voxel (IN_CH = 32 channels): the grain's orientation quaternion
+// (4) and phase (1), the prescribed macroscopic increment d_k / |d_k| (9; d
+// is dFbar on strain-controlled components, 0 on stress-controlled ones),
+// the previous increment's normalised fluctuation increment y_{k-1} (9) and
+// its direction d_{k-1} / |d_{k-1}| (9).  Output (9): the correction c with
+// y_k ~ s y_{k-1} + c, s = cos(d_k, d_{k-1}), where
+// y_k = (F_k - F_{k-1} - dFbar_k) / |d_k|.  The head starts at zero, so an
+// untrained network reproduces the plain extrapolation.  bfloat16 weights
+// and activations, FP32 accumulation on the tensor cores (unet_kernels.cuh),
+// FP32 master weights updated by Adam.  The whole network is periodic
+// (wrapping 3x3x3 taps, 2x2x2 pooling, nearest upsampling), so one set of
+// weights serves any cubic grid whose size is a multiple of 8.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,11 +34,13 @@ struct LayerDef {
 };
 // e1a e1b e2a e2b e3a e3b e4a e4b d3a d3b d2a d2b d1a d1b
 constexpr int NL = 14;
-constexpr LayerDef kL[NL] = {{14, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64},  {64, 64}, {64, 64},
+constexpr int IN_CH = 32;
+constexpr LayerDef kL[NL] = {{IN_CH, 16}, {16, 16}, {16, 32}, {32, 32}, {32, 64},  {64, 64}, {64, 64},
                              {64, 64}, {128, 64}, {64, 64}, {96, 32}, {32, 32}, {48, 16}, {16, 16}};
 constexpr int HEAD_IN = 16, HEAD_OUT = 9;
 
 inline int pad16(int c) { return (c + 15) / 16 * 16; }
+constexpr float GRAD_CLIP = 1.0f;  // global gradient-norm bound of a training step
 
 struct View {
     bf16* p;
@@ -65,7 +71,7 @@ struct gff_unet {
     float* Y = nullptr;
     float* dY = nullptr;
     double* d_loss = nullptr;
-    // training samples (grid sample_n): inputs [V][16] bf16, targets [V][9] f32
+    // training samples (grid sample_n): inputs [V][IN_CH] bf16, targets [V][9] f32
     int sample_n = 0;
     std::vector<bf16*> sx;
     std::vector<float*> sy;
@@ -130,7 +136,7 @@ gff_status ensure_buffers(gff_unet* u, int n) {
         int level, ch;
     };
     // forward activations and their gradients
-    Want w[] = {{&u->X, 0, 16},     {&u->Ae1a, 0, 16},  {&u->CAT1, 0, 48},  {&u->P1, 1, 16},    {&u->Ae2a, 1, 32},
+    Want w[] = {{&u->X, 0, IN_CH},     {&u->Ae1a, 0, 16},  {&u->CAT1, 0, 48},  {&u->P1, 1, 16},    {&u->Ae2a, 1, 32},
                 {&u->CAT2, 1, 96},  {&u->P2, 2, 32},    {&u->Ae3a, 2, 64},  {&u->CAT3, 2, 128}, {&u->P3, 3, 64},
                 {&u->Ae4a, 3, 64},  {&u->E4, 3, 64},    {&u->Ad3a, 2, 64},  {&u->D3, 2, 64},    {&u->Ad2a, 1, 32},
                 {&u->D2, 1, 32},    {&u->Ad1a, 0, 16},  {&u->D1, 0, 16},    {&u->gAe1a, 0, 16}, {&u->gCAT1, 0, 48},
@@ -289,27 +295,59 @@ gff_status backward(gff_unet* u, View X, cudaStream_t st) {
 
 // ---------------------------------------------------------------- solver glue
 __global__ void k_unet_input(const int* __restrict__ gid, const float* __restrict__ gq /* [ng][5] */, Nine9 dfn,
+                             const float* __restrict__ yprev /* [9][V] or null */, Nine9 dprev,
                              bf16* __restrict__ x, long long V) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
         const float* q = gq + 5LL * gid[v];
-        bf16* r = x + v * 16;
+        bf16* r = x + v * IN_CH;
         for (int c = 0; c < 5; ++c) r[c] = __float2bfloat16(q[c]);
-        for (int c = 0; c < 9; ++c) r[5 + c] = __float2bfloat16((float)dfn.v[c]);
-        r[14] = r[15] = __float2bfloat16(0.f);
+        for (int c = 0; c < 9; ++c) {
+            r[5 + c] = __float2bfloat16((float)dfn.v[c]);
+            r[14 + c] = __float2bfloat16(yprev ? yprev[c * V + v] : 0.f);
+            r[23 + c] = __float2bfloat16((float)dprev.v[c]);
+        }
     }
 }
 
-// target[v][c] = (F[c][v] - Fprev[c][v] - dFbar[c]) / |d|
-__global__ void k_unet_target(const double* __restrict__ F, const double* __restrict__ Fp, Nine9 dF, double inv,
+// target[v][c] = y[c][v] - s yprev[c][v]
+__global__ void k_unet_target(const float* __restrict__ y, const float* __restrict__ yprev, float s,
                               float* __restrict__ t, long long V) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
-        for (int c = 0; c < 9; ++c) t[v * 9 + c] = (float)((F[c * V + v] - Fp[c * V + v] - dF.v[c]) * inv);
+        for (int c = 0; c < 9; ++c) t[v * 9 + c] = y[c * V + v] - (yprev ? s * yprev[c * V + v] : 0.f);
 }
 
-// field[c][v] = scale * y[v][c]   (network output to the solver's SoA layout, FP32)
-__global__ void k_unet_to_field(const float* __restrict__ y, double scale, float* __restrict__ f, long long V) {
+// field[c][v] = scale (s yprev[c][v] + corr[v][c])   (either part may be null)
+__global__ void k_guess_field(const float* __restrict__ yprev, float s, const float* __restrict__ corr, float scale,
+                              float* __restrict__ f, long long V) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x)
-        for (int c = 0; c < 9; ++c) f[c * V + v] = (float)(scale * y[v * 9 + c]);
+        for (int c = 0; c < 9; ++c) {
+            float a = yprev ? s * yprev[c * V + v] : 0.f;
+            if (corr) a += corr[v * 9 + c];
+            f[c * V + v] = scale * a;
+        }
+}
+
+double norm9(const double* a) {
+    double s = 0.0;
+    for (int c = 0; c < 9; ++c) s += a[c] * a[c];
+    return std::sqrt(s);
+}
+
+// Network inputs for an increment with prescribed change d after the recorded history (yprev, dprev: may be
+// absent).  Returns s = cos(d, dprev) (0 without history).
+double make_input(gff_unet* u, gff_handle* h, const double* d, const float* yprev, const double* dprev, bf16* x,
+                  cudaStream_t st) {
+    const double nd = norm9(d), np = dprev ? norm9(dprev) : 0.0;
+    Nine9 dfn, dpn;
+    double s = 0.0;
+    for (int c = 0; c < 9; ++c) {
+        dfn.v[c] = d[c] / nd;
+        dpn.v[c] = np > 0 ? dprev[c] / np : 0.0;
+        s += dfn.v[c] * dpn.v[c];
+    }
+    (void)u;
+    k_unet_input<<<grid_of(h->N), 256, 0, st>>>(h->d_gid, h->d_gq, dfn, np > 0 ? yprev : nullptr, dpn, x, h->N);
+    return s;
 }
 
 }  // namespace
@@ -317,30 +355,43 @@ __global__ void k_unet_to_field(const float* __restrict__ y, double scale, float
 // ---------------------------------------------------------------- used by the solver (api.cu)
 namespace gff {
 
-// dF^0 = G^(|dFbar| net(q, phase, dFbar / |dFbar|)) added to the handle's zero-fluctuation start d_Fk
-cudaError_t unet_warm_start(gff_unet* u, gff_handle* h, const double* dFbar) {
-    double nrm = 0.0;
-    for (int c = 0; c < 9; ++c) nrm += dFbar[c] * dFbar[c];
-    nrm = std::sqrt(nrm);
+// F^0 += G^(|d| (s y_{k-1} + U(x)))  (network) or G^(|d| s y_{k-1})  (u null: extrapolation)
+cudaError_t warm_guess(gff_unet* u, gff_handle* h, const double* d9, int* applied) {
+    *applied = 0;
+    const double nrm = norm9(d9);
     if (!(nrm > 0)) return cudaSuccess;
-    if (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz) return cudaErrorInvalidValue;
-    if (ensure_buffers(u, h->grid.nx) != GFF_OK) return cudaErrorMemoryAllocation;
+    const bool hist = h->nhist >= 1;
+    if (!u && !hist) return cudaSuccess;  // nothing to extrapolate
     cudaStream_t st = h->stream;
-    Nine9 dfn;
-    for (int c = 0; c < 9; ++c) dfn.v[c] = dFbar[c] / nrm;
-    k_unet_input<<<grid_of(h->N), 256, 0, st>>>(h->d_gid, h->d_gq, dfn, u->X.p, h->N);
-    if (forward(u, u->X, st) != GFF_OK) return cudaErrorUnknown;
-    k_unet_to_field<<<grid_of(h->N), 256, 0, st>>>(u->Y, nrm, h->d_x32, h->N);
+    const float* yprev = hist ? h->d_yhist + (size_t)h->ycur * 9 * h->N : nullptr;
+    double s = 0.0;
+    if (hist) {
+        const double np = norm9(h->prev_d9);
+        for (int c = 0; c < 9; ++c) s += d9[c] * h->prev_d9[c];
+        s /= nrm * np;
+    }
+    const float* corr = nullptr;
+    if (u) {
+        if (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz) return cudaErrorInvalidValue;
+        if (ensure_buffers(u, h->grid.nx) != GFF_OK) return cudaErrorMemoryAllocation;
+        make_input(u, h, d9, yprev, hist ? h->prev_d9 : nullptr, u->X.p, st);
+        if (forward(u, u->X, st) != GFF_OK) return cudaErrorUnknown;
+        corr = u->Y;
+    }
+    k_guess_field<<<grid_of(h->N), 256, 0, st>>>(yprev, (float)s, corr, (float)nrm, h->d_x32, h->N);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     ProjArgs pa;
     pa.kind = h->opt.projection;
     for (int c = 0; c < 9; ++c) pa.mask[c] = 0.f;  // compatible, zero mean
     OutArgs oa;
     oa.scale = 1.0 / (double)h->N;
     for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
-    cudaError_t e = launch_galerkin<float>(h, h->d_x32, (const float*)nullptr, h->d_Ap32, pa, oa,
-                                           reinterpret_cast<float2*>(h->d_spec));
+    e = launch_galerkin<float>(h, h->d_x32, (const float*)nullptr, h->d_Ap32, pa, oa, reinterpret_cast<float2*>(h->d_spec));
     if (e != cudaSuccess) return e;
-    return launch_axpy_to64<float>(h->d_Fk, h->d_Ap32, 9 * h->N, st);
+    e = launch_axpy_to64<float>(h->d_Fk, h->d_Ap32, 9 * h->N, st);
+    if (e == cudaSuccess) *applied = 1;
+    return e;
 }
 
 }  // namespace gff
@@ -366,7 +417,7 @@ UEXPORT gff_status gff_unet_create(uint64_t seed, gff_unet** out) {
     u->off_hb = off;
     off += HEAD_OUT;
     u->nparam = off;
-    // He-uniform initial weights from a SplitMix64 stream, zero biases and padding
+    // He-uniform convolution weights from a SplitMix64 stream; zero biases, padding and head
     std::vector<float> w(off, 0.f);
     uint64_t s = seed;
     auto unif = [&]() { return (double)(sm64(s) >> 11) * (1.0 / 9007199254740992.0); };
@@ -377,8 +428,7 @@ UEXPORT gff_status gff_unet_create(uint64_t seed, gff_unet** out) {
             for (int o = 0; o < co; ++o)
                 for (int i = 0; i < ci; ++i) w[u->off_w[l] + ((size_t)t * co + o) * cip + i] = (float)((2 * unif() - 1) * lim);
     }
-    const double limh = std::sqrt(6.0 / HEAD_IN);
-    for (int k = 0; k < HEAD_OUT * HEAD_IN; ++k) w[u->off_hw + k] = (float)((2 * unif() - 1) * limh);
+    // the head starts at zero: the untrained network adds nothing to the extrapolation
     cudaError_t e = cudaSuccess;
     void** bufs[] = {(void**)&u->d_w, (void**)&u->d_g, (void**)&u->d_m, (void**)&u->d_v};
     for (auto b : bufs)
@@ -474,9 +524,8 @@ UEXPORT gff_status gff_unet_eval_host(gff_unet* u, int n, const float* x, const 
     gff_status st = ensure_buffers(u, n);
     if (st != GFF_OK) return st;
     const long long V = (long long)n * n * n;
-    std::vector<bf16> xb((size_t)V * 16);
-    for (long long v = 0; v < V; ++v)
-        for (int c = 0; c < 16; ++c) xb[v * 16 + c] = __float2bfloat16(c < 14 ? x[v * 14 + c] : 0.f);
+    std::vector<bf16> xb((size_t)V * IN_CH);
+    for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16(x[i]);
     UTRY(cudaMemcpy(u->X.p, xb.data(), xb.size() * sizeof(bf16), cudaMemcpyHostToDevice));
     if ((st = forward(u, u->X, nullptr)) != GFF_OK) return st;
     UTRY(cudaMemcpy(y, u->Y, (size_t)V * 9 * sizeof(float), cudaMemcpyDeviceToHost));
@@ -502,31 +551,24 @@ UEXPORT gff_status gff_unet_eval_host(gff_unet* u, int n, const float* x, const 
 // Keep the last increment of h (inputs and the fluctuation-increment target) as a training sample.
 UEXPORT gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h) {
     if (!u || !h) return GFF_ERR_ARG;
-    if (!h->have_prev) return ufail(u, GFF_ERR_STATE, "the handle has no completed increment");
+    if (h->nhist < 1) return ufail(u, GFF_ERR_STATE, "the handle has no completed increment with a strain increment");
     if (h->grid.nx != h->grid.ny || h->grid.ny != h->grid.nz || h->grid.nx % 8)
         return ufail(u, GFF_ERR_ARG, "samples need cubic grids with n divisible by 8");
     if (u->sample_n && u->sample_n != h->grid.nx) return ufail(u, GFF_ERR_ARG, "all samples must share one grid");
-    // the network sees the prescribed (strain-controlled) increment, as in gff::unet_warm_start
-    double nrm = 0.0;
-    for (int c = 0; c < 9; ++c) nrm += h->prev_d9[c] * h->prev_d9[c];
-    nrm = std::sqrt(nrm);
-    if (!(nrm > 0)) return ufail(u, GFF_ERR_ARG, "no prescribed strain increment");
     const long long V = h->N;
     bf16* x = nullptr;
     float* t = nullptr;
-    UTRY(cudaMalloc(&x, (size_t)V * 16 * sizeof(bf16)));
+    UTRY(cudaMalloc(&x, (size_t)V * IN_CH * sizeof(bf16)));
     cudaError_t e = cudaMalloc(&t, (size_t)V * 9 * sizeof(float));
     if (e != cudaSuccess) {
         cudaFree(x);
         return ufail(u, GFF_ERR_OOM, "U-Net sample", e);
     }
-    Nine9 dfn, dF;
-    for (int c = 0; c < 9; ++c) {
-        dfn.v[c] = h->prev_d9[c] / nrm;
-        dF.v[c] = h->prev_dFbar[c];
-    }
-    k_unet_input<<<grid_of(V), 256, 0, h->stream>>>(h->d_gid, h->d_gq, dfn, x, V);
-    k_unet_target<<<grid_of(V), 256, 0, h->stream>>>(h->d_F, h->d_Fprev, dF, 1.0 / nrm, t, V);
+    // increment k = the last completed one; its predecessor k-1 is on record when nhist = 2
+    const float* yk = h->d_yhist + (size_t)h->ycur * 9 * V;
+    const float* ykm1 = h->nhist >= 2 ? h->d_yhist + (size_t)(h->ycur ^ 1) * 9 * V : nullptr;
+    const double s = make_input(u, h, h->prev_d9, ykm1, ykm1 ? h->prev2_d9 : nullptr, x, h->stream);
+    k_unet_target<<<grid_of(V), 256, 0, h->stream>>>(yk, ykm1, (float)s, t, V);
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         cudaFree(x);
@@ -560,7 +602,7 @@ UEXPORT gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* los
             }
         }
         const int sidx = order[k % ns];
-        View X{u->sx[sidx], 16};
+        View X{u->sx[sidx], IN_CH};
         if ((st = forward(u, X, nullptr)) != GFF_OK) return st;
         UTRY(cudaMemsetAsync(u->d_loss, 0, sizeof(double), nullptr));
         k_mse<<<grid_of(V * 9), 256>>>(u->Y, u->sy[sidx], u->dY, V * 9, u->d_loss);
@@ -568,8 +610,11 @@ UEXPORT gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* los
         ++u->adam_t;
         const float b1 = 0.9f, b2 = 0.999f;
         const float c1 = 1.f - std::pow(b1, (float)u->adam_t), c2 = 1.f - std::pow(b2, (float)u->adam_t);
-        k_adam<<<grid_of((long long)u->nparam), 256>>>(u->d_w, u->d_g, u->d_m, u->d_v, (long long)u->nparam, (float)lr,
-                                                      b1, b2, 1e-8f, c1, c2);
+        const double lr_k = lr * 0.5 * (1.0 + std::cos(M_PI * (double)k / (double)steps));  // cosine decay
+        UTRY(cudaMemsetAsync(u->d_loss + 1, 0, sizeof(double), nullptr));
+        k_sumsq<<<grid_of((long long)u->nparam), 256>>>(u->d_g, (long long)u->nparam, u->d_loss + 1);
+        k_adam<<<grid_of((long long)u->nparam), 256>>>(u->d_w, u->d_g, u->d_m, u->d_v, (long long)u->nparam,
+                                                      (float)lr_k, b1, b2, 1e-8f, c1, c2, u->d_loss + 1, GRAD_CLIP);
         if ((st = refresh_copies(u, nullptr)) != GFF_OK) return st;
         if (losses) {
             UTRY(cudaMemcpy(&losses[k], u->d_loss, sizeof(double), cudaMemcpyDeviceToHost));

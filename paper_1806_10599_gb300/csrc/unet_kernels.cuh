@@ -312,11 +312,31 @@ __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ y, const 
     }
 }
 
-// Adam on the flat parameter vector (FP32 master weights)
+// out += sum_i g[i]^2
+__global__ void __launch_bounds__(256) k_sumsq(const float* __restrict__ g, long long n, double* __restrict__ out) {
+    __shared__ double part[8];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += (double)g[i] * g[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += part[w];
+        atomicAdd(out, tot);
+    }
+}
+
+// Adam on the flat parameter vector (FP32 master weights); the gradient is
+// scaled down to global norm `clip` when sqrt(*gn2) exceeds it
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       long long n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       const double* __restrict__ gn2, float clip) {
+    const double gn = sqrt(*gn2);
+    const float sc = gn > clip ? (float)(clip / gn) : 1.f;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float gi = g[i];
+        const float gi = sc * g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
         m[i] = mi;

@@ -85,6 +85,12 @@ __global__ void __launch_bounds__(TPB) k_add_const9(double* __restrict__ F, cons
         F[i] = Fsrc[i] + d.v[i / N];
 }
 
+__global__ void __launch_bounds__(TPB) k_fluct_incr(float* __restrict__ y, const double* __restrict__ Fk,
+                                                    const double* __restrict__ F, Nine d, double inv, long long N) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < 9 * N; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (float)((Fk[i] - F[i] - d.v[i / N]) * inv);
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(TPB) k_axpy_to64(double* __restrict__ y, const Tin* __restrict__ x, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -357,6 +363,14 @@ cudaError_t launch_add_const9(double* F, const double* Fsrc, const double* d9, l
 template <typename Tin>
 cudaError_t launch_axpy_to64(double* y, const Tin* x, long long n, cudaStream_t s) {
     k_axpy_to64<Tin><<<grid_for(n), TPB, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fluct_incr(float* y, const double* Fk, const double* F, const double* dF9, double inv, long long N,
+                              cudaStream_t s) {
+    Nine d;
+    for (int c = 0; c < 9; ++c) d.v[c] = dF9[c];
+    k_fluct_incr<<<grid_for(9 * N), TPB, 0, s>>>(y, Fk, F, d, inv, N);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@ GFF_ERR_STATE = -7
 GFF_ERR_IO = -8
 
 GFF_PROJ_CONTINUOUS, GFF_PROJ_DISCRETE = 0, 1
+GFF_WARM_OFF, GFF_WARM_NET_IF_BETTER, GFF_WARM_NET, GFF_WARM_EXTRAPOLATE = 0, 1, 2, 3
+UNET_IN = 32  # input channels of the warm-start network
 GFF_PREC_FP64, GFF_PREC_MIXED = 0, 1
 GFF_MAT_SVK_CUBIC, GFF_MAT_SVK_ISO, GFF_MAT_CP_FCC = 0, 1, 2
 (GFF_FIELD_F, GFF_FIELD_P, GFF_FIELD_K, GFF_FIELD_FP_INV, GFF_FIELD_CHI,
@@ -356,9 +358,9 @@ def gff_unet_load(u, path):
 
 
 def gff_unet_eval_host(u, n, x, target=None):
-    """x [V][14] -> y [V][9]; with a target also (loss, grads)."""
+    """x [V][UNET_IN] -> y [V][9]; with a target also (loss, grads)."""
     V = n ** 3
-    xa, xp = _host(np.asarray(x).reshape(V, 14), np.float32)
+    xa, xp = _host(np.asarray(x).reshape(V, UNET_IN), np.float32)
     y = np.empty((V, 9), dtype=np.float32)
     if target is None:
         _ucheck(u, _lib.gff_unet_eval_host(u, n, xp, None, y.ctypes.data_as(c_void_p), None, None))

@@ -1,7 +1,9 @@
-"""Warm-start network on the GPU against the FP64 oracle (oracle/unet.py)
-with the same bfloat16 rounding points: forward output, loss and every
-parameter gradient; training lowers the loss; the solver reaches the same
-solution from the learned start as from the zero-fluctuation start.
+"""Warm starts.  The network on the GPU against the FP64 oracle
+(oracle/unet.py) with the same bfloat16 rounding points: forward output,
+loss and every parameter gradient; training lowers the loss; the solver
+reaches the same solution from the learned start and from the extrapolated
+start as from the zero-fluctuation start, and extrapolation lowers the first
+residual of monotone increments.
 
 Tolerance: a bfloat16 network is chaotic at the rounding level -- weights
 perturbed by 1e-6 (relative) move the oracle's own output by ~0.6 % and its
@@ -50,7 +52,7 @@ def test_forward_and_gradients_match_oracle(n):
     rng = np.random.default_rng(6)
     for name in p:  # non-zero biases exercise the bias paths
         p[name] = (p[name][0], 0.1 * rng.standard_normal(p[name][1].shape))
-    x = rng.standard_normal((14, n, n, n))
+    x = rng.standard_normal((U.IN_CH, n, n, n))
     t = 0.5 * rng.standard_normal((9, n, n, n))
     u = g.gff_unet_create(1)
     try:
@@ -58,7 +60,7 @@ def test_forward_and_gradients_match_oracle(n):
         g.gff_unet_set_params(u, flat(p).astype(np.float32))
         assert np.array_equal(g.gff_unet_get_params(u), flat(p).astype(np.float32))
         p32 = unflat(flat(p).astype(np.float32).astype(np.float64))
-        y, loss, grads = g.gff_unet_eval_host(u, n, x.reshape(14, V).T, t.reshape(9, V).T)
+        y, loss, grads = g.gff_unet_eval_host(u, n, x.reshape(U.IN_CH, V).T, t.reshape(9, V).T)
         yo, cache = U.forward(p32, x, round_bf16=True)
         lo, dy = U.mse(yo, t)
         go = U.backward(p32, cache, dy, round_bf16=True)
@@ -89,7 +91,7 @@ def test_forward_and_gradients_match_oracle(n):
 
 def _solve(g, ms, hist, u=None, mode=0, tol=1e-10):
     h = g.create_rve(ms, gpu_materials({0: CP_FCC}), g.make_options(newton_tol=tol, cg_tol=1e-8))
-    if u is not None:
+    if mode:
         g.gff_set_warm_start(h, u, mode)
     return h, g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
 
@@ -142,3 +144,27 @@ def test_training_lowers_the_loss_and_warm_start_keeps_the_solution(tmp_path):
         for h in hs:
             g.gff_destroy(h)
         g.gff_unet_destroy(u)
+
+
+def test_extrapolation_keeps_the_solution_and_lowers_the_first_residual():
+    torch_cuda()
+    g = gff()
+    ms = polycrystal(16, 6, 34)
+    hist = cyclic_history(0.01, 1).head(12)  # monotone: elastic, then plastic
+    hs = []
+    try:
+        h0, (P0, r0) = _solve(g, ms, hist)
+        h3, (P3, r3) = _solve(g, ms, hist, None, mode=g.GFF_WARM_EXTRAPOLATE)
+        hs += [h0, h3]
+        assert r3[0].warm_start_used == 0  # no history yet
+        assert all(r.warm_start_used == 1 for r in r3[1:])
+        for k in range(hist.nsteps):
+            assert np.linalg.norm(P3[k] - P0[k]) <= 1e-7 * np.linalg.norm(P0[k])
+        N = ms.n_voxels
+        assert rel_l2(g.gff_get_field(h3, g.GFF_FIELD_F, N), g.gff_get_field(h0, g.GFF_FIELD_F, N)) <= 1e-7
+        ratio = np.mean([a.residual_first / b.residual_first for a, b in zip(r3[1:], r0[1:])])
+        assert ratio < 0.5, ratio
+        assert sum(r.newton_iters for r in r3) <= sum(r.newton_iters for r in r0)
+    finally:
+        for h in hs:
+            g.gff_destroy(h)

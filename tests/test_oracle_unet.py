@@ -47,7 +47,7 @@ def test_linear_maps_and_their_adjoints():
 
 def test_network_gradient_matches_finite_differences():
     p = U.init_params(3)
-    x = _rand((14, 8, 8, 8), 9)
+    x = _rand((U.IN_CH, 8, 8, 8), 9)
     t = _rand((9, 8, 8, 8), 10)
     y, cache = U.forward(p, x)
     loss, dy = U.mse(y, t)
