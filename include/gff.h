@@ -271,6 +271,9 @@ gff_status gff_unet_eval_host(gff_unet* u, int n, const float* x, const float* t
  * samples share one grid.  The increment must have a prescribed strain
  * increment (|d_k| > 0). */
 gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h);
+/* A training sample from host arrays x [V][32], target [V][9] (n^3 grid,
+ * n divisible by 8, the same n as the other samples). */
+gff_status gff_unet_add_sample_host(gff_unet* u, int n, const float* x, const float* target);
 int gff_unet_num_samples(const gff_unet* u);
 /* `steps` Adam steps (peak lr with a cosine decay to 0 over the steps, betas
  * 0.9/0.999, gradients clipped to global norm 1), one sample per step,

@@ -581,6 +581,30 @@ UEXPORT gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h) {
     return GFF_OK;
 }
 
+// A training sample from host arrays: x [V][IN_CH], target [V][9] on an n^3 grid.
+UEXPORT gff_status gff_unet_add_sample_host(gff_unet* u, int n, const float* x, const float* target) {
+    if (!u || !x || !target || n < 8 || n % 8) return u ? ufail(u, GFF_ERR_ARG, "bad sample args") : GFF_ERR_ARG;
+    if (u->sample_n && u->sample_n != n) return ufail(u, GFF_ERR_ARG, "all samples must share one grid");
+    const long long V = (long long)n * n * n;
+    std::vector<bf16> xb((size_t)V * IN_CH);
+    for (size_t i = 0; i < xb.size(); ++i) xb[i] = __float2bfloat16(x[i]);
+    bf16* dx = nullptr;
+    float* dt = nullptr;
+    UTRY(cudaMalloc(&dx, xb.size() * sizeof(bf16)));
+    cudaError_t e = cudaMalloc(&dt, (size_t)V * 9 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dx, xb.data(), xb.size() * sizeof(bf16), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dt, target, (size_t)V * 9 * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dx);
+        cudaFree(dt);
+        return ufail(u, GFF_ERR_CUDA, "U-Net sample", e);
+    }
+    u->sx.push_back(dx);
+    u->sy.push_back(dt);
+    u->sample_n = n;
+    return GFF_OK;
+}
+
 UEXPORT int gff_unet_num_samples(const gff_unet* u) { return u ? (int)u->sx.size() : 0; }
 
 // Adam steps over the stored samples (one sample per step, shuffled epochs).

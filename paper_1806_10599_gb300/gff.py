@@ -117,6 +117,7 @@ _SIGS = {
     "gff_unet_load": (c_int, [c_void_p, ctypes.c_char_p]),
     "gff_unet_eval_host": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_unet_add_sample": (c_int, [c_void_p, c_void_p]),
+    "gff_unet_add_sample_host": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "gff_unet_num_samples": (c_int, [c_void_p]),
     "gff_unet_train": (c_int, [c_void_p, c_int, c_double, c_void_p]),
     "gff_set_warm_start": (c_int, [c_void_p, c_void_p, c_int]),
@@ -375,6 +376,14 @@ def gff_unet_eval_host(u, n, x, target=None):
 
 def gff_unet_add_sample(u, h):
     return _ucheck(u, _lib.gff_unet_add_sample(u, h))
+
+
+def gff_unet_add_sample_host(u, n, x, target):
+    """x [V][UNET_IN], target [V][9] on an n^3 grid."""
+    V = n ** 3
+    xa, xp = _host(np.asarray(x).reshape(V, UNET_IN), np.float32)
+    ta, tp = _host(np.asarray(target).reshape(V, 9), np.float32)
+    return _ucheck(u, _lib.gff_unet_add_sample_host(u, int(n), xp, tp))
 
 
 def gff_unet_num_samples(u):
