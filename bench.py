@@ -8,7 +8,8 @@ value = applies/s over all ranks.  The JSON line also carries the FP32 and
 discrete-projection variants, the per-kernel roofline of the dominant kernel,
 the end-to-end rate with host buffers, the CPU-oracle baseline, SM clocks
 sampled during the timed region, and the seconds per crystal-plasticity load
-increment (64^3, 200 grains, +-1 % strain cycles) in FP64 and in mixed precision.
+increment (64^3, 200 grains, +-1 % strain cycles) in FP64, in mixed precision,
+and in mixed precision started from the extrapolated last increment.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gff|reference]
 """
@@ -41,7 +42,8 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gff", "reference"], default="gff")
-    p.add_argument("--increments", type=int, default=6, help="CP increments timed per precision (0: skip)")
+    p.add_argument("--increments", type=int, default=12,
+                   help="CP increments timed per variant: FP64, mixed, mixed + extrapolated start (0: skip)")
     p.add_argument("--cpu-applies", type=int, default=3, help="oracle applies in the CPU baseline sample")
     p.add_argument("--batch-increments", type=int, default=2,
                    help="increments of the 32-RVE batch, batched and one by one (0: skip)")
@@ -274,14 +276,14 @@ def per_kernel_ms(g, h, prec, X, Y, reps):
     return [a / reps for a in acc]
 
 
-def time_increments(g, torch, nsteps, precision):
+def time_increments(g, torch, nsteps, precision, warm=0):
     try:
-        return _time_increments(g, torch, nsteps, precision)
+        return _time_increments(g, torch, nsteps, precision, warm)
     except Exception as e:  # report, do not lose the apply measurement
         return {"error": str(e)}
 
 
-def _time_increments(g, torch, nsteps, precision):
+def _time_increments(g, torch, nsteps, precision, warm):
     from rve_inputs import cyclic_history, polycrystal
 
     ms = polycrystal(64, 200, 2)
@@ -289,6 +291,8 @@ def _time_increments(g, torch, nsteps, precision):
     opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3 if precision == 0 else 1e-3)
     h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts)
     try:
+        if warm:
+            g.gff_set_warm_start(h, None, warm)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Pm, reps = g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
@@ -402,7 +406,8 @@ def run_gpu(args, world, rank, local):
         inc = {"workload": ("64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1 pct "
                             "strain cycles, first %d increments (dt 0.05 s), Newton tol 1e-6") % args.increments,
                "fp64": time_increments(g, torch, args.increments, 0),
-               "mixed": time_increments(g, torch, args.increments, 1)}
+               "mixed": time_increments(g, torch, args.increments, 1),
+               "mixed_extrapolated": time_increments(g, torch, args.increments, 1, g.GFF_WARM_EXTRAPOLATE)}
     g.gff_destroy(h)
     g.gff_destroy(hd)
     batch = None
