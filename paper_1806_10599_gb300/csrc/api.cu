@@ -223,6 +223,58 @@ struct gff_hostdata {
 
 namespace {
 
+// Orthonormal basis of the symmetric traceless 3x3 tensors (Frobenius product).
+void deviatoric_basis(double e[5][9]) {
+    const double r2 = std::sqrt(0.5), r6 = std::sqrt(1.0 / 6.0);
+    for (int i = 0; i < 5; ++i)
+        for (int k = 0; k < 9; ++k) e[i][k] = 0.0;
+    e[0][0] = r2, e[0][4] = -r2;                     // (E11 - E22) / sqrt 2
+    e[1][0] = -r6, e[1][4] = -r6, e[1][8] = 2 * r6;  // (2 E33 - E11 - E22) / sqrt 6
+    e[2][1] = e[2][3] = r2;                          // (E12 + E21) / sqrt 2
+    e[3][2] = e[3][6] = r2;                          // (E13 + E31) / sqrt 2
+    e[4][5] = e[4][7] = r2;                          // (E23 + E32) / sqrt 2
+}
+
+// out[0..59] = P [5][12], P_ia = e_i : sym(S0_a); out[60..84] = C5^-1 [5][5],
+// C5_ij = e_i : C : e_j.  False if C5 is not invertible.
+bool deviatoric_factors(const double* S0, const double* C, double* out) {
+    double e[5][9];
+    deviatoric_basis(e);
+    for (int i = 0; i < 5; ++i)
+        for (int a = 0; a < 12; ++a) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) v += e[i][3 * k + l] * 0.5 * (S0[9 * a + 3 * k + l] + S0[9 * a + 3 * l + k]);
+            out[12 * i + a] = v;
+        }
+    double M[5][10];  // [C5 | I], Gauss-Jordan with partial pivoting
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            double v = 0.0;
+            for (int ij = 0; ij < 9; ++ij)
+                for (int kl = 0; kl < 9; ++kl) v += e[i][ij] * C[9 * ij + kl] * e[j][kl];
+            M[i][j] = v;
+            M[i][5 + j] = i == j ? 1.0 : 0.0;
+        }
+    for (int k = 0; k < 5; ++k) {
+        int p = k;
+        for (int i = k + 1; i < 5; ++i)
+            if (std::fabs(M[i][k]) > std::fabs(M[p][k])) p = i;
+        if (!(std::fabs(M[p][k]) > 0.0)) return false;
+        for (int j = 0; j < 10; ++j) std::swap(M[k][j], M[p][j]);
+        const double inv = 1.0 / M[k][k];
+        for (int j = 0; j < 10; ++j) M[k][j] *= inv;
+        for (int i = 0; i < 5; ++i)
+            if (i != k) {
+                const double f = M[i][k];
+                for (int j = 0; j < 10; ++j) M[i][j] -= f * M[k][j];
+            }
+    }
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) out[60 + 5 * i + j] = M[i][5 + j];
+    return true;
+}
+
 gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const std::vector<int>& phase) {
     const int ng = h->ngrains;
     std::vector<double> C(81 * (size_t)ng), S0(108 * (size_t)ng), nrmprm((36 + 5 + 144) * (size_t)ng);
@@ -250,21 +302,9 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
                 nrmprm[36 * (size_t)g + 3 * a + i] = mr[i];
             }
         }
-        // H_ab = S0_a : C : sym(S0_b), the slip interaction at small elastic strain
-        double* Hg = &nrmprm[41 * (size_t)ng + 144 * (size_t)g];
-        const double* Sg = &S0[108 * (size_t)g];
-        const double* Cg = &C[81 * (size_t)g];
-        for (int a = 0; a < 12; ++a)
-            for (int b = 0; b < 12; ++b) {
-                double v = 0.0;
-                for (int ij = 0; ij < 9; ++ij)
-                    for (int kl = 0; kl < 9; ++kl) {
-                        const int k = kl / 3, l = kl % 3;
-                        const double symb = 0.5 * (Sg[9 * b + 3 * k + l] + Sg[9 * b + 3 * l + k]);
-                        v += Sg[9 * a + ij] * Cg[9 * ij + kl] * symb;
-                    }
-                Hg[12 * a + b] = v;
-            }
+        // factors of the small-strain slip interaction H = P^T C5 P (see cp_correction_lowrank)
+        if (!deviatoric_factors(&S0[108 * (size_t)g], &C[81 * (size_t)g], &nrmprm[41 * (size_t)ng + 144 * (size_t)g]))
+            return fail(h, GFF_ERR_ARG, "grain %d: stiffness not positive definite on deviatoric strains", g);
         double* pr = &nrmprm[36 * (size_t)ng + 5 * (size_t)g];
         pr[0] = mt.gdot0;
         pr[1] = mt.p_exp;

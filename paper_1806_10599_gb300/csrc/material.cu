@@ -244,40 +244,120 @@ __device__ void cp_jacobian_exact(const T* F, const T* A, const T* dg, const dou
     }
 }
 
-// Small-elastic-strain Jacobian: dtau_a/ddg_b ~ -H_ab with the per-grain
-// constant H_ab = S0_a : C : sym(S0_b) (Ce ~ I, S << C).  Used only to
-// choose Newton steps; the residual stays exact, so the root is unchanged.
-__device__ void cp_jacobian_approx(const double* __restrict__ H, const double* dg, const CPParamsDev& pr, double coef,
-                                   const double* chi, const double* dh, double* J) {
-    const double g = pr.tau0;
-    for (int a = 0; a < NSLIP; ++a) {
-        const double fa = (coef / g) * dh[a];
-        for (int b = 0; b < NSLIP; ++b) J[a * NSLIP + b] = fa * __ldg(H + a * NSLIP + b);
-        const double den = 1.0 + pr.d * fabs(dg[a]);
-        const double dchi = (pr.c - pr.d * sgn(dg[a]) * chi[a]) / den;
-        J[a * NSLIP + a] += 1.0 + fa * dchi;
+// Newton correction with the small-elastic-strain Jacobian.  At Ce ~ I and
+// S << C, dtau_a/ddg_b ~ -H_ab with the per-grain constant
+// H_ab = S0_a : C : sym(S0_b), so J = D + F H with the diagonals
+// D_a = 1 + f_a dchi_a >= 1 and F_a = f_a = (coef/tau0) h'_a >= 0.  The
+// symmetric traceless sym(S0_a) live in the 5-dimensional deviatoric space:
+// with an orthonormal basis e_i of it, sym(S0_a) = sum_i P_ia e_i and
+// H = P^T C5 P, C5_ij = e_i : C : e_j.  J x = r is then solved through the
+// 5 x 5 SPD system (C5^-1 + P G P^T) u = P D^-1 r, G = D^-1 F, and
+// x = D^-1 (r - F P^T u) -- the same correction as a 12 x 12 solve with J,
+// at a fraction of the work and registers.  PC holds P [5][12] then C5^-1
+// [5][5] for the grain.  The correction only steers the iteration: the FP64
+// residual decides convergence.
+template <typename TJ>
+__device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__ PC, const double* dg,
+                                                      const CPParamsDev& pr, double coef, const double* chi,
+                                                      const double* dh, const double* r, double* x) {
+    const TJ cg = (TJ)(coef / pr.tau0), c = (TJ)pr.c, d = (TJ)pr.d;
+    TJ A[15], b[5];  // packed lower triangle of C5^-1 + P G P^T, and P D^-1 r
+    {
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            b[i] = (TJ)0;
+#pragma unroll
+            for (int j = 0; j <= i; ++j) A[k++] = (TJ)__ldg(PC + 60 + 5 * i + j);
+        }
     }
+    TJ f[NSLIP], Di[NSLIP];
+#pragma unroll
+    for (int a = 0; a < NSLIP; ++a) {
+        f[a] = cg * (TJ)dh[a];
+        const TJ dga = (TJ)dg[a];
+        const TJ dchi = (c - d * sgn(dga) * (TJ)chi[a]) / ((TJ)1 + d * fabs(dga));
+        Di[a] = (TJ)1 / ((TJ)1 + f[a] * dchi);
+        const TJ ga = f[a] * Di[a], ra = (TJ)r[a] * Di[a];
+        TJ p[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) p[i] = (TJ)__ldg(PC + 12 * i + a);
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            b[i] = fma(ra, p[i], b[i]);
+#pragma unroll
+            for (int j = 0; j <= i; ++j) A[k] = fma(ga * p[i], p[j], A[k]), ++k;
+        }
+    }
+    // A = L diag(q) L^T (no pivoting: A is SPD)
+    TJ L[5][5], q[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        TJ s = A[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k] * q[k];
+        if (!(s > (TJ)0)) return false;
+        q[j] = s;
+        const TJ inv = (TJ)1 / s;
+#pragma unroll
+        for (int i = j + 1; i < 5; ++i) {
+            TJ t = A[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k] * q[k];
+            L[i][j] = t * inv;
+        }
+    }
+    TJ u[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        TJ t = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= L[i][k] * u[k];
+        u[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) u[i] /= q[i];
+#pragma unroll
+    for (int i = 4; i >= 0; --i) {
+#pragma unroll
+        for (int k = i + 1; k < 5; ++k) u[i] -= L[k][i] * u[k];
+    }
+#pragma unroll
+    for (int a = 0; a < NSLIP; ++a) {
+        TJ t = (TJ)0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) t = fma((TJ)__ldg(PC + 12 * i + a), u[i], t);
+        x[a] = (double)(Di[a] * ((TJ)r[a] - f[a] * t));
+    }
+    return true;
 }
 
-// Local Newton on dg from the given start; approximate or exact Jacobian (FP64).
+// Local Newton on dg from the given start.  lowrank: corrections from the
+// small-elastic-strain Jacobian in precision TJ; otherwise the exact
+// Jacobian with pivoting in FP64.
+template <typename TJ>
 __device__ bool cp_local_solve(const double* F, const double* A, const double* chin, const double* __restrict__ S0,
-                               const double* __restrict__ C, const double* __restrict__ H, const CPParamsDev& pr,
-                               double coef, int p, bool approx, int maxit, double* dg, ElState& st, double* chi,
+                               const double* __restrict__ C, const double* __restrict__ PC, const CPParamsDev& pr,
+                               double coef, int p, bool lowrank, int maxit, double* dg, ElState& st, double* chi,
                                double* dh) {
-    double J[NSLIP * NSLIP];
-    int piv[NSLIP];
     for (int it = 0; it <= maxit; ++it) {
         double r[NSLIP];
         const double rmax = cp_residual(F, A, chin, dg, S0, C, pr, coef, p, st, chi, dh, r);
         if (rmax <= 1e-14) return true;
         if (it == maxit || !(rmax < 1e300)) return false;
-        if (approx)
-            cp_jacobian_approx(H, dg, pr, coef, chi, dh, J);
-        else
+        if (lowrank) {
+            double x[NSLIP];
+            if (!cp_correction_lowrank<TJ>(PC, dg, pr, coef, chi, dh, r, x)) return false;
+            for (int a = 0; a < NSLIP; ++a) dg[a] -= x[a];
+        } else {
+            double J[NSLIP * NSLIP];
+            int piv[NSLIP];
             cp_jacobian_exact<double>(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
-        if (!lu_factor<NSLIP>(J, piv)) return false;
-        lu_solve<NSLIP>(J, piv, r);
-        for (int a = 0; a < NSLIP; ++a) dg[a] -= r[a];
+            if (!lu_factor<NSLIP>(J, piv)) return false;
+            lu_solve<NSLIP>(J, piv, r);
+            for (int a = 0; a < NSLIP; ++a) dg[a] -= r[a];
+        }
     }
     return false;
 }
@@ -388,10 +468,12 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
     double dg[NSLIP], dh[NSLIP], chi[NSLIP];
     ElState st;
     for (int a = 0; a < NSLIP; ++a) dg[a] = dg0 ? dg0[a] : 0.0;
-    bool conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh);
+    // FP64 corrections: J is ill-conditioned (cond ~ 1e8 and more) once slip
+    // systems are active, beyond what an FP32 solve can steer
+    bool conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh);
     if (!conv) {  // fall back: exact Newton from dg = 0
         for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
-        conv = cp_local_solve(F, A, chin, S0, C, H, pr, coef, p, false, 300, dg, st, chi, dh);
+        conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, false, 300, dg, st, chi, dh);
     }
     out.ok = conv;
     double FeS[9];
@@ -442,7 +524,7 @@ struct ConstArgs {
     const int* gid;
     const double* C;
     const double* S0;
-    const double* H;  // [ngrains][144] small-strain slip-interaction matrix
+    const double* H;  // [ngrains][144]: P [5][12], C5^-1 [5][5] of the small-strain Jacobian (cp_correction_lowrank)
     int warm;         // 1: start the local Newton from dg (previous iterate)
     const int* gkind;
     const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
