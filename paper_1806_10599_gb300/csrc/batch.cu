@@ -105,7 +105,7 @@ BatchLaunch make_launch(Batch& B, const std::vector<RveApply>& rv, RveApply* d_r
     for (int r = 0; r < B.n; ++r) {
         const GridDev& g = rv[r].g;
         start_pl[r + 1] = start_pl[r] + 9 * g.nz;
-        start_z[r + 1] = start_z[r] + (int)(((long long)g.ny * g.nxh + tn.wz - 1) / tn.wz);
+        start_z[r + 1] = start_z[r] + zproj_blocks(g, tn.wz);
         bl.smem_plane = std::max(bl.smem_plane, batch_plane_smem(g.nx, g.ny, (int)sizeof(typename C2<T>::t)));
         bl.smem_z = std::max(bl.smem_z, batch_z_smem<T>(g, tn.wz));
         bl.vin = bl.vin && vec_aligned<T>(g, rv[r].x) && (!withK || vec_aligned<T>(g, rv[r].K));

@@ -367,13 +367,17 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, cons
 }
 
 // ---------------------------------------------------------------- pass 2: z transform + projection
+// G_ijkl = delta_ik n_j n_l maps row i of the tensor onto row i only
+// (y_ij = n_j sum_l x_il n_l), so a block takes one tensor row (components
+// 3i, 3i+1, 3i+2) and W consecutive (ky, kx) columns: 3 x nz x W values,
+// each row segment of W contiguous complex values read and written whole.
 template <typename T, int W>
 __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec, const GridDev& g,
                                            const ProjArgs& pa, const int blk, unsigned char* sm_raw) {
     using C = typename C2<T>::t;
     const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
-    C* s = reinterpret_cast<C*>(sm_raw);  // [9][nz][W]
-    C* twz = s + 9 * nz * W;
+    C* s = reinterpret_cast<C*>(sm_raw);  // [3][nz][W]
+    C* twz = s + 3 * nz * W;
     T* qx = reinterpret_cast<T*>(twz + nz);
     T* qy = qx + nxh;
     T* qz = qy + ny;
@@ -381,7 +385,9 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
     int* fqz = fqy + ny;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long nF = (long long)ny * nxh;
-    const long long f0 = (long long)blk * W;
+    const int row = blk % 3;
+    const long long f0 = (long long)(blk / 3) * W;
+    C* base = spec + (long long)(3 * row) * nz * nF;  // component 3 row, z = 0
 
     for (int i = tid; i < nz; i += nthr) {
         twz[i] = twp<T>(g, 2)[i];
@@ -393,54 +399,51 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
         fqy[i] = g.fqy[i];
     }
     for (int i = tid; i < nxh; i += nthr) qx[i] = qtp<T>(g, pa.kind, 0)[i];
-    for (int e = tid; e < 9 * nz * W; e += nthr) {
+    for (int e = tid; e < 3 * nz * W; e += nthr) {
         const int w = e % W;
-        const long long cz = e / W;
+        const long long cz = e / W;  // (component within the row) * nz + z
         const long long f = f0 + w;
-        s[e] = f < nF ? spec[cz * nF + f] : mk<C>((T)0, (T)0);
+        s[e] = f < nF ? base[cz * nF + f] : mk<C>((T)0, (T)0);
     }
     __syncthreads();
-    fft_lines<T, false>(s, twz, g.az, W, 1, 9, nz * W, W, tid, nthr);
+    fft_lines<T, false>(s, twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
 
+    const T m0 = (T)pa.mask[3 * row], m1 = (T)pa.mask[3 * row + 1], m2 = (T)pa.mask[3 * row + 2];
     for (int e = tid; e < nz * W; e += nthr) {
         const int w = e % W, pz = e / W;
         const long long f = f0 + w;
         if (f >= nF) continue;
         const int py = (int)(f / nxh), kx = (int)(f - (long long)py * nxh);
         const int ky = fqy[py], kz = fqz[pz];
-        C v[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) v[c] = s[(c * nz + pz) * W + w];
+        C* p0 = s + pz * W + w;
+        C v0 = p0[0], v1 = p0[nz * W], v2 = p0[2 * nz * W];
         if (kx == 0 && ky == 0 && kz == 0) {
-#pragma unroll
-            for (int c = 0; c < 9; ++c) v[c] = cscale(v[c], (T)pa.mask[c]);
+            v0 = cscale(v0, m0);
+            v1 = cscale(v1, m1);
+            v2 = cscale(v2, m2);
         } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
-#pragma unroll
-            for (int c = 0; c < 9; ++c) v[c] = mk<C>((T)0, (T)0);
+            v0 = v1 = v2 = mk<C>((T)0, (T)0);
         } else {
             const T a = qx[kx], b = qy[ky], d = qz[kz];
             const T inv = (T)1 / sqrt(a * a + b * b + d * d);
             const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                // t_i = sum_l x_il n_l ; y_ij = t_i n_j   (G_ijkl = delta_ik n_j n_l)
-                const C t = mk<C>(v[3 * i].x * n0 + v[3 * i + 1].x * n1 + v[3 * i + 2].x * n2,
-                                  v[3 * i].y * n0 + v[3 * i + 1].y * n1 + v[3 * i + 2].y * n2);
-                v[3 * i] = cscale(t, n0);
-                v[3 * i + 1] = cscale(t, n1);
-                v[3 * i + 2] = cscale(t, n2);
-            }
+            // t = sum_l x_il n_l ; y_ij = t n_j
+            const C t = mk<C>(v0.x * n0 + v1.x * n1 + v2.x * n2, v0.y * n0 + v1.y * n1 + v2.y * n2);
+            v0 = cscale(t, n0);
+            v1 = cscale(t, n1);
+            v2 = cscale(t, n2);
         }
-#pragma unroll
-        for (int c = 0; c < 9; ++c) s[(c * nz + pz) * W + w] = v[c];
+        p0[0] = v0;
+        p0[nz * W] = v1;
+        p0[2 * nz * W] = v2;
     }
     __syncthreads();
-    fft_lines<T, true>(s, twz, g.az, W, 1, 9, nz * W, W, tid, nthr);
-    for (int e = tid; e < 9 * nz * W; e += nthr) {
+    fft_lines<T, true>(s, twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+    for (int e = tid; e < 3 * nz * W; e += nthr) {
         const int w = e % W;
         const long long cz = e / W;
         const long long f = f0 + w;
-        if (f < nF) spec[cz * nF + f] = s[e];
+        if (f < nF) base[cz * nF + f] = s[e];
     }
 }
 
@@ -546,11 +549,11 @@ __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __re
     plane_inv_body<T, VEC>(spec, y, g, oa, blockIdx.x, blockIdx.y, sm_raw);
 }
 
-template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 4 : 8; }
+template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 16; }
 
 template <typename T> size_t zproj_smem(const GridDev& g, int W = zproj_width<T>()) {
     using C = typename C2<T>::t;
-    return (size_t)9 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
+    return (size_t)3 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
            (g.ny + g.nz) * sizeof(int) + 16;
 }
 
@@ -603,9 +606,8 @@ template <typename T, int W>
 cudaError_t launch_z_w(const GridDev& g, int threads, typename C2<T>::t* spec, const ProjArgs& pa, const int* skip,
                        cudaStream_t st) {
     const size_t smB = zproj_smem<T>(g, W);
-    const long long nF = (long long)g.ny * g.nxh;
     allow_smem(k_zproj<T, W>, smB);
-    k_zproj<T, W><<<(int)((nF + W - 1) / W), threads, smB, st>>>(spec, g, pa, skip);
+    k_zproj<T, W><<<zproj_blocks(g, W), threads, smB, st>>>(spec, g, pa, skip);
     return cudaGetLastError();
 }
 
@@ -617,6 +619,7 @@ cudaError_t launch_z(const GridDev& g, int W, int threads, typename C2<T>::t* sp
         case 4: return launch_z_w<T, 4>(g, threads, spec, pa, skip, st);
         case 8: return launch_z_w<T, 8>(g, threads, spec, pa, skip, st);
         case 16: return launch_z_w<T, 16>(g, threads, spec, pa, skip, st);
+        case 32: return launch_z_w<T, 32>(g, threads, spec, pa, skip, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -685,7 +688,7 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     cudaError_t e = pick_fastest(2, tv, reps, st, [&](int i) { return launch_fwd<T>(g, tp[i], x, K, spec, nullptr, st, vin); }, &b);
     if (e != cudaSuccess) return e;
     tn.t_fwd = tp[b];
-    const int wz[4] = {2, 4, 8, 16};
+    const int wz[4] = {4, 8, 16, 32};
     const int tz[2] = {128, 256};
     bool zv[8];
     for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i / 2]) <= SMEM_MAX;
@@ -800,6 +803,7 @@ cudaError_t launch_galerkin_batch(const BatchLaunch& bl, const ProjArgs& pa, cud
         case 4: e = launch_zb<T, 4>(bl, pa, st); break;
         case 8: e = launch_zb<T, 8>(bl, pa, st); break;
         case 16: e = launch_zb<T, 16>(bl, pa, st); break;
+        case 32: e = launch_zb<T, 32>(bl, pa, st); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -939,11 +943,10 @@ cudaError_t noalloc_launch(const GridDev& g, const T* x, T* y, const ProjArgs& p
     const size_t smB = zproj_smem<T>(g);
     constexpr int W = zproj_width<T>();
     const dim3 gridA(9, g.nz);
-    const long long nF = (long long)g.ny * g.nxh;
     allow_smem(k_plane_fwd<T, false, false>, smA);
     k_plane_fwd<T, false, false><<<gridA, 512, smA, st>>>(x, nullptr, spec, g, nullptr);
     allow_smem(k_zproj<T, W>, smB);
-    k_zproj<T, W><<<(int)((nF + W - 1) / W), 256, smB, st>>>(spec, g, pa, nullptr);
+    k_zproj<T, W><<<zproj_blocks(g, W), 256, smB, st>>>(spec, g, pa, nullptr);
     allow_smem(k_plane_inv<T, false>, smA);
     k_plane_inv<T, false><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr);
     return cudaGetLastError();

@@ -164,7 +164,7 @@ struct gff_handle {
     bool K32_valid = false;
     bool grains_ready = false;
     void* hostdata = nullptr;  // host copies of the orientations and phases
-    gff::Tune tune[2] = {{512, 4, 256, 512}, {512, 8, 256, 512}};  // [0] FP64, [1] FP32
+    gff::Tune tune[2] = {{512, 8, 256, 512}, {512, 16, 256, 512}};  // [0] FP64, [1] FP32
     bool tuned = false;
     // warm starts: history of the completed increments.  d is an increment's
     // prescribed average F change (0 on stress-controlled components) and
@@ -202,12 +202,14 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
                             const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr,
                             const int* skip = nullptr);
 size_t plane_smem_bytes(int nx, int ny, int elem);
+// Blocks of the z pass: one per tensor row (3) and W (ky, kx) columns.
+inline int zproj_blocks(const GridDev& g, int W) { return 3 * (int)(((long long)g.ny * g.nxh + W - 1) / W); }
 // Times every candidate launch shape of the three kernels on the handle's own
 // buffers and stores the fastest in h->tune (results do not depend on it).
 cudaError_t autotune_galerkin(gff_handle* h);
 
 // Batched apply: rv (device, n entries), start arrays (device) for the plane
-// kernels (9 nz blocks per RVE) and the z kernel (ceil(ny nxh / wz) blocks).
+// kernels (9 nz blocks per RVE) and the z kernel (zproj_blocks per RVE).
 struct BatchLaunch {
     int n;
     const RveApply* rv;
