@@ -34,39 +34,6 @@ gff_status fail(gff_handle* h, gff_status st, const char* fmt, ...) {
 }
 
 // ------------------------------------------------------------------ axis plans and tables
-bool make_plan(int n, AxisPlan& p) {
-    if (n < 4 || n > MAXN || (n & 1)) return false;
-    int m = n, a2 = 0, a3 = 0, a5 = 0;
-    while (m % 2 == 0) { m /= 2; ++a2; }
-    while (m % 3 == 0) { m /= 3; ++a3; }
-    while (m % 5 == 0) { m /= 5; ++a5; }
-    if (m != 1) return false;
-    p.n = n;
-    p.nst = 0;
-    while (a2 >= 3) { p.radix[p.nst++] = 8; a2 -= 3; }
-    if (a2 == 2) p.radix[p.nst++] = 4;
-    if (a2 == 1) p.radix[p.nst++] = 2;
-    for (int i = 0; i < a5; ++i) p.radix[p.nst++] = 5;
-    for (int i = 0; i < a3; ++i) p.radix[p.nst++] = 3;
-    return p.nst <= MAXST;
-}
-
-// Frequency held at position `pos` after the in-place forward (decimation in
-// frequency) transform: pos = sum_i p_i m_i with m_i = n / (r_0...r_i), and
-// the frequency is p_0 + r_0 p_1 + r_0 r_1 p_2 + ...
-int freq_of_pos(int pos, const AxisPlan& p) {
-    int f = 0, mult = 1, len = p.n;
-    for (int i = 0; i < p.nst; ++i) {
-        const int m = len / p.radix[i];
-        const int d = pos / m;
-        pos -= d * m;
-        f += d * mult;
-        mult *= p.radix[i];
-        len = m;
-    }
-    return f;
-}
-
 struct TableLayout {
     size_t tw64, tw32, posx, fqy, fqz, qt64, qt32, total;
 };
@@ -89,7 +56,7 @@ gff_status build_tables(gff_handle* h) {
     const int n3[3] = {h->grid.nx, h->grid.ny, h->grid.nz};
     AxisPlan* pl[3] = {&h->g.ax, &h->g.ay, &h->g.az};
     for (int a = 0; a < 3; ++a)
-        if (!make_plan(n3[a], *pl[a]))
+        if (!make_axis_plan(n3[a], *pl[a]))
             return fail(h, GFF_ERR_ARG, "grid axis %d: n = %d unsupported (even, 4..%d, factors 2,3,5)", a, n3[a], MAXN);
     const TableLayout L = table_layout();
     std::vector<unsigned char> host(L.total, 0);
@@ -120,9 +87,9 @@ gff_status build_tables(gff_handle* h) {
             qt32[(1 * 3 + a) * MAXN + k] = (float)qd;
         }
     }
-    for (int p = 0; p < h->grid.nx; ++p) posx[freq_of_pos(p, h->g.ax)] = p;
-    for (int p = 0; p < h->grid.ny; ++p) fqy[p] = freq_of_pos(p, h->g.ay);
-    for (int p = 0; p < h->grid.nz; ++p) fqz[p] = freq_of_pos(p, h->g.az);
+    for (int p = 0; p < h->grid.nx; ++p) posx[axis_freq_of_pos(p, h->g.ax)] = p;
+    for (int p = 0; p < h->grid.ny; ++p) fqy[p] = axis_freq_of_pos(p, h->g.ay);
+    for (int p = 0; p < h->grid.nz; ++p) fqz[p] = axis_freq_of_pos(p, h->g.az);
     cudaError_t e = cudaMalloc(&h->tables, L.total);
     if (e != cudaSuccess) return fail(h, GFF_ERR_OOM, "tables: %s", cudaGetErrorString(e));
     e = cudaMemcpy(h->tables, host.data(), L.total, cudaMemcpyHostToDevice);

@@ -14,11 +14,13 @@
 //   k_plane_inv  one CTA per (c, z): inverse y, complex-to-real x, epilogue
 //                out = scale * y + add_c.
 //
-// Each axis transform is an in-place mixed-radix (2, 3, 4, 5, 8) FFT in
+// Each axis transform is an in-place mixed-radix (2, 3, 4, 5, 8, 16) FFT in
 // shared memory: forward = decimation in frequency (natural order in,
 // digit-reversed out), inverse = the same stages replayed backwards with
 // conjugate twiddles (digit-reversed in, natural out), so no reordering pass
 // is needed; the projection reads the frequency of each position from a table.
+// The common lengths (16 ... 128) have two-stage plans with compile-time
+// radices (fft2_lines); the others run the generic stages.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -133,6 +135,48 @@ template <bool INV, typename C> struct Bfly<5, INV, C> {
     }
 };
 
+// a * (c -+ i s): multiplication by a constant twiddle exp(-+ i theta), c = cos, s = sin
+template <bool INV, typename C, typename T>
+__device__ __forceinline__ C twc(C a, T c, T s) {
+    return INV ? mk<C>(a.x * c - a.y * s, a.y * c + a.x * s) : mk<C>(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+// radix 16 as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2,
+// X[k1 + 4 k2] = sum_n2 w4^(n2 k2) w16^(n2 k1) sum_n1 x[4 n1 + n2] w4^(n1 k1)
+template <bool INV, typename C> struct Bfly<16, INV, C> {
+    static __device__ __forceinline__ void run(C* v) {
+        using T = decltype(C::x);
+        const T c1 = (T)0.92387953251128675613;  // cos(pi / 8)
+        const T s1 = (T)0.38268343236508977173;  // sin(pi / 8)
+        const T h = (T)0.70710678118654752440;   // cos(pi / 4)
+        C y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+            C a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+            Bfly<4, INV, C>::run(a);
+#pragma unroll
+            for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = a[k1];
+        }
+        // w16^m for m = n2 k1: 1 (c1, s1), 2 (h, h), 3 (s1, c1), 4 (-+ i), 6 (-h, h), 9 (-c1, -s1)
+        y[1][1] = twc<INV>(y[1][1], c1, s1);
+        y[1][2] = twc<INV>(y[1][2], h, h);
+        y[1][3] = twc<INV>(y[1][3], s1, c1);
+        y[2][1] = twc<INV>(y[2][1], h, h);
+        y[2][2] = rot90<INV>(y[2][2]);
+        y[2][3] = twc<INV>(y[2][3], -h, h);
+        y[3][1] = twc<INV>(y[3][1], s1, c1);
+        y[3][2] = twc<INV>(y[3][2], -h, h);
+        y[3][3] = twc<INV>(y[3][3], -c1, -s1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            C b[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Bfly<4, INV, C>::run(b);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+        }
+    }
+};
+
 // ---------------------------------------------------------------- one radix stage
 // Lines l = ls * NLF + lf start at s + ls*SS + lf*SF; elements are ES apart.
 // Sub-arrays of length `len` are split by radix R with stride m = len / R.
@@ -183,6 +227,7 @@ __device__ __forceinline__ void stage_dispatch(int R, typename C2<T>::t* s, cons
                                                int len, int NLF, int SF, int NLS, int SS, int ES, int tid,
                                                int nthr) {
     switch (R) {
+        case 16: run_stage<T, 16, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
         case 8: run_stage<T, 8, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
         case 4: run_stage<T, 4, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
         case 2: run_stage<T, 2, INV>(s, tw, n, len, NLF, SF, NLS, SS, ES, tid, nthr); break;
@@ -192,11 +237,95 @@ __device__ __forceinline__ void stage_dispatch(int R, typename C2<T>::t* s, cons
     }
 }
 
-// Whole transform of a batch of lines; ends with a barrier.
+// q = x / d, r = x - q d for 0 <= x < 2^22 and d >= 1 (invd = 1 / d as float):
+// the float quotient is within one of the true one, and one correction fixes it.
+__device__ __forceinline__ int divmod_f(int x, int d, float invd, int& r) {
+    int q = __float2int_rz(__int2float_rn(x) * invd);
+    r = x - q * d;
+    if (r < 0) {
+        --q;
+        r += d;
+    } else if (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return q;
+}
+
+// Two-stage transform of length N = R1 R2 (the plans of the common sizes):
+// the radix-R1 stage over stride R2 with twiddles w_N^(p j), then radix R2
+// over contiguous runs without twiddles -- the generic stages below with
+// compile-time radices and one (float) division per butterfly.
+template <typename T, int R1, int R2, bool TWIDDLED, bool INV>
+__device__ __forceinline__ void fft2_stage(typename C2<T>::t* s, const typename C2<T>::t* tw, int NLF, float invNLF,
+                                           int SF, int NLS, int SS, int ES, int tid, int nthr) {
+    using C = typename C2<T>::t;
+    // TWIDDLED: radix R1, tasks j < R2, elements j + q R2; else radix R2, tasks sub < R1, elements sub R2 + q
+    constexpr int R = TWIDDLED ? R1 : R2;
+    constexpr int TASKS = TWIDDLED ? R2 : R1;
+    const int total = NLF * TASKS * NLS;
+    const int st = (TWIDDLED ? R2 : 1) * ES;
+    for (int idx = tid; idx < total; idx += nthr) {
+        int lf = 0, t = idx;
+        if (NLF > 1) t = divmod_f(idx, NLF, invNLF, lf);
+        const int task = t % TASKS, lsl = t / TASKS;
+        C* base = s + lsl * SS + lf * SF + (TWIDDLED ? task : task * R2) * ES;
+        C v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = base[q * st];
+        if (TWIDDLED && INV && task) {
+#pragma unroll
+            for (int p = 1; p < R; ++p) v[p] = cmulc(v[p], tw[p * task]);
+        }
+        Bfly<R, INV, C>::run(v);
+        if (TWIDDLED && !INV && task) {
+#pragma unroll
+            for (int p = 1; p < R; ++p) v[p] = cmul(v[p], tw[p * task]);
+        }
+#pragma unroll
+        for (int p = 0; p < R; ++p) base[p * st] = v[p];
+    }
+}
+
+template <typename T, int R1, int R2, bool INV>
+__device__ __forceinline__ void fft2_lines(typename C2<T>::t* s, const typename C2<T>::t* tw, int NLF, int SF,
+                                           int NLS, int SS, int ES, int tid, int nthr) {
+    const float invNLF = 1.0f / (float)NLF;
+    if (!INV) {
+        fft2_stage<T, R1, R2, true, false>(s, tw, NLF, invNLF, SF, NLS, SS, ES, tid, nthr);
+        __syncthreads();
+        fft2_stage<T, R1, R2, false, false>(s, tw, NLF, invNLF, SF, NLS, SS, ES, tid, nthr);
+    } else {
+        fft2_stage<T, R1, R2, false, true>(s, tw, NLF, invNLF, SF, NLS, SS, ES, tid, nthr);
+        __syncthreads();
+        fft2_stage<T, R1, R2, true, true>(s, tw, NLF, invNLF, SF, NLS, SS, ES, tid, nthr);
+    }
+    __syncthreads();
+}
+
+// Whole transform of a batch of lines; ends with a barrier.  Not inlined:
+// every kernel calls the same four instances (precision x direction).
 template <typename T, bool INV>
-__device__ void fft_lines(typename C2<T>::t* s, const typename C2<T>::t* tw, const AxisPlan& pl, int NLF, int SF,
+__device__ __noinline__ void fft_lines(typename C2<T>::t* s, const typename C2<T>::t* tw, const AxisPlan& pl, int NLF, int SF,
                           int NLS, int SS, int ES, int tid, int nthr) {
     const int n = pl.n;
+    if (pl.nst == 2) {
+        const int r1 = pl.radix[0], r2 = pl.radix[1];
+#define GFF_FFT2(A, B)                                                                  \
+    if (r1 == A && r2 == B) {                                                           \
+        fft2_lines<T, A, B, INV>(s, tw, NLF, SF, NLS, SS, ES, tid, nthr);               \
+        return;                                                                         \
+    }
+        GFF_FFT2(16, 8)
+        GFF_FFT2(8, 8)
+        GFF_FFT2(16, 5)
+        GFF_FFT2(16, 3)
+        GFF_FFT2(8, 5)
+        GFF_FFT2(8, 4)
+        GFF_FFT2(8, 3)
+        GFF_FFT2(4, 4)
+#undef GFF_FFT2
+    }
     if (!INV) {
         int len = n;
         for (int k = 0; k < pl.nst; ++k) {
@@ -571,6 +700,46 @@ template <typename K> void allow_smem(K kern, size_t bytes) {
 
 }  // namespace
 
+bool make_axis_plan(int n, AxisPlan& p) {
+    if (n < 4 || n > MAXN || (n & 1)) return false;
+    int m = n, a2 = 0, a3 = 0, a5 = 0;
+    while (m % 2 == 0) { m /= 2; ++a2; }
+    while (m % 3 == 0) { m /= 3; ++a3; }
+    while (m % 5 == 0) { m /= 5; ++a5; }
+    if (m != 1) return false;
+    p.n = n;
+    p.nst = 0;
+    // two stages where fft2_lines has the pair
+    static const int pairs[8][2] = {{16, 8}, {8, 8}, {16, 5}, {16, 3}, {8, 5}, {8, 4}, {8, 3}, {4, 4}};
+    for (const auto& pr : pairs)
+        if (pr[0] * pr[1] == n) {
+            p.nst = 2;
+            p.radix[0] = pr[0];
+            p.radix[1] = pr[1];
+            return true;
+        }
+    while (a2 >= 4) { p.radix[p.nst++] = 16; a2 -= 4; }
+    if (a2 == 3) p.radix[p.nst++] = 8;
+    if (a2 == 2) p.radix[p.nst++] = 4;
+    if (a2 == 1) p.radix[p.nst++] = 2;
+    for (int i = 0; i < a5; ++i) p.radix[p.nst++] = 5;
+    for (int i = 0; i < a3; ++i) p.radix[p.nst++] = 3;
+    return p.nst <= MAXST;
+}
+
+int axis_freq_of_pos(int pos, const AxisPlan& p) {
+    int f = 0, mult = 1, len = p.n;
+    for (int i = 0; i < p.nst; ++i) {
+        const int m = len / p.radix[i];
+        const int d = pos / m;
+        pos -= d * m;
+        f += d * mult;
+        mult *= p.radix[i];
+        len = m;
+    }
+    return f;
+}
+
 size_t plane_smem_bytes(int nx, int ny, int elem) {
     return (size_t)ny * (nx / 2 + 1) * elem + (size_t)(nx + ny) * elem + (size_t)nx * sizeof(int) + 16;
 }
@@ -615,7 +784,6 @@ template <typename T>
 cudaError_t launch_z(const GridDev& g, int W, int threads, typename C2<T>::t* spec, const ProjArgs& pa,
                      const int* skip, cudaStream_t st) {
     switch (W) {
-        case 2: return launch_z_w<T, 2>(g, threads, spec, pa, skip, st);
         case 4: return launch_z_w<T, 4>(g, threads, spec, pa, skip, st);
         case 8: return launch_z_w<T, 8>(g, threads, spec, pa, skip, st);
         case 16: return launch_z_w<T, 16>(g, threads, spec, pa, skip, st);
@@ -799,7 +967,6 @@ cudaError_t launch_galerkin_batch(const BatchLaunch& bl, const ProjArgs& pa, cud
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (bl.tn.wz) {
-        case 2: e = launch_zb<T, 2>(bl, pa, st); break;
         case 4: e = launch_zb<T, 4>(bl, pa, st); break;
         case 8: e = launch_zb<T, 8>(bl, pa, st); break;
         case 16: e = launch_zb<T, 16>(bl, pa, st); break;
@@ -904,36 +1071,10 @@ cudaError_t noalloc_scratch(void** out) {
     return cudaSuccess;
 }
 
-bool noalloc_plan(int n, AxisPlan& p) {
-    if (n < 4 || n > MAXN || (n & 1)) return false;
-    int m = n, a2 = 0, a3 = 0, a5 = 0;
-    while (m % 2 == 0) { m /= 2; ++a2; }
-    while (m % 3 == 0) { m /= 3; ++a3; }
-    while (m % 5 == 0) { m /= 5; ++a5; }
-    if (m != 1) return false;
-    p.n = n;
-    p.nst = 0;
-    while (a2 >= 3) { p.radix[p.nst++] = 8; a2 -= 3; }
-    if (a2 == 2) p.radix[p.nst++] = 4;
-    if (a2 == 1) p.radix[p.nst++] = 2;
-    for (int i = 0; i < a5; ++i) p.radix[p.nst++] = 5;
-    for (int i = 0; i < a3; ++i) p.radix[p.nst++] = 3;
-    return p.nst <= MAXST;
-}
+bool noalloc_plan(int n, AxisPlan& p) { return make_axis_plan(n, p); }
 
 // frequency at position pos after the in-place forward transform of plan p
-int noalloc_freq(int pos, const AxisPlan& p) {
-    int f = 0, mult = 1, len = p.n;
-    for (int i = 0; i < p.nst; ++i) {
-        const int m = len / p.radix[i];
-        const int d = pos / m;
-        pos -= d * m;
-        f += d * mult;
-        mult *= p.radix[i];
-        len = m;
-    }
-    return f;
-}
+int noalloc_freq(int pos, const AxisPlan& p) { return axis_freq_of_pos(pos, p); }
 
 template <typename T>
 cudaError_t noalloc_launch(const GridDev& g, const T* x, T* y, const ProjArgs& pa, const OutArgs& oa,

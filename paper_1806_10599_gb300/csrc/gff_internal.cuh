@@ -202,6 +202,11 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
                             const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr,
                             const int* skip = nullptr);
 size_t plane_smem_bytes(int nx, int ny, int elem);
+// Mixed-radix plan of one axis (false: n unsupported) and the frequency held
+// at position pos after the forward (decimation in frequency) transform:
+// pos = sum_i p_i m_i with m_i = n / (r_0 ... r_i), frequency p_0 + r_0 p_1 + ...
+bool make_axis_plan(int n, AxisPlan& p);
+int axis_freq_of_pos(int pos, const AxisPlan& p);
 // Blocks of the z pass: one per tensor row (3) and W (ky, kx) columns.
 inline int zproj_blocks(const GridDev& g, int W) { return 3 * (int)(((long long)g.ny * g.nxh + W - 1) / W); }
 // Times every candidate launch shape of the three kernels on the handle's own
