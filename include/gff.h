@@ -169,8 +169,9 @@ gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t*
  * candidate on this grid; results are bitwise the same for every choice.
  * gff_step runs it once per handle if it has not been run.  Uses the handle's
  * work buffers (call it before setting up an apply by hand, or call
- * gff_constitutive again afterwards).  tiles_out (host, 8 ints, may be NULL):
- * {fwd threads, z columns, z threads, inv threads} for FP64 then FP32. */
+ * gff_constitutive again afterwards).  tiles_out (host, 10 ints, may be NULL):
+ * {fwd threads, z columns, z threads, inv threads, inv persistent blocks
+ * (0: one block per plane)} for FP64 then FP32. */
 gff_status gff_autotune(gff_handle* h, int* tiles_out);
 
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */

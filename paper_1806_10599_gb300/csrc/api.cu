@@ -636,6 +636,9 @@ GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, con
     for (int i = 0; i < 4; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
     if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "timed apply: %s", cudaGetErrorString(e));
+    int tmo = 0;
+    GFF_TRY(cudaMemcpy(&tmo, h->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost));
+    if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in the inverse FFT pass timed out");
     return GFF_OK;
 }
 
@@ -655,10 +658,11 @@ GFF_EXPORT gff_status gff_autotune(gff_handle* h, int* tiles_out) {
     GFF_TRY(autotune_galerkin(h));
     if (tiles_out)
         for (int p = 0; p < 2; ++p) {
-            tiles_out[4 * p + 0] = h->tune[p].t_fwd;
-            tiles_out[4 * p + 1] = h->tune[p].wz;
-            tiles_out[4 * p + 2] = h->tune[p].t_z;
-            tiles_out[4 * p + 3] = h->tune[p].t_inv;
+            tiles_out[5 * p + 0] = h->tune[p].t_fwd;
+            tiles_out[5 * p + 1] = h->tune[p].wz;
+            tiles_out[5 * p + 2] = h->tune[p].t_z;
+            tiles_out[5 * p + 3] = h->tune[p].t_inv;
+            tiles_out[5 * p + 4] = h->tune[p].inv_blocks;
         }
     return GFF_OK;
 }
@@ -785,17 +789,20 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         GFF_TRY(launch_dot<double>(h->d_b, h->d_b, n, h->d_red, h->d_scal, h->stream));
         GFF_TRY(launch_dot<double>(h->d_P, h->d_P, n, h->d_red + RED_BLOCKS, h->d_scal + 1, h->stream));
         GFF_TRY(cudaMemcpyAsync(h->d_scal + 2, h->d_flag, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+        GFF_TRY(cudaMemcpyAsync(h->d_scal + 3, h->d_flag + 2, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
         GFF_TRY(cudaEventRecord(ev[2], h->stream));
-        double s3[3];
-        gff_status st2 = fetch(h, h->d_scal, 3, s3);
+        double s3[4];
+        gff_status st2 = fetch(h, h->d_scal, 4, s3);
         if (st2 != GFF_OK) return st2;
         float ms01 = 0.f, ms12 = 0.f;
         GFF_TRY(cudaEventElapsedTime(&ms01, ev[0], ev[1]));
         GFF_TRY(cudaEventElapsedTime(&ms12, ev[1], ev[2]));
         t_const += 1e-3 * ms01;
         t_res += 1e-3 * ms12;
-        int flag;
+        int flag, tmo;
         std::memcpy(&flag, &s3[2], sizeof(int));
+        std::memcpy(&tmo, &s3[3], sizeof(int));
+        if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in the inverse FFT pass timed out");
         if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
         rr_b = s3[0];
         nb = std::sqrt(s3[0]);

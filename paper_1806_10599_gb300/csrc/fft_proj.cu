@@ -26,6 +26,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "bulk_copy.cuh"
 #include "gff_internal.cuh"
 
 namespace gff {
@@ -585,33 +586,18 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
 }
 
 // ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
+// Inverse y transform, merge of the packed rows, complex-to-real x transform
+// and epilogue of one plane already in shared memory s (tables loaded).
 template <typename T, bool VEC>
-__device__ __forceinline__ void plane_inv_body(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
-                                               const GridDev& g, const OutArgs& oa, const int c, const int z,
-                                               unsigned char* sm_raw) {
+__device__ __forceinline__ void plane_inv_compute(typename C2<T>::t* s, T* __restrict__ y, const GridDev& g,
+                                                  const OutArgs& oa, const int c, const int z,
+                                                  const typename C2<T>::t* twx, const typename C2<T>::t* twy,
+                                                  const int* posx) {
     using C = typename C2<T>::t;
     const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
-    C* s = reinterpret_cast<C*>(sm_raw);
-    C* twx = s + ny * ls;
-    C* twy = twx + nx;
-    int* posx = reinterpret_cast<int*>(twy + ny);
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
-
-    for (int i = tid; i < nx; i += nthr) {
-        twx[i] = twp<T>(g, 0)[i];
-        posx[i] = g.posx[i];
-    }
-    for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
-    const C* in = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
-    {
-        const int nq = ny * nxh * (int)sizeof(C) / 16;
-        const float4* src4 = reinterpret_cast<const float4*>(in);
-        float4* dst4 = reinterpret_cast<float4*>(s);
-        for (int e = tid; e < nq; e += nthr) dst4[e] = __ldg(src4 + e);
-    }
-    __syncthreads();
     fft_lines<T, true>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
     // merge the half spectra of rows 2r, 2r+1 into one packed complex row
     // Z_k = A_k + i B_k over all k (Hermitian symmetry of real rows), in the
@@ -670,12 +656,104 @@ __device__ __forceinline__ void plane_inv_body(const typename C2<T>::t* __restri
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void plane_tables(const GridDev& g, typename C2<T>::t* twx, typename C2<T>::t* twy,
+                                             int* posx) {
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        twx[i] = twp<T>(g, 0)[i];
+        posx[i] = g.posx[i];
+    }
+    for (int i = threadIdx.x; i < g.ny; i += blockDim.x) twy[i] = twp<T>(g, 1)[i];
+}
+
+template <typename T, bool VEC>
+__device__ __forceinline__ void plane_inv_body(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
+                                               const GridDev& g, const OutArgs& oa, const int c, const int z,
+                                               unsigned char* sm_raw) {
+    using C = typename C2<T>::t;
+    const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh;
+    C* s = reinterpret_cast<C*>(sm_raw);
+    C* twx = s + ny * ls;
+    C* twy = twx + nx;
+    int* posx = reinterpret_cast<int*>(twy + ny);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    plane_tables<T>(g, twx, twy, posx);
+    const C* in = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
+    {
+        const int nq = ny * nxh * (int)sizeof(C) / 16;
+        const float4* src4 = reinterpret_cast<const float4*>(in);
+        float4* dst4 = reinterpret_cast<float4*>(s);
+        for (int e = tid; e < nq; e += nthr) dst4[e] = __ldg(src4 + e);
+    }
+    __syncthreads();
+    plane_inv_compute<T, VEC>(s, y, g, oa, c, z, twx, twy, posx);
+}
+
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
                                                    GridDev g, OutArgs oa, const int* __restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     plane_inv_body<T, VEC>(spec, y, g, oa, blockIdx.x, blockIdx.y, sm_raw);
+}
+
+// Persistent variant: each block walks the planes p = blockIdx.x + k gridDim.x
+// (p = c nz + z) with two plane buffers; while one plane is transformed, the
+// next arrives by a bulk asynchronous copy (the half-spectrum plane is one
+// contiguous run), so the loads overlap the shared-memory FFT work.
+template <typename T> size_t plane_stream_smem(const GridDev& g) {
+    using C = typename C2<T>::t;
+    return 2 * (size_t)g.ny * g.nxh * sizeof(C) + (size_t)(g.nx + g.ny) * sizeof(C) + g.nx * sizeof(int) + 32;
+}
+
+template <typename T, bool VEC>
+__global__ void __launch_bounds__(512) k_plane_inv_stream(const typename C2<T>::t* __restrict__ spec,
+                                                          T* __restrict__ y, GridDev g, OutArgs oa,
+                                                          const int* __restrict__ skip, int* __restrict__ err) {
+    using C = typename C2<T>::t;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int nx = g.nx, ny = g.ny, plane = ny * g.nxh;
+    const uint32_t bytes = (uint32_t)(plane * sizeof(C));  // multiple of 16 (ny even)
+    C* buf[2] = {reinterpret_cast<C*>(sm_raw), reinterpret_cast<C*>(sm_raw) + plane};
+    C* twx = buf[1] + plane;
+    C* twy = twx + nx;
+    int* posx = reinterpret_cast<int*>(twy + ny);
+    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(posx + nx) + 7) & ~uintptr_t(7));
+    const int total = 9 * g.nz;
+    plane_tables<T>(g, twx, twy, posx);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    int p = blockIdx.x;
+    if (threadIdx.x == 0 && p < total) bulk_load(buf[0], spec + (long long)p * plane, bytes, &bar[0]);
+    uint32_t phase[2] = {0u, 0u};
+    int cur = 0;
+    for (; p < total; p += gridDim.x) {
+        const int nextp = p + gridDim.x;
+        if (threadIdx.x == 0 && nextp < total) {
+            fence_proxy_async_smem();  // the other buffer's last readers finished at the barrier below
+            bulk_load(buf[cur ^ 1], spec + (long long)nextp * plane, bytes, &bar[cur ^ 1]);
+        }
+        const bool ok = mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+        if (__syncthreads_or(!ok)) {
+            // record, let the copies in flight land (bounded), leave
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+                if (nextp < total) mbar_wait(&bar[cur ^ 1], phase[cur ^ 1], BULK_WAIT_CYCLES);
+            }
+            __syncthreads();
+            return;
+        }
+        phase[cur] ^= 1u;
+        plane_inv_compute<T, VEC>(buf[cur], y, g, oa, p / g.nz, p % g.nz, twx, twy, posx);
+        __syncthreads();
+        cur ^= 1;
+    }
 }
 
 template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 16; }
@@ -793,8 +871,19 @@ cudaError_t launch_z(const GridDev& g, int W, int threads, typename C2<T>::t* sp
 }
 
 template <typename T>
-cudaError_t launch_inv(const GridDev& g, int threads, const typename C2<T>::t* spec, T* y, const OutArgs& oa,
-                       const int* skip, cudaStream_t st, bool vout) {
+cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename C2<T>::t* spec, T* y,
+                       const OutArgs& oa, const int* skip, cudaStream_t st, bool vout, int* err) {
+    if (blocks > 0) {
+        const size_t sm = plane_stream_smem<T>(g);
+        if (vout) {
+            allow_smem(k_plane_inv_stream<T, true>, sm);
+            k_plane_inv_stream<T, true><<<blocks, threads, sm, st>>>(spec, y, g, oa, skip, err);
+        } else {
+            allow_smem(k_plane_inv_stream<T, false>, sm);
+            k_plane_inv_stream<T, false><<<blocks, threads, sm, st>>>(spec, y, g, oa, skip, err);
+        }
+        return cudaGetLastError();
+    }
     const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
     const dim3 gridA(9, g.nz);
     if (vout) {
@@ -841,6 +930,27 @@ cudaError_t pick_fastest(int ncand, const bool* valid, int reps, cudaStream_t st
     return e;
 }
 
+// blocks of the persistent inverse pass: all that fit on the GPU at once, at most one per plane
+template <typename T>
+int inv_stream_blocks(const GridDev& g, int threads, bool vout) {
+    const size_t sm = plane_stream_smem<T>(g);
+    if (sm > SMEM_MAX) return 0;
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cudaError_t e;
+    if (vout) {
+        allow_smem(k_plane_inv_stream<T, true>, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_plane_inv_stream<T, true>, threads, sm);
+    } else {
+        allow_smem(k_plane_inv_stream<T, false>, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_plane_inv_stream<T, false>, threads, sm);
+    }
+    if (e != cudaSuccess || per < 1) return 0;
+    const int total = 9 * g.nz;
+    return nsm * per < total ? nsm * per : total;
+}
+
 template <typename T>
 cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     using C = typename C2<T>::t;
@@ -870,9 +980,15 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     OutArgs oa;
     oa.scale = 1.0;
     for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
-    e = pick_fastest(2, tv, reps, st, [&](int i) { return launch_inv<T>(g, tp[i], spec, y, oa, nullptr, st, vec_ok<T>(g, y)); }, &b);
+    // one block per plane, or the persistent streamed pass, each with 256 or 512 threads
+    const bool vout = vec_ok<T>(g, y);
+    int ib[4] = {0, 0, inv_stream_blocks<T>(g, 256, vout), inv_stream_blocks<T>(g, 512, vout)};
+    const bool iv[4] = {true, true, ib[2] > 0, ib[3] > 0};
+    int* err = h->d_flag + 2;
+    e = pick_fastest(4, iv, reps, st, [&](int i) { return launch_inv<T>(g, tp[i % 2], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
     if (e != cudaSuccess) return e;
-    tn.t_inv = tp[b];
+    tn.t_inv = tp[b % 2];
+    tn.inv_blocks = ib[b];
     return cudaSuccess;
 }
 
@@ -1009,7 +1125,7 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, skip, h->stream);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], h->stream);
-    e = launch_inv<T>(g, tn.t_inv, spec, y, oa, skip, h->stream, vout);
+    e = launch_inv<T>(g, tn.t_inv, tn.inv_blocks, spec, y, oa, skip, h->stream, vout, h->d_flag + 2);
     if (ev) cudaEventRecord(ev[3], h->stream);
     return e;
 }

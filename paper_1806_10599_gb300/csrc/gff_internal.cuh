@@ -93,6 +93,7 @@ struct Tune {
     int wz;     // (ky, kx) columns per k_zproj block
     int t_z;    // threads of k_zproj
     int t_inv;  // threads of k_plane_inv
+    int inv_blocks;  // > 0: persistent streamed inverse pass with this many blocks
 };
 
 struct Nine9 {
@@ -155,7 +156,7 @@ struct gff_handle {
     double* d_dg = nullptr;    // [12][N] slip increments of the trial
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
-    int* d_flag = nullptr;     // device status word (CP failures)
+    int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out copy waits
     // reductions
     double* d_red = nullptr;   // partial sums
     double* d_scal = nullptr;  // final scalars
@@ -164,7 +165,7 @@ struct gff_handle {
     bool K32_valid = false;
     bool grains_ready = false;
     void* hostdata = nullptr;  // host copies of the orientations and phases
-    gff::Tune tune[2] = {{512, 8, 256, 512}, {512, 16, 256, 512}};  // [0] FP64, [1] FP32
+    gff::Tune tune[2] = {{512, 8, 256, 512, 0}, {512, 16, 256, 512, 0}};  // [0] FP64, [1] FP32
     bool tuned = false;
     // warm starts: history of the completed increments.  d is an increment's
     // prescribed average F change (0 on stress-controlled components) and

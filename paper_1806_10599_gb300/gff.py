@@ -242,10 +242,10 @@ def gff_apply_operator_timed(h, precision, mask9, x_dev, y_dev):
 
 
 def gff_autotune(h):
-    """Returns {fwd threads, z columns, z threads, inv threads} for FP64 and FP32."""
-    t = (ctypes.c_int * 8)()
+    """Returns {fwd threads, z columns, z threads, inv threads, inv persistent blocks} for FP64 and FP32."""
+    t = (ctypes.c_int * 10)()
     _check(h, _lib.gff_autotune(h, ctypes.cast(t, c_void_p)))
-    return {"fp64": list(t[0:4]), "fp32": list(t[4:8])}
+    return {"fp64": list(t[0:5]), "fp32": list(t[5:10])}
 
 
 def gff_project(h, precision, mask9, x_dev, y_dev):
