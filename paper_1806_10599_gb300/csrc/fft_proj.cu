@@ -371,85 +371,6 @@ template <> struct V16<float> {
     }
 };
 
-// ---------------------------------------------------------------- warp-owned lines
-// The same two-stage transform, but one warp takes whole lines -- line k of
-// the warp starts at s + base + k lstride, elements ES apart -- and needs only
-// __syncwarp between its stages: warps never wait for each other.
-template <typename T, int R1, int R2, bool TWIDDLED, bool INV>
-__device__ __forceinline__ void warp_stage(typename C2<T>::t* s, const typename C2<T>::t* tw, int base, int lstride,
-                                           int nk, int ES, int lane) {
-    using C = typename C2<T>::t;
-    constexpr int R = TWIDDLED ? R1 : R2;
-    constexpr int TASKS = TWIDDLED ? R2 : R1;
-    const int total = nk * TASKS;
-    const int st = (TWIDDLED ? R2 : 1) * ES;
-    for (int t = lane; t < total; t += 32) {
-        const int k = t / TASKS, task = t - k * TASKS;
-        C* p = s + base + k * lstride + (TWIDDLED ? task : task * R2) * ES;
-        C v[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = p[q * st];
-        if (TWIDDLED && INV && task) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmulc(v[q], tw[q * task]);
-        }
-        Bfly<R, INV, C>::run(v);
-        if (TWIDDLED && !INV && task) {
-#pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], tw[q * task]);
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q) p[q * st] = v[q];
-    }
-}
-
-template <typename T, int R1, int R2, bool INV>
-__device__ __forceinline__ void warp_fft2(typename C2<T>::t* s, const typename C2<T>::t* tw, int base, int lstride,
-                                          int nk, int ES, int lane) {
-    if (!INV) {
-        warp_stage<T, R1, R2, true, false>(s, tw, base, lstride, nk, ES, lane);
-        __syncwarp();
-        warp_stage<T, R1, R2, false, false>(s, tw, base, lstride, nk, ES, lane);
-    } else {
-        warp_stage<T, R1, R2, false, true>(s, tw, base, lstride, nk, ES, lane);
-        __syncwarp();
-        warp_stage<T, R1, R2, true, true>(s, tw, base, lstride, nk, ES, lane);
-    }
-    __syncwarp();
-}
-
-// plans with a warp-owned (two-stage) implementation
-__host__ __device__ __forceinline__ bool warp_plan(const AxisPlan& p) {
-    if (p.nst != 2) return false;
-    const int a = p.radix[0], b = p.radix[1];
-    return (a == 16 && (b == 8 || b == 5 || b == 3)) || (a == 8 && (b == 8 || b == 5 || b == 4 || b == 3)) ||
-           (a == 4 && b == 4);
-}
-
-// transform of the warp's lines (warp_plan(pl) must hold); not inlined, as fft_lines
-template <typename T, bool INV>
-__device__ __noinline__ void warp_lines(typename C2<T>::t* s, const typename C2<T>::t* tw, const AxisPlan& pl,
-                                        int base, int lstride, int nk, int ES, int lane) {
-    const int r1 = pl.radix[0], r2 = pl.radix[1];
-#define GFF_WFFT(A, B)                                                     \
-    if (r1 == A && r2 == B) {                                              \
-        warp_fft2<T, A, B, INV>(s, tw, base, lstride, nk, ES, lane);       \
-        return;                                                            \
-    }
-    GFF_WFFT(16, 8)
-    GFF_WFFT(8, 8)
-    GFF_WFFT(16, 5)
-    GFF_WFFT(16, 3)
-    GFF_WFFT(8, 5)
-    GFF_WFFT(8, 4)
-    GFF_WFFT(8, 3)
-    GFF_WFFT(4, 4)
-#undef GFF_WFFT
-}
-
-// number of the lines w, w + nw, w + 2 nw, ... below n
-__device__ __forceinline__ int owned(int n, int w, int nw) { return n > w ? (n - w + nw - 1) / nw : 0; }
-
 template <typename T, bool WITH_K, bool VEC>
 __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T* __restrict__ K,
                                                typename C2<T>::t* __restrict__ spec, const GridDev& g, const int c,
@@ -469,97 +390,6 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
         posx[i] = g.posx[i];
     }
     for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
-
-    if (warp_plan(g.ax) && warp_plan(g.ay)) {
-        // warp w owns the packed rows r = w, w + nw, ... (real rows 2r, 2r+1)
-        // through contraction, x transform and split, then the columns
-        // kx = w, w + nw, ... through the y transform: two block barriers
-        const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5, kh = nx / 2;
-        const int nr = owned(half, warp, nw);
-        const T* Kc = WITH_K ? K + (long long)c * 9 * N : nullptr;
-        for (int k = 0; k < nr; ++k) {
-            const int r = warp + k * nw;
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const long long row0 = pl + (long long)(2 * r + h2) * nx;
-                T* dst = reinterpret_cast<T*>(s + r * 2 * ls) + h2;
-                if (VEC) {
-                    using VT = typename V16<T>::t;
-                    constexpr int VW = V16<T>::n;
-                    for (int xv = lane; xv < nx / VW; xv += 32) {
-                        const long long v0 = row0 + xv * VW;
-                        T acc[VW];
-                        if (WITH_K) {
-                            VT kv[9], xq[9];
-#pragma unroll
-                            for (int d = 0; d < 9; ++d) {
-                                kv[d] = __ldg(reinterpret_cast<const VT*>(Kc + d * N + v0));
-                                xq[d] = __ldg(reinterpret_cast<const VT*>(x + d * N + v0));
-                            }
-#pragma unroll
-                            for (int j = 0; j < VW; ++j) {
-                                T t = (T)0;
-#pragma unroll
-                                for (int d = 0; d < 9; ++d) t = fma(V16<T>::get(kv[d], j), V16<T>::get(xq[d], j), t);
-                                acc[j] = t;
-                            }
-                        } else {
-                            const VT xv4 = __ldg(reinterpret_cast<const VT*>(x + c * N + v0));
-#pragma unroll
-                            for (int j = 0; j < VW; ++j) acc[j] = V16<T>::get(xv4, j);
-                        }
-#pragma unroll
-                        for (int j = 0; j < VW; ++j) dst[2 * (xv * VW + j)] = acc[j];
-                    }
-                } else {
-                    for (int xi = lane; xi < nx; xi += 32) {
-                        T a = (T)0;
-                        if (WITH_K) {
-#pragma unroll
-                            for (int d = 0; d < 9; ++d) a = fma(__ldg(Kc + d * N + row0 + xi), __ldg(x + d * N + row0 + xi), a);
-                        } else {
-                            a = __ldg(x + c * N + row0 + xi);
-                        }
-                        dst[2 * xi] = a;
-                    }
-                }
-            }
-        }
-        __syncthreads();  // the twiddle tables
-        warp_lines<T, false>(s, twx, g.ax, warp * 2 * ls, nw * 2 * ls, nr, 1, lane);
-        for (int k = 0; k < nr; ++k) {
-            C* row = s + (warp + k * nw) * 2 * ls;
-            C A[3], B[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int kk = lane + 32 * t;
-                if (kk <= kh) {
-                    const C zk = row[posx[kk]];
-                    const C zm = row[posx[kk == 0 ? 0 : nx - kk]];
-                    A[t] = mk<C>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
-                    B[t] = mk<C>((zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5);
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int kk = lane + 32 * t;
-                if (kk <= kh) {
-                    row[kk] = A[t];
-                    row[ls + kk] = B[t];
-                }
-            }
-        }
-        __syncthreads();
-        warp_lines<T, false>(s, twy, g.ay, warp, nw, owned(nxh, warp, nw), ls, lane);
-        __syncthreads();
-        C* out = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
-        const int nq = ny * nxh * (int)sizeof(C) / 16;
-        const float4* src4 = reinterpret_cast<const float4*>(s);
-        float4* dst4 = reinterpret_cast<float4*>(out);
-        for (int e = tid; e < nq; e += nthr) dst4[e] = src4[e];
-        return;
-    }
 
     if (VEC) {
         // 16-byte loads of VW consecutive voxels of one row; K row c is read
@@ -747,106 +577,12 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
     }
 }
 
-// The same pass with warp-owned lines (warp_plan(g.az)): shared memory holds
-// line (3 w + i) -- component 3 row + i of column w -- contiguously at stride
-// nz + 1 (the padding spreads the column-wise fills over the banks); warp v
-// takes columns [v cpw, (v + 1) cpw) through the forward transform, the
-// projection and the inverse transform without block barriers.
 template <typename T, int W>
-__device__ __forceinline__ void zproj_body_warp(typename C2<T>::t* __restrict__ spec, const GridDev& g,
-                                                const ProjArgs& pa, const int blk, unsigned char* sm_raw) {
-    using C = typename C2<T>::t;
-    const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh, lz = nz + 1;
-    C* s = reinterpret_cast<C*>(sm_raw);  // [W][3][nz + 1]
-    C* twz = s + 3 * W * lz;
-    T* qx = reinterpret_cast<T*>(twz + nz);
-    T* qy = qx + nxh;
-    T* qz = qy + ny;
-    int* fqy = reinterpret_cast<int*>(qz + nz);
-    int* fqz = fqy + ny;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const long long nF = (long long)ny * nxh;
-    const int row = blk % 3;
-    const long long f0 = (long long)(blk / 3) * W;
-    C* base = spec + (long long)(3 * row) * nz * nF;
-
-    for (int i = tid; i < nz; i += nthr) {
-        twz[i] = twp<T>(g, 2)[i];
-        qz[i] = qtp<T>(g, pa.kind, 2)[i];
-        fqz[i] = g.fqz[i];
-    }
-    for (int i = tid; i < ny; i += nthr) {
-        qy[i] = qtp<T>(g, pa.kind, 1)[i];
-        fqy[i] = g.fqy[i];
-    }
-    for (int i = tid; i < nxh; i += nthr) qx[i] = qtp<T>(g, pa.kind, 0)[i];
-    // W consecutive complex values per (component, z): thread (w, z0) with w fastest
-    const int w = tid % W, zs = nthr / W;
-    const long long f = f0 + w;
-    const bool in = f < nF;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-        for (int zz = tid / W; zz < nz; zz += zs)
-            s[(3 * w + i) * lz + zz] = in ? base[((long long)i * nz + zz) * nF + f] : mk<C>((T)0, (T)0);
-    __syncthreads();
-
-    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-    const int cpw = (W + nw - 1) / nw;
-    const int wa = warp * cpw, wb = min(W, wa + cpw);
-    if (wa < wb) {
-        warp_lines<T, false>(s, twz, g.az, 3 * wa * lz, lz, 3 * (wb - wa), 1, lane);
-        const T m0 = (T)pa.mask[3 * row], m1 = (T)pa.mask[3 * row + 1], m2 = (T)pa.mask[3 * row + 2];
-        for (int wc = wa; wc < wb; ++wc) {
-            const long long fc = f0 + wc;
-            if (fc >= nF) break;
-            const int py = (int)(fc / nxh), kx = (int)(fc - (long long)py * nxh);
-            const int ky = fqy[py];
-            const T a = qx[kx], b = qy[ky];
-            const bool edge_xy = kx == nx / 2 || ky == ny / 2;
-            C* l0 = s + 3 * wc * lz;
-            for (int pz = lane; pz < nz; pz += 32) {
-                const int kz = fqz[pz];
-                C v0 = l0[pz], v1 = l0[lz + pz], v2 = l0[2 * lz + pz];
-                if (kx == 0 && ky == 0 && kz == 0) {
-                    v0 = cscale(v0, m0);
-                    v1 = cscale(v1, m1);
-                    v2 = cscale(v2, m2);
-                } else if (edge_xy || kz == nz / 2) {
-                    v0 = v1 = v2 = mk<C>((T)0, (T)0);
-                } else {
-                    const T d = qz[kz];
-                    const T inv = (T)1 / sqrt(a * a + b * b + d * d);
-                    const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
-                    const C t = mk<C>(v0.x * n0 + v1.x * n1 + v2.x * n2, v0.y * n0 + v1.y * n1 + v2.y * n2);
-                    v0 = cscale(t, n0);
-                    v1 = cscale(t, n1);
-                    v2 = cscale(t, n2);
-                }
-                l0[pz] = v0;
-                l0[lz + pz] = v1;
-                l0[2 * lz + pz] = v2;
-            }
-        }
-        __syncwarp();
-        warp_lines<T, true>(s, twz, g.az, 3 * wa * lz, lz, 3 * (wb - wa), 1, lane);
-    }
-    __syncthreads();
-    if (in) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            for (int zz = tid / W; zz < nz; zz += zs) base[((long long)i * nz + zz) * nF + f] = s[(3 * w + i) * lz + zz];
-    }
-}
-
-template <typename T, int W>
-__global__ void __launch_bounds__(512) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa,
+__global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa,
                                               const int* __restrict__ skip) {
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    if (warp_plan(g.az))
-        zproj_body_warp<T, W>(spec, g, pa, blockIdx.x, sm_raw);
-    else
-        zproj_body<T, W>(spec, g, pa, blockIdx.x, sm_raw);
+    zproj_body<T, W>(spec, g, pa, blockIdx.x, sm_raw);
 }
 
 // ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
@@ -862,69 +598,6 @@ __device__ __forceinline__ void plane_inv_compute(typename C2<T>::t* s, T* __res
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
-    if (warp_plan(g.ax) && warp_plan(g.ay)) {
-        // columns kx = w, w + nw, ... then packed rows r = w, w + nw, ... per warp
-        const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5, kh = nx / 2;
-        warp_lines<T, true>(s, twy, g.ay, warp, nw, owned(nxh, warp, nw), ls, lane);
-        __syncthreads();
-        const int nr = owned(half, warp, nw);
-        for (int k = 0; k < nr; ++k) {
-            C* row = s + (warp + k * nw) * 2 * ls;
-            C A[3], B[3];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int kk = lane + 32 * t;
-                if (kk <= kh) {
-                    A[t] = row[kk];
-                    B[t] = row[ls + kk];
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                const int kk = lane + 32 * t;
-                if (kk <= kh) {
-                    if (kk == 0 || kk == kh) {
-                        row[posx[kk]] = mk<C>(A[t].x, B[t].x);
-                    } else {
-                        row[posx[kk]] = mk<C>(A[t].x - B[t].y, A[t].y + B[t].x);
-                        row[posx[nx - kk]] = mk<C>(A[t].x + B[t].y, B[t].x - A[t].y);
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        warp_lines<T, true>(s, twx, g.ax, warp * 2 * ls, nw * 2 * ls, nr, 1, lane);
-        const T sc = (T)oa.scale, ad = (T)oa.add[c];
-        T* yc = y + c * N;
-        for (int k = 0; k < nr; ++k) {
-            const int r = warp + k * nw;
-            const C* row = s + r * 2 * ls;
-            T* y0 = yc + pl + (long long)(2 * r) * nx;
-            if (VEC) {
-                using VT = typename V16<T>::t;
-                constexpr int VW = V16<T>::n;
-                for (int xv = lane; xv < nx / VW; xv += 32) {
-                    T o0[VW], o1[VW];
-#pragma unroll
-                    for (int j = 0; j < VW; ++j) {
-                        const C zv = row[xv * VW + j];
-                        o0[j] = fma(sc, zv.x, ad);
-                        o1[j] = fma(sc, zv.y, ad);
-                    }
-                    *reinterpret_cast<VT*>(y0 + xv * VW) = *reinterpret_cast<const VT*>(o0);
-                    *reinterpret_cast<VT*>(y0 + nx + xv * VW) = *reinterpret_cast<const VT*>(o1);
-                }
-            } else {
-                for (int xi = lane; xi < nx; xi += 32) {
-                    const C zv = row[xi];
-                    y0[xi] = fma(sc, zv.x, ad);
-                    y0[nx + xi] = fma(sc, zv.y, ad);
-                }
-            }
-        }
-        return;
-    }
     fft_lines<T, true>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
     // merge the half spectra of rows 2r, 2r+1 into one packed complex row
     // Z_k = A_k + i B_k over all k (Hermitian symmetry of real rows), in the
@@ -1087,8 +760,7 @@ template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 
 
 template <typename T> size_t zproj_smem(const GridDev& g, int W = zproj_width<T>()) {
     using C = typename C2<T>::t;
-    // [W][3][nz + 1] (warp-owned layout; the block layout [3][nz][W] fits inside)
-    return (size_t)3 * W * (g.nz + 1) * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
+    return (size_t)3 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
            (g.ny + g.nz) * sizeof(int) + 16;
 }
 
@@ -1295,7 +967,7 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     if (e != cudaSuccess) return e;
     tn.t_fwd = tp[b];
     const int wz[4] = {4, 8, 16, 32};
-    const int tz[2] = {256, 512};
+    const int tz[2] = {128, 256};
     bool zv[8];
     for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i / 2]) <= SMEM_MAX;
     ProjArgs pa;
@@ -1359,16 +1031,13 @@ __global__ void __launch_bounds__(512) k_plane_fwd_batch(const RveApply* __restr
 }
 
 template <typename T, int W>
-__global__ void __launch_bounds__(512) k_zproj_batch(const RveApply* __restrict__ rv, const int* __restrict__ start,
+__global__ void __launch_bounds__(256) k_zproj_batch(const RveApply* __restrict__ rv, const int* __restrict__ start,
                                                     int n, ProjArgs pa) {
     const int r = find_rve(start, n, blockIdx.x);
     const RveApply& a = rv[r];
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    if (warp_plan(a.g.az))
-        zproj_body_warp<T, W>(static_cast<typename C2<T>::t*>(a.spec), a.g, pa, blockIdx.x - start[r], sm_raw);
-    else
-        zproj_body<T, W>(static_cast<typename C2<T>::t*>(a.spec), a.g, pa, blockIdx.x - start[r], sm_raw);
+    zproj_body<T, W>(static_cast<typename C2<T>::t*>(a.spec), a.g, pa, blockIdx.x - start[r], sm_raw);
 }
 
 template <typename T, bool VEC>
