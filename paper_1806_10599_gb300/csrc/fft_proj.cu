@@ -501,6 +501,11 @@ __global__ void __launch_bounds__(512) k_plane_fwd(const T* __restrict__ x, cons
 // (y_ij = n_j sum_l x_il n_l), so a block takes one tensor row (components
 // 3i, 3i+1, 3i+2) and W consecutive (ky, kx) columns: 3 x nz x W values,
 // each row segment of W contiguous complex values read and written whole.
+template <typename T> __device__ __forceinline__ T rnorm3(T a, T b, T d) { return (T)1 / sqrt(a * a + b * b + d * d); }
+template <> __device__ __forceinline__ float rnorm3<float>(float a, float b, float d) {
+    return rsqrtf(a * a + b * b + d * d);
+}
+
 template <typename T, int W>
 __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec, const GridDev& g,
                                            const ProjArgs& pa, const int blk, unsigned char* sm_raw) {
@@ -511,28 +516,30 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
     T* qx = reinterpret_cast<T*>(twz + nz);
     T* qy = qx + nxh;
     T* qz = qy + ny;
-    int* fqy = reinterpret_cast<int*>(qz + nz);
-    int* fqz = fqy + ny;
+    int* fqz = reinterpret_cast<int*>(qz + nz);
+    int* colk = fqz + nz;  // [W]: kx | ky << 16 of the block's columns, -1 past the end
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const long long nF = (long long)ny * nxh;
+    // spectrum indices fit in 32 bits (9 nz ny nxh < 2^31 for axes <= MAXN)
+    const int nF = ny * nxh;
     const int row = blk % 3;
-    const long long f0 = (long long)(blk / 3) * W;
-    C* base = spec + (long long)(3 * row) * nz * nF;  // component 3 row, z = 0
+    const int f0 = (blk / 3) * W;
+    C* base = spec + 3 * row * nz * nF;  // component 3 row, z = 0
 
     for (int i = tid; i < nz; i += nthr) {
         twz[i] = twp<T>(g, 2)[i];
         qz[i] = qtp<T>(g, pa.kind, 2)[i];
         fqz[i] = g.fqz[i];
     }
-    for (int i = tid; i < ny; i += nthr) {
-        qy[i] = qtp<T>(g, pa.kind, 1)[i];
-        fqy[i] = g.fqy[i];
-    }
+    for (int i = tid; i < ny; i += nthr) qy[i] = qtp<T>(g, pa.kind, 1)[i];
     for (int i = tid; i < nxh; i += nthr) qx[i] = qtp<T>(g, pa.kind, 0)[i];
+    for (int w = tid; w < W; w += nthr) {
+        const int f = f0 + w;
+        const int py = f / nxh;
+        colk[w] = f < nF ? (f - py * nxh) | (g.fqy[py] << 16) : -1;
+    }
     for (int e = tid; e < 3 * nz * W; e += nthr) {
-        const int w = e % W;
-        const long long cz = e / W;  // (component within the row) * nz + z
-        const long long f = f0 + w;
+        const int w = e % W, cz = e / W;  // cz = (component within the row) * nz + z
+        const int f = f0 + w;
         s[e] = f < nF ? base[cz * nF + f] : mk<C>((T)0, (T)0);
     }
     __syncthreads();
@@ -541,10 +548,9 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
     const T m0 = (T)pa.mask[3 * row], m1 = (T)pa.mask[3 * row + 1], m2 = (T)pa.mask[3 * row + 2];
     for (int e = tid; e < nz * W; e += nthr) {
         const int w = e % W, pz = e / W;
-        const long long f = f0 + w;
-        if (f >= nF) continue;
-        const int py = (int)(f / nxh), kx = (int)(f - (long long)py * nxh);
-        const int ky = fqy[py], kz = fqz[pz];
+        const int ck = colk[w];
+        if (ck < 0) continue;
+        const int kx = ck & 0xffff, ky = ck >> 16, kz = fqz[pz];
         C* p0 = s + pz * W + w;
         C v0 = p0[0], v1 = p0[nz * W], v2 = p0[2 * nz * W];
         if (kx == 0 && ky == 0 && kz == 0) {
@@ -555,7 +561,7 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
             v0 = v1 = v2 = mk<C>((T)0, (T)0);
         } else {
             const T a = qx[kx], b = qy[ky], d = qz[kz];
-            const T inv = (T)1 / sqrt(a * a + b * b + d * d);
+            const T inv = rnorm3(a, b, d);
             const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
             // t = sum_l x_il n_l ; y_ij = t n_j
             const C t = mk<C>(v0.x * n0 + v1.x * n1 + v2.x * n2, v0.y * n0 + v1.y * n1 + v2.y * n2);
@@ -570,9 +576,8 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
     __syncthreads();
     fft_lines<T, true>(s, twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
     for (int e = tid; e < 3 * nz * W; e += nthr) {
-        const int w = e % W;
-        const long long cz = e / W;
-        const long long f = f0 + w;
+        const int w = e % W, cz = e / W;
+        const int f = f0 + w;
         if (f < nF) base[cz * nF + f] = s[e];
     }
 }
@@ -706,8 +711,11 @@ template <typename T> size_t plane_stream_smem(const GridDev& g) {
     return 2 * (size_t)g.ny * g.nxh * sizeof(C) + (size_t)(g.nx + g.ny) * sizeof(C) + g.nx * sizeof(int) + 32;
 }
 
+// up to 1024 threads in FP32; FP64 would spill at that register budget
+template <typename T> constexpr int inv_stream_max_threads() { return sizeof(T) == 4 ? 1024 : 512; }
+
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(512) k_plane_inv_stream(const typename C2<T>::t* __restrict__ spec,
+__global__ void __launch_bounds__(inv_stream_max_threads<T>()) k_plane_inv_stream(const typename C2<T>::t* __restrict__ spec,
                                                           T* __restrict__ y, GridDev g, OutArgs oa,
                                                           const int* __restrict__ skip, int* __restrict__ err) {
     using C = typename C2<T>::t;
@@ -761,7 +769,7 @@ template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 
 template <typename T> size_t zproj_smem(const GridDev& g, int W = zproj_width<T>()) {
     using C = typename C2<T>::t;
     return (size_t)3 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
-           (g.ny + g.nz) * sizeof(int) + 16;
+           (g.nz + W) * sizeof(int) + 16;
 }
 
 constexpr size_t SMEM_MAX = 227 * 1024;
@@ -980,14 +988,15 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     OutArgs oa;
     oa.scale = 1.0;
     for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
-    // one block per plane, or the persistent streamed pass, each with 256 or 512 threads
+    // one block per plane with 256 or 512 threads, or the persistent streamed pass with 512 or 1024
     const bool vout = vec_ok<T>(g, y);
-    int ib[4] = {0, 0, inv_stream_blocks<T>(g, 256, vout), inv_stream_blocks<T>(g, 512, vout)};
+    const int ti[4] = {256, 512, inv_stream_max_threads<T>() / 2, inv_stream_max_threads<T>()};
+    int ib[4] = {0, 0, inv_stream_blocks<T>(g, 512, vout), inv_stream_blocks<T>(g, 1024, vout)};
     const bool iv[4] = {true, true, ib[2] > 0, ib[3] > 0};
     int* err = h->d_flag + 2;
-    e = pick_fastest(4, iv, reps, st, [&](int i) { return launch_inv<T>(g, tp[i % 2], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
+    e = pick_fastest(4, iv, reps, st, [&](int i) { return launch_inv<T>(g, ti[i], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
     if (e != cudaSuccess) return e;
-    tn.t_inv = tp[b % 2];
+    tn.t_inv = ti[b];
     tn.inv_blocks = ib[b];
     return cudaSuccess;
 }
