@@ -244,7 +244,7 @@ bool deviatoric_factors(const double* S0, const double* C, double* out) {
 
 gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const std::vector<int>& phase) {
     const int ng = h->ngrains;
-    std::vector<double> C(81 * (size_t)ng), S0(108 * (size_t)ng), nrmprm((36 + 5 + 144) * (size_t)ng);
+    std::vector<double> C(81 * (size_t)ng), S0(GEO_STRIDE * (size_t)ng), nrmprm((36 + 5 + 144) * (size_t)ng);
     std::vector<int> kind(ng);
     double s[12][3], m[12][3];
     slip_systems(s, m);
@@ -264,13 +264,25 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
                 sr[i] = R[3 * i] * s[a][0] + R[3 * i + 1] * s[a][1] + R[3 * i + 2] * s[a][2];
                 mr[i] = R[3 * i] * m[a][0] + R[3 * i + 1] * m[a][1] + R[3 * i + 2] * m[a][2];
             }
+            double* geo = &S0[GEO_STRIDE * (size_t)g];
             for (int i = 0; i < 3; ++i) {
-                for (int j = 0; j < 3; ++j) S0[108 * (size_t)g + 9 * a + 3 * i + j] = sr[i] * mr[j];
+                for (int j = 0; j < 3; ++j) geo[GEO_S0 + 9 * a + 3 * i + j] = sr[i] * mr[j];
                 nrmprm[36 * (size_t)g + 3 * a + i] = mr[i];
+                geo[GEO_DIR + 3 * a + i] = sr[i];
+                if (a % 3 == 0) geo[GEO_NRM + a + i] = mr[i];  // plane a / 3: systems 3p .. 3p+2 share it
             }
         }
+        {
+            // Voigt stiffness: pairs 11, 22, 33, 23, 13, 12
+            const int vi[6] = {0, 1, 2, 1, 0, 0}, vj[6] = {0, 1, 2, 2, 2, 1};
+            double* geo = &S0[GEO_STRIDE * (size_t)g];
+            const double* Cg = &C[81 * (size_t)g];
+            for (int I = 0; I < 6; ++I)
+                for (int J = 0; J < 6; ++J)
+                    geo[GEO_C6 + 6 * I + J] = Cg[9 * (3 * vi[I] + vj[I]) + 3 * vi[J] + vj[J]];
+        }
         // factors of the small-strain slip interaction H = P^T C5 P (see cp_correction_lowrank)
-        if (!deviatoric_factors(&S0[108 * (size_t)g], &C[81 * (size_t)g], &nrmprm[41 * (size_t)ng + 144 * (size_t)g]))
+        if (!deviatoric_factors(&S0[GEO_STRIDE * (size_t)g], &C[81 * (size_t)g], &nrmprm[41 * (size_t)ng + 144 * (size_t)g]))
             return fail(h, GFF_ERR_ARG, "grain %d: stiffness not positive definite on deviatoric strains", g);
         double* pr = &nrmprm[36 * (size_t)ng + 5 * (size_t)g];
         pr[0] = mt.gdot0;
@@ -479,7 +491,8 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
     h->ngrains = ngrains;
     gff_status st;
     if ((st = dalloc(h, (void**)&h->d_C, 81 * (size_t)ngrains * sizeof(double), "C")) != GFF_OK) return st;
-    if ((st = dalloc(h, (void**)&h->d_S0, 108 * (size_t)ngrains * sizeof(double), "S0")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_S0, GEO_STRIDE * (size_t)ngrains * sizeof(double), "slip geometry")) != GFF_OK)
+        return st;
     if ((st = dalloc(h, (void**)&h->d_nrm, (41 + 144) * (size_t)ngrains * sizeof(double), "normals")) != GFF_OK)
         return st;
     if ((st = dalloc(h, (void**)&h->d_gkind, (size_t)ngrains * sizeof(int), "kind")) != GFF_OK) return st;

@@ -102,7 +102,14 @@ struct Nine9 {
 
 struct CPParamsDev {
     double gdot0, p, tau0, c, d;
+    double itau0;  // 1 / tau0
 };
+
+// Per-grain slip geometry block (FP64): the 12 Schmid tensors S0_a = s_a (x) m_a
+// [12][9], the slip directions s_a [12][3], the 4 plane normals m_p [4][3]
+// (systems 3p, 3p+1, 3p+2 share plane p) and the stiffness in Voigt order
+// (11, 22, 33, 23, 13, 12) [6][6].
+constexpr int GEO_S0 = 0, GEO_DIR = 108, GEO_NRM = 144, GEO_C6 = 156, GEO_STRIDE = 192;
 
 }  // namespace gff
 

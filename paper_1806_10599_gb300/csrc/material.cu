@@ -144,30 +144,70 @@ template <typename T> struct ElStateT {
 };
 using ElState = ElStateT<double>;
 
-__device__ void elastic_state(const double* F, const double* A, const double* dg, const double* __restrict__ S0,
-                              const double* __restrict__ C, ElState& st) {
+// Uses the grain's slip planes (three systems per normal m_p) and the Voigt
+// stiffness: Lp = sum_p (sum_(a in p) dg_a s_a) (x) m_p, tau_a = s_a . (M m_p),
+// Ce and S computed as the symmetric tensors they are.
+__device__ void elastic_state(const double* F, const double* A, const double* dg, const double* __restrict__ geo,
+                              ElState& st) {
+    const double* sd = geo + GEO_DIR;
+    const double* mn = geo + GEO_NRM;
+    const double* C6 = geo + GEO_C6;
     double Lp[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Lp[k] = 0.0;
-    for (int a = 0; a < NSLIP; ++a)
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Lp[k] = fma(dg[a], __ldg(S0 + 9 * a + k), Lp[k]);
+    for (int p = 0; p < 4; ++p) {
+        double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = fma(dg[3 * p + i], __ldg(sd + 3 * (3 * p + i) + j), v[j]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Lp[3 * j + k] = fma(v[j], __ldg(mn + 3 * p + k), Lp[3 * j + k]);
+    }
     double IL[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) IL[k] = ((k % 4) == 0 ? 1.0 : 0.0) - Lp[k];
     mm(A, IL, st.Fpi);
     mm(F, st.Fpi, st.Fe);
-    mtm(st.Fe, st.Fe, st.Ce);
-    double E[9];
+    // Ce = Fe^T Fe (symmetric)
 #pragma unroll
-    for (int k = 0; k < 9; ++k) E[k] = 0.5 * (st.Ce[k] - ((k % 4) == 0 ? 1.0 : 0.0));
-    c_ddot(C, E, st.S);
-    mm(st.Ce, st.S, st.M);
-    for (int a = 0; a < NSLIP; ++a) {
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            const double c = st.Fe[i] * st.Fe[j] + st.Fe[3 + i] * st.Fe[3 + j] + st.Fe[6 + i] * st.Fe[6 + j];
+            st.Ce[3 * i + j] = c;
+            st.Ce[3 * j + i] = c;
+        }
+    // S = C : E, E = (Ce - I) / 2, in Voigt form (engineering shears)
+    const double e[6] = {0.5 * (st.Ce[0] - 1.0), 0.5 * (st.Ce[4] - 1.0), 0.5 * (st.Ce[8] - 1.0),
+                         st.Ce[5], st.Ce[2], st.Ce[1]};
+    double sv[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
         double t = 0.0;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) t = fma(st.M[k], __ldg(S0 + 9 * a + k), t);
-        st.tau[a] = t;
+        for (int J = 0; J < 6; ++J) t = fma(__ldg(C6 + 6 * I + J), e[J], t);
+        sv[I] = t;
+    }
+    st.S[0] = sv[0], st.S[4] = sv[1], st.S[8] = sv[2];
+    st.S[5] = st.S[7] = sv[3];
+    st.S[2] = st.S[6] = sv[4];
+    st.S[1] = st.S[3] = sv[5];
+    mm(st.Ce, st.S, st.M);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const double m0 = __ldg(mn + 3 * p), m1 = __ldg(mn + 3 * p + 1), m2 = __ldg(mn + 3 * p + 2);
+        double Mm[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Mm[j] = st.M[3 * j] * m0 + st.M[3 * j + 1] * m1 + st.M[3 * j + 2] * m2;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double* s = sd + 3 * (3 * p + i);
+            st.tau[3 * p + i] = __ldg(s) * Mm[0] + __ldg(s + 1) * Mm[1] + __ldg(s + 2) * Mm[2];
+        }
     }
 }
 
@@ -199,14 +239,14 @@ __device__ void dstate_ddg(const T* F, const T* A, const double* __restrict__ S0
 
 // Residual r_a(dg) and the quantities the Jacobians need; returns max |r_a|.
 __device__ double cp_residual(const double* F, const double* A, const double* chin, const double* dg,
-                              const double* __restrict__ S0, const double* __restrict__ C, const CPParamsDev& pr,
-                              double coef, int p, ElState& st, double* chi, double* dh, double* r) {
-    elastic_state(F, A, dg, S0, C, st);
+                              const double* __restrict__ geo, const CPParamsDev& pr, double coef, int p, ElState& st,
+                              double* chi, double* dh, double* r) {
+    elastic_state(F, A, dg, geo, st);
     double rmax = 0.0;
     for (int a = 0; a < NSLIP; ++a) {
         const double den = 1.0 + pr.d * fabs(dg[a]);
         chi[a] = (chin[a] + pr.c * dg[a]) / den;
-        const double x = (st.tau[a] - chi[a]) / pr.tau0;
+        const double x = (st.tau[a] - chi[a]) * pr.itau0;
         const double ax = fabs(x);
         const double axp1 = ipow(ax, p - 1);
         dh[a] = p * axp1;
@@ -343,7 +383,7 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
                                double* dh) {
     for (int it = 0; it <= maxit; ++it) {
         double r[NSLIP];
-        const double rmax = cp_residual(F, A, chin, dg, S0, C, pr, coef, p, st, chi, dh, r);
+        const double rmax = cp_residual(F, A, chin, dg, S0, pr, coef, p, st, chi, dh, r);
         if (rmax <= 1e-14) return true;
         if (it == maxit || !(rmax < 1e300)) return false;
         if (lowrank) {
@@ -567,18 +607,19 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         pr.tau0 = gp[2];
         pr.c = gp[3];
         pr.d = gp[4];
+        pr.itau0 = 1.0 / pr.tau0;
         double dg0[12];
         if (a.warm)
             for (int s2 = 0; s2 < NSLIP; ++s2) dg0[s2] = a.dg[s2 * N + v];
         CPOut o;
         if (F32T) {
             float K[81];
-            cp_update<float>(F, A, chin, a.dt, a.S0 + 108LL * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K, o);
+            cp_update<float>(F, A, chin, a.dt, a.S0 + (long long)GEO_STRIDE * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K, o);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
             double K[81];
-            cp_update<double>(F, A, chin, a.dt, a.S0 + 108LL * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K,
+            cp_update<double>(F, A, chin, a.dt, a.S0 + (long long)GEO_STRIDE * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K,
                               o);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
@@ -661,7 +702,7 @@ __global__ void __launch_bounds__(TPB) k_fip_accumulate(FipArgs a) {
     const long long N = a.N;
     const int gi = a.gid[v];
     if (a.gkind[gi] != GFF_MAT_CP_FCC) return;
-    const double* S0 = a.S0 + 108LL * gi;
+    const double* S0 = a.S0 + (long long)GEO_STRIDE * gi;
     const double* nr = a.nrm + 36LL * gi;
     double dDp[9];
 #pragma unroll
