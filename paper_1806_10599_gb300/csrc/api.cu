@@ -824,6 +824,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         return GFF_OK;
     };
 
+    const bool dg_prev = first_eval_warm(h, d9);
     // warm starts: mode 1 keeps the network's guess only if its residual beats the zero
     // start's, mode 2 always, mode 3 extrapolates the last increment without a network
     int wmode = h->opt.warm_start;
@@ -831,28 +832,28 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     if (wmode) {
         double res_zero = -1.0;
         if (wmode == GFF_WARM_NET_IF_BETTER) {
-            if ((st = evaluate(false)) != GFF_OK) return st;
+            if ((st = evaluate(dg_prev)) != GFF_OK) return st;
             res_zero = res;
         }
         int applied = 0;
         cudaError_t e = warm_guess(wmode == GFF_WARM_EXTRAPOLATE ? nullptr : h->unet, h, d9, &applied);
         if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "warm start: %s", cudaGetErrorString(e));
-        st = applied ? evaluate(false) : GFF_OK;
+        st = applied ? evaluate(dg_prev) : GFF_OK;
         if (st != GFF_OK && st != GFF_ERR_CP_FAIL) return st;
         warm_used = applied;
         // a guess the return map cannot take, or one with a non-finite residual, is dropped in
         // every mode; mode 1 also drops a guess that does not beat the zero start
         if (!applied) {
-            if (wmode != GFF_WARM_NET_IF_BETTER && (st = evaluate(false)) != GFF_OK) return st;
+            if (wmode != GFF_WARM_NET_IF_BETTER && (st = evaluate(dg_prev)) != GFF_OK) return st;
         } else if (st == GFF_ERR_CP_FAIL || !std::isfinite(res) ||
                    (wmode == GFF_WARM_NET_IF_BETTER && !(res < res_zero))) {
             h->err.clear();
             GFF_TRY(launch_add_const9(h->d_Fk, h->d_F, d9, N, h->stream));
-            if ((st = evaluate(false)) != GFF_OK) return st;
+            if ((st = evaluate(dg_prev)) != GFF_OK) return st;
             warm_used = 0;
         }
     } else {
-        if ((st = evaluate(false)) != GFF_OK) return st;
+        if ((st = evaluate(dg_prev)) != GFF_OK) return st;
     }
     res_first = res;
     for (int it = 0; it <= h->opt.newton_max; ++it) {
@@ -895,6 +896,38 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
 }  // namespace
 
 namespace gff {
+bool first_eval_warm(const gff_handle* h, const double* d9) {
+    if (h->nhist < 1) return false;
+    double dd = 0.0, a2 = 0.0, b2 = 0.0;
+    for (int c = 0; c < 9; ++c) {
+        dd += d9[c] * h->prev_d9[c];
+        a2 += d9[c] * d9[c];
+        b2 += h->prev_d9[c] * h->prev_d9[c];
+    }
+    return a2 > 0 && b2 > 0 && dd > 0.5 * std::sqrt(a2 * b2);
+}
+
+gff_status record_history(gff_handle* h, const double* d9, const double* dF, cudaStream_t st) {
+    double dn = 0.0;
+    for (int c = 0; c < 9; ++c) dn += d9[c] * d9[c];
+    dn = std::sqrt(dn);
+    if (dn > 0) {
+        const int slot = h->ycur ^ 1;
+        const long long N = h->N;
+        GFF_TRY(launch_fluct_incr(h->d_yhist + (size_t)slot * 9 * N, h->d_Fk, h->d_F, dF, 1.0 / dn, N, st));
+        h->ycur = slot;
+        h->nhist = h->nhist < 2 ? h->nhist + 1 : 2;
+    } else {
+        h->nhist = 0;  // a purely stress-controlled increment has no direction: history restarts
+    }
+    for (int c = 0; c < 9; ++c) {
+        h->prev_dFbar[c] = dF[c];
+        h->prev2_d9[c] = h->prev_d9[c];
+        h->prev_d9[c] = d9[c];
+    }
+    return GFF_OK;
+}
+
 // Grain tables uploaded and launch shapes tuned: what gff_step does before its first increment.
 gff_status prepare_for_increments(gff_handle* h) {
     gff_status st = ensure_grains(h);
@@ -920,22 +953,13 @@ gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
     GFF_TRY(launch_sum9(h->d_Fk, N, h->d_red + 9 * RED_BLOCKS, h->d_scal + 9, h->stream));
     GFF_TRY(launch_sum9(h->d_F, N, h->d_red + 18 * RED_BLOCKS, h->d_scal + 18, h->stream));
     if ((st = fetch(h, h->d_scal, 27, s)) != GFF_OK) return st;
-    double dF[9], dn = 0.0;
+    double dF[9];
     for (int c = 0; c < 9; ++c) {
         rep->Pmacro[c] = s[c] / (double)N;
         rep->Fmacro[c] = s[9 + c] / (double)N;
         dF[c] = (s[9 + c] - s[18 + c]) / (double)N;
-        dn += h->cur_d9[c] * h->cur_d9[c];
     }
-    dn = std::sqrt(dn);
-    if (dn > 0) {
-        const int slot = h->ycur ^ 1;
-        GFF_TRY(launch_fluct_incr(h->d_yhist + (size_t)slot * 9 * N, h->d_Fk, h->d_F, dF, 1.0 / dn, N, h->stream));
-        h->ycur = slot;
-        h->nhist = h->nhist < 2 ? h->nhist + 1 : 2;
-    } else {
-        h->nhist = 0;  // a purely stress-controlled increment has no direction: history restarts
-    }
+    if ((st = record_history(h, h->cur_d9, dF, h->stream)) != GFF_OK) return st;
     GFF_TRY(cudaMemcpyAsync(h->d_F, h->d_Fk, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     if (h->any_cp) {
         GFF_TRY(cudaMemcpyAsync(h->d_Fpi, h->d_Fpi_t, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -945,12 +969,7 @@ gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
     // mixed precision leaves only the FP32 tangent of the last Newton iterate
     h->K_valid = h->opt.precision != GFF_PREC_MIXED;
     h->K32_valid = h->opt.precision == GFF_PREC_MIXED;
-    for (int c = 0; c < 9; ++c) {
-        h->prev_dFbar[c] = dF[c];
-        h->Pmacro_committed[c] = rep->Pmacro[c];
-        h->prev2_d9[c] = h->prev_d9[c];
-        h->prev_d9[c] = h->cur_d9[c];
-    }
+    for (int c = 0; c < 9; ++c) h->Pmacro_committed[c] = rep->Pmacro[c];
     GFF_TRY(cudaStreamSynchronize(h->stream));
     return GFF_OK;
 }

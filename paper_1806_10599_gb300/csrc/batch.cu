@@ -316,10 +316,17 @@ gff_status run(Batch& B, int nsteps, const double* dt, const double* Fbar, const
         BTRY(cudaStreamSynchronize(B.st));
         double add9[9];
         for (int c = 0; c < 9; ++c) add9[c] = mk[c] ? Pb[c] : 0.0;
+        // per RVE: mean F of the committed state, prescribed change, warm first return maps (as gff_step)
+        std::vector<double> Fold(9 * n);
+        std::vector<char> warm0(n);
         for (int r = 0; r < n; ++r) {
-            double d9[9];
-            for (int c = 0; c < 9; ++c) d9[c] = mk[c] ? 0.0 : Fb[c] - B.h_pin[9 * r + c] / (double)B.h[r]->N;
-            BTRY(launch_add_const9(B.h[r]->d_Fk, B.h[r]->d_F, d9, B.h[r]->N, B.st));
+            gff_handle* h = B.h[r];
+            for (int c = 0; c < 9; ++c) {
+                Fold[9 * r + c] = B.h_pin[9 * r + c] / (double)h->N;
+                h->cur_d9[c] = mk[c] ? 0.0 : Fb[c] - Fold[9 * r + c];
+            }
+            warm0[r] = first_eval_warm(h, h->cur_d9);
+            BTRY(launch_add_const9(h->d_Fk, h->d_F, h->cur_d9, h->N, B.st));
         }
         {
             gff_status st = set_residual_epilogue(B, add9);
@@ -338,7 +345,9 @@ gff_status run(Batch& B, int nsteps, const double* dt, const double* Fbar, const
             std::memcpy(B.h_pin, ina.data(), 2 * n * sizeof(int));
             BTRY(cudaMemcpyAsync(B.d_inactive, B.h_pin, 2 * n * sizeof(int), cudaMemcpyHostToDevice, B.st));
             BTRY(cudaMemsetAsync(B.d_cpflag, 0, n * sizeof(int), B.st));
-            BTRY(launch_constitutive_batch(B.h, n, dt[k], B.mixed ? TANGENT_F32 : TANGENT_F64, it > 0, B.d_inactive,
+            bool warm[MAX_BATCH];
+            for (int r = 0; r < n; ++r) warm[r] = it > 0 || warm0[r];
+            BTRY(launch_constitutive_batch(B.h, n, dt[k], B.mixed ? TANGENT_F32 : TANGENT_F64, warm, B.d_inactive,
                                            B.d_cpflag, B.d_cscratch, B.st));
             BTRY(launch_galerkin_batch<double>(B.bl_res, pa, B.st));
             gff_status st = GFF_OK;
@@ -420,7 +429,20 @@ gff_status run(Batch& B, int nsteps, const double* dt, const double* Fbar, const
                 ++newton[r];
             }
         }
-        // commit the converged RVEs; the others keep their last committed state
+        // commit the converged RVEs; the others keep their last committed state.  First the
+        // increment history (mean F change, normalised fluctuation increment) as gff_step keeps it.
+        for (int r = 0; r < n; ++r)
+            if (conv[r]) BTRY(launch_sum9(B.h[r]->d_Fk, B.h[r]->N, B.d_partial, B.d_out + 9 * r, B.st));
+        BTRY(cudaMemcpyAsync(B.h_pin, B.d_out, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, B.st));
+        BTRY(cudaStreamSynchronize(B.st));
+        for (int r = 0; r < n; ++r) {
+            if (!conv[r]) continue;
+            gff_handle* h = B.h[r];
+            double dF[9];
+            for (int c = 0; c < 9; ++c) dF[c] = B.h_pin[9 * r + c] / (double)h->N - Fold[9 * r + c];
+            gff_status sh = record_history(h, h->cur_d9, dF, B.st);
+            if (sh != GFF_OK) return sh;
+        }
         for (int r = 0; r < n; ++r) {
             gff_handle* h = B.h[r];
             if (!conv[r] && status[r] == GFF_OK) status[r] = GFF_ERR_NO_CONVERGENCE;

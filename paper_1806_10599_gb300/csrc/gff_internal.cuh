@@ -202,6 +202,13 @@ cudaError_t warm_guess(struct gff_unet* u, gff_handle* h, const double* d9, int*
 
 // ---- host helpers (api.cu)
 gff_status prepare_for_increments(gff_handle* h);
+// The return maps of an increment's first evaluation start from the last
+// evaluated slip increments when the prescribed change d9 keeps the direction
+// of the previous increment's (cosine > 1/2), else from zero.
+bool first_eval_warm(const gff_handle* h, const double* d9);
+// Increment history of a converged increment (h->d_Fk not yet committed):
+// y = (Fk - F - dF) / |d9| into the free slot, d9 and its predecessors kept.
+gff_status record_history(gff_handle* h, const double* d9, const double* dF, cudaStream_t st);
 void set_error(gff_handle* h, const char* msg);
 
 // ---- launchers (fft_proj.cu)
@@ -287,7 +294,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
 cudaError_t launch_fip_accumulate(gff_handle* h);
 // Batched constitutive update of the RVEs hs[0..n) (skip[r] != 0: RVE r is left alone);
 // cpflag[r] counts return-map failures of RVE r.
-cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, bool warm,
+cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
                                       const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st);
 size_t constitutive_batch_scratch_bytes();
 cudaError_t launch_fip_reset(gff_handle* h);

@@ -828,7 +828,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     return cudaGetLastError();
 }
 
-cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, bool warm,
+cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
                                       const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st) {
     ConstArgs args[MAX_BATCH];
     int start[MAX_BATCH + 1];
@@ -841,7 +841,7 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.C = h->d_C;
         a.S0 = h->d_S0;
         a.H = h->d_nrm + 41LL * h->ngrains;
-        a.warm = warm ? 1 : 0;
+        a.warm = warm[r] ? 1 : 0;
         a.gkind = h->d_gkind;
         a.gprm = h->d_nrm + 36LL * h->ngrains;
         a.Fpi_n = h->d_Fpi;

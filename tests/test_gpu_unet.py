@@ -185,10 +185,11 @@ def test_training_lowers_the_loss_and_warm_start_keeps_the_solution(tmp_path):
         F0 = g.gff_get_field(h0, g.GFF_FIELD_F, ms.n_voxels)
         F2 = g.gff_get_field(h2, g.GFF_FIELD_F, ms.n_voxels)
         assert rel_l2(F2, F0) <= 1e-7
-        # mode 1: where the guess was not kept, the increment is the plain one, bit for bit
+        # mode 1: where the guess was not kept, the increment is the plain one (the return maps of
+        # the re-evaluated zero start begin from other slip increments: equal to their tolerance)
         for k in range(hist.nsteps):
             if r1[k].warm_start_used == 0 and all(r.warm_start_used == 0 for r in r1[:k]):
-                assert np.array_equal(P1[k], P0[k])
+                assert np.linalg.norm(P1[k] - P0[k]) <= 1e-12 * np.linalg.norm(P0[k])
             assert r1[k].residual_first <= r0[k].residual_first * (1 + 1e-12) or r1[k].warm_start_used == 0
     finally:
         for h in hs:
