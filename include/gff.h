@@ -296,8 +296,11 @@ gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode);
 gff_status gff_reset_fips(gff_handle* h);
 gff_status gff_get_fips(gff_handle* h, double* pcyc_g, double* wcyc_g, double* fs_g);
 
-/* Committed state to/from a raw little-endian file (header + F, internal
- * variables, FIP accumulators).  Loading requires the same grid. */
+/* Committed state to/from a raw little-endian file: header, increment
+ * history (the last prescribed increments and normalised fluctuation
+ * increments the warm starts use), F, internal variables, FIP accumulators
+ * and the last slip increments, so that a resumed run repeats the original
+ * bit for bit.  Loading requires the same grid. */
 gff_status gff_save_state(gff_handle* h, const char* path);
 gff_status gff_load_state(gff_handle* h, const char* path);
 

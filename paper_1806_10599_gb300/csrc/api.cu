@@ -1072,19 +1072,35 @@ GFF_EXPORT gff_status gff_get_fips(gff_handle* h, double* pcyc_g, double* wcyc_g
 }
 
 // ------------------------------------------------------------------ checkpoint
-static const char kMagic[8] = {'G', 'F', 'F', 'S', 'T', 'A', 'T', '1'};
+static const char kMagic[8] = {'G', 'F', 'F', 'S', 'T', 'A', 'T', '2'};
+
+// Host part of the increment history: everything the next increment's start reads.
+struct HistHeader {
+    int32_t nhist, ycur, pad[2];
+    double prev_d9[9], prev2_d9[9], prev_dFbar[9], Pmacro[9];
+};
 
 GFF_EXPORT gff_status gff_save_state(gff_handle* h, const char* path) {
     if (!h || !path) return fail(h, GFF_ERR_ARG, "bad args");
     const long long N = h->N;
-    const size_t counts[4] = {9 * (size_t)N, 9 * (size_t)N, 12 * (size_t)N, NACC * (size_t)N};
-    double* src[4] = {h->d_F, h->d_Fpi, h->d_chi, h->d_acc};
+    const size_t counts[5] = {9 * (size_t)N, 9 * (size_t)N, 12 * (size_t)N, NACC * (size_t)N, 12 * (size_t)N};
+    double* src[5] = {h->d_F, h->d_Fpi, h->d_chi, h->d_acc, h->d_dg};
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(h, GFF_ERR_IO, "cannot open %s", path);
     int32_t hdr[4] = {h->grid.nx, h->grid.ny, h->grid.nz, NACC};
-    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1;
+    HistHeader hh{};
+    hh.nhist = h->nhist;
+    hh.ycur = h->ycur;
+    for (int c = 0; c < 9; ++c) {
+        hh.prev_d9[c] = h->prev_d9[c];
+        hh.prev2_d9[c] = h->prev2_d9[c];
+        hh.prev_dFbar[c] = h->prev_dFbar[c];
+        hh.Pmacro[c] = h->Pmacro_committed[c];
+    }
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              std::fwrite(&hh, sizeof hh, 1, f) == 1;
     std::vector<double> buf;
-    for (int i = 0; i < 4 && ok; ++i) {
+    for (int i = 0; i < 5 && ok; ++i) {
         buf.resize(counts[i]);
         cudaError_t e = cudaMemcpy(buf.data(), src[i], counts[i] * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
@@ -1093,6 +1109,15 @@ GFF_EXPORT gff_status gff_save_state(gff_handle* h, const char* path) {
         }
         ok = std::fwrite(buf.data(), sizeof(double), counts[i], f) == counts[i];
     }
+    if (ok) {
+        std::vector<float> yb(18 * (size_t)N);
+        cudaError_t e = cudaMemcpy(yb.data(), h->d_yhist, yb.size() * sizeof(float), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(h, GFF_ERR_CUDA, "save: %s", cudaGetErrorString(e));
+        }
+        ok = std::fwrite(yb.data(), sizeof(float), yb.size(), f) == yb.size();
+    }
     ok = (std::fclose(f) == 0) && ok;
     return ok ? GFF_OK : fail(h, GFF_ERR_IO, "write failed: %s", path);
 }
@@ -1100,19 +1125,21 @@ GFF_EXPORT gff_status gff_save_state(gff_handle* h, const char* path) {
 GFF_EXPORT gff_status gff_load_state(gff_handle* h, const char* path) {
     if (!h || !path) return fail(h, GFF_ERR_ARG, "bad args");
     const long long N = h->N;
-    const size_t counts[4] = {9 * (size_t)N, 9 * (size_t)N, 12 * (size_t)N, NACC * (size_t)N};
-    double* dst[4] = {h->d_F, h->d_Fpi, h->d_chi, h->d_acc};
+    const size_t counts[5] = {9 * (size_t)N, 9 * (size_t)N, 12 * (size_t)N, NACC * (size_t)N, 12 * (size_t)N};
+    double* dst[5] = {h->d_F, h->d_Fpi, h->d_chi, h->d_acc, h->d_dg};
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(h, GFF_ERR_IO, "cannot open %s", path);
     char mg[8];
     int32_t hdr[4];
+    HistHeader hh{};
     bool ok = std::fread(mg, 1, 8, f) == 8 && std::memcmp(mg, kMagic, 8) == 0 && std::fread(hdr, sizeof hdr, 1, f) == 1;
     if (ok && (hdr[0] != h->grid.nx || hdr[1] != h->grid.ny || hdr[2] != h->grid.nz || hdr[3] != NACC)) {
         std::fclose(f);
         return fail(h, GFF_ERR_ARG, "state file grid %dx%dx%d does not match", hdr[0], hdr[1], hdr[2]);
     }
+    ok = ok && std::fread(&hh, sizeof hh, 1, f) == 1 && hh.nhist >= 0 && hh.nhist <= 2 && (hh.ycur == 0 || hh.ycur == 1);
     std::vector<double> buf;
-    for (int i = 0; i < 4 && ok; ++i) {
+    for (int i = 0; i < 5 && ok; ++i) {
         buf.resize(counts[i]);
         ok = std::fread(buf.data(), sizeof(double), counts[i], f) == counts[i];
         if (ok) {
@@ -1123,11 +1150,29 @@ GFF_EXPORT gff_status gff_load_state(gff_handle* h, const char* path) {
             }
         }
     }
+    if (ok) {
+        std::vector<float> yb(18 * (size_t)N);
+        ok = std::fread(yb.data(), sizeof(float), yb.size(), f) == yb.size();
+        if (ok) {
+            cudaError_t e = cudaMemcpy(h->d_yhist, yb.data(), yb.size() * sizeof(float), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                std::fclose(f);
+                return fail(h, GFF_ERR_CUDA, "load: %s", cudaGetErrorString(e));
+            }
+        }
+    }
     std::fclose(f);
     if (!ok) return fail(h, GFF_ERR_IO, "read failed or not a state file: %s", path);
     GFF_TRY(cudaMemcpy(h->d_Fk, h->d_F, 9 * N * sizeof(double), cudaMemcpyDeviceToDevice));
     h->K_valid = h->K32_valid = false;
-    h->nhist = 0;  // the increment history is not part of the state file
+    h->nhist = hh.nhist;
+    h->ycur = hh.ycur;
+    for (int c = 0; c < 9; ++c) {
+        h->prev_d9[c] = hh.prev_d9[c];
+        h->prev2_d9[c] = hh.prev2_d9[c];
+        h->prev_dFbar[c] = hh.prev_dFbar[c];
+        h->Pmacro_committed[c] = hh.Pmacro[c];
+    }
     return GFF_OK;
 }
 
