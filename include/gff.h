@@ -106,6 +106,9 @@ typedef struct {
     double t_linear;       /* device time in the CG solves, s                */
     int warm_start_used;   /* 1: the Newton iteration started from the warm-start guess */
     double residual_first; /* ||b|| / ||P|| at the start the Newton iteration used     */
+    int cp_fallbacks;      /* voxel return maps that needed the exact-Newton fallback */
+    double cp_local_iters; /* local Newton iterations per voxel, summed over the
+                              increment's constitutive evaluations                  */
 } gff_step_report;
 
 typedef struct gff_unet gff_unet;

@@ -420,7 +420,7 @@ GFF_EXPORT gff_status gff_create(const gff_grid* grid, const gff_options* opt, g
         {(void**)&h->d_Fpi, f64, "Fpi"},    {(void**)&h->d_chi, 12 * N * sizeof(double), "chi"},
         {(void**)&h->d_Fpi_t, f64, "Fpi_t"}, {(void**)&h->d_chi_t, 12 * N * sizeof(double), "chi_t"},
         {(void**)&h->d_dg, 12 * N * sizeof(double), "dg"}, {(void**)&h->d_tau, 12 * N * sizeof(double), "tau"},
-        {(void**)&h->d_acc, NACC * N * sizeof(double), "fip"}, {(void**)&h->d_flag, 16, "flag"},
+        {(void**)&h->d_acc, NACC * N * sizeof(double), "fip"}, {(void**)&h->d_flag, 32, "flag"},
         {(void**)&h->d_red, 32 * RED_BLOCKS * sizeof(double), "reduce"},
         {(void**)&h->d_scal, 64 * sizeof(double), "scalars"},
         {(void**)&h->d_gid, N * sizeof(int), "grain id"},
@@ -472,7 +472,7 @@ static gff_status reset_state(gff_handle* h) {
     GFF_TRY(cudaMemset(h->d_chi, 0, 12 * N * sizeof(double)));
     GFF_TRY(cudaMemset(h->d_P, 0, 9 * N * sizeof(double)));
     GFF_TRY(cudaMemset(h->d_acc, 0, NACC * N * sizeof(double)));
-    GFF_TRY(cudaMemset(h->d_flag, 0, 16));
+    GFF_TRY(cudaMemset(h->d_flag, 0, 32));
     GFF_TRY(launch_fip_reset(h));
     GFF_TRY(cudaDeviceSynchronize());
     h->K_valid = h->K32_valid = false;
@@ -772,13 +772,13 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
         }
     } evg{ev};
-    int warm_used = 0;
-    double res_first = 0.0;
+    int warm_used = 0, cp_fb = 0;
+    double res_first = 0.0, cp_its = 0.0;
     // the report is written on every exit, failed attempts included (cut-back adds them up)
     struct RepGuard {
         gff_step_report* r;
-        const int &newton, &cgsum, &warm_used;
-        const double &res, &t_const, &t_res, &t_lin, &res_first;
+        const int &newton, &cgsum, &warm_used, &cp_fb;
+        const double &res, &t_const, &t_res, &t_lin, &res_first, &cp_its;
         ~RepGuard() {
             if (!r) return;
             r->newton_iters = newton;
@@ -789,12 +789,15 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             r->t_linear = t_lin;
             r->warm_start_used = warm_used;
             r->residual_first = res_first;
+            r->cp_fallbacks = cp_fb;
+            r->cp_local_iters = cp_its;
         }
-    } repg{rep, newton, cgsum, warm_used, res, t_const, t_res, t_lin, res_first};
+    } repg{rep, newton, cgsum, warm_used, cp_fb, res, t_const, t_res, t_lin, res_first, cp_its};
 
     // P, K at d_Fk and the residual b = -G_M(P) + M : Pbar with its norms
     auto evaluate = [&](bool warm_dg) -> gff_status {
         GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+        GFF_TRY(cudaMemsetAsync(h->d_flag + 4, 0, 2 * sizeof(int), h->stream));
         GFF_TRY(cudaEventRecord(ev[0], h->stream));
         GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, warm_dg));
         GFF_TRY(cudaEventRecord(ev[1], h->stream));
@@ -803,18 +806,22 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         GFF_TRY(launch_dot<double>(h->d_P, h->d_P, n, h->d_red + RED_BLOCKS, h->d_scal + 1, h->stream));
         GFF_TRY(cudaMemcpyAsync(h->d_scal + 2, h->d_flag, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
         GFF_TRY(cudaMemcpyAsync(h->d_scal + 3, h->d_flag + 2, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+        GFF_TRY(cudaMemcpyAsync(h->d_scal + 4, h->d_flag + 4, 2 * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
         GFF_TRY(cudaEventRecord(ev[2], h->stream));
-        double s3[4];
-        gff_status st2 = fetch(h, h->d_scal, 4, s3);
+        double s3[5];
+        gff_status st2 = fetch(h, h->d_scal, 5, s3);
         if (st2 != GFF_OK) return st2;
         float ms01 = 0.f, ms12 = 0.f;
         GFF_TRY(cudaEventElapsedTime(&ms01, ev[0], ev[1]));
         GFF_TRY(cudaEventElapsedTime(&ms12, ev[1], ev[2]));
         t_const += 1e-3 * ms01;
         t_res += 1e-3 * ms12;
-        int flag, tmo;
+        int flag, tmo, stats[2];
         std::memcpy(&flag, &s3[2], sizeof(int));
         std::memcpy(&tmo, &s3[3], sizeof(int));
+        std::memcpy(stats, &s3[4], 2 * sizeof(int));
+        cp_fb += stats[0];
+        cp_its += (double)stats[1] / (double)N;
         if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in the inverse FFT pass timed out");
         if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
         rr_b = s3[0];
@@ -988,6 +995,8 @@ gff_status step_with_cuts(gff_handle* h, double dt, const double* Fbar, const ui
     acc->t_constitutive += rep.t_constitutive;
     acc->t_residual += rep.t_residual;
     acc->t_linear += rep.t_linear;
+    acc->cp_fallbacks += rep.cp_fallbacks;
+    acc->cp_local_iters += rep.cp_local_iters;
     acc->residual = rep.residual;
     if (depth == 0) {
         acc->warm_start_used = rep.warm_start_used;

@@ -163,7 +163,8 @@ struct gff_handle {
     double* d_dg = nullptr;    // [12][N] slip increments of the trial
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
-    int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out copy waits
+    int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out copy waits,
+                               // [4] return-map fallbacks, [5] local Newton iterations
     // reductions
     double* d_red = nullptr;   // partial sums
     double* d_scal = nullptr;  // final scalars

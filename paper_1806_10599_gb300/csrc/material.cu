@@ -84,6 +84,8 @@ struct CPOut {
     double dg[12];
     double tau[12];
     bool ok;
+    bool fallback;  // the small-strain iteration failed; the exact Newton from zero ran
+    int iters;      // local Newton iterations, both tries
 };
 
 // LU with partial pivoting of an NN x NN row-major matrix, in place.
@@ -380,10 +382,11 @@ template <typename TJ>
 __device__ bool cp_local_solve(const double* F, const double* A, const double* chin, const double* __restrict__ S0,
                                const double* __restrict__ C, const double* __restrict__ PC, const CPParamsDev& pr,
                                double coef, int p, bool lowrank, int maxit, double* dg, ElState& st, double* chi,
-                               double* dh) {
+                               double* dh, int* iters) {
     for (int it = 0; it <= maxit; ++it) {
         double r[NSLIP];
         const double rmax = cp_residual(F, A, chin, dg, S0, pr, coef, p, st, chi, dh, r);
+        *iters = it;
         if (rmax <= 1e-14) return true;
         if (it == maxit || !(rmax < 1e300)) return false;
         if (lowrank) {
@@ -510,11 +513,14 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
     for (int a = 0; a < NSLIP; ++a) dg[a] = dg0 ? dg0[a] : 0.0;
     // FP64 corrections: J is ill-conditioned (cond ~ 1e8 and more) once slip
     // systems are active, beyond what an FP32 solve can steer
-    bool conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh);
+    int it1 = 0, it2 = 0;
+    bool conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh, &it1);
+    out.fallback = !conv;
     if (!conv) {  // fall back: exact Newton from dg = 0
         for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
-        conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, false, 300, dg, st, chi, dh);
+        conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, false, 300, dg, st, chi, dh, &it2);
     }
+    out.iters = it1 + it2;
     out.ok = conv;
     double FeS[9];
     mm(st.Fe, st.S, FeS);
@@ -579,6 +585,7 @@ struct ConstArgs {
     double* dg;
     double* tau;
     int* flag;
+    int* stats;  // [2] (may be null): voxels whose return map fell back, local Newton iterations
     long long N;
     const int* skip;  // batched launches: RVE left alone when *skip != 0
 };
@@ -595,6 +602,7 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
     double F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = a.F[k * N + v];
+    int n_fb = 0, n_it = 0;
     if (kind == GFF_MAT_CP_FCC) {
         double A[9], chin[12];
 #pragma unroll
@@ -629,6 +637,8 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
             }
         }
         if (!o.ok) atomicAdd(a.flag, 1);
+        n_fb = o.fallback ? 1 : 0;
+        n_it = o.iters;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             a.P[k * N + v] = o.P[k];
@@ -658,6 +668,14 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
             a.chi_t[s * N + v] = a.chi_n[s * N + v];
             a.dg[s * N + v] = 0.0;
             a.tau[s * N + v] = 0.0;
+        }
+    }
+    if (a.stats) {  // one atomic per warp
+        const unsigned m = __activemask();
+        const int sfb = __reduce_add_sync(m, n_fb), sit = __reduce_add_sync(m, n_it);
+        if ((int)(threadIdx.x & 31) == __ffs(m) - 1) {
+            if (sfb) atomicAdd(a.stats, sfb);
+            atomicAdd(a.stats + 1, sit);
         }
     }
 }
@@ -818,6 +836,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.dg = h->d_dg;
     a.tau = h->d_tau;
     a.flag = h->d_flag;
+    a.stats = h->d_flag + 4;
     a.N = h->N;
     a.skip = nullptr;
     const int blocks = (int)((h->N + TPB - 1) / TPB);
@@ -855,6 +874,7 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.dg = h->d_dg;
         a.tau = h->d_tau;
         a.flag = cpflag_dev + r;
+        a.stats = nullptr;
         a.N = h->N;
         a.skip = skip_dev + 2 * r;
         start[r + 1] = start[r] + (int)((h->N + TPB - 1) / TPB);

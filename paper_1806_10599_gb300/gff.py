@@ -75,6 +75,8 @@ class gff_step_report(ctypes.Structure):
         ("t_linear", c_double),
         ("warm_start_used", c_int),
         ("residual_first", c_double),
+        ("cp_fallbacks", c_int),
+        ("cp_local_iters", c_double),
     ]
 
 
