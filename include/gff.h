@@ -83,7 +83,8 @@ typedef struct {
 typedef struct {
     int projection;    /* GFF_PROJ_*                                               */
     int precision;     /* GFF_PREC_FP64 or GFF_PREC_MIXED (FP32 CG/FFT/projection) */
-    double newton_tol; /* stop when ||b||_2 / ||P||_2 <= newton_tol                */
+    double newton_tol; /* stop when ||b||_2 / ||P||_2 <= newton_tol; the return maps
+                          converge to max(1e-14, min(1e-11, 1e-5 newton_tol))    */
     double cg_tol;     /* CG stops when ||r|| <= max(cg_tol ||b||, 0.1 newton_tol ||P||) */
     int newton_max, cg_max;
     int max_cuts;      /* increment halvings allowed after a CP or Newton failure   */

@@ -103,7 +103,17 @@ struct Nine9 {
 struct CPParamsDev {
     double gdot0, p, tau0, c, d;
     double itau0;  // 1 / tau0
+    double rtol;   // return-map convergence: max_a |r_a| <= rtol
 };
+
+// Return-map tolerance for a Newton tolerance t on ||b|| / ||P||: a slip error
+// dg moves P by about C dg ~ 1e3 |P| dg, so max|r| <= 1e-5 t keeps the local
+// error two orders below the equilibrium tolerance; never looser than 1e-11
+// nor tighter than 1e-14.
+inline double return_map_tol(double newton_tol) {
+    const double t = 1e-5 * newton_tol;
+    return t < 1e-14 ? 1e-14 : (t > 1e-11 ? 1e-11 : t);
+}
 
 // Per-grain slip geometry block (FP64): the 12 Schmid tensors S0_a = s_a (x) m_a
 // [12][9], the slip directions s_a [12][3], the 4 plane normals m_p [4][3]

@@ -387,7 +387,7 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
         double r[NSLIP];
         const double rmax = cp_residual(F, A, chin, dg, S0, pr, coef, p, st, chi, dh, r);
         *iters = it;
-        if (rmax <= 1e-14) return true;
+        if (rmax <= pr.rtol) return true;
         if (it == maxit || !(rmax < 1e300)) return false;
         if (lowrank) {
             double x[NSLIP];
@@ -572,6 +572,7 @@ struct ConstArgs {
     const double* S0;
     const double* H;  // [ngrains][144]: P [5][12], C5^-1 [5][5] of the small-strain Jacobian (cp_correction_lowrank)
     int warm;         // 1: start the local Newton from dg (previous iterate)
+    double rtol;      // return-map tolerance (return_map_tol)
     const int* gkind;
     const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
     const double* Fpi_n;
@@ -616,6 +617,7 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         pr.c = gp[3];
         pr.d = gp[4];
         pr.itau0 = 1.0 / pr.tau0;
+        pr.rtol = a.rtol;
         double dg0[12];
         if (a.warm)
             for (int s2 = 0; s2 < NSLIP; ++s2) dg0[s2] = a.dg[s2 * N + v];
@@ -823,6 +825,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.S0 = h->d_S0;
     a.H = h->d_nrm + 41LL * h->ngrains;
     a.warm = warm ? 1 : 0;
+    a.rtol = return_map_tol(h->opt.newton_tol);
     a.gkind = h->d_gkind;
     a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
     a.Fpi_n = h->d_Fpi;
@@ -861,6 +864,7 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.S0 = h->d_S0;
         a.H = h->d_nrm + 41LL * h->ngrains;
         a.warm = warm[r] ? 1 : 0;
+        a.rtol = return_map_tol(h->opt.newton_tol);
         a.gkind = h->d_gkind;
         a.gprm = h->d_nrm + 36LL * h->ngrains;
         a.Fpi_n = h->d_Fpi;
