@@ -293,6 +293,14 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
     }
     GFF_TRY(cudaMemcpy(h->d_C, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice));
     GFF_TRY(cudaMemcpy(h->d_S0, S0.data(), S0.size() * sizeof(double), cudaMemcpyHostToDevice));
+    {
+        std::vector<float> g32(G32_STRIDE * (size_t)ng, 0.f);
+        for (int g = 0; g < ng; ++g) {
+            for (int k = 0; k < 108; ++k) g32[G32_STRIDE * (size_t)g + G32_S0 + k] = (float)S0[GEO_STRIDE * (size_t)g + GEO_S0 + k];
+            for (int k = 0; k < 81; ++k) g32[G32_STRIDE * (size_t)g + G32_C + k] = (float)C[81 * (size_t)g + k];
+        }
+        GFF_TRY(cudaMemcpy(h->d_geo32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     GFF_TRY(cudaMemcpy(h->d_nrm, nrmprm.data(), nrmprm.size() * sizeof(double), cudaMemcpyHostToDevice));
     GFF_TRY(cudaMemcpy(h->d_gkind, kind.data(), kind.size() * sizeof(int), cudaMemcpyHostToDevice));
     std::vector<float> gq(5 * (size_t)ng);
@@ -441,7 +449,7 @@ GFF_EXPORT void gff_destroy(gff_handle* h) {
     dfree(h->d_p); dfree(h->d_Ap); dfree(h->d_K32); dfree(h->d_b32); dfree(h->d_x32); dfree(h->d_r32);
     dfree(h->d_p32); dfree(h->d_Ap32); dfree(h->d_spec); dfree(h->d_Fpi); dfree(h->d_chi); dfree(h->d_Fpi_t);
     dfree(h->d_chi_t); dfree(h->d_dg); dfree(h->d_tau); dfree(h->d_acc); dfree(h->d_flag); dfree(h->d_red);
-    dfree(h->d_scal); dfree(h->d_gq); dfree(h->d_yhist);
+    dfree(h->d_scal); dfree(h->d_gq); dfree(h->d_yhist); dfree(h->d_geo32);
     if (h->h_scal) cudaFreeHost(h->h_scal);
     delete reinterpret_cast<gff_hostdata*>(h->hostdata);
     delete h;
@@ -487,7 +495,7 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
         if (grain_id[v] < 0 || grain_id[v] >= ngrains) return fail(h, GFF_ERR_ARG, "grain_id[%lld] out of range", v);
     for (int g = 0; g < ngrains; ++g)
         if (grain_phase[g] < 0 || grain_phase[g] >= 8) return fail(h, GFF_ERR_ARG, "grain_phase[%d] out of range", g);
-    dfree(h->d_C); dfree(h->d_S0); dfree(h->d_nrm); dfree(h->d_gkind); dfree(h->d_gq);
+    dfree(h->d_C); dfree(h->d_S0); dfree(h->d_nrm); dfree(h->d_gkind); dfree(h->d_gq); dfree(h->d_geo32);
     h->ngrains = ngrains;
     gff_status st;
     if ((st = dalloc(h, (void**)&h->d_C, 81 * (size_t)ngrains * sizeof(double), "C")) != GFF_OK) return st;
@@ -496,6 +504,9 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
     if ((st = dalloc(h, (void**)&h->d_nrm, (41 + 144) * (size_t)ngrains * sizeof(double), "normals")) != GFF_OK)
         return st;
     if ((st = dalloc(h, (void**)&h->d_gkind, (size_t)ngrains * sizeof(int), "kind")) != GFF_OK) return st;
+    if ((st = dalloc(h, (void**)&h->d_geo32, G32_STRIDE * (size_t)ngrains * sizeof(float), "FP32 slip geometry")) !=
+        GFF_OK)
+        return st;
     if ((st = dalloc(h, (void**)&h->d_gq, 5 * (size_t)ngrains * sizeof(float), "grain quaternions")) != GFF_OK)
         return st;
     GFF_TRY(cudaMemcpy(h->d_gid, grain_id, h->N * sizeof(int), cudaMemcpyHostToDevice));

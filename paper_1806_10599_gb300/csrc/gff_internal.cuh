@@ -120,6 +120,8 @@ inline double return_map_tol(double newton_tol) {
 // (systems 3p, 3p+1, 3p+2 share plane p) and the stiffness in Voigt order
 // (11, 22, 33, 23, 13, 12) [6][6].
 constexpr int GEO_S0 = 0, GEO_DIR = 108, GEO_NRM = 144, GEO_C6 = 156, GEO_STRIDE = 192;
+// FP32 copies for the FP32 tangent: S0 [12][9], C [81].
+constexpr int G32_S0 = 0, G32_C = 108, G32_STRIDE = 192;
 
 }  // namespace gff
 
@@ -140,6 +142,7 @@ struct gff_handle {
     double* d_C = nullptr;
     double* d_S0 = nullptr;
     double* d_nrm = nullptr;
+    float* d_geo32 = nullptr;  // [ngrains][G32_STRIDE]
     int* d_gkind = nullptr;
     int* d_gphase = nullptr;
     gff_material mat[8];

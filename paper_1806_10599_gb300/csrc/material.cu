@@ -53,11 +53,12 @@ __device__ __forceinline__ double ddot9(const double* a, const double* b) {
     for (int k = 0; k < 9; ++k) s = fma(a[k], b[k], s);
     return s;
 }
-// S = C : E (C has minor symmetries; stored in FP64, used in T)
-template <typename T> __device__ __forceinline__ void c_ddot(const double* __restrict__ C, const T* E, T* S) {
+// S = C : E (C has minor symmetries; stored in TC, used in T)
+template <typename T, typename TC>
+__device__ __forceinline__ void c_ddot(const TC* __restrict__ C, const T* E, T* S) {
 #pragma unroll
     for (int ij = 0; ij < 9; ++ij) {
-        const double* Cr = C + 9 * ij;
+        const TC* Cr = C + 9 * ij;
         T s = (T)0;
 #pragma unroll
         for (int kl = 0; kl < 9; ++kl) s = fma((T)__ldg(Cr + kl), E[kl], s);
@@ -217,11 +218,11 @@ __device__ void elastic_state(const double* F, const double* A, const double* dg
 //   dFpi_b = -A S0_b, dFe_b = F dFpi_b, dCe_b = dFe_b^T Fe + Fe^T dFe_b,
 //   dS_b = C : dCe_b / 2.
 template <typename T>
-__device__ void dstate_ddg(const T* F, const T* A, const double* __restrict__ S0_b, const double* __restrict__ C,
+__device__ void dstate_ddg(const T* F, const T* A, const T* __restrict__ S0_b, const T* __restrict__ C,
                            const ElStateT<T>& st, T* dFpi, T* dFe, T* dCe, T* dS) {
     T Sb[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Sb[k] = (T)__ldg(S0_b + k);
+    for (int k = 0; k < 9; ++k) Sb[k] = __ldg(S0_b + k);
     mm(A, Sb, dFpi);
 #pragma unroll
     for (int k = 0; k < 9; ++k) dFpi[k] = -dFpi[k];
@@ -258,10 +259,10 @@ __device__ double cp_residual(const double* F, const double* A, const double* ch
     return rmax;
 }
 
-// Exact Jacobian dr_a/ddg_b at the state st, in precision T.
+// Exact Jacobian dr_a/ddg_b at the state st, in precision T (S0 and C given in T).
 template <typename T>
-__device__ void cp_jacobian_exact(const T* F, const T* A, const T* dg, const double* __restrict__ S0,
-                                  const double* __restrict__ C, const CPParamsDev& pr, double coef,
+__device__ void cp_jacobian_exact(const T* F, const T* A, const T* dg, const T* __restrict__ S0,
+                                  const T* __restrict__ C, const CPParamsDev& pr, double coef,
                                   const ElStateT<T>& st, const T* chi, const T* dh, T* J) {
     const T cg = (T)(coef / pr.tau0), c = (T)pr.c, d = (T)pr.d;
     for (int b = 0; b < NSLIP; ++b) {
@@ -274,7 +275,7 @@ __device__ void cp_jacobian_exact(const T* F, const T* A, const T* dg, const dou
         for (int a = 0; a < NSLIP; ++a) {
             T dtau = (T)0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) dtau = fma(dM[k], (T)__ldg(S0 + 9 * a + k), dtau);
+            for (int k = 0; k < 9; ++k) dtau = fma(dM[k], __ldg(S0 + 9 * a + k), dtau);
             T v = -cg * dh[a] * dtau;
             if (a == b) {
                 const T den = (T)1 + d * fabs(dg[a]);
@@ -405,11 +406,12 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
     return false;
 }
 
-// Consistent tangent K = dP/dF at the converged return map, in precision T:
+// Consistent tangent K = dP/dF at the converged return map, in precision T
+// (the grain's S0 and C given in T, so no conversions in the loops):
 //   K = dP/dF|_dg + (dP/ddg) (ddg/dF),  J ddg/dF = (coef/g) h' dtau/dF|_dg.
 template <typename T>
-__device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd, const double* __restrict__ S0,
-                           const double* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& sd,
+__device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd, const T* __restrict__ S0,
+                           const T* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& sd,
                            const double* chid, const double* dhd, T* K) {
     T F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
     ElStateT<T> st;
@@ -487,7 +489,7 @@ __device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd
         for (int a = 0; a < NSLIP; ++a) {
             T dtau = (T)0;
 #pragma unroll
-            for (int q = 0; q < 9; ++q) dtau = fma(dM[q], (T)__ldg(S0 + 9 * a + q), dtau);
+            for (int q = 0; q < 9; ++q) dtau = fma(dM[q], __ldg(S0 + 9 * a + q), dtau);
             rhs[a] = cg * dh[a] * dtau;
         }
         lu_solve<NSLIP>(J, piv, rhs);
@@ -504,8 +506,8 @@ __device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd
 template <typename T>
 __device__ void cp_update(const double* F, const double* A, const double* chin, double dt,
                           const double* __restrict__ S0, const double* __restrict__ C, const double* __restrict__ H,
-                          const CPParamsDev& pr, const double* dg0 /* 12 or null */, T* K /* 81 or null */,
-                          CPOut& out) {
+                          const T* __restrict__ S0t, const T* __restrict__ Ct, const CPParamsDev& pr,
+                          const double* dg0 /* 12 or null */, T* K /* 81 or null */, CPOut& out) {
     const double coef = dt * pr.gdot0;
     const int p = (int)pr.p;
     double dg[NSLIP], dh[NSLIP], chi[NSLIP];
@@ -532,7 +534,7 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
         out.dg[a] = dg[a];
         out.tau[a] = st.tau[a];
     }
-    if (K && conv) out.ok = cp_tangent<T>(F, A, dg, S0, C, pr, coef, st, chi, dh, K);
+    if (K && conv) out.ok = cp_tangent<T>(F, A, dg, S0t, Ct, pr, coef, st, chi, dh, K);
 }
 
 __device__ void svk_update(const double* F, const double* __restrict__ C, double* P, double* K) {
@@ -570,6 +572,7 @@ struct ConstArgs {
     const int* gid;
     const double* C;
     const double* S0;
+    const float* G32;  // [ngrains][G32_STRIDE]: S0 and C in FP32 for the FP32 tangent
     const double* H;  // [ngrains][144]: P [5][12], C5^-1 [5][5] of the small-strain Jacobian (cp_correction_lowrank)
     int warm;         // 1: start the local Newton from dg (previous iterate)
     double rtol;      // return-map tolerance (return_map_tol)
@@ -624,13 +627,16 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         CPOut o;
         if (F32T) {
             float K[81];
-            cp_update<float>(F, A, chin, a.dt, a.S0 + (long long)GEO_STRIDE * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K, o);
+            const float* g32 = a.G32 + (long long)G32_STRIDE * gi;
+            cp_update<float>(F, A, chin, a.dt, a.S0 + (long long)GEO_STRIDE * gi, C, a.H + 144LL * gi, g32 + G32_S0,
+                             g32 + G32_C, pr, a.warm ? dg0 : nullptr, K, o);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
             double K[81];
-            cp_update<double>(F, A, chin, a.dt, a.S0 + (long long)GEO_STRIDE * gi, C, a.H + 144LL * gi, pr, a.warm ? dg0 : nullptr, K,
-                              o);
+            const double* geo = a.S0 + (long long)GEO_STRIDE * gi;
+            cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
+                              K, o);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
             if (a.K32) {
@@ -823,6 +829,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.gid = h->d_gid;
     a.C = h->d_C;
     a.S0 = h->d_S0;
+    a.G32 = h->d_geo32;
     a.H = h->d_nrm + 41LL * h->ngrains;
     a.warm = warm ? 1 : 0;
     a.rtol = return_map_tol(h->opt.newton_tol);
@@ -862,6 +869,7 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.gid = h->d_gid;
         a.C = h->d_C;
         a.S0 = h->d_S0;
+        a.G32 = h->d_geo32;
         a.H = h->d_nrm + 41LL * h->ngrains;
         a.warm = warm[r] ? 1 : 0;
         a.rtol = return_map_tol(h->opt.newton_tol);
