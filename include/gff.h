@@ -173,10 +173,21 @@ gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t*
  * candidate on this grid; results are bitwise the same for every choice.
  * gff_step runs it once per handle if it has not been run.  Uses the handle's
  * work buffers (call it before setting up an apply by hand, or call
- * gff_constitutive again afterwards).  tiles_out (host, 10 ints, may be NULL):
+ * gff_constitutive again afterwards).  tiles_out (host, 12 ints, may be NULL):
  * {fwd threads, z columns, z threads, inv threads, inv persistent blocks
- * (0: one block per plane)} for FP64 then FP32. */
+ * (0: one block per plane)} for FP64 then FP32, then the persistent TMA z
+ * pass's blocks for FP64 and FP32 (0: one block per strip). */
 gff_status gff_autotune(gff_handle* h, int* tiles_out);
+
+/* Sets the launch shapes instead of tuning them: tiles (host, 12 ints) in the
+ * layout gff_autotune writes.  Allowed: fwd threads 256/512; z columns
+ * 4/8/16/32 with z threads 128/256 (one block per strip), or, with TMA z
+ * blocks > 0, z columns 8/16 and z threads 256/512; inv threads 256/512, or
+ * with inv persistent blocks > 0 up to 1024 (FP32) / 512 (FP64).  Every
+ * shape performs the same operations in the same order, so results do not
+ * depend on them.  Returns GFF_ERR_ARG, changing nothing, for a shape the
+ * grid cannot use (shared memory, or no tensor-map support for TMA). */
+gff_status gff_set_tiles(gff_handle* h, const int* tiles);
 
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */
 gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9,

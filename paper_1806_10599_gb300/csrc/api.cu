@@ -662,7 +662,7 @@ GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, con
     if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "timed apply: %s", cudaGetErrorString(e));
     int tmo = 0;
     GFF_TRY(cudaMemcpy(&tmo, h->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in the inverse FFT pass timed out");
+    if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in an FFT pass timed out");
     return GFF_OK;
 }
 
@@ -677,6 +677,21 @@ GFF_EXPORT gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode) {
     return GFF_OK;
 }
 
+GFF_EXPORT gff_status gff_set_tiles(gff_handle* h, const int* tiles) {
+    if (!h || !tiles) return fail(h, GFF_ERR_ARG, "bad tiles args");
+    Tune t[2];
+    for (int p = 0; p < 2; ++p) {
+        t[p].t_fwd = tiles[5 * p + 0];
+        t[p].wz = tiles[5 * p + 1];
+        t[p].t_z = tiles[5 * p + 2];
+        t[p].t_inv = tiles[5 * p + 3];
+        t[p].inv_blocks = tiles[5 * p + 4];
+        t[p].z_blocks = tiles[10 + p];
+    }
+    if (!set_tiles(h, t[0], t[1])) return fail(h, GFF_ERR_ARG, "launch shapes not supported for this grid");
+    return GFF_OK;
+}
+
 GFF_EXPORT gff_status gff_autotune(gff_handle* h, int* tiles_out) {
     if (!h) return GFF_ERR_ARG;
     GFF_TRY(autotune_galerkin(h));
@@ -687,6 +702,7 @@ GFF_EXPORT gff_status gff_autotune(gff_handle* h, int* tiles_out) {
             tiles_out[5 * p + 2] = h->tune[p].t_z;
             tiles_out[5 * p + 3] = h->tune[p].t_inv;
             tiles_out[5 * p + 4] = h->tune[p].inv_blocks;
+            tiles_out[10 + p] = h->tune[p].z_blocks;
         }
     return GFF_OK;
 }
@@ -833,7 +849,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         std::memcpy(stats, &s3[4], 2 * sizeof(int));
         cp_fb += stats[0];
         cp_its += (double)stats[1] / (double)N;
-        if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in the inverse FFT pass timed out");
+        if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in an FFT pass timed out");
         if (flag) return fail(h, GFF_ERR_CP_FAIL, "return map failed in %d voxels", flag);
         rr_b = s3[0];
         nb = std::sqrt(s3[0]);

@@ -506,51 +506,68 @@ template <> __device__ __forceinline__ float rnorm3<float>(float a, float b, flo
     return rsqrtf(a * a + b * b + d * d);
 }
 
-template <typename T, int W>
-__device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec, const GridDev& g,
-                                           const ProjArgs& pa, const int blk, unsigned char* sm_raw) {
+// Shared tables of the z pass: twiddles, wave-vector components, frequencies
+// of the z positions, and the block's column frequencies colk[W]
+// (kx | ky << 16, -1 past the end).
+template <typename T> struct ZTables {
+    typename C2<T>::t* twz;
+    T *qx, *qy, *qz;
+    int *fqz, *colk;
+};
+
+template <typename T> __device__ __forceinline__ ZTables<T> ztables_at(unsigned char* p, const GridDev& g) {
     using C = typename C2<T>::t;
-    const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = g.nxh;
-    C* s = reinterpret_cast<C*>(sm_raw);  // [3][nz][W]
-    C* twz = s + 3 * nz * W;
-    T* qx = reinterpret_cast<T*>(twz + nz);
-    T* qy = qx + nxh;
-    T* qz = qy + ny;
-    int* fqz = reinterpret_cast<int*>(qz + nz);
-    int* colk = fqz + nz;  // [W]: kx | ky << 16 of the block's columns, -1 past the end
+    ZTables<T> tb;
+    tb.twz = reinterpret_cast<C*>(p);
+    tb.qx = reinterpret_cast<T*>(tb.twz + g.nz);
+    tb.qy = tb.qx + g.nxh;
+    tb.qz = tb.qy + g.ny;
+    tb.fqz = reinterpret_cast<int*>(tb.qz + g.nz);
+    tb.colk = tb.fqz + g.nz;
+    return tb;
+}
+template <typename T> __host__ __device__ constexpr size_t ztables_bytes(int nz, int ny, int nxh, int W) {
+    return (size_t)nz * sizeof(typename C2<T>::t) + (size_t)(nxh + ny + nz) * sizeof(T) + (size_t)(nz + W) * sizeof(int);
+}
+
+template <typename T>
+__device__ __forceinline__ void zproj_tables(const GridDev& g, const ProjArgs& pa, const ZTables<T>& tb) {
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // spectrum indices fit in 32 bits (9 nz ny nxh < 2^31 for axes <= MAXN)
-    const int nF = ny * nxh;
-    const int row = blk % 3;
-    const int f0 = (blk / 3) * W;
-    C* base = spec + 3 * row * nz * nF;  // component 3 row, z = 0
+    for (int i = tid; i < g.nz; i += nthr) {
+        tb.twz[i] = twp<T>(g, 2)[i];
+        tb.qz[i] = qtp<T>(g, pa.kind, 2)[i];
+        tb.fqz[i] = g.fqz[i];
+    }
+    for (int i = tid; i < g.ny; i += nthr) tb.qy[i] = qtp<T>(g, pa.kind, 1)[i];
+    for (int i = tid; i < g.nxh; i += nthr) tb.qx[i] = qtp<T>(g, pa.kind, 0)[i];
+}
 
-    for (int i = tid; i < nz; i += nthr) {
-        twz[i] = twp<T>(g, 2)[i];
-        qz[i] = qtp<T>(g, pa.kind, 2)[i];
-        fqz[i] = g.fqz[i];
-    }
-    for (int i = tid; i < ny; i += nthr) qy[i] = qtp<T>(g, pa.kind, 1)[i];
-    for (int i = tid; i < nxh; i += nthr) qx[i] = qtp<T>(g, pa.kind, 0)[i];
-    for (int w = tid; w < W; w += nthr) {
+// Column frequencies of the strip starting at f0 (before the strip's first barrier).
+template <typename T, int W>
+__device__ __forceinline__ void zproj_columns(const GridDev& g, int f0, const ZTables<T>& tb) {
+    const int nF = g.ny * g.nxh;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
         const int f = f0 + w;
-        const int py = f / nxh;
-        colk[w] = f < nF ? (f - py * nxh) | (g.fqy[py] << 16) : -1;
+        const int py = f / g.nxh;
+        tb.colk[w] = f < nF ? (f - py * g.nxh) | (g.fqy[py] << 16) : -1;
     }
-    for (int e = tid; e < 3 * nz * W; e += nthr) {
-        const int w = e % W, cz = e / W;  // cz = (component within the row) * nz + z
-        const int f = f0 + w;
-        s[e] = f < nF ? base[cz * nF + f] : mk<C>((T)0, (T)0);
-    }
-    __syncthreads();
-    fft_lines<T, false>(s, twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+}
 
+// Forward z transform, projection and inverse z transform of one loaded strip
+// s = [3][nz][W] (tensor row `row`); ends with a barrier.
+template <typename T, int W>
+__device__ __forceinline__ void zproj_strip(typename C2<T>::t* s, const GridDev& g, const ProjArgs& pa, int row,
+                                            const ZTables<T>& tb) {
+    using C = typename C2<T>::t;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    fft_lines<T, false>(s, tb.twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
     const T m0 = (T)pa.mask[3 * row], m1 = (T)pa.mask[3 * row + 1], m2 = (T)pa.mask[3 * row + 2];
     for (int e = tid; e < nz * W; e += nthr) {
         const int w = e % W, pz = e / W;
-        const int ck = colk[w];
+        const int ck = tb.colk[w];
         if (ck < 0) continue;
-        const int kx = ck & 0xffff, ky = ck >> 16, kz = fqz[pz];
+        const int kx = ck & 0xffff, ky = ck >> 16, kz = tb.fqz[pz];
         C* p0 = s + pz * W + w;
         C v0 = p0[0], v1 = p0[nz * W], v2 = p0[2 * nz * W];
         if (kx == 0 && ky == 0 && kz == 0) {
@@ -560,7 +577,7 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
         } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
             v0 = v1 = v2 = mk<C>((T)0, (T)0);
         } else {
-            const T a = qx[kx], b = qy[ky], d = qz[kz];
+            const T a = tb.qx[kx], b = tb.qy[ky], d = tb.qz[kz];
             const T inv = rnorm3(a, b, d);
             const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
             // t = sum_l x_il n_l ; y_ij = t n_j
@@ -574,7 +591,31 @@ __device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec,
         p0[2 * nz * W] = v2;
     }
     __syncthreads();
-    fft_lines<T, true>(s, twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+    fft_lines<T, true>(s, tb.twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void zproj_body(typename C2<T>::t* __restrict__ spec, const GridDev& g,
+                                           const ProjArgs& pa, const int blk, unsigned char* sm_raw) {
+    using C = typename C2<T>::t;
+    const int nz = g.nz;
+    C* s = reinterpret_cast<C*>(sm_raw);  // [3][nz][W]
+    const ZTables<T> tb = ztables_at<T>(reinterpret_cast<unsigned char*>(s + 3 * nz * W), g);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    // spectrum indices fit in 32 bits (9 nz ny nxh < 2^31 for axes <= MAXN)
+    const int nF = g.ny * g.nxh;
+    const int row = blk % 3;
+    const int f0 = (blk / 3) * W;
+    C* base = spec + 3 * row * nz * nF;  // component 3 row, z = 0
+    zproj_tables<T>(g, pa, tb);
+    zproj_columns<T, W>(g, f0, tb);
+    for (int e = tid; e < 3 * nz * W; e += nthr) {
+        const int w = e % W, cz = e / W;  // cz = (component within the row) * nz + z
+        const int f = f0 + w;
+        s[e] = f < nF ? base[cz * nF + f] : mk<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    zproj_strip<T, W>(s, g, pa, row, tb);
     for (int e = tid; e < 3 * nz * W; e += nthr) {
         const int w = e % W, cz = e / W;
         const int f = f0 + w;
@@ -588,6 +629,78 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     zproj_body<T, W>(spec, g, pa, blockIdx.x, sm_raw);
+}
+
+// Persistent z pass on the tensor-memory accelerator: the half spectrum seen as
+// a 3-D tensor [9 components][nz][ny nxh columns] (64-bit elements), a strip
+// (3 components of one tensor row, all z, W columns) is one TMA box whose
+// shared-memory image is exactly the [3][nz][W] layout the transforms use.
+// Blocks walk the strips with two buffers: the next strip's load and the
+// previous strip's store run while the current strip is transformed.  Waits
+// on the load barrier are bounded (timeout -> *err = 1, GFF_ERR_TIMEOUT).
+template <typename T, int W> __host__ __device__ constexpr size_t zstrip_bytes(int nz) {
+    return (((size_t)3 * nz * W * sizeof(typename C2<T>::t)) + 127) / 128 * 128;
+}
+template <typename T, int W> size_t ztma_smem(const GridDev& g) {
+    // + 127 bytes of alignment, 7 of barrier padding, 16 of barriers
+    return 2 * zstrip_bytes<T, W>(g.nz) + ztables_bytes<T>(g.nz, g.ny, g.nxh, W) + 160;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(512) k_zproj_tma(const __grid_constant__ CUtensorMap tm, GridDev g, ProjArgs pa,
+                                                  const int* __restrict__ skip, int* __restrict__ err) {
+    using C = typename C2<T>::t;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    unsigned char* p = sm_raw + ((128u - (smem_addr(sm_raw) & 127u)) & 127u);  // 128-byte aligned boxes
+    const size_t sb = zstrip_bytes<T, W>(g.nz);
+    C* buf[2] = {reinterpret_cast<C*>(p), reinterpret_cast<C*>(p + sb)};
+    const ZTables<T> tb = ztables_at<T>(p + 2 * sb, g);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(
+        (reinterpret_cast<uintptr_t>(tb.colk + W) + 7) & ~uintptr_t(7));
+    constexpr int K = (int)(sizeof(C) / 8);  // 64-bit elements per complex value
+    const uint32_t bytes = (uint32_t)(3 * g.nz * W * sizeof(C));
+    const int nF = g.ny * g.nxh, total = 3 * ((nF + W - 1) / W);
+    zproj_tables<T>(g, pa, tb);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    int s = blockIdx.x;
+    if (threadIdx.x == 0 && s < total) tma_load_3d(buf[0], &tm, (s / 3) * W * K, 0, 3 * (s % 3), &bar[0], bytes);
+    uint32_t phase[2] = {0u, 0u};
+    int cur = 0;
+    for (; s < total; s += gridDim.x) {
+        const int nxt = s + gridDim.x;
+        if (threadIdx.x == 0 && nxt < total) {
+            bulk_wait_read_all();  // the other buffer's store (previous strip) has left shared memory
+            tma_load_3d(buf[cur ^ 1], &tm, (nxt / 3) * W * K, 0, 3 * (nxt % 3), &bar[cur ^ 1], bytes);
+        }
+        zproj_columns<T, W>(g, (s / 3) * W, tb);
+        const bool ok = mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+                if (nxt < total) mbar_wait(&bar[cur ^ 1], phase[cur ^ 1], BULK_WAIT_CYCLES);
+                bulk_wait_all();
+            }
+            __syncthreads();
+            return;
+        }
+        phase[cur] ^= 1u;
+        zproj_strip<T, W>(buf[cur], g, pa, s % 3, tb);
+        fence_proxy_async_smem();  // the transforms' writes, before the asynchronous store reads them
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma_store_3d(&tm, (s / 3) * W * K, 0, 3 * (s % 3), buf[cur]);
+            bulk_commit();
+        }
+        cur ^= 1;
+    }
+    if (threadIdx.x == 0) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------- pass 3: inverse 2D transform + epilogue
@@ -768,8 +881,7 @@ template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 
 
 template <typename T> size_t zproj_smem(const GridDev& g, int W = zproj_width<T>()) {
     using C = typename C2<T>::t;
-    return (size_t)3 * g.nz * W * sizeof(C) + g.nz * sizeof(C) + (g.nxh + g.ny + g.nz) * sizeof(T) +
-           (g.nz + W) * sizeof(int) + 16;
+    return (size_t)3 * g.nz * W * sizeof(C) + ztables_bytes<T>(g.nz, g.ny, g.nxh, W) + 16;
 }
 
 constexpr size_t SMEM_MAX = 227 * 1024;
@@ -878,6 +990,96 @@ cudaError_t launch_z(const GridDev& g, int W, int threads, typename C2<T>::t* sp
     }
 }
 
+template <typename T> int tune_index() { return sizeof(T) == 8 ? 0 : 1; }
+
+// ---- TMA z pass: tensor maps and launch
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static std::mutex mu;
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+template <typename T> constexpr int zmap_slot(int W) { return W == 8 ? 0 : (W == 16 ? 1 : -1); }
+
+// The handle's half spectrum as [9][nz][ny nxh] 64-bit elements, box (W k, nz, 3); null if unavailable.
+template <typename T>
+const CUtensorMap* zmap(gff_handle* h, int W) {
+    using C = typename C2<T>::t;
+    const int pi = tune_index<T>(), wi = zmap_slot<T>(W);
+    if (wi < 0) return nullptr;
+    if (h->zmap_ok[pi][wi]) return &h->zmap[pi][wi];
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return nullptr;
+    const GridDev& g = h->g;
+    const cuuint64_t K = sizeof(C) / 8, nF = (cuuint64_t)g.ny * g.nxh;
+    const cuuint64_t dims[3] = {nF * K, (cuuint64_t)g.nz, 9};
+    const cuuint64_t strides[2] = {nF * sizeof(C), nF * g.nz * sizeof(C)};  // bytes, multiples of 16 (ny even)
+    const cuuint32_t box[3] = {(cuuint32_t)(W * K), (cuuint32_t)g.nz, 3};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(&h->zmap[pi][wi], CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, h->d_spec, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return nullptr;
+    h->zmap_ok[pi][wi] = true;
+    return &h->zmap[pi][wi];
+}
+
+template <typename T, int W>
+cudaError_t launch_z_tma_w(gff_handle* h, int threads, int blocks, const ProjArgs& pa, const int* skip,
+                           cudaStream_t st) {
+    const CUtensorMap* tm = zmap<T>(h, W);
+    if (!tm) return cudaErrorNotSupported;
+    const size_t sm = ztma_smem<T, W>(h->g);
+    allow_smem(k_zproj_tma<T, W>, sm);
+    k_zproj_tma<T, W><<<blocks, threads, sm, st>>>(*tm, h->g, pa, skip, h->d_flag + 2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_z_tma(gff_handle* h, int W, int threads, int blocks, const ProjArgs& pa, const int* skip,
+                         cudaStream_t st) {
+    switch (W) {
+        case 8: return launch_z_tma_w<T, 8>(h, threads, blocks, pa, skip, st);
+        case 16: return launch_z_tma_w<T, 16>(h, threads, blocks, pa, skip, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// blocks of the TMA z pass: all that fit at once, at most one per strip; 0 if it cannot run
+template <typename T, int W>
+int z_tma_blocks_w(gff_handle* h, int threads) {
+    const size_t sm = ztma_smem<T, W>(h->g);
+    if (sm > SMEM_MAX || !zmap<T>(h, W)) return 0;
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    allow_smem(k_zproj_tma<T, W>, sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zproj_tma<T, W>, threads, sm) != cudaSuccess ||
+        per < 1)
+        return 0;
+    const int total = zproj_blocks(h->g, W);
+    return nsm * per < total ? nsm * per : total;
+}
+template <typename T>
+int z_tma_blocks(gff_handle* h, int W, int threads) {
+    return W == 8 ? z_tma_blocks_w<T, 8>(h, threads) : (W == 16 ? z_tma_blocks_w<T, 16>(h, threads) : 0);
+}
+
 template <typename T>
 cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename C2<T>::t* spec, T* y,
                        const OutArgs& oa, const int* skip, cudaStream_t st, bool vout, int* err) {
@@ -904,7 +1106,6 @@ cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename
     return cudaGetLastError();
 }
 
-template <typename T> int tune_index() { return sizeof(T) == 8 ? 0 : 1; }
 
 // fastest candidate of one kernel: run(i) launches candidate i `reps` times
 template <typename F>
@@ -974,17 +1175,27 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     cudaError_t e = pick_fastest(2, tv, reps, st, [&](int i) { return launch_fwd<T>(g, tp[i], x, K, spec, nullptr, st, vin); }, &b);
     if (e != cudaSuccess) return e;
     tn.t_fwd = tp[b];
-    const int wz[4] = {4, 8, 16, 32};
-    const int tz[2] = {128, 256};
-    bool zv[8];
-    for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i / 2]) <= SMEM_MAX;
+    // z pass: one block per strip (W 4..32, 128 or 256 threads), or the persistent TMA pass (W 8, 16; 256, 512)
+    const int wz[12] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16};
+    const int tz[12] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512};
+    int zb[12] = {0};
+    bool zv[12];
+    for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i]) <= SMEM_MAX;
+    for (int i = 8; i < 12; ++i) {
+        zb[i] = z_tma_blocks<T>(h, wz[i], tz[i]);
+        zv[i] = zb[i] > 0;
+    }
     ProjArgs pa;
     pa.kind = GFF_PROJ_CONTINUOUS;
     for (int c = 0; c < 9; ++c) pa.mask[c] = 0.f;
-    e = pick_fastest(8, zv, reps, st, [&](int i) { return launch_z<T>(g, wz[i / 2], tz[i % 2], spec, pa, nullptr, st); }, &b);
+    e = pick_fastest(12, zv, reps, st, [&](int i) {
+        return zb[i] ? launch_z_tma<T>(h, wz[i], tz[i], zb[i], pa, nullptr, st)
+                     : launch_z<T>(g, wz[i], tz[i], spec, pa, nullptr, st);
+    }, &b);
     if (e != cudaSuccess) return e;
-    tn.wz = wz[b / 2];
-    tn.t_z = tz[b % 2];
+    tn.wz = wz[b];
+    tn.t_z = tz[b];
+    tn.z_blocks = zb[b];
     OutArgs oa;
     oa.scale = 1.0;
     for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
@@ -1002,6 +1213,34 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
 }
 
 }  // namespace
+
+// Launch shapes set by the caller (gff_set_tiles): checked against what each variant supports.
+template <typename T>
+bool tiles_valid(gff_handle* h, const Tune& t) {
+    const GridDev& g = h->g;
+    if ((t.t_fwd != 256 && t.t_fwd != 512) || (t.t_inv != 256 && t.t_inv != 512 && t.t_inv != 1024)) return false;
+    if (t.wz != 4 && t.wz != 8 && t.wz != 16 && t.wz != 32) return false;
+    if (t.inv_blocks < 0 || t.z_blocks < 0) return false;
+    if (t.z_blocks > 0) {
+        if ((t.t_z != 256 && t.t_z != 512) || z_tma_blocks<T>(h, t.wz, t.t_z) < 1) return false;
+    } else if ((t.t_z != 128 && t.t_z != 256) || zproj_smem<T>(g, t.wz) > SMEM_MAX) {
+        return false;
+    }
+    if (t.inv_blocks > 0) {
+        if (plane_stream_smem<T>(g) > SMEM_MAX || t.t_inv > inv_stream_max_threads<T>()) return false;
+    } else if (t.t_inv > 512) {
+        return false;
+    }
+    return true;
+}
+
+bool set_tiles(gff_handle* h, const Tune& t64, const Tune& t32) {
+    if (!tiles_valid<double>(h, t64) || !tiles_valid<float>(h, t32)) return false;
+    h->tune[0] = t64;
+    h->tune[1] = t32;
+    h->tuned = true;
+    return true;
+}
 
 cudaError_t autotune_galerkin(gff_handle* h) {
     // the kernels' cost does not depend on the values: the handle's vectors serve as inputs
@@ -1131,7 +1370,11 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     cudaError_t e = launch_fwd<T>(g, tn.t_fwd, x, K, spec, skip, h->stream, vin);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], h->stream);
-    e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, skip, h->stream);
+    // the TMA pass addresses the handle's own spectrum through its tensor map
+    if (tn.z_blocks > 0 && static_cast<const void*>(spec) == h->d_spec)
+        e = launch_z_tma<T>(const_cast<gff_handle*>(h), tn.wz, tn.t_z, tn.z_blocks, pa, skip, h->stream);
+    else
+        e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, skip, h->stream);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[2], h->stream);
     e = launch_inv<T>(g, tn.t_inv, tn.inv_blocks, spec, y, oa, skip, h->stream, vout, h->d_flag + 2);

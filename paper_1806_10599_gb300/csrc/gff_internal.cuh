@@ -1,6 +1,7 @@
 // Internal declarations of libgff: device tables, the handle, launchers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -94,6 +95,7 @@ struct Tune {
     int t_z;    // threads of k_zproj
     int t_inv;  // threads of k_plane_inv
     int inv_blocks;  // > 0: persistent streamed inverse pass with this many blocks
+    int z_blocks;    // > 0: persistent TMA z pass (k_zproj_tma) with this many blocks
 };
 
 struct Nine9 {
@@ -176,7 +178,7 @@ struct gff_handle {
     double* d_dg = nullptr;    // [12][N] slip increments of the trial
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
-    int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out copy waits,
+    int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out bulk-copy waits,
                                // [4] return-map fallbacks, [5] local Newton iterations
     // reductions
     double* d_red = nullptr;   // partial sums
@@ -186,7 +188,10 @@ struct gff_handle {
     bool K32_valid = false;
     bool grains_ready = false;
     void* hostdata = nullptr;  // host copies of the orientations and phases
-    gff::Tune tune[2] = {{512, 8, 256, 512, 0}, {512, 16, 256, 512, 0}};  // [0] FP64, [1] FP32
+    gff::Tune tune[2] = {{512, 8, 256, 512, 0, 0}, {512, 16, 256, 512, 0, 0}};  // [0] FP64, [1] FP32
+    // tensor maps of the half spectrum for the TMA z pass: [precision][W = 8, 16], built on first use
+    CUtensorMap zmap[2][2];
+    bool zmap_ok[2][2] = {{false, false}, {false, false}};
     bool tuned = false;
     // warm starts: history of the completed increments.  d is an increment's
     // prescribed average F change (0 on stress-controlled components) and
@@ -241,6 +246,8 @@ inline int zproj_blocks(const GridDev& g, int W) { return 3 * (int)(((long long)
 // Times every candidate launch shape of the three kernels on the handle's own
 // buffers and stores the fastest in h->tune (results do not depend on it).
 cudaError_t autotune_galerkin(gff_handle* h);
+// Launch shapes chosen by the caller; false (nothing changed) if a shape is unsupported.
+bool set_tiles(gff_handle* h, const Tune& t64, const Tune& t32);
 
 // Batched apply: rv (device, n entries), start arrays (device) for the plane
 // kernels (9 nz blocks per RVE) and the z kernel (zproj_blocks per RVE).

@@ -103,6 +103,7 @@ _SIGS = {
     "gff_project": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "gff_apply_operator_timed": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_autotune": (c_int, [c_void_p, c_void_p]),
+    "gff_set_tiles": (c_int, [c_void_p, c_void_p]),
     "gff_project_noalloc": (c_int, [_P(gff_grid), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
     "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -244,10 +245,17 @@ def gff_apply_operator_timed(h, precision, mask9, x_dev, y_dev):
 
 
 def gff_autotune(h):
-    """Returns {fwd threads, z columns, z threads, inv threads, inv persistent blocks} for FP64 and FP32."""
-    t = (ctypes.c_int * 10)()
+    """Returns {fwd threads, z columns, z threads, inv threads, inv persistent blocks, TMA z blocks}
+    for FP64 and FP32."""
+    t = (ctypes.c_int * 12)()
     _check(h, _lib.gff_autotune(h, ctypes.cast(t, c_void_p)))
-    return {"fp64": list(t[0:5]), "fp32": list(t[5:10])}
+    return {"fp64": list(t[0:5]) + [t[10]], "fp32": list(t[5:10]) + [t[11]]}
+
+
+def gff_set_tiles(h, fp64, fp32):
+    """Launch shapes in the layout gff_autotune returns: 6 ints per precision."""
+    t = (ctypes.c_int * 12)(*(list(fp64[:5]) + list(fp32[:5]) + [fp64[5], fp32[5]]))
+    return _check(h, _lib.gff_set_tiles(h, ctypes.cast(t, c_void_p)))
 
 
 def gff_project(h, precision, mask9, x_dev, y_dev):

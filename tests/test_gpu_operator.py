@@ -140,3 +140,43 @@ def test_apply_without_tangent_is_a_state_error():
         assert e.value.status == g.GFF_ERR_STATE
     finally:
         g.gff_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_launch_shapes_give_identical_results(prec):
+    """Every launch shape -- one block per z strip or the persistent TMA z pass,
+    one block per plane or the persistent bulk-copy inverse pass, with few blocks
+    so that each walks several strips / planes -- computes the same operations in
+    the same order: results equal bit for bit, and match the oracle."""
+    torch = torch_cuda()
+    g = gff()
+    shape = (32, 32, 32)
+    nz, ny, nx = shape
+    ms = polycrystal(nx, 6, 9)
+    h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options())
+    try:
+        g.gff_constitutive(h, 1.0)
+        x = _field(11, shape).reshape(9, -1)
+        X = torch.from_numpy(x.copy()).cuda()
+        if prec == 1:
+            X = X.float()
+        outs = []
+        # (fwd threads, W, z threads, inv threads, inv blocks, TMA z blocks)
+        shapes = [(512, 8, 256, 512, 0, 0), (256, 8, 256, 256, 0, 7), (512, 16, 512, 512, 5, 3),
+                  (256, 16, 128, 512, 0, 0)]
+        for s in shapes:
+            g.gff_set_tiles(h, s, s)
+            Y = torch.empty_like(X)
+            g.gff_apply_operator(h, prec, None, X, Y)
+            torch.cuda.synchronize()
+            outs.append(Y.double().cpu().numpy())
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        F = np.tile(np.eye(3).reshape(3, 3, 1, 1, 1), (1, 1) + shape)
+        _, K = voxel_K_oracle(ms, F)
+        ref = sp.GK(K, x.reshape(3, 3, nz, ny, nx), ms.L, sp.KIND_CONTINUOUS)
+        assert rel_l2(outs[0], ref.reshape(9, -1)) <= (1e-12 if prec == 0 else 2e-6)
+        with pytest.raises(g.GffError):
+            g.gff_set_tiles(h, (512, 4, 256, 512, 0, 5), (512, 4, 256, 512, 0, 5))  # no TMA at W = 4
+    finally:
+        g.gff_destroy(h)
