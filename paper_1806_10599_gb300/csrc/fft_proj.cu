@@ -381,6 +381,7 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
     C* twx = s + ny * ls;
     C* twy = twx + nx;
     int* posx = reinterpret_cast<int*>(twy + ny);
+    int* posy = posx + nx;  // position of each y frequency after the forward y transform
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
@@ -389,7 +390,10 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
         twx[i] = twp<T>(g, 0)[i];
         posx[i] = g.posx[i];
     }
-    for (int i = tid; i < ny; i += nthr) twy[i] = twp<T>(g, 1)[i];
+    for (int i = tid; i < ny; i += nthr) {
+        twy[i] = twp<T>(g, 1)[i];
+        posy[g.fqy[i]] = i;
+    }
 
     if (VEC) {
         // 16-byte loads of VW consecutive voxels of one row; K row c is read
@@ -477,8 +481,27 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
         }
     }
     __syncthreads();
-    // y transform of the nxh columns
-    fft_lines<T, false>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
+    // y transform: columns kx = 0 and nx/2 of real rows are real, so one complex
+    // transform Z = X_0 + i X_h carries both and nx/2 columns are transformed, not nx/2 + 1
+    for (int yy = tid; yy < ny; yy += nthr) s[yy * ls].y = s[yy * ls + kh].x;
+    __syncthreads();
+    fft_lines<T, false>(s, twy, g.ay, kh, 1, 1, 0, ls, tid, nthr);
+    {
+        // X_0(k) = (Z(k) + conj Z(-k)) / 2, X_h(k) = (Z(k) - conj Z(-k)) / 2i (one position per thread)
+        C zp, zq;
+        const bool act = tid < ny;
+        if (act) {
+            const int kk = g.fqy[tid];
+            zp = s[tid * ls];
+            zq = s[posy[kk == 0 ? 0 : ny - kk] * ls];
+        }
+        __syncthreads();
+        if (act) {
+            s[tid * ls] = mk<C>((zp.x + zq.x) * (T)0.5, (zp.y - zq.y) * (T)0.5);
+            s[tid * ls + kh] = mk<C>((zp.y + zq.y) * (T)0.5, (zq.x - zp.x) * (T)0.5);
+        }
+        __syncthreads();
+    }
     C* out = spec + ((long long)c * g.nz + z) * (long long)ny * nxh;
     // the plane is contiguous in both places and ny * nxh * sizeof(C) is a multiple of 16
     const int nq = ny * nxh * (int)sizeof(C) / 16;
@@ -716,7 +739,16 @@ __device__ __forceinline__ void plane_inv_compute(typename C2<T>::t* s, T* __res
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
-    fft_lines<T, true>(s, twy, g.ay, nxh, 1, 1, 0, ls, tid, nthr);
+    const int kh0 = nx / 2;
+    // columns kx = 0 and nx/2 transform back to real columns: one complex transform of X_0 + i X_h
+    for (int yy = tid; yy < ny; yy += nthr) {
+        const C a = s[yy * ls], b = s[yy * ls + kh0];
+        s[yy * ls] = mk<C>(a.x - b.y, a.y + b.x);
+    }
+    __syncthreads();
+    fft_lines<T, true>(s, twy, g.ay, kh0, 1, 1, 0, ls, tid, nthr);
+    for (int yy = tid; yy < ny; yy += nthr) s[yy * ls + kh0].x = s[yy * ls].y;
+    __syncthreads();
     // merge the half spectra of rows 2r, 2r+1 into one packed complex row
     // Z_k = A_k + i B_k over all k (Hermitian symmetry of real rows), in the
     // digit-reversed order the inverse x pass expects
@@ -939,7 +971,7 @@ int axis_freq_of_pos(int pos, const AxisPlan& p) {
 }
 
 size_t plane_smem_bytes(int nx, int ny, int elem) {
-    return (size_t)ny * (nx / 2 + 1) * elem + (size_t)(nx + ny) * elem + (size_t)nx * sizeof(int) + 16;
+    return (size_t)ny * (nx / 2 + 1) * elem + (size_t)(nx + ny) * elem + (size_t)(nx + ny) * sizeof(int) + 16;
 }
 
 namespace {
