@@ -955,7 +955,6 @@ gff_status record_history(gff_handle* h, const double* d9, const double* dF, cud
         h->nhist = 0;  // a purely stress-controlled increment has no direction: history restarts
     }
     for (int c = 0; c < 9; ++c) {
-        h->prev_dFbar[c] = dF[c];
         h->prev2_d9[c] = h->prev_d9[c];
         h->prev_d9[c] = d9[c];
     }
@@ -1113,7 +1112,7 @@ static const char kMagic[8] = {'G', 'F', 'F', 'S', 'T', 'A', 'T', '2'};
 // Host part of the increment history: everything the next increment's start reads.
 struct HistHeader {
     int32_t nhist, ycur, pad[2];
-    double prev_d9[9], prev2_d9[9], prev_dFbar[9], Pmacro[9];
+    double prev_d9[9], prev2_d9[9], Pmacro[9];
 };
 
 GFF_EXPORT gff_status gff_save_state(gff_handle* h, const char* path) {
@@ -1130,7 +1129,6 @@ GFF_EXPORT gff_status gff_save_state(gff_handle* h, const char* path) {
     for (int c = 0; c < 9; ++c) {
         hh.prev_d9[c] = h->prev_d9[c];
         hh.prev2_d9[c] = h->prev2_d9[c];
-        hh.prev_dFbar[c] = h->prev_dFbar[c];
         hh.Pmacro[c] = h->Pmacro_committed[c];
     }
     bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
@@ -1206,7 +1204,6 @@ GFF_EXPORT gff_status gff_load_state(gff_handle* h, const char* path) {
     for (int c = 0; c < 9; ++c) {
         h->prev_d9[c] = hh.prev_d9[c];
         h->prev2_d9[c] = hh.prev2_d9[c];
-        h->prev_dFbar[c] = hh.prev_dFbar[c];
         h->Pmacro_committed[c] = hh.Pmacro[c];
     }
     return GFF_OK;

@@ -200,7 +200,6 @@ struct gff_handle {
     float* d_yhist = nullptr;    // [2][9][N]: y of the last two completed increments
     int ycur = 0;                // slot of the last completed increment's y
     int nhist = 0;               // consecutive completed increments with |d| > 0 on record (0..2)
-    double prev_dFbar[9] = {0};  // average F change of the last completed increment
     double Pmacro_committed[9] = {0};  // average P of the committed state
     double cur_d9[9] = {0};      // d of the increment being solved
     double prev_d9[9] = {0};     // d of the last completed increment
