@@ -296,6 +296,11 @@ int gff_unet_num_samples(const gff_unet* u);
  * shuffled epochs; losses (host, steps, may be NULL) receives each step's
  * loss. */
 gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* losses);
+/* How gff_unet_train picks samples: 0 (default) shuffled epochs; 1 each step
+ * draws a sample with probability 1/(2 n) + e_i / (2 sum e), e_i the mean
+ * square of sample i's target, so the increments the extrapolation predicts
+ * worst (first increments, load reversals) are seen more often. */
+gff_status gff_unet_set_sampling(gff_unet* u, int mode);
 /* Initial guess of h's increments: mode 0 zero-fluctuation start; 1 network
  * guess, kept only when its first residual is below the zero start's (costs
  * one more constitutive evaluation per increment); 2 network guess always;

@@ -15,6 +15,7 @@
 // FP32 master weights updated by Adam.  The whole network is periodic
 // (wrapping 3x3x3 taps, 2x2x2 pooling, nearest upsampling), so one set of
 // weights serves any cubic grid whose size is a multiple of 8.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -75,6 +76,8 @@ struct gff_unet {
     int sample_n = 0;
     std::vector<bf16*> sx;
     std::vector<float*> sy;
+    std::vector<double> se;  // mean square of each sample's target
+    int sampling = 0;        // 0: shuffled epochs; 1: half uniform, half in proportion to se
     std::string err;
 };
 
@@ -548,6 +551,22 @@ UEXPORT gff_status gff_unet_eval_host(gff_unet* u, int n, const float* x, const 
     return grads ? copy_params(u, grads, u->d_g) : GFF_OK;
 }
 
+// Mean square of a device target of n values (for the sampling weights).
+static gff_status target_energy(gff_unet* u, const float* t, long long n, double* e) {
+    double* d = nullptr;
+    UTRY(cudaMalloc(&d, sizeof(double)));
+    cudaError_t err = cudaMemset(d, 0, sizeof(double));
+    if (err == cudaSuccess) {
+        k_sumsq<<<grid_of(n), 256>>>(t, n, d);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaMemcpy(e, d, sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (err != cudaSuccess) return ufail(u, GFF_ERR_CUDA, "U-Net sample", err);
+    *e /= (double)n;
+    return GFF_OK;
+}
+
 // Keep the last increment of h (inputs and the fluctuation-increment target) as a training sample.
 UEXPORT gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h) {
     if (!u || !h) return GFF_ERR_ARG;
@@ -575,8 +594,16 @@ UEXPORT gff_status gff_unet_add_sample(gff_unet* u, gff_handle* h) {
         cudaFree(t);
         return ufail(u, GFF_ERR_CUDA, "U-Net sample", e);
     }
+    double en = 0.0;
+    gff_status se = target_energy(u, t, V * 9, &en);
+    if (se != GFF_OK) {
+        cudaFree(x);
+        cudaFree(t);
+        return se;
+    }
     u->sx.push_back(x);
     u->sy.push_back(t);
+    u->se.push_back(en);
     u->sample_n = h->grid.nx;
     return GFF_OK;
 }
@@ -599,13 +626,22 @@ UEXPORT gff_status gff_unet_add_sample_host(gff_unet* u, int n, const float* x, 
         cudaFree(dt);
         return ufail(u, GFF_ERR_CUDA, "U-Net sample", e);
     }
+    double en = 0.0;
+    for (long long i = 0; i < V * 9; ++i) en += (double)target[i] * target[i];
     u->sx.push_back(dx);
     u->sy.push_back(dt);
+    u->se.push_back(en / (double)(V * 9));
     u->sample_n = n;
     return GFF_OK;
 }
 
 UEXPORT int gff_unet_num_samples(const gff_unet* u) { return u ? (int)u->sx.size() : 0; }
+
+UEXPORT gff_status gff_unet_set_sampling(gff_unet* u, int mode) {
+    if (!u || mode < 0 || mode > 1) return u ? ufail(u, GFF_ERR_ARG, "sampling mode must be 0 or 1") : GFF_ERR_ARG;
+    u->sampling = mode;
+    return GFF_OK;
+}
 
 // Adam steps over the stored samples (one sample per step, shuffled epochs).
 UEXPORT gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* losses) {
@@ -617,15 +653,33 @@ UEXPORT gff_status gff_unet_train(gff_unet* u, int steps, double lr, double* los
     const int ns = (int)u->sx.size();
     std::vector<int> order(ns);
     uint64_t rs = u->seed ^ 0xA5A5A5A5ULL ^ (uint64_t)u->adam_t;
-    for (int k = 0; k < steps; ++k) {
-        if (k % ns == 0) {  // new epoch: Fisher-Yates shuffle
-            for (int i = 0; i < ns; ++i) order[i] = i;
-            for (int i = ns - 1; i > 0; --i) {
-                const int j = (int)(sm64(rs) % (uint64_t)(i + 1));
-                std::swap(order[i], order[j]);
-            }
+    // importance sampling: cumulative weights 1/(2 ns) + se_i / (2 sum se)
+    std::vector<double> cum(ns);
+    {
+        double tot = 0.0;
+        for (double e : u->se) tot += e;
+        double c = 0.0;
+        for (int i = 0; i < ns; ++i) {
+            c += 0.5 / ns + (tot > 0 ? 0.5 * u->se[i] / tot : 0.5 / ns);
+            cum[i] = c;
         }
-        const int sidx = order[k % ns];
+    }
+    for (int k = 0; k < steps; ++k) {
+        int sidx;
+        if (u->sampling == 1) {
+            const double r = (double)(sm64(rs) >> 11) * (1.0 / 9007199254740992.0) * cum[ns - 1];
+            sidx = (int)(std::upper_bound(cum.begin(), cum.end(), r) - cum.begin());
+            if (sidx >= ns) sidx = ns - 1;
+        } else {
+            if (k % ns == 0) {  // new epoch: Fisher-Yates shuffle
+                for (int i = 0; i < ns; ++i) order[i] = i;
+                for (int i = ns - 1; i > 0; --i) {
+                    const int j = (int)(sm64(rs) % (uint64_t)(i + 1));
+                    std::swap(order[i], order[j]);
+                }
+            }
+            sidx = order[k % ns];
+        }
         View X{u->sx[sidx], IN_CH};
         if ((st = forward(u, X, nullptr)) != GFF_OK) return st;
         UTRY(cudaMemsetAsync(u->d_loss, 0, sizeof(double), nullptr));

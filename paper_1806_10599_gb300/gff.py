@@ -122,6 +122,7 @@ _SIGS = {
     "gff_unet_add_sample": (c_int, [c_void_p, c_void_p]),
     "gff_unet_add_sample_host": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
     "gff_unet_num_samples": (c_int, [c_void_p]),
+    "gff_unet_set_sampling": (c_int, [c_void_p, c_int]),
     "gff_unet_train": (c_int, [c_void_p, c_int, c_double, c_void_p]),
     "gff_set_warm_start": (c_int, [c_void_p, c_void_p, c_int]),
     "gff_reset_fips": (c_int, [c_void_p]),
@@ -394,6 +395,10 @@ def gff_unet_add_sample_host(u, n, x, target):
     xa, xp = _host(np.asarray(x).reshape(V, UNET_IN), np.float32)
     ta, tp = _host(np.asarray(target).reshape(V, 9), np.float32)
     return _ucheck(u, _lib.gff_unet_add_sample_host(u, int(n), xp, tp))
+
+
+def gff_unet_set_sampling(u, mode):
+    return _ucheck(u, _lib.gff_unet_set_sampling(u, int(mode)))
 
 
 def gff_unet_num_samples(u):

@@ -92,12 +92,15 @@ def main():
     ap.add_argument("--eval-grains", type=int, default=500)
     ap.add_argument("--eval-increments", type=int, default=20)
     ap.add_argument("--weights", default=None, help="save the trained weights here")
+    ap.add_argument("--sampling", type=int, default=1,
+                    help="0: shuffled epochs; 1: samples drawn in proportion to their target energy (half uniform)")
     a = ap.parse_args()
     u = g.gff_unet_create(1)
     try:
         t0 = time.perf_counter()
         collect(u, [5000 + i for i in range(a.train_rves)], increments=a.train_increments)
         t1 = time.perf_counter()
+        g.gff_unet_set_sampling(u, a.sampling)
         losses = g.gff_unet_train(u, a.steps, a.lr)
         t2 = time.perf_counter()
         if a.weights:
