@@ -150,10 +150,10 @@ gff_status gff_get_field(gff_handle* h, int which, double* host);
  * without committing internal variables. */
 gff_status gff_constitutive(gff_handle* h, double dt);
 
-/* y = G_M(K : x)  (Eq. newlinop) with the K of the last constitutive
- * evaluation (gff_constitutive, or the last Newton iterate of gff_step; after
- * a mixed-precision gff_step only the FP32 tangent exists, so an FP64 apply
- * returns GFF_ERR_STATE until gff_constitutive is called).  precision GFF_PREC_FP64: x_dev, y_dev are double[9N];
+/* y = G_M(K : x)  (Eq. newlinop) with the K of the last gff_constitutive.
+ * gff_step computes tangents only where a Newton correction needs them, never
+ * at the converged iterate, so after a step (or gff_set_field of F) an apply
+ * returns GFF_ERR_STATE until gff_constitutive is called.  precision GFF_PREC_FP64: x_dev, y_dev are double[9N];
  * GFF_PREC_MIXED: float[9N] and K rounded to FP32.  mask9 (host, may be NULL)
  * marks stress-controlled components: the zero frequency of the operator is
  * diag(mask9) instead of 0.  x_dev and y_dev may not overlap. */

@@ -826,7 +826,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
         GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
         GFF_TRY(cudaMemsetAsync(h->d_flag + 4, 0, 2 * sizeof(int), h->stream));
         GFF_TRY(cudaEventRecord(ev[0], h->stream));
-        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, warm_dg));
+        GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, warm_dg, CONST_P));
         GFF_TRY(cudaEventRecord(ev[1], h->stream));
         GFF_TRY(launch_galerkin<double>(h, h->d_P, (const double*)nullptr, h->d_b, pa, ores, h->d_spec));
         GFF_TRY(launch_dot<double>(h->d_b, h->d_b, n, h->d_red, h->d_scal, h->stream));
@@ -897,6 +897,20 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             break;
         }
         if (it == h->opt.newton_max) break;
+        // the tangent only now that a Newton correction needs it (the converged iterate never does)
+        {
+            GFF_TRY(cudaMemsetAsync(h->d_flag, 0, sizeof(int), h->stream));
+            GFF_TRY(cudaEventRecord(ev[0], h->stream));
+            GFF_TRY(launch_constitutive(h, h->d_Fk, dt, mixed ? TANGENT_F32 : TANGENT_F64, false, CONST_K));
+            GFF_TRY(cudaEventRecord(ev[1], h->stream));
+            int kflag = 0;
+            GFF_TRY(cudaMemcpyAsync(&kflag, h->d_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            GFF_TRY(cudaStreamSynchronize(h->stream));
+            float ms01 = 0.f;
+            GFF_TRY(cudaEventElapsedTime(&ms01, ev[0], ev[1]));
+            t_const += 1e-3 * ms01;
+            if (kflag) return fail(h, GFF_ERR_CP_FAIL, "tangent failed in %d voxels", kflag);
+        }
         const double stop = std::fmax(h->opt.cg_tol * nb, 0.1 * h->opt.newton_tol * nP);
         int its = 0;
         GFF_TRY(cudaEventRecord(ev[2], h->stream));
@@ -999,9 +1013,8 @@ gff_status commit_increment(gff_handle* h, gff_step_report* rep) {
         GFF_TRY(cudaMemcpyAsync(h->d_chi, h->d_chi_t, 12 * N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         GFF_TRY(launch_fip_accumulate(h));
     }
-    // mixed precision leaves only the FP32 tangent of the last Newton iterate
-    h->K_valid = h->opt.precision != GFF_PREC_MIXED;
-    h->K32_valid = h->opt.precision == GFF_PREC_MIXED;
+    // the converged iterate's tangent is never computed: K is stale until gff_constitutive
+    h->K_valid = h->K32_valid = false;
     for (int c = 0; c < 9; ++c) h->Pmacro_committed[c] = rep->Pmacro[c];
     GFF_TRY(cudaStreamSynchronize(h->stream));
     return GFF_OK;

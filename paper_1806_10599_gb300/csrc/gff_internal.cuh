@@ -310,7 +310,11 @@ size_t batch_plane_smem(int nx, int ny, int elem);
 // TANGENT_F32 computes the crystal-plasticity tangent in FP32 and writes only K32.
 // warm: start each voxel's local Newton from the slip increments left in d_dg by the previous call.
 enum { TANGENT_F64 = 0, TANGENT_F64_AND_F32 = 1, TANGENT_F32 = 2 };
-cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm = false);
+// part: CONST_ALL (P and K), CONST_P (return map and P; K untouched), CONST_K (K at
+// the slips the last CONST_P launch stored; P and the trial state untouched).
+enum { CONST_ALL = 0, CONST_P = 1, CONST_K = 2 };
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm = false,
+                                int part = CONST_ALL);
 cudaError_t launch_fip_accumulate(gff_handle* h);
 // Batched constitutive update of the RVEs hs[0..n) (skip[r] != 0: RVE r is left alone);
 // cpflag[r] counts return-map failures of RVE r.

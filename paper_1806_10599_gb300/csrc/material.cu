@@ -597,7 +597,27 @@ struct ConstArgs {
 // F32T: the crystal-plasticity tangent is computed in FP32 and only K32 is
 // written (mixed precision); otherwise the tangent is FP64, written to K and,
 // when K32 is set, also rounded into K32.
-template <bool F32T>
+// The tangent alone, at the slips dg of the last return map (stored by a
+// PART_P launch): the elastic state and the residual terms are rebuilt at dg
+// -- the same function of the same values, so K equals what the return map's
+// own tangent would have been, bit for bit.
+template <typename T>
+__device__ bool cp_tangent_at(const double* F, const double* A, const double* chin, const double* dg, double dt,
+                              const double* __restrict__ geo, const T* __restrict__ S0t, const T* __restrict__ Ct,
+                              const CPParamsDev& pr, T* K) {
+    const double coef = dt * pr.gdot0;
+    ElState st;
+    double chi[NSLIP], dh[NSLIP], r[NSLIP];
+    cp_residual(F, A, chin, dg, geo, pr, coef, (int)pr.p, st, chi, dh, r);
+    return cp_tangent<T>(F, A, dg, S0t, Ct, pr, coef, st, chi, dh, K);
+}
+
+// PART_ALL: return map, P and the tangent; PART_P: return map and P (K left as
+// it was); PART_K: the tangent at the stored slips (P and the trial state
+// left as they were).
+enum { PART_ALL = 0, PART_P = 1, PART_K = 2 };
+
+template <bool F32T, int PART>
 __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const long long v) {
     const long long N = a.N;
     const int gi = a.gid[v];
@@ -621,20 +641,45 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         pr.d = gp[4];
         pr.itau0 = 1.0 / pr.tau0;
         pr.rtol = a.rtol;
+        const double* geo = a.S0 + (long long)GEO_STRIDE * gi;
+        const float* g32 = a.G32 + (long long)G32_STRIDE * gi;
+        if (PART == PART_K) {
+            double dg[12];
+            for (int s = 0; s < NSLIP; ++s) dg[s] = a.dg[s * N + v];
+            bool ok;
+            if (F32T) {
+                float K[81];
+                ok = cp_tangent_at<float>(F, A, chin, dg, a.dt, geo, g32 + G32_S0, g32 + G32_C, pr, K);
+#pragma unroll
+                for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
+            } else {
+                double K[81];
+                ok = cp_tangent_at<double>(F, A, chin, dg, a.dt, geo, geo + GEO_S0, C, pr, K);
+#pragma unroll
+                for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
+                if (a.K32) {
+#pragma unroll
+                    for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
+                }
+            }
+            if (!ok) atomicAdd(a.flag, 1);
+            return;
+        }
         double dg0[12];
         if (a.warm)
             for (int s2 = 0; s2 < NSLIP; ++s2) dg0[s2] = a.dg[s2 * N + v];
         CPOut o;
-        if (F32T) {
+        if (PART == PART_P) {
+            cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
+                              (double*)nullptr, o);
+        } else if (F32T) {
             float K[81];
-            const float* g32 = a.G32 + (long long)G32_STRIDE * gi;
-            cp_update<float>(F, A, chin, a.dt, a.S0 + (long long)GEO_STRIDE * gi, C, a.H + 144LL * gi, g32 + G32_S0,
-                             g32 + G32_C, pr, a.warm ? dg0 : nullptr, K, o);
+            cp_update<float>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, g32 + G32_S0, g32 + G32_C, pr,
+                             a.warm ? dg0 : nullptr, K, o);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
             double K[81];
-            const double* geo = a.S0 + (long long)GEO_STRIDE * gi;
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
                               K, o);
 #pragma unroll
@@ -660,25 +705,29 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
     } else {
         double P[9], K[81];
         svk_update(F, C, P, K);
+        if (PART != PART_K) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) a.P[k * N + v] = P[k];
-        if (!F32T) {
+            for (int k = 0; k < 9; ++k) a.P[k * N + v] = P[k];
 #pragma unroll
-            for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
+            for (int k = 0; k < 9; ++k) a.Fpi_t[k * N + v] = a.Fpi_n[k * N + v];
+            for (int s = 0; s < NSLIP; ++s) {
+                a.chi_t[s * N + v] = a.chi_n[s * N + v];
+                a.dg[s * N + v] = 0.0;
+                a.tau[s * N + v] = 0.0;
+            }
         }
-        if (a.K32) {
+        if (PART != PART_P) {
+            if (!F32T) {
 #pragma unroll
-            for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
-        }
+                for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
+            }
+            if (a.K32) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) a.Fpi_t[k * N + v] = a.Fpi_n[k * N + v];
-        for (int s = 0; s < NSLIP; ++s) {
-            a.chi_t[s * N + v] = a.chi_n[s * N + v];
-            a.dg[s * N + v] = 0.0;
-            a.tau[s * N + v] = 0.0;
+                for (int k = 0; k < 81; ++k) a.K32[k * N + v] = (float)K[k];
+            }
         }
     }
-    if (a.stats) {  // one atomic per warp
+    if (PART != PART_K && a.stats) {  // one atomic per warp
         const unsigned m = __activemask();
         const int sfb = __reduce_add_sync(m, n_fb), sit = __reduce_add_sync(m, n_it);
         if ((int)(threadIdx.x & 31) == __ffs(m) - 1) {
@@ -688,11 +737,11 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
     }
 }
 
-template <bool F32T>
+template <bool F32T, int PART>
 __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.N) return;
-    constitutive_voxel<F32T>(a, v);
+    constitutive_voxel<F32T, PART>(a, v);
 }
 
 // one launch over the voxels of several RVEs: RVE r owns blocks [start[r], start[r+1])
@@ -705,7 +754,7 @@ __global__ void __launch_bounds__(TPB) k_constitutive_batch(const ConstArgs* __r
     if (a.skip && *a.skip) return;
     const long long v = (long long)(blockIdx.x - start[r]) * blockDim.x + threadIdx.x;
     if (v >= a.N) return;
-    constitutive_voxel<F32T>(a, v);
+    constitutive_voxel<F32T, PART_ALL>(a, v);
 }
 
 // ---------------------------------------------------------------- fatigue indicator parameters
@@ -823,7 +872,7 @@ __global__ void k_grain_final(const double* sums, int ngrains, double fs_k, doub
 
 }  // namespace
 
-cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm) {
+cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm, int part) {
     ConstArgs a;
     a.F = F;
     a.gid = h->d_gid;
@@ -850,10 +899,20 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.N = h->N;
     a.skip = nullptr;
     const int blocks = (int)((h->N + TPB - 1) / TPB);
-    if (tangent == TANGENT_F32)
-        k_constitutive<true><<<blocks, TPB, 0, h->stream>>>(a);
-    else
-        k_constitutive<false><<<blocks, TPB, 0, h->stream>>>(a);
+    const bool f32 = tangent == TANGENT_F32;
+    switch (part) {
+        case CONST_P:
+            if (f32) k_constitutive<true, PART_P><<<blocks, TPB, 0, h->stream>>>(a);
+            else k_constitutive<false, PART_P><<<blocks, TPB, 0, h->stream>>>(a);
+            break;
+        case CONST_K:
+            if (f32) k_constitutive<true, PART_K><<<blocks, TPB, 0, h->stream>>>(a);
+            else k_constitutive<false, PART_K><<<blocks, TPB, 0, h->stream>>>(a);
+            break;
+        default:
+            if (f32) k_constitutive<true, PART_ALL><<<blocks, TPB, 0, h->stream>>>(a);
+            else k_constitutive<false, PART_ALL><<<blocks, TPB, 0, h->stream>>>(a);
+    }
     return cudaGetLastError();
 }
 
