@@ -689,12 +689,14 @@ GFF_EXPORT gff_status gff_set_tiles(gff_handle* h, const int* tiles) {
         t[p].z_blocks = tiles[10 + p];
     }
     if (!set_tiles(h, t[0], t[1])) return fail(h, GFF_ERR_ARG, "launch shapes not supported for this grid");
+    GFF_TRY(preload_constitutive());
     return GFF_OK;
 }
 
 GFF_EXPORT gff_status gff_autotune(gff_handle* h, int* tiles_out) {
     if (!h) return GFF_ERR_ARG;
     GFF_TRY(autotune_galerkin(h));
+    GFF_TRY(preload_constitutive());  // kernels loaded now, not inside the first increment
     if (tiles_out)
         for (int p = 0; p < 2; ++p) {
             tiles_out[5 * p + 0] = h->tune[p].t_fwd;
@@ -981,6 +983,7 @@ gff_status prepare_for_increments(gff_handle* h) {
     if (st != GFF_OK) return st;
     if (!h->tuned) {
         cudaError_t e = autotune_galerkin(h);
+        if (e == cudaSuccess) e = preload_constitutive();
         if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
     }
     return GFF_OK;
@@ -1068,7 +1071,10 @@ GFF_EXPORT gff_status gff_step(gff_handle* h, double dt, const double Fbar[9], c
     const auto t0 = std::chrono::steady_clock::now();
     gff_step_report rep;
     std::memset(&rep, 0, sizeof rep);
-    if (!h->tuned) GFF_TRY(autotune_galerkin(h));
+    if (!h->tuned) {
+        GFF_TRY(autotune_galerkin(h));
+        GFF_TRY(preload_constitutive());
+    }
     st = step_with_cuts(h, dt, Fbar, mask, Pbar, 0, &rep);
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (report) *report = rep;

@@ -316,6 +316,7 @@ enum { CONST_ALL = 0, CONST_P = 1, CONST_K = 2 };
 cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm = false,
                                 int part = CONST_ALL);
 cudaError_t launch_fip_accumulate(gff_handle* h);
+cudaError_t preload_constitutive();
 // Batched constitutive update of the RVEs hs[0..n) (skip[r] != 0: RVE r is left alone);
 // cpflag[r] counts return-map failures of RVE r.
 cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,

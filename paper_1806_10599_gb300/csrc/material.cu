@@ -872,6 +872,21 @@ __global__ void k_grain_final(const double* sums, int ngrains, double fs_k, doub
 
 }  // namespace
 
+// Loads every constitutive kernel now (with lazy module loading the first launch of
+// each would otherwise pay for it inside the caller's first increment).
+cudaError_t preload_constitutive() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_constitutive<true, PART_ALL>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<true, PART_P>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<true, PART_K>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<false, PART_ALL>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<false, PART_P>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<false, PART_K>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<true>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<false>);
+    return e;
+}
+
 cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm, int part) {
     ConstArgs a;
     a.F = F;
