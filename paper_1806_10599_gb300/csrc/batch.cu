@@ -348,7 +348,7 @@ gff_status run(Batch& B, int nsteps, const double* dt, const double* Fbar, const
             bool warm[MAX_BATCH];
             for (int r = 0; r < n; ++r) warm[r] = it > 0 || warm0[r];
             BTRY(launch_constitutive_batch(B.h, n, dt[k], B.mixed ? TANGENT_F32 : TANGENT_F64, warm, B.d_inactive,
-                                           B.d_cpflag, B.d_cscratch, B.st));
+                                           B.d_cpflag, B.d_cscratch, B.st, CONST_P));
             BTRY(launch_galerkin_batch<double>(B.bl_res, pa, B.st));
             gff_status st = GFF_OK;
             BTRY(launch_dot_batch<double>(n, B.d_nb, B.d_partial, B.d_out, B.st));
@@ -384,6 +384,27 @@ gff_status run(Batch& B, int nsteps, const double* dt, const double* Fbar, const
                 any = true;
             }
             if (!any) break;
+            // tangents of the RVEs that take a Newton correction (as gff_step: never at a converged iterate)
+            {
+                std::vector<int> inak(2 * n, 0);
+                for (int r = 0; r < n; ++r) inak[2 * r] = rr0[r] >= 0 ? 0 : 1;
+                std::memcpy(B.h_pin, inak.data(), 2 * n * sizeof(int));
+                BTRY(cudaMemcpyAsync(B.d_inactive, B.h_pin, 2 * n * sizeof(int), cudaMemcpyHostToDevice, B.st));
+                BTRY(cudaMemsetAsync(B.d_cpflag, 0, n * sizeof(int), B.st));
+                bool nowarm[MAX_BATCH] = {false};
+                BTRY(launch_constitutive_batch(B.h, n, dt[k], B.mixed ? TANGENT_F32 : TANGENT_F64, nowarm,
+                                               B.d_inactive, B.d_cpflag, B.d_cscratch, B.st, CONST_K));
+                BTRY(cudaMemcpyAsync(B.h_pin, B.d_cpflag, n * sizeof(int), cudaMemcpyDeviceToHost, B.st));
+                BTRY(cudaStreamSynchronize(B.st));
+                std::vector<int> kf(n);
+                std::memcpy(kf.data(), B.h_pin, n * sizeof(int));
+                for (int r = 0; r < n; ++r)
+                    if (rr0[r] >= 0 && kf[r]) {
+                        status[r] = GFF_ERR_CP_FAIL;
+                        active[r] = false;
+                        rr0[r] = -1.0;
+                    }
+            }
             // right-hand sides and starting vectors of the active RVEs
             for (int r = 0; r < n; ++r) {
                 if (rr0[r] < 0) continue;
@@ -454,8 +475,7 @@ gff_status run(Batch& B, int nsteps, const double* dt, const double* Fbar, const
                 BTRY(cudaMemcpyAsync(h->d_chi, h->d_chi_t, 12 * N * sizeof(double), cudaMemcpyDeviceToDevice, B.st));
                 BTRY(launch_fip_accumulate(h));
             }
-            h->K_valid = !B.mixed;
-            h->K32_valid = B.mixed;
+            h->K_valid = h->K32_valid = false;  // the converged iterate's tangent is not computed
             BTRY(launch_sum9(h->d_P, N, B.d_partial, B.d_out + 18 * r, B.st));
             BTRY(launch_sum9(h->d_F, N, B.d_partial, B.d_out + 18 * r + 9, B.st));
         }

@@ -320,7 +320,8 @@ cudaError_t preload_constitutive();
 // Batched constitutive update of the RVEs hs[0..n) (skip[r] != 0: RVE r is left alone);
 // cpflag[r] counts return-map failures of RVE r.
 cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
-                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st);
+                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st,
+                                      int part = CONST_ALL);
 size_t constitutive_batch_scratch_bytes();
 cudaError_t launch_fip_reset(gff_handle* h);
 cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs);

@@ -745,7 +745,7 @@ __global__ void __launch_bounds__(TPB) k_constitutive(ConstArgs a) {
 }
 
 // one launch over the voxels of several RVEs: RVE r owns blocks [start[r], start[r+1])
-template <bool F32T>
+template <bool F32T, int PART>
 __global__ void __launch_bounds__(TPB) k_constitutive_batch(const ConstArgs* __restrict__ args,
                                                             const int* __restrict__ start, int n) {
     int r = 0;
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(TPB) k_constitutive_batch(const ConstArgs* __r
     if (a.skip && *a.skip) return;
     const long long v = (long long)(blockIdx.x - start[r]) * blockDim.x + threadIdx.x;
     if (v >= a.N) return;
-    constitutive_voxel<F32T, PART_ALL>(a, v);
+    constitutive_voxel<F32T, PART>(a, v);
 }
 
 // ---------------------------------------------------------------- fatigue indicator parameters
@@ -882,8 +882,10 @@ cudaError_t preload_constitutive() {
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<false, PART_ALL>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<false, PART_P>);
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive<false, PART_K>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<true>);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<false>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<true, PART_P>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<true, PART_K>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<false, PART_P>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_constitutive_batch<false, PART_K>);
     return e;
 }
 
@@ -932,7 +934,8 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
 }
 
 cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
-                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st) {
+                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st,
+                                      int part) {
     ConstArgs args[MAX_BATCH];
     int start[MAX_BATCH + 1];
     start[0] = 0;
@@ -971,10 +974,20 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
     cudaError_t e = cudaMemcpyAsync(dargs, args, sizeof(ConstArgs) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dstart, start, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    if (tangent == TANGENT_F32)
-        k_constitutive_batch<true><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
-    else
-        k_constitutive_batch<false><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+    const bool f32 = tangent == TANGENT_F32;
+    switch (part) {
+        case CONST_P:
+            if (f32) k_constitutive_batch<true, PART_P><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            else k_constitutive_batch<false, PART_P><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            break;
+        case CONST_K:
+            if (f32) k_constitutive_batch<true, PART_K><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            else k_constitutive_batch<false, PART_K><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            break;
+        default:
+            if (f32) k_constitutive_batch<true, PART_ALL><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            else k_constitutive_batch<false, PART_ALL><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+    }
     return cudaGetLastError();
 }
 
