@@ -241,14 +241,16 @@ __device__ void dstate_ddg(const T* F, const T* A, const T* __restrict__ S0_b, c
 }
 
 // Residual r_a(dg) and the quantities the Jacobians need; returns max |r_a|.
+// iden[a] = 1 / (1 + d |dg_a|), the backstress denominator, kept for the correction.
 __device__ double cp_residual(const double* F, const double* A, const double* chin, const double* dg,
                               const double* __restrict__ geo, const CPParamsDev& pr, double coef, int p, ElState& st,
-                              double* chi, double* dh, double* r) {
+                              double* chi, double* dh, double* r, double* iden) {
     elastic_state(F, A, dg, geo, st);
     double rmax = 0.0;
     for (int a = 0; a < NSLIP; ++a) {
-        const double den = 1.0 + pr.d * fabs(dg[a]);
-        chi[a] = (chin[a] + pr.c * dg[a]) / den;
+        const double id = 1.0 / (1.0 + pr.d * fabs(dg[a]));
+        iden[a] = id;
+        chi[a] = (chin[a] + pr.c * dg[a]) * id;
         const double x = (st.tau[a] - chi[a]) * pr.itau0;
         const double ax = fabs(x);
         const double axp1 = ipow(ax, p - 1);
@@ -302,8 +304,9 @@ __device__ void cp_jacobian_exact(const T* F, const T* A, const T* dg, const T* 
 template <typename TJ>
 __device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__ PC, const double* dg,
                                                       const CPParamsDev& pr, double coef, const double* chi,
-                                                      const double* dh, const double* r, double* x) {
-    const TJ cg = (TJ)(coef / pr.tau0), c = (TJ)pr.c, d = (TJ)pr.d;
+                                                      const double* dh, const double* iden, const double* r,
+                                                      double* x) {
+    const TJ cg = (TJ)(coef * pr.itau0), c = (TJ)pr.c, d = (TJ)pr.d;
     TJ A[15], b[5];  // packed lower triangle of C5^-1 + P G P^T, and P D^-1 r
     {
         int k = 0;
@@ -319,8 +322,9 @@ __device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__
     for (int a = 0; a < NSLIP; ++a) {
         f[a] = cg * (TJ)dh[a];
         const TJ dga = (TJ)dg[a];
-        const TJ dchi = (c - d * sgn(dga) * (TJ)chi[a]) / ((TJ)1 + d * fabs(dga));
-        Di[a] = (TJ)1 / ((TJ)1 + f[a] * dchi);
+        const TJ dchi = (c - d * sgn(dga) * (TJ)chi[a]) * (TJ)iden[a];
+        // the correction only steers the iteration: an FP32 reciprocal is accurate enough
+        Di[a] = (TJ)__frcp_rn((float)((TJ)1 + f[a] * dchi));
         const TJ ga = f[a] * Di[a], ra = (TJ)r[a] * Di[a];
         TJ p[5];
 #pragma unroll
@@ -334,7 +338,7 @@ __device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__
         }
     }
     // A = L diag(q) L^T (no pivoting: A is SPD)
-    TJ L[5][5], q[5];
+    TJ L[5][5], q[5], iq[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
         TJ s = A[j * (j + 1) / 2 + j];
@@ -343,6 +347,7 @@ __device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__
         if (!(s > (TJ)0)) return false;
         q[j] = s;
         const TJ inv = (TJ)1 / s;
+        iq[j] = inv;
 #pragma unroll
         for (int i = j + 1; i < 5; ++i) {
             TJ t = A[i * (i + 1) / 2 + j];
@@ -360,7 +365,7 @@ __device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__
         u[i] = t;
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) u[i] /= q[i];
+    for (int i = 0; i < 5; ++i) u[i] *= iq[i];
 #pragma unroll
     for (int i = 4; i >= 0; --i) {
 #pragma unroll
@@ -386,13 +391,14 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
                                double* dh, int* iters) {
     for (int it = 0; it <= maxit; ++it) {
         double r[NSLIP];
-        const double rmax = cp_residual(F, A, chin, dg, S0, pr, coef, p, st, chi, dh, r);
+        double iden[NSLIP];
+        const double rmax = cp_residual(F, A, chin, dg, S0, pr, coef, p, st, chi, dh, r, iden);
         *iters = it;
         if (rmax <= pr.rtol) return true;
         if (it == maxit || !(rmax < 1e300)) return false;
         if (lowrank) {
             double x[NSLIP];
-            if (!cp_correction_lowrank<TJ>(PC, dg, pr, coef, chi, dh, r, x)) return false;
+            if (!cp_correction_lowrank<TJ>(PC, dg, pr, coef, chi, dh, iden, r, x)) return false;
             for (int a = 0; a < NSLIP; ++a) dg[a] -= x[a];
         } else {
             double J[NSLIP * NSLIP];
@@ -607,8 +613,8 @@ __device__ bool cp_tangent_at(const double* F, const double* A, const double* ch
                               const CPParamsDev& pr, T* K) {
     const double coef = dt * pr.gdot0;
     ElState st;
-    double chi[NSLIP], dh[NSLIP], r[NSLIP];
-    cp_residual(F, A, chin, dg, geo, pr, coef, (int)pr.p, st, chi, dh, r);
+    double chi[NSLIP], dh[NSLIP], r[NSLIP], iden[NSLIP];
+    cp_residual(F, A, chin, dg, geo, pr, coef, (int)pr.p, st, chi, dh, r, iden);
     return cp_tangent<T>(F, A, dg, S0t, Ct, pr, coef, st, chi, dh, K);
 }
 
