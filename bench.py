@@ -323,6 +323,7 @@ def _time_increments(g, torch, nsteps, precision, warm):
     return {"s_per_increment": dt / nsteps, "newton": [r.newton_iters for r in reps],
             "cp_local_iters_per_voxel": [round(r.cp_local_iters, 2) for r in reps],
             "cp_fallbacks": [r.cp_fallbacks for r in reps],
+            "s_each": [round(r.seconds, 4) for r in reps],
             "cg": [r.cg_iters for r in reps], "P11_MPa_last": Pm[-1][0] / 1e6,
             "s_constitutive": sum(r.t_constitutive for r in reps) / nsteps,
             "s_residual": sum(r.t_residual for r in reps) / nsteps,
