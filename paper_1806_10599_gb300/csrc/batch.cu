@@ -98,6 +98,12 @@ BatchLaunch make_launch(Batch& B, const std::vector<RveApply>& rv, RveApply* d_r
     bl.n = B.n;
     bl.rv = d_rv;
     bl.tn = tn;
+    // the batched passes run the one-block-per-strip z kernel (at most 256 threads)
+    // and the one-block-per-plane inverse (at most 512): the thread counts of the
+    // persistent variants (TMA z pass, streamed inverse) are mapped onto them.
+    // Every launch shape gives the same bits, so the results do not change.
+    bl.tn.t_z = std::min(bl.tn.t_z, 256);
+    bl.tn.t_inv = std::min(bl.tn.t_inv, 512);
     bl.withK = withK;
     bl.vin = bl.vout = true;
     start_pl.assign(B.n + 1, 0);

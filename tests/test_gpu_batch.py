@@ -54,6 +54,34 @@ def test_batch_equals_one_by_one_bitwise(precision):
             g.gff_destroy(h)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_accepts_persistent_launch_shapes(precision):
+    """The batched passes have no persistent variants: handles whose launch
+    shapes select the TMA z pass (512 threads) or the streamed inverse pass
+    (up to 1024 threads) still batch, with the bits of the one-by-one run."""
+    torch_cuda()
+    g = gff()
+    hist = cyclic_history(0.01, 1).head(2)
+    opts = dict(precision=precision, newton_tol=1e-9 if precision == 0 else 1e-7, cg_tol=1e-6)
+    rves = _rves()
+    singles, batch = [], []
+    try:
+        for ms, kinds in rves:
+            singles.append(g.create_rve(ms, gpu_materials(kinds), g.make_options(**opts)))
+            h = g.create_rve(ms, gpu_materials(kinds), g.make_options(**opts))
+            batch.append(h)
+            # (threads fwd, W, threads z, threads inv, inverse blocks, z blocks)
+            g.gff_set_tiles(h, (512, 8, 512, 512, 7, 3), (256, 16, 512, 1024, 5, 3))
+        ref = [g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start) for h in singles]
+        Pm, reps, stat = g.gff_batch_run(batch, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+        assert (stat == 0).all()
+        for r in range(len(rves)):
+            assert np.array_equal(Pm[r], ref[r][0]), r
+    finally:
+        for h in singles + batch:
+            g.gff_destroy(h)
+
+
 def test_batch_rejects_mismatched_options():
     torch_cuda()
     g = gff()
