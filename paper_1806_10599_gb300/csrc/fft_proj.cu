@@ -371,6 +371,16 @@ template <> struct V16<float> {
     }
 };
 
+// Split (pass 1) and merge (pass 3) of the packed rows: a warp takes SPLIT_ROWS
+// packed rows, each lane one row and the frequencies k = kg + SPLIT_G t.  The
+// positions of k after the x transform are digit-reversed (neighbouring k lie 8
+// or 16 values apart), so lanes spread over rows as well as over k keep the
+// shared-memory accesses at most 2-way conflicted in FP32.  FP64 keeps one row
+// per warp: several rows per warp would not fit its register budget.
+template <typename T> constexpr int SPLIT_ROWS = sizeof(T) == 4 ? 4 : 1;
+template <typename T> constexpr int SPLIT_G = 32 / SPLIT_ROWS<T>;
+template <typename T> constexpr int SPLIT_K = (MAXN / 2 + SPLIT_G<T>) / SPLIT_G<T>;  // covers k = 0 .. MAXN/2
+
 template <typename T, bool WITH_K, bool VEC>
 __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T* __restrict__ K,
                                                typename C2<T>::t* __restrict__ spec, const GridDev& g, const int c,
@@ -397,39 +407,57 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
 
     if (VEC) {
         // 16-byte loads of VW consecutive voxels of one row; K row c is read
-        // once, the 9 components of x are shared by the 9 CTAs of this plane
+        // once, the 9 components of x are shared by the 9 CTAs of this plane.
+        // Lanes 2i and 2i+1 take the same VW voxels of rows 2r and 2r+1 (the
+        // real and imaginary parts of packed row r) and swap halves, so that
+        // each writes VW/2 whole complex values -- one 16-byte shared-memory
+        // store, contiguous across the warp.
         using VT = typename V16<T>::t;
-        constexpr int VW = V16<T>::n;
-        const int nxv = nx / VW;
-        T* sf = reinterpret_cast<T*>(s);
-        for (int e = tid; e < ny * nxv; e += nthr) {
-            const int yy = e / nxv, xv = e - yy * nxv;
-            const long long v0 = pl + (long long)yy * nx + xv * VW;
+        constexpr int VW = V16<T>::n, HW = VW / 2;
+        const int nxv = nx / VW, total = ny * nxv;  // total is even
+        const int lane = tid & 31;
+        for (int e0 = tid - lane; e0 < total; e0 += nthr) {  // warp-uniform trip count
+            const int e = e0 + lane;
+            const bool act = e < total;  // the partner e ^ 1 is active too
+            const int p = e & 1, q = e >> 1;
+            const int r = q / nxv, xv = q - r * nxv;
+            const long long v0 = pl + (long long)(2 * r + p) * nx + xv * VW;
             T acc[VW];
-            if (WITH_K) {
-                const T* Kc = K + (long long)c * 9 * N;
-                VT kv[9], xq[9];
 #pragma unroll
-                for (int d = 0; d < 9; ++d) {
-                    kv[d] = __ldg(reinterpret_cast<const VT*>(Kc + d * N + v0));
-                    xq[d] = __ldg(reinterpret_cast<const VT*>(x + d * N + v0));
+            for (int j = 0; j < VW; ++j) acc[j] = (T)0;
+            if (act) {
+                if (WITH_K) {
+                    const T* Kc = K + (long long)c * 9 * N;
+                    VT kv[9], xq[9];
+#pragma unroll
+                    for (int d = 0; d < 9; ++d) {
+                        kv[d] = __ldg(reinterpret_cast<const VT*>(Kc + d * N + v0));
+                        xq[d] = __ldg(reinterpret_cast<const VT*>(x + d * N + v0));
+                    }
+#pragma unroll
+                    for (int j = 0; j < VW; ++j) {
+                        T t = (T)0;
+#pragma unroll
+                        for (int d = 0; d < 9; ++d) t = fma(V16<T>::get(kv[d], j), V16<T>::get(xq[d], j), t);
+                        acc[j] = t;
+                    }
+                } else {
+                    const VT xv4 = __ldg(reinterpret_cast<const VT*>(x + c * N + v0));
+#pragma unroll
+                    for (int j = 0; j < VW; ++j) acc[j] = V16<T>::get(xv4, j);
                 }
-#pragma unroll
-                for (int j = 0; j < VW; ++j) {
-                    T t = (T)0;
-#pragma unroll
-                    for (int d = 0; d < 9; ++d) t = fma(V16<T>::get(kv[d], j), V16<T>::get(xq[d], j), t);
-                    acc[j] = t;
-                }
-            } else {
-                const VT xv4 = __ldg(reinterpret_cast<const VT*>(x + c * N + v0));
-#pragma unroll
-                for (int j = 0; j < VW; ++j) acc[j] = V16<T>::get(xv4, j);
             }
-            // row yy is the real (even) or imaginary (odd) part of packed row yy/2
-            T* dst = sf + 2 * ((yy >> 1) * 2 * ls + xv * VW) + (yy & 1);
+            // lane p = 0 keeps voxels 0..HW-1 and receives their imaginary parts;
+            // lane p = 1 keeps voxels HW..VW-1 and receives their real parts
+            VT o;
+            T* op = reinterpret_cast<T*>(&o);
 #pragma unroll
-            for (int j = 0; j < VW; ++j) dst[2 * j] = acc[j];
+            for (int j = 0; j < HW; ++j) {
+                const T recv = __shfl_xor_sync(0xffffffffu, p ? acc[j] : acc[HW + j], 1);
+                op[2 * j] = p ? recv : acc[j];
+                op[2 * j + 1] = p ? acc[HW + j] : recv;
+            }
+            if (act) *reinterpret_cast<VT*>(s + r * 2 * ls + xv * VW + p * HW) = o;
         }
     } else {
         for (int e = tid; e < half * nx; e += nthr) {
@@ -453,37 +481,55 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
         }
     }
     __syncthreads();
-    // x transform of the ny/2 packed rows (row pair r at offset 2 r ls)
-    fft_lines<T, false>(s, twx, g.ax, 1, 0, half, 2 * ls, 1, tid, nthr);
-    // split each packed row into the half spectra of its two real rows
+    // x transform of the ny/2 packed rows (row pair r at offset 2 r ls); rows are the
+    // fast thread index, so that neighbouring lanes read neighbouring rows rather than
+    // butterflies 8 or 16 elements apart in one row (fewer shared-memory bank conflicts)
+    fft_lines<T, false>(s, twx, g.ax, half, 2 * ls, 1, 0, 1, tid, nthr);
+    // split each packed row into the half spectra of its two real rows.  Columns
+    // kx = 0 and nx/2 of a real row are real, so one complex y transform of
+    // Z = X_0 + i X_h carries both and nx/2 columns are transformed, not nx/2 + 1:
+    // column 0 receives X_h as its imaginary part here (column nx/2 is rebuilt
+    // after the y transform).
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5, kh = nx / 2;
-    for (int r = warp; r < half; r += nw) {
+    const int jr = lane % SPLIT_ROWS<T>, kg = lane / SPLIT_ROWS<T>;
+    for (int r0 = warp * SPLIT_ROWS<T>; r0 < half; r0 += nw * SPLIT_ROWS<T>) {  // warp-uniform
+        const int r = r0 + jr;
+        const bool rok = r < half;
         C* row = s + r * 2 * ls;
-        C A[3], B[3];
+        C A[SPLIT_K<T>], B[SPLIT_K<T>];
+        T ah = (T)0, bh = (T)0;
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int k = lane + 32 * t;
-            if (k <= kh) {
+        for (int t = 0; t < SPLIT_K<T>; ++t) {
+            const int k = kg + SPLIT_G<T> * t;
+            if (rok && k <= kh) {
                 const C zk = row[posx[k]];
                 const C zm = row[posx[k == 0 ? 0 : nx - k]];
                 A[t] = mk<C>((zk.x + zm.x) * (T)0.5, (zk.y - zm.y) * (T)0.5);
                 B[t] = mk<C>((zk.y + zm.y) * (T)0.5, (zm.x - zk.x) * (T)0.5);
+                if (k == kh) {
+                    ah = A[t].x;
+                    bh = B[t].x;
+                }
             }
         }
+        // X_h of both rows, from the lane holding k = nx/2 to the lane holding k = 0 (same row)
+        const int src = jr + SPLIT_ROWS<T> * (kh % SPLIT_G<T>);
+        ah = __shfl_sync(0xffffffffu, ah, src);
+        bh = __shfl_sync(0xffffffffu, bh, src);
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int k = lane + 32 * t;
-            if (k <= kh) {
+        for (int t = 0; t < SPLIT_K<T>; ++t) {
+            const int k = kg + SPLIT_G<T> * t;
+            if (!rok) continue;
+            if (k == 0) {
+                row[0] = mk<C>(A[t].x, ah);
+                row[ls] = mk<C>(B[t].x, bh);
+            } else if (k < kh) {
                 row[k] = A[t];
                 row[ls + k] = B[t];
             }
         }
     }
-    __syncthreads();
-    // y transform: columns kx = 0 and nx/2 of real rows are real, so one complex
-    // transform Z = X_0 + i X_h carries both and nx/2 columns are transformed, not nx/2 + 1
-    for (int yy = tid; yy < ny; yy += nthr) s[yy * ls].y = s[yy * ls + kh].x;
     __syncthreads();
     fft_lines<T, false>(s, twy, g.ay, kh, 1, 1, 0, ls, tid, nthr);
     {
@@ -747,28 +793,33 @@ __device__ __forceinline__ void plane_inv_compute(typename C2<T>::t* s, T* __res
     }
     __syncthreads();
     fft_lines<T, true>(s, twy, g.ay, kh0, 1, 1, 0, ls, tid, nthr);
-    for (int yy = tid; yy < ny; yy += nthr) s[yy * ls + kh0].x = s[yy * ls].y;
-    __syncthreads();
     // merge the half spectra of rows 2r, 2r+1 into one packed complex row
     // Z_k = A_k + i B_k over all k (Hermitian symmetry of real rows), in the
-    // digit-reversed order the inverse x pass expects
+    // digit-reversed order the inverse x pass expects; the real column nx/2
+    // is the imaginary part of column 0 after the y transform
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5, kh = nx / 2;
-    for (int r = warp; r < half; r += nw) {
+    const int jr = lane % SPLIT_ROWS<T>, kg = lane / SPLIT_ROWS<T>;
+    for (int r0 = warp * SPLIT_ROWS<T>; r0 < half; r0 += nw * SPLIT_ROWS<T>) {  // warp-uniform
+        const int r = r0 + jr;
+        const bool rok = r < half;
         C* row = s + r * 2 * ls;
-        C A[3], B[3];
+        C A[SPLIT_K<T>], B[SPLIT_K<T>];
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int k = lane + 32 * t;
-            if (k <= kh) {
+        for (int t = 0; t < SPLIT_K<T>; ++t) {
+            const int k = kg + SPLIT_G<T> * t;
+            if (rok && k < kh) {
                 A[t] = row[k];
                 B[t] = row[ls + k];
+            } else if (rok && k == kh) {
+                A[t] = mk<C>(row[0].y, (T)0);
+                B[t] = mk<C>(row[ls].y, (T)0);
             }
         }
         __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int k = lane + 32 * t;
-            if (k <= kh) {
+        for (int t = 0; t < SPLIT_K<T>; ++t) {
+            const int k = kg + SPLIT_G<T> * t;
+            if (rok && k <= kh) {
                 if (k == 0 || k == kh) {
                     row[posx[k]] = mk<C>(A[t].x, B[t].x);
                 } else {
@@ -779,21 +830,36 @@ __device__ __forceinline__ void plane_inv_compute(typename C2<T>::t* s, T* __res
         }
     }
     __syncthreads();
-    fft_lines<T, true>(s, twx, g.ax, 1, 0, half, 2 * ls, 1, tid, nthr);
+    fft_lines<T, true>(s, twx, g.ax, half, 2 * ls, 1, 0, 1, tid, nthr);  // rows fastest, as in pass 1
     const T sc = (T)oa.scale, ad = (T)oa.add[c];
     T* yc = y + c * N;
     if (VEC) {
+        // the mirror of the load in pass 1: lanes 2i, 2i+1 each read VW/2 whole
+        // complex values (16 bytes) of packed row r, swap halves, and write VW
+        // voxels of rows 2r (real parts) and 2r+1 (imaginary parts)
         using VT = typename V16<T>::t;
-        constexpr int VW = V16<T>::n;
-        const int nxv = nx / VW;
-        const T* sf = reinterpret_cast<const T*>(s);
-        for (int e = tid; e < ny * nxv; e += nthr) {
-            const int yy = e / nxv, xv = e - yy * nxv;
-            const T* src = sf + 2 * ((yy >> 1) * 2 * ls + xv * VW) + (yy & 1);
-            T o[VW];
+        constexpr int VW = V16<T>::n, HW = VW / 2;
+        const int nxv = nx / VW, total = ny * nxv;
+        const int lane = tid & 31;
+        for (int e0 = tid - lane; e0 < total; e0 += nthr) {
+            const int e = e0 + lane;
+            const bool act = e < total;
+            const int p = e & 1, q = e >> 1;
+            const int r = q / nxv, xv = q - r * nxv;
+            VT in;
+            T* ip = reinterpret_cast<T*>(&in);
 #pragma unroll
-            for (int j = 0; j < VW; ++j) o[j] = fma(sc, src[2 * j], ad);
-            *reinterpret_cast<VT*>(yc + pl + (long long)yy * nx + xv * VW) = *reinterpret_cast<const VT*>(o);
+            for (int j = 0; j < VW; ++j) ip[j] = (T)0;
+            if (act) in = *reinterpret_cast<const VT*>(s + r * 2 * ls + xv * VW + p * HW);
+            VT o;
+            T* op = reinterpret_cast<T*>(&o);
+#pragma unroll
+            for (int j = 0; j < HW; ++j) {
+                const T recv = __shfl_xor_sync(0xffffffffu, p ? ip[2 * j] : ip[2 * j + 1], 1);
+                op[j] = fma(sc, p ? recv : ip[2 * j], ad);
+                op[HW + j] = fma(sc, p ? ip[2 * j + 1] : recv, ad);
+            }
+            if (act) *reinterpret_cast<VT*>(yc + pl + (long long)(2 * r + p) * nx + xv * VW) = o;
         }
     } else {
         for (int e = tid; e < half * nx; e += nthr) {
@@ -839,12 +905,43 @@ __device__ __forceinline__ void plane_inv_body(const typename C2<T>::t* __restri
     plane_inv_compute<T, VEC>(s, y, g, oa, c, z, twx, twy, posx);
 }
 
+// One block per plane (c, z) = (blockIdx.x, blockIdx.y).  The half-spectrum
+// plane is one contiguous run: a single bulk asynchronous copy brings it into
+// shared memory while the threads load the tables.  The wait is bounded
+// (timeout -> *err = 1 when err is set, and the block leaves).
 template <typename T, bool VEC>
 __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __restrict__ spec, T* __restrict__ y,
-                                                   GridDev g, OutArgs oa, const int* __restrict__ skip) {
+                                                   GridDev g, OutArgs oa, const int* __restrict__ skip,
+                                                   int* __restrict__ err) {
+    using C = typename C2<T>::t;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    plane_inv_body<T, VEC>(spec, y, g, oa, blockIdx.x, blockIdx.y, sm_raw);
+    const int nx = g.nx, plane = g.ny * g.nxh;
+    C* s = reinterpret_cast<C*>(sm_raw);
+    C* twx = s + plane;
+    C* twy = twx + nx;
+    int* posx = reinterpret_cast<int*>(twy + g.ny);
+    // in the ny ints after posx that only the forward pass uses (plane_smem_bytes)
+    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(posx + nx) + 7) & ~uintptr_t(7));
+    const int c = blockIdx.x, z = blockIdx.y;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();  // the barrier is initialised before any thread waits on it
+    if (threadIdx.x == 0)  // plane * sizeof(C) is a multiple of 16 (ny even), the plane start too
+        bulk_load(s, spec + ((long long)c * g.nz + z) * plane, (uint32_t)(plane * sizeof(C)), bar);
+    plane_tables<T>(g, twx, twy, posx);
+    const bool ok = mbar_wait(bar, 0u, BULK_WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            if (err) atomicExch(err, 1);
+            mbar_wait(bar, 0u, BULK_WAIT_CYCLES);  // let the copy land (bounded) before leaving
+        }
+        __syncthreads();
+        return;
+    }
+    plane_inv_compute<T, VEC>(s, y, g, oa, c, z, twx, twy, posx);
 }
 
 // Persistent variant: each block walks the planes p = blockIdx.x + k gridDim.x
@@ -1130,10 +1227,10 @@ cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename
     const dim3 gridA(9, g.nz);
     if (vout) {
         allow_smem(k_plane_inv<T, true>, smA);
-        k_plane_inv<T, true><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip);
+        k_plane_inv<T, true><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip, err);
     } else {
         allow_smem(k_plane_inv<T, false>, smA);
-        k_plane_inv<T, false><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip);
+        k_plane_inv<T, false><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip, err);
     }
     return cudaGetLastError();
 }
@@ -1489,7 +1586,7 @@ cudaError_t noalloc_launch(const GridDev& g, const T* x, T* y, const ProjArgs& p
     allow_smem(k_zproj<T, W>, smB);
     k_zproj<T, W><<<zproj_blocks(g, W), 256, smB, st>>>(spec, g, pa, nullptr);
     allow_smem(k_plane_inv<T, false>, smA);
-    k_plane_inv<T, false><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr);
+    k_plane_inv<T, false><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr, nullptr);
     return cudaGetLastError();
 }
 
