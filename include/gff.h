@@ -185,8 +185,11 @@ gff_status gff_autotune(gff_handle* h, int* tiles_out);
  * blocks > 0, z columns 8/16 and z threads 256/512; inv threads 256/512, or
  * with inv persistent blocks > 0 up to 1024 (FP32) / 512 (FP64).  Every
  * shape performs the same operations in the same order, so results do not
- * depend on them.  Returns GFF_ERR_ARG, changing nothing, for a shape the
- * grid cannot use (shared memory, or no tensor-map support for TMA). */
+ * depend on them.  gff_batch_run uses the shapes of its largest RVE and runs
+ * one-block-per-strip / one-block-per-plane kernels: persistent shapes are
+ * mapped onto them (z threads at most 256, inv threads at most 512).  Returns
+ * GFF_ERR_ARG, changing nothing, for a shape the grid cannot use (shared
+ * memory, or no tensor-map support for TMA). */
 gff_status gff_set_tiles(gff_handle* h, const int* tiles);
 
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */
