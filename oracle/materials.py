@@ -17,7 +17,7 @@ without stating its equations; Eq. gamma_dot gives the flow rule):
   (Eq. gamma_dot with g_c + g_s = tau0 and exponent 1/m = p),
   P = Fe S Fp^-T.
 The local residual r_a = dg_a - dt gdot0 h((tau_a - chi_a)/g) is solved by a
-plain Newton iteration from dg = 0 and K = dP/dF follows by implicit
+plain Newton iteration from dg = 0, voxel by voxel, and K = dP/dF follows by implicit
 differentiation of r = 0.
 """
 
@@ -133,13 +133,29 @@ def _flow(x, p):
     return np.sign(x) * ax**p, p * ax ** (p - 1)
 
 
+def _T(A):
+    """Transpose of the last two axes (3x3 tensors of a batch)."""
+    return np.swapaxes(A, -1, -2)
+
+
+def _ddot_C(C, E):
+    """S_ij = C_ijkl E_kl for a batch of tensors E (..., 3, 3)."""
+    return (E.reshape(E.shape[:-2] + (9,)) @ C.reshape(9, 9).T).reshape(E.shape)
+
+
+def _resolve(M, S0):
+    """M : S0_a for a batch of tensors M (..., 3, 3) -> (..., 12)."""
+    return M.reshape(M.shape[:-2] + (9,)) @ S0.reshape(12, 9).T
+
+
 def _elastic_state(F, A, dg, S0, C):
-    """Fp^-1, Fe, Ce, S and resolved stresses for slip increments dg."""
-    Fpi = np.einsum("vik,vkj->vij", A, _I3 - np.einsum("va,aij->vij", dg, S0))
-    Fe = np.einsum("vik,vkj->vij", F, Fpi)
-    Ce = np.einsum("vki,vkj->vij", Fe, Fe)
-    S = np.einsum("ijkl,vkl->vij", C, 0.5 * (Ce - _I3))
-    tau = np.einsum("vik,vkj,aij->va", Ce, S, S0)
+    """Fp^-1, Fe, Ce, S and resolved stresses for slip increments dg.
+    (Batched 3x3 products are written with @; index form in the comments.)"""
+    Fpi = A @ (_I3 - (dg @ S0.reshape(12, 9)).reshape(-1, 3, 3))  # A_ik (delta_kj - dg_a S0_a,kj)
+    Fe = F @ Fpi
+    Ce = _T(Fe) @ Fe                                              # Fe_ki Fe_kj
+    S = _ddot_C(C, 0.5 * (Ce - _I3))
+    tau = _resolve(Ce @ S, S0)                                    # (Ce S)_ij S0_a,ij
     return Fpi, Fe, Ce, S, tau
 
 
@@ -154,62 +170,68 @@ def cp_return_map(F, Fpi_n, chi_n, dt, S0, C, prm, tol=1e-14, maxit=100):
     dg = np.zeros((V, 12))
     g = prm.tau0
     coef = dt * prm.gdot0
-    conv = np.zeros(V, dtype=bool)
 
-    def residual_and_jac(dg):
-        Fpi, Fe, Ce, S, tau = _elastic_state(F, A, dg, S0, C)
+    def residual_and_jac(dg, sel=slice(None)):
+        """Local residual r(dg) and Jacobian dr/ddg of the voxels `sel`."""
+        Fs, As, chis = F[sel], A[sel], chi_n[sel]
+        Fpi, Fe, Ce, S, tau = _elastic_state(Fs, As, dg, S0, C)
         den = 1.0 + prm.d_af * np.abs(dg)
-        chi = (chi_n + prm.c_af * dg) / den
+        chi = (chis + prm.c_af * dg) / den
         x = (tau - chi) / g
         h, dh = _flow(x, prm.p)
         r = dg - coef * h
-        # d tau_a / d dg_b
-        dFpi = -np.einsum("vik,bkj->vbij", A, S0)  # (V,12,3,3)
-        dFe = np.einsum("vik,vbkj->vbij", F, dFpi)
-        dCe = np.einsum("vbki,vkj->vbij", dFe, Fe) + np.einsum("vki,vbkj->vbij", Fe, dFe)
-        dS = np.einsum("ijkl,vbkl->vbij", C, 0.5 * dCe)
-        dM = np.einsum("vbik,vkj->vbij", dCe, S) + np.einsum("vik,vbkj->vbij", Ce, dS)
-        dtau = np.einsum("vbij,aij->vab", dM, S0)
+        # d tau_a / d dg_b (derivatives along axis b = 1 of the (V,12,3,3) arrays)
+        dFpi = -(As[:, None] @ S0)                                 # -A_ik S0_b,kj
+        dFe = Fs[:, None] @ dFpi
+        dCe = _T(dFe) @ Fe[:, None] + _T(Fe)[:, None] @ dFe
+        dS = _ddot_C(C, 0.5 * dCe)
+        dM = dCe @ S[:, None] + Ce[:, None] @ dS
+        dtau = _T(_resolve(dM, S0))                                # [v, a, b] = dM_b : S0_a
         dchi = (prm.c_af - prm.d_af * np.sign(dg) * chi) / den
         J = np.eye(12)[None] - (coef / g) * dh[:, :, None] * (dtau - dchi[:, :, None] * np.eye(12)[None])
         return r, J, (Fpi, Fe, Ce, S, tau, chi, dh)
 
+    # Each voxel's Newton iteration is independent: a voxel stops at its first
+    # iterate with max|r| <= tol, the others go on (up to maxit iterations).
+    active = np.arange(V)
     for _ in range(maxit):
-        r, J, st = residual_and_jac(dg)
-        conv = np.max(np.abs(r), axis=1) <= tol
-        if conv.all():
+        r, J, _st = residual_and_jac(dg[active], active)
+        todo = np.max(np.abs(r), axis=1) > tol
+        if not todo.any():
             break
-        dg = dg - np.linalg.solve(J, r[..., None])[..., 0]
-    else:
-        r, J, st = residual_and_jac(dg)
-        conv = np.max(np.abs(r), axis=1) <= tol
+        active = active[todo]
+        dg[active] = dg[active] - np.linalg.solve(J[todo], r[todo][..., None])[..., 0]
+    r, J, st = residual_and_jac(dg)
+    conv = np.max(np.abs(r), axis=1) <= tol
 
     Fpi, Fe, Ce, S, tau, chi, dh = st
-    P = np.einsum("vik,vkl,vjl->vij", Fe, S, Fpi)
+    P = Fe @ S @ _T(Fpi)                                           # Fe_ik S_kl Fpi_jl
 
     # ---- consistent tangent by implicit differentiation
     K = np.empty((V, 3, 3, 3, 3))
     Jinv = np.linalg.inv(J)
-    dFpi_b = -np.einsum("vik,bkj->vbij", A, S0)
-    dFe_b = np.einsum("vik,vbkj->vbij", F, dFpi_b)
-    dCe_b = np.einsum("vbki,vkj->vbij", dFe_b, Fe) + np.einsum("vki,vbkj->vbij", Fe, dFe_b)
-    dS_b = np.einsum("ijkl,vbkl->vbij", C, 0.5 * dCe_b)
+    # dP / d dg_b at fixed F, (V,12,3,3)
+    dFpi_b = -(A[:, None] @ S0)
+    dFe_b = F[:, None] @ dFpi_b
+    dCe_b = _T(dFe_b) @ Fe[:, None] + _T(Fe)[:, None] @ dFe_b
+    dS_b = _ddot_C(C, 0.5 * dCe_b)
     dP_b = (
-        np.einsum("vbik,vkl,vjl->vbij", dFe_b, S, Fpi)
-        + np.einsum("vik,vbkl,vjl->vbij", Fe, dS_b, Fpi)
-        + np.einsum("vik,vkl,vbjl->vbij", Fe, S, dFpi_b)
+        dFe_b @ (S @ _T(Fpi))[:, None]
+        + Fe[:, None] @ dS_b @ _T(Fpi)[:, None]
+        + (Fe @ S)[:, None] @ _T(dFpi_b)
     )
     for k in range(3):
         for l in range(3):
             E = np.zeros((3, 3))
             E[k, l] = 1.0
-            dFe = np.einsum("ik,vkj->vij", E, Fpi)
-            dCe = np.einsum("vki,vkj->vij", dFe, Fe) + np.einsum("vki,vkj->vij", Fe, dFe)
-            dS = np.einsum("ijkl,vkl->vij", C, 0.5 * dCe)
-            dP = np.einsum("vik,vkl,vjl->vij", dFe, S, Fpi) + np.einsum("vik,vkl,vjl->vij", Fe, dS, Fpi)
-            dM = np.einsum("vik,vkj->vij", dCe, S) + np.einsum("vik,vkj->vij", Ce, dS)
-            dtau = np.einsum("vij,aij->va", dM, S0)
+            # dP / dF_kl at fixed dg, and d dg / dF_kl from J d dg = -dr
+            dFe = E @ Fpi
+            dCe = _T(dFe) @ Fe + _T(Fe) @ dFe
+            dS = _ddot_C(C, 0.5 * dCe)
+            dP = dFe @ S @ _T(Fpi) + Fe @ dS @ _T(Fpi)
+            dM = dCe @ S + Ce @ dS
+            dtau = _resolve(dM, S0)
             dr = -(coef / g) * dh * dtau
-            ddg = -np.einsum("vab,vb->va", Jinv, dr)
-            K[:, :, :, k, l] = dP + np.einsum("vbij,vb->vij", dP_b, ddg)
+            ddg = -(Jinv @ dr[..., None])[..., 0]
+            K[:, :, :, k, l] = dP + (ddg[:, None] @ dP_b.reshape(V, 12, 9)).reshape(V, 3, 3)
     return {"P": P, "K": K, "Fpi": Fpi, "chi": chi, "dg": dg, "tau": tau, "conv": conv}
