@@ -4,12 +4,22 @@
 Step = one Galerkin-operator apply y = G(K : x) (Eq. newlinop) at 128^3 voxels
 in FP64 with the continuous projection, K = the rotated cubic stiffness of a
 500-grain periodic Voronoi polycrystal (the tangent at F = I), x ~ N(0, 1).
-value = applies/s over all ranks.  The JSON line also carries the FP32 and
-discrete-projection variants, the per-kernel roofline of the dominant kernel,
-the end-to-end rate with host buffers, the CPU-oracle baseline, SM clocks
-sampled during the timed region, and the seconds per crystal-plasticity load
-increment (64^3, 200 grains, +-1 % strain cycles) in FP64, in mixed precision,
-and in mixed precision started from the extrapolated last increment.
+value = applies/s over all ranks.  The JSON line also carries:
+  * the FP32 and discrete-projection variants and the per-kernel roofline of
+    the dominant kernel, against the measured HBM copy bandwidth or the FP64
+    FMA throughput measured here (gff_measure_fp64_peak);
+  * the CG vector kernels' bandwidth at 128^3 (FP64 and FP32);
+  * the end-to-end rate through gff_apply_operator_host (pinned host x in,
+    host y out, copies inside the call);
+  * seconds per cyclic load increment over one full +-1 % strain cycle
+    (80 increments, Newton tolerance 1e-6) for the 64^3 / 200-grain RVE
+    (FP64, mixed, mixed + extrapolated start; continuous and discrete
+    projection) and the 128^3 / 500-grain RVE (FP64 zero start, mixed zero
+    start, mixed + extrapolated start, mixed + learned U-Net start trained
+    inside the run), each with its macroscopic-P error against the FP64 arm
+    and the SM clocks sampled over the arm;
+  * the 32-RVE batch; the CPU oracle (one thread, all host cores, and per
+    load increment).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gff|reference]
 """
@@ -44,9 +54,13 @@ def parse():
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gff", "reference"], default="gff")
-    p.add_argument("--increments", type=int, default=12,
-                   help="CP increments timed per variant: FP64, mixed, mixed + extrapolated start (0: skip)")
+    p.add_argument("--increments", type=int, default=80,
+                   help="load increments per arm of the cyclic-increment measurements (80 = one cycle; 0: skip)")
+    p.add_argument("--config5", type=int, default=1, help="1: also the 128^3 / 500-grain arms")
+    p.add_argument("--unet-train-steps", type=int, default=400, help="Adam steps of the in-run U-Net training")
+    p.add_argument("--unet-train-rves", type=int, default=2, help="64^3 RVEs whose increments train the U-Net")
     p.add_argument("--cpu-applies", type=int, default=3, help="oracle applies in the CPU baseline sample")
+    p.add_argument("--cpu-increments", type=int, default=1, help="1: time the oracle per load increment too")
     p.add_argument("--batch-increments", type=int, default=2,
                    help="increments of the 32-RVE batch, batched and one by one (0: skip)")
     p.add_argument("--grid", type=int, default=N_GRID, help="grid size (smaller grids only for profiling runs)")
@@ -215,6 +229,77 @@ def oracle_apply_rate(napplies, n=N_GRID):
     return napplies / dt, dt
 
 
+def _oracle_apply_worker(napplies, n):
+    return oracle_apply_rate(napplies, n)
+
+
+def host_info():
+    """Host core count and CPU model (for the CPU-baseline record)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    mem = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable"):
+                mem = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model, "mem_available_bytes": mem}
+
+
+def oracle_apply_rate_all_cores(napplies, n, info):
+    """Independent oracle applies in a spawn process pool, one per core (one
+    BLAS/FFT thread each), as many processes as the host memory allows
+    (about 3 GB each at 128^3).  Aggregate applies/s and processes used."""
+    import concurrent.futures
+    import multiprocessing
+
+    procs = info["nproc"] or 1
+    if info["mem_available_bytes"]:
+        procs = max(1, min(procs, int(0.5 * info["mem_available_bytes"] / (3.0 * (n / 128.0) ** 3 * 1e9))))
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(var, "1")
+    ctx = multiprocessing.get_context("spawn")
+    t0 = time.perf_counter()
+    with concurrent.futures.ProcessPoolExecutor(max_workers=procs, mp_context=ctx) as ex:
+        res = list(ex.map(_oracle_apply_worker, [napplies] * procs, [n] * procs))
+    wall = time.perf_counter() - t0
+    # each worker's timed loop excludes its start-up and input generation; the rate is the sum of theirs
+    return sum(r for r, _ in res), procs, wall
+
+
+def oracle_increment_seconds():
+    """Oracle seconds per load increment on one host thread: config 1 (16^3,
+    cubic SVK, mixed control, all 5 steps) and the first 20 increments of the
+    config-2 loading on a 16^3 / 8-grain crystal-plasticity RVE (the 64^3 /
+    200-grain RVE's grain density), extrapolated to 64^3 by the voxel count."""
+    from oracle.solver import CP_FCC, SVK_CUBIC, Material, OracleRVE, Options
+    from rve_inputs import cyclic_history, polycrystal, ramp_history
+
+    out = {}
+    o = OracleRVE(polycrystal(16, 8, 1), {0: Material(SVK_CUBIC)}, Options(newton_tol=1e-8, cg_tol=1e-8))
+    h1 = ramp_history()
+    t0 = time.perf_counter()
+    o.run(h1)
+    out["config1_16cube_s_per_increment"] = (time.perf_counter() - t0) / h1.nsteps
+    o = OracleRVE(polycrystal(16, 8, 2), {0: Material(CP_FCC)}, Options(newton_tol=1e-6, cg_tol=1e-3))
+    h2 = cyclic_history(0.01, 1).head(20)
+    t0 = time.perf_counter()
+    o.run(h2)
+    s16 = (time.perf_counter() - t0) / h2.nsteps
+    out["config2_loading_16cube_s_per_increment"] = s16
+    out["config2_64cube_s_per_increment_extrapolated"] = s16 * 64
+    out["note"] = "64^3 figure extrapolated from the 16^3 sample by the voxel count (64x); one thread"
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -295,39 +380,132 @@ def per_kernel_ms(g, h, prec, X, Y, reps):
     return [a / reps for a in acc]
 
 
-def time_increments(g, torch, nsteps, precision, warm=0):
+def time_arm(g, torch, ms, hist, precision, projection=0, warm=0, unet=None, clock_index=None):
+    """One arm of the cyclic-increment measurement: the whole history through
+    gff_run_history on a fresh handle, timed on the host around the call (the
+    launch shapes are tuned before).  Returns seconds per increment, the
+    macroscopic P of every increment and per-increment diagnostics."""
     try:
-        return _time_increments(g, torch, nsteps, precision, warm)
-    except Exception as e:  # report, do not lose the apply measurement
+        opts = g.make_options(precision=precision, projection=projection, newton_tol=1e-6, cg_tol=1e-3)
+        h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts)
+        try:
+            if warm:
+                g.gff_set_warm_start(h, unet, warm)
+            g.gff_autotune(h)  # outside the timed region
+            torch.cuda.synchronize()
+            clk = ClockSampler(clock_index) if clock_index is not None else None
+            if clk:
+                clk.start()
+            t0 = time.perf_counter()
+            Pm, reps = g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            clocks = clk.stop() if clk else None
+        finally:
+            g.gff_destroy(h)
+    except Exception as e:  # report, do not lose the other measurements
         return {"error": str(e)}
+    n = len(reps)
+    return {"s_per_cyclic_increment": dt / n, "increments": n, "seconds": dt,
+            "newton_mean": sum(r.newton_iters for r in reps) / n, "cg_mean": sum(r.cg_iters for r in reps) / n,
+            "cuts": sum(r.cuts for r in reps), "residual_max": max(r.residual for r in reps),
+            "residual_first_mean": sum(r.residual_first for r in reps) / n,
+            "cp_local_iters_per_voxel_mean": sum(r.cp_local_iters for r in reps) / n,
+            "cp_fallbacks": sum(r.cp_fallbacks for r in reps),
+            "s_constitutive": sum(r.t_constitutive for r in reps) / n,
+            "s_residual": sum(r.t_residual for r in reps) / n, "s_linear": sum(r.t_linear for r in reps) / n,
+            "P11_MPa_peak": max(p[0] for p in Pm) / 1e6, "P11_MPa_min": min(p[0] for p in Pm) / 1e6,
+            "clocks": clocks, "_Pm": Pm.tolist()}
 
 
-def _time_increments(g, torch, nsteps, precision, warm):
+def macro_errors(arms, ref_key):
+    """Each arm's largest relative macroscopic-P deviation from the reference arm over the history."""
+    import numpy as np
+
+    ref = arms.get(ref_key, {}).get("_Pm")
+    for k, a in arms.items():
+        if "_Pm" not in a:
+            continue
+        if ref is not None and len(a["_Pm"]) == len(ref):
+            P, R = np.array(a["_Pm"]), np.array(ref)
+            a["macroP_rel_err_vs_" + ref_key] = float(max(np.linalg.norm(P[i] - R[i]) / np.linalg.norm(R[i])
+                                                          for i in range(len(R))))
+    for a in arms.values():
+        a.pop("_Pm", None)
+    return arms
+
+
+def train_unet(g, torch, rves, steps, increments):
+    """The learned warm start, trained inside the run on the solver's own load
+    increments of `rves` 64^3 / 200-grain RVEs (seeds 5000+i, one +-1 % cycle,
+    mixed precision): a bounded data collection plus `steps` Adam steps."""
+    from paper_1806_10599_gb300 import warmstart
+
+    u = g.gff_unet_create(1)
+    t0 = time.perf_counter()
+    warmstart.collect(u, [5000 + i for i in range(rves)], increments=increments)
+    t1 = time.perf_counter()
+    g.gff_unet_set_sampling(u, 1)
+    losses = g.gff_unet_train(u, steps, 1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    k = max(1, min(50, steps // 4))
+    info = {"rves": rves, "increments_per_rve": increments, "samples": g.gff_unet_num_samples(u), "steps": steps,
+            "data_s": t1 - t0, "train_s": t2 - t1, "loss_first": float(sum(losses[:k]) / k),
+            "loss_last": float(sum(losses[-k:]) / k)}
+    return u, info
+
+
+def cyclic_increments(g, torch, args, clock_index):
+    """Seconds per cyclic increment, mixed vs FP64 (the metric's second half)."""
     from rve_inputs import cyclic_history, polycrystal
 
-    ms = polycrystal(64, 200, 2)
-    hist = cyclic_history(0.01, 1).head(nsteps)
-    opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3 if precision == 0 else 1e-3)
-    h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts)
-    try:
-        if warm:
-            g.gff_set_warm_start(h, None, warm)
-        g.gff_autotune(h)  # outside the timed region
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Pm, reps = g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-    finally:
-        g.gff_destroy(h)
-    return {"s_per_increment": dt / nsteps, "newton": [r.newton_iters for r in reps],
-            "cp_local_iters_per_voxel": [round(r.cp_local_iters, 2) for r in reps],
-            "cp_fallbacks": [r.cp_fallbacks for r in reps],
-            "s_each": [round(r.seconds, 4) for r in reps],
-            "cg": [r.cg_iters for r in reps], "P11_MPa_last": Pm[-1][0] / 1e6,
-            "s_constitutive": sum(r.t_constitutive for r in reps) / nsteps,
-            "s_residual": sum(r.t_residual for r in reps) / nsteps,
-            "s_linear": sum(r.t_linear for r in reps) / nsteps}
+    hist = cyclic_history(0.01, 1).head(args.increments)
+    out = {}
+    ms2 = polycrystal(64, 200, 2)
+    arms = {}
+    for proj, pname in ((0, "continuous"), (1, "discrete")):
+        arms["fp64_" + pname] = time_arm(g, torch, ms2, hist, 0, proj, clock_index=clock_index)
+        arms["mixed_" + pname] = time_arm(g, torch, ms2, hist, 1, proj, clock_index=clock_index)
+        arms["mixed_extrapolated_" + pname] = time_arm(g, torch, ms2, hist, 1, proj, g.GFF_WARM_EXTRAPOLATE,
+                                                       clock_index=clock_index)
+    macro_errors({k: v for k, v in arms.items() if k.endswith("continuous")}, "fp64_continuous")
+    macro_errors({k: v for k, v in arms.items() if k.endswith("discrete")}, "fp64_discrete")
+    out["config2"] = {"workload": "64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1 pct "
+                                  "strain cycle, %d increments (dt 0.05 s), Newton tol 1e-6, CG tol 1e-3"
+                                  % hist.nsteps, "arms": arms}
+    if args.config5:
+        ms5 = polycrystal(128, 500, 5)
+        arms5 = {"fp64_zero": time_arm(g, torch, ms5, hist, 0, clock_index=clock_index),
+                 "mixed_zero": time_arm(g, torch, ms5, hist, 1, clock_index=clock_index),
+                 "mixed_extrapolated": time_arm(g, torch, ms5, hist, 1, 0, g.GFF_WARM_EXTRAPOLATE,
+                                                clock_index=clock_index)}
+        unet_info = None
+        if args.unet_train_steps > 0:
+            try:
+                u, unet_info = train_unet(g, torch, args.unet_train_rves, args.unet_train_steps, 80)
+                try:
+                    arms5["mixed_unet"] = time_arm(g, torch, ms5, hist, 1, 0, g.GFF_WARM_NET, unet=u,
+                                                   clock_index=clock_index)
+                finally:
+                    g.gff_unet_destroy(u)
+            except Exception as e:
+                unet_info = {"error": str(e)}
+        macro_errors(arms5, "fp64_zero")
+        f64 = arms5["fp64_zero"].get("s_per_cyclic_increment")
+        target = {}
+        for k in ("mixed_unet", "mixed_extrapolated"):
+            v = arms5.get(k, {}).get("s_per_cyclic_increment")
+            if f64 and v:
+                target[k + "_speedup_vs_fp64_zero"] = f64 / v
+        if "mixed_unet_speedup_vs_fp64_zero" in target:
+            target["north_star_met"] = (target["mixed_unet_speedup_vs_fp64_zero"] > 1.0
+                                        and arms5["mixed_unet"].get("residual_max", 1.0) <= 1e-6)
+        out["config5"] = {"workload": "128^3, 500-grain periodic Voronoi (seed 5), FCC crystal plasticity, R=-1 "
+                                      "+-1 pct strain cycle, %d increments, Newton tol 1e-6, CG tol 1e-3; U-Net "
+                                      "trained in this run" % hist.nsteps,
+                          "arms": arms5, "unet_training": unet_info, "target": target}
+    return out
 
 
 def time_batch(g, torch, nsteps, precision):
@@ -396,7 +574,8 @@ def run_gpu(args, world, rank, local):
     Y32 = torch.empty_like(X32)
 
     vis = [d for d in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if d.strip()]
-    clocks = ClockSampler(vis[local].strip() if local < len(vis) else str(local))
+    clock_index = vis[local].strip() if local < len(vis) else str(local)
+    clocks = ClockSampler(clock_index)
     if rank == 0:
         clocks.start()
     ms64 = time_applies(torch, g, h, g.GFF_PREC_FP64, X, Y, args.steps, args.warmup, world)
@@ -405,34 +584,30 @@ def run_gpu(args, world, rank, local):
     msd = time_applies(torch, g, hd, g.GFF_PREC_FP64, X, Y, args.steps, args.warmup, world)
     k64 = per_kernel_ms(g, h, g.GFF_PREC_FP64, X, Y, max(5, args.steps // 2))
     k32 = per_kernel_ms(g, h, g.GFF_PREC_MIXED, X32, Y32, max(5, args.steps // 2))
+    fp64_peak = g.gff_measure_fp64_peak()
+    g.gff_destroy(hd)
 
-    # end to end: pinned host x -> device, apply, device -> pinned host y, every step
+    # end to end through the C ABI with host buffers: pinned x in, y out, copies inside the call
     xh = torch.from_numpy(x).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     for _ in range(args.warmup):
-        X.copy_(xh, non_blocking=True)
-        g.gff_apply_operator(h, g.GFF_PREC_FP64, None, X, Y)
-        yh.copy_(Y, non_blocking=True)
-    torch.cuda.synchronize()
+        g.gff_apply_operator_host(h, g.GFF_PREC_FP64, None, xh, yh)
     barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        X.copy_(xh, non_blocking=True)
-        g.gff_apply_operator(h, g.GFF_PREC_FP64, None, X, Y)
-        yh.copy_(Y, non_blocking=True)
-    torch.cuda.synchronize()
+        g.gff_apply_operator_host(h, g.GFF_PREC_FP64, None, xh, yh)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     barrier(world)
+    # the CG vector kernels on the same grid (the handle's work vectors)
+    cg64 = g.gff_cg_kernels_timed(h, g.GFF_PREC_FP64, 20)
+    cg32 = g.gff_cg_kernels_timed(h, g.GFF_PREC_MIXED, 20)
+    g.gff_destroy(h)
+    del X, Y, X32, Y32
+    torch.cuda.empty_cache()
 
     inc = None
     if args.increments > 0 and rank == 0:
-        inc = {"workload": ("64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1 pct "
-                            "strain cycles, first %d increments (dt 0.05 s), Newton tol 1e-6") % args.increments,
-               "fp64": time_increments(g, torch, args.increments, 0),
-               "mixed": time_increments(g, torch, args.increments, 1),
-               "mixed_extrapolated": time_increments(g, torch, args.increments, 1, g.GFF_WARM_EXTRAPOLATE)}
-    g.gff_destroy(h)
-    g.gff_destroy(hd)
+        inc = cyclic_increments(g, torch, args, clock_index)
     batch = None
     if args.batch_increments > 0 and rank == 0:
         batch = {"workload": "32 RVEs (7x32^3, 7x48^3, 6x64^3, 6x80^3, 6x96^3; 50-300 grains, seeds 4000+i), FCC "
@@ -443,14 +618,41 @@ def run_gpu(args, world, rank, local):
         return
     cpu = None
     if world == 1 and args.cpu_applies > 0:
+        info = host_info()
         rate, secs = oracle_apply_rate(args.cpu_applies, args.grid)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d oracle applies at %d^3 (numpy FP64, one thread), %.1f s"
-                         % (args.cpu_applies, args.grid, secs)}
+                         % (args.cpu_applies, args.grid, secs), "host": info}
+        try:
+            rall, procs, wall = oracle_apply_rate_all_cores(args.cpu_applies, args.grid, info)
+            cpu["all_cores"] = {"value": rall, "unit": UNIT, "cores": procs,
+                                "sample": "%d independent oracle processes x %d applies at %d^3, %.1f s wall"
+                                          % (procs, args.cpu_applies, args.grid, wall)}
+        except Exception as e:
+            cpu["all_cores"] = {"error": str(e)}
+        if args.cpu_increments:
+            try:
+                cpu["increments"] = oracle_increment_seconds()
+            except Exception as e:
+                cpu["increments"] = {"error": str(e)}
     raw = {"ms64": ms64, "ms32": ms32, "msd": msd, "k64": k64, "k32": k32, "e2e_s": e2e_s,
            "xbytes": int(x.nbytes), "clocks": clk, "increment": inc, "cpu": cpu, "tiles": tiles,
-           "batch": batch}
+           "batch": batch, "fp64_peak_gflops": fp64_peak[0], "cg64": cg64, "cg32": cg32}
     print(json.dumps(build_line(args, world, raw, *measured_peaks())), flush=True)
+
+
+def cg_kernel_roofline(ms3, n_elems, elem, peak):
+    """GB/s and HBM fraction of the CG vector kernels: p.Ap reads 2 vectors;
+    the update reads x, p, r, Ap and writes x, r; p = r + beta p reads 2 and
+    writes 1 (each vector n_elems values of elem bytes)."""
+    accesses = [2, 6, 3]
+    names = ["dot p.Ap (k_dot_partial_skip + k_final_alpha)", "x, r update + r.r (k_cg_update_dev + k_final_beta)",
+             "p = r + beta p (k_xpby_dev)"]
+    out = {}
+    for nm, a, ms in zip(names, accesses, ms3):
+        gbs = a * n_elems * elem / (ms * 1e-3) / 1e9 if ms > 0 else None
+        out[nm] = {"ms": ms, "bytes": a * n_elems * elem, "gbs": gbs, "frac": gbs / peak if gbs else None}
+    return out
 
 
 def build_line(args, world, raw, peaks, src):
@@ -461,16 +663,19 @@ def build_line(args, world, raw, peaks, src):
     b64 = kernel_bytes_per_voxel(args.grid, 8)
     b32 = kernel_bytes_per_voxel(args.grid, 4)
     fl = kernel_flops_per_voxel(args.grid)
+    fp64_peak = raw.get("fp64_peak_gflops")
+    fp64_src = "measured here (FP64 FMA chains, gff_measure_fp64_peak)" if fp64_peak else "nominal GB300 FP64 rate"
+    fp64_peak = fp64_peak or FP64_PEAK_NOMINAL_GFLOPS
     names = ["k_plane_fwd (K:x + forward x/y transforms)", "k_zproj (z transforms + projection)",
              "k_plane_inv (inverse y/x transforms)"]
     dom = max(range(3), key=lambda i: k64[i])
     gbs = [b64[i] * nvox / (k64[i] * 1e-3) / 1e9 for i in range(3)]
     gfl = [fl[i] * nvox / (k64[i] * 1e-3) / 1e9 for i in range(3)]
     hbm_frac = gbs[dom] / peak
-    alu_frac = gfl[dom] / FP64_PEAK_NOMINAL_GFLOPS
+    alu_frac = gfl[dom] / fp64_peak
     if alu_frac > hbm_frac:
-        roof = {"bound": "alu", "kernel": names[dom], "achieved": gfl[dom], "peak": FP64_PEAK_NOMINAL_GFLOPS,
-                "unit": "GFLOP/s", "frac": alu_frac, "peak_source": "nominal GB300 FP64 rate",
+        roof = {"bound": "alu", "kernel": names[dom], "achieved": gfl[dom], "peak": fp64_peak,
+                "unit": "GFLOP/s", "frac": alu_frac, "peak_source": fp64_src,
                 "hbm_achieved_gbs": gbs[dom], "hbm_frac": hbm_frac, "hbm_peak_source": src}
     else:
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": gbs[dom], "peak": peak, "unit": "GB/s",
@@ -478,27 +683,37 @@ def build_line(args, world, raw, peaks, src):
     roof["traffic"] = measured_traffic(args.grid) if dom == 0 else None
     roof["algorithmic_bytes_per_launch"] = b64[dom] * nvox
     roof["kernel_ms"] = k64
+    roof["all_kernels_gflops"] = gfl
+    roof["all_kernels_gbs"] = gbs
     dom32 = max(range(3), key=lambda i: k32[i])
     gbs32 = [b32[i] * nvox / (k32[i] * 1e-3) / 1e9 for i in range(3)]
     roof32 = {"bound": "hbm", "kernel": names[dom32], "achieved": gbs32[dom32], "peak": peak, "unit": "GB/s",
               "frac": gbs32[dom32] / peak, "peak_source": src, "kernel_ms": k32, "all_kernels_gbs": gbs32,
+              "all_kernels_frac": [v / peak for v in gbs32],
               "apply_gbs": sum(b32) * nvox / (sum(k32) * 1e-3) / 1e9, "traffic": None,
               "algorithmic_bytes_per_launch": b32[dom32] * nvox}
     steps = args.steps
+    cg = None
+    if raw.get("cg64") and raw.get("cg32"):
+        cg = {"grid": [args.grid] * 3, "fp64": cg_kernel_roofline(raw["cg64"], 9 * nvox, 8, peak),
+              "fp32": cg_kernel_roofline(raw["cg32"], 9 * nvox, 4, peak)}
     return {
         "metric": METRIC, "value": world * steps / (raw["ms64"] * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": steps, "warmup": args.warmup, "ms_per_step": raw["ms64"] / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.grid), "roofline": roof, "cpu_baseline": raw["cpu"],
         "e2e": {"value": world * steps / raw["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": raw["xbytes"],
-                "d2h_bytes_per_step": raw["xbytes"]},
+                "d2h_bytes_per_step": raw["xbytes"],
+                "how": "gff_apply_operator_host per step: pinned host x -> device, apply, device -> pinned host y"},
         "gpu_launches": 3 * steps, "clocks": raw["clocks"],
+        "fp64_tflops_measured": (raw.get("fp64_peak_gflops") or 0) / 1e3 or None,
         "variants": {
             "fp32_apply": {"value": world * steps / (raw["ms32"] * 1e-3), "unit": UNIT, "dtype": "f32",
                            "roofline": roof32},
             "discrete_projection_fp64": {"value": world * steps / (raw["msd"] * 1e-3), "unit": UNIT,
                                          "dtype": "f64"},
         },
+        "cg_kernels": cg,
         "increment": raw["increment"],
         "autotuned_tiles": raw.get("tiles"),
         "batch": raw.get("batch"),

@@ -53,7 +53,11 @@ typedef enum {
 enum { GFF_PROJ_CONTINUOUS = 0, GFF_PROJ_DISCRETE = 1 };
 enum { GFF_PREC_FP64 = 0, GFF_PREC_MIXED = 1 };
 enum { GFF_WARM_OFF = 0, GFF_WARM_NET_IF_BETTER = 1, GFF_WARM_NET = 2, GFF_WARM_EXTRAPOLATE = 3 };
-enum { GFF_MAT_SVK_CUBIC = 0, GFF_MAT_SVK_ISO = 1, GFF_MAT_CP_FCC = 2 };
+/* GFF_MAT_NEOHOOKE: compressible neo-Hookean solid (E, nu as Lame constants),
+ * evaluated the way an FE user material is: Cauchy stress and Jaumann-rate
+ * tangent per voxel, converted to P and dP/dF by the formulas of Appendix A
+ * (gff_umat_tangent). */
+enum { GFF_MAT_SVK_CUBIC = 0, GFF_MAT_SVK_ISO = 1, GFF_MAT_CP_FCC = 2, GFF_MAT_NEOHOOKE = 3 };
 enum {
     GFF_FIELD_F = 0,      /* deformation gradient, 9 per voxel          */
     GFF_FIELD_P = 1,      /* first Piola-Kirchhoff stress, 9 per voxel  */
@@ -168,6 +172,28 @@ gff_status gff_apply_operator(gff_handle* h, int precision, const uint8_t* mask9
 gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t* mask9,
                                     const void* x_dev, void* y_dev, float* ms_out);
 
+/* gff_apply_operator with HOST buffers, for callers without device memory of
+ * their own: x_host is copied into the handle's work vector, the operator
+ * applied, y copied back to y_host (double[9N] for GFF_PREC_FP64, float[9N]
+ * for GFF_PREC_MIXED; pinned host memory makes the copies asynchronous and
+ * fast).  Returns when y_host is written, with the status of gff_sync.  It
+ * uses the handle's CG work vectors as device buffers. */
+gff_status gff_apply_operator_host(gff_handle* h, int precision, const uint8_t* mask9, const void* x_host,
+                                   void* y_host);
+
+/* Measurement helpers (no counterpart in the paper).
+ * gff_cg_kernels_timed: durations in ms, averaged over `reps`, of the vector
+ * kernels of one conjugate-gradient iteration on this handle's work vectors
+ * (overwritten): ms_out[0] the dot product p.Ap with alpha, [1] x += alpha p,
+ * r -= alpha Ap with the new r.r and beta, [2] p = r + beta p.  Algorithmic
+ * traffic per element: 2, 6 and 3 vector accesses.
+ * gff_measure_fp64_peak: FP64 FMA throughput of the current GPU (independent
+ * FMA chains on every SM, best of 5 launches timed with CUDA events), in
+ * GFLOP/s (2 flops per FMA); ms_out (may be NULL) the launch's duration.
+ * Allocates and frees a 1.2 MB buffer. */
+gff_status gff_cg_kernels_timed(gff_handle* h, int precision, int reps, float* ms_out);
+gff_status gff_measure_fp64_peak(double* gflops_out, double* ms_out);
+
 /* Choose the launch shapes of the three apply kernels (threads of the plane
  * kernels, columns per block and threads of the z kernel) by timing every
  * candidate on this grid; results are bitwise the same for every choice.
@@ -192,6 +218,32 @@ gff_status gff_autotune(gff_handle* h, int* tiles_out);
  * memory, or no tensor-map support for TMA). */
 gff_status gff_set_tiles(gff_handle* h, const int* tiles);
 
+/* gff_apply_operator and gff_project return once their kernels are queued on
+ * the handle's stream.  gff_sync waits for the stream and reports what the
+ * device recorded meanwhile: GFF_ERR_TIMEOUT if a bounded wait of an FFT pass
+ * on an asynchronous (TMA) copy gave up since the last check -- the planes it
+ * left uncomputed are NaN in y -- and clears that record; else GFF_OK.
+ * gff_step checks the same record itself after every residual. */
+gff_status gff_sync(gff_handle* h);
+
+/* Budget, in SM clock cycles, of the first wait of each FFT pass on its
+ * asynchronous (TMA) copies; cycles < 0 restores the default (about two
+ * seconds).  A budget of 0 gives up at once: the pass records the timeout,
+ * lets its copies land (waiting at most the default budget) and skips its
+ * work, which exercises the error path of gff_sync without any fault.  For
+ * tests of that path; the default is the only sensible value otherwise. */
+gff_status gff_set_wait_limit(gff_handle* h, long long cycles);
+
+/* How the crystal-plasticity return maps are iterated (the paper leaves it
+ * open; the root of the backward-Euler residual of Eq. gamma_dot is the same):
+ * GFF_RETURN_MAP_DEFAULT: Newton steps with the small-elastic-strain Jacobian
+ *   from the previous iterate's slips, then, if that fails, exact Newton from
+ *   zero slip (the fallback, counted in gff_step_report.cp_fallbacks);
+ * GFF_RETURN_MAP_EXACT: exact Newton (12x12 LU with partial pivoting) from
+ *   zero slip only -- every return map counts as a fallback. */
+enum { GFF_RETURN_MAP_DEFAULT = 0, GFF_RETURN_MAP_EXACT = 1 };
+gff_status gff_set_return_map(gff_handle* h, int mode);
+
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */
 gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9,
                        const void* x_dev, void* y_dev);
@@ -209,11 +261,19 @@ gff_status gff_project(gff_handle* h, int precision, const uint8_t* mask9,
  * limited to nx*ny*nz <= 32768 voxels (axes as for gff_create), larger ones
  * return GFF_ERR_ARG.  The first call on a device looks up that array's
  * address (make this first call before any stream capture).  No cudaMalloc,
- * cudaFree or other allocating routine is called.  All calls share the one
- * array per device, so calls whose device work overlaps (different streams,
- * or host threads) race and corrupt each other's results; serialise them.
- * Returns GFF_ERR_ARG for bad arguments, GFF_ERR_CUDA on a CUDA error (no
- * handle, so no message). */
+ * cudaFree or other allocating routine is called, and no host memory is
+ * copied: the grid tables are written into the array by a kernel queued on
+ * `stream` ahead of the projection.  All calls share the one array per
+ * device and each call overwrites it, so calls whose device work overlaps
+ * (different streams, or host threads) race and corrupt each other's
+ * results; serialise them.
+ * The call returns once its kernels are queued, before they run, so it has
+ * no status word for device-side failures: if the bounded wait on a plane's
+ * asynchronous copy ever gives up (its limit is about two seconds, for a copy
+ * of microseconds), that plane of y is written as NaN.
+ * Returns GFF_ERR_ARG for bad arguments and GFF_ERR_CUDA on a CUDA error (no
+ * handle, so no message) -- also, without clearing it, when a CUDA error left
+ * by an earlier call is still pending on entry. */
 gff_status gff_project_noalloc(const gff_grid* grid, int projection, int precision,
                                const uint8_t* mask9, const void* x_dev, void* y_dev, void* stream);
 
@@ -318,6 +378,33 @@ gff_status gff_set_warm_start(gff_handle* h, gff_unet* u, int mode);
  * wcyc_g[ngrains*12], fs_g[ngrains] (Fatemi-Socie); any may be NULL. */
 gff_status gff_reset_fips(gff_handle* h);
 gff_status gff_get_fips(gff_handle* h, double* pcyc_g, double* wcyc_g, double* fs_g);
+
+/* Appendix A: what an Abaqus-style user material returns -- the Cauchy stress
+ * sigma and the tangent C^ab of the Jaumann rate of the Kirchhoff stress
+ * (Eq. ABAtang) -- converted into the first Piola-Kirchhoff stress
+ * P = J sigma F^-T (Eq. fPK) and the tangent K = dP/dF the FFT solver needs
+ * (the final expression of Appendix A), for n voxels on the device.
+ * Layouts: F_dev, sigma_dev, P_dev double[9][n]; Cab_dev, K_dev double[81][n]
+ * with index 9 (3i + j) + (3k + l) (C^ab with its minor symmetries).  The
+ * work is queued on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * no handle, no allocation.  GFF_ERR_ARG for n < 0 or null pointers,
+ * GFF_ERR_CUDA on a launch error. */
+gff_status gff_umat_tangent(long long n, const double* F_dev, const double* sigma_dev, const double* Cab_dev,
+                            double* P_dev, double* K_dev, void* stream);
+
+/* Band-averaged dissipated energy W_cyc^b (Eq. Wmax) of the current cycle's
+ * accumulators.  Each crystal-plastic grain is cut into bands of `width`
+ * (a length, units of gff_grid.L) parallel to each of its four {111} slip
+ * planes: a voxel's band for plane p is floor(s / width + 1/2), s = (x - x_ref).m_p,
+ * x - x_ref the minimum-image offset (per axis in [-n/2, n/2) voxels) of its
+ * centre from the grain's reference voxel (the grain's lowest voxel index),
+ * m_p the plane's unit normal in the sample frame.  W_cyc of the plane's three
+ * systems is averaged over every band; wb_g[ngrains] (may be NULL) receives
+ * each grain's largest band average (0 for other phases), wb_max (may be NULL)
+ * the largest over the RVE.  Allocates a temporary device buffer of about
+ * 16 ngrains (sqrt(Lx^2 + Ly^2 + Lz^2) / width + 4) doubles (GFF_ERR_ARG above
+ * 2 GB). */
+gff_status gff_get_band_fips(gff_handle* h, double width, double* wb_g, double* wb_max);
 
 /* Committed state to/from a raw little-endian file: header, increment
  * history (the last prescribed increments and normalised fluctuation

@@ -79,3 +79,62 @@ def grain_fips(acc, grain_id_flat, ngrains, cp_grain, fs_k=0.5, fs_sigma_y=153e6
         sn = acc["sn"][sel].mean(axis=0)
         fs[gi] = np.max(0.5 * dgam * (1.0 + fs_k * sn / fs_sigma_y))
     return pc, w, fs
+
+
+def band_coordinates(grain_id, L):
+    """Minimum-image voxel offsets of every voxel from its grain's reference
+    voxel (the grain's voxel with the lowest flat index), in voxel units per
+    axis (x, y, z), each in [-n/2, n/2), and the voxel spacings h (x, y, z).
+    grain_id (nz, ny, nx)."""
+    nz, ny, nx = grain_id.shape
+    g = grain_id.reshape(-1)
+    order = np.argsort(g, kind="stable")
+    first = np.full(int(g.max()) + 1, -1)
+    gs = g[order]
+    starts = np.r_[0, np.nonzero(np.diff(gs))[0] + 1]
+    first[gs[starts]] = order[starts]
+    ref = first[g]
+    iz, iy, ix = np.unravel_index(np.arange(g.size), (nz, ny, nx))
+    rz, ry, rx = np.unravel_index(ref, (nz, ny, nx))
+    d = []
+    for i, r, n in ((ix, rx, nx), (iy, ry, ny), (iz, rz, nz)):
+        di = np.mod(i - r, n)
+        d.append(np.where(di >= n / 2.0, di - n, di))
+    h = np.array([L[0] / nx, L[1] / ny, L[2] / nz])
+    return np.stack(d, axis=1).astype(np.float64), h
+
+
+def band_fips(w_acc, grain_id, plane_normals, cp_grain, L, width):
+    """Band-averaged dissipated energy W_cyc^b of Eq. Wmax per grain.
+
+    Bands of width `width` (a length) parallel to each of a grain's four
+    {111} slip planes cut the grain: the band index of a voxel for plane p is
+    floor(s / width + 1/2), s = (x - x_ref) . m_p (the reference voxel sits in
+    the middle of band 0), with x - x_ref the minimum-image
+    offset of the voxel centre from the grain's reference voxel and m_p the
+    sample-frame unit normal of the plane.  For each band, W_cyc^beta is
+    averaged over the band's voxels for the three systems beta on that plane
+    (systems 3p, 3p+1, 3p+2); the grain's value is the largest such average
+    over its bands, planes and systems (Eq. Wmax before the max over grains).
+
+    w_acc (V, 12) per-voxel W_cyc; grain_id (nz, ny, nx); plane_normals
+    (ngrains, 4, 3); cp_grain (ngrains,) bool.  Returns (ngrains,) with 0 for
+    grains that are not crystal-plastic or empty."""
+    ngrains = plane_normals.shape[0]
+    d, h = band_coordinates(grain_id, L)
+    off = d * h[None, :]
+    g = grain_id.reshape(-1)
+    out = np.zeros(ngrains)
+    for gi in range(ngrains):
+        sel = np.nonzero(g == gi)[0]
+        if not cp_grain[gi] or sel.size == 0:
+            continue
+        best = -np.inf
+        for p in range(4):
+            s = off[sel] @ plane_normals[gi, p]
+            band = np.floor(s / width + 0.5).astype(np.int64)
+            for j in np.unique(band):
+                in_band = sel[band == j]
+                best = max(best, w_acc[in_band][:, 3 * p:3 * p + 3].mean(axis=0).max())
+        out[gi] = best
+    return out

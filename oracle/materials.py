@@ -235,3 +235,49 @@ def cp_return_map(F, Fpi_n, chi_n, dt, S0, C, prm, tol=1e-14, maxit=100):
             ddg = -(Jinv @ dr[..., None])[..., 0]
             K[:, :, :, k, l] = dP + (ddg[:, None] @ dP_b.reshape(V, 12, 9)).reshape(V, 3, 3)
     return {"P": P, "K": K, "Fpi": Fpi, "chi": chi, "dg": dg, "tau": tau, "conv": conv}
+
+
+# --------------------------------------------------------------------------- Appendix A: umat-style tangents
+def umat_to_PK(F, sigma, Cab):
+    """First Piola-Kirchhoff stress and tangent K = dP/dF from what an Abaqus
+    umat returns (Appendix A): the Cauchy stress sigma and the tangent C^ab of
+    the Jaumann rate of the Kirchhoff stress (Eq. ABAtang), at the deformation
+    gradient F.  All arrays batched over voxels: F, sigma (V,3,3), Cab
+    (V,3,3,3,3) with minor symmetries.
+
+      P = J sigma F^-T                                            (Eq. fPK)
+      d tau_ip / d F_kl = J C_ipkm Fi_lm + 1/2 delta_ik Fi_lm tau_mp
+                          - 1/2 Fi_li tau_kp + 1/2 delta_pk Fi_lm tau_im
+                          - 1/2 Fi_lp tau_ik                      (Eq. tau_F_function_Cab)
+      K_ijkl = d tau_ip / d F_kl Fi_jp - tau_ip Fi_lp Fi_jk      (Eqs. indexx, derivativeinv)
+    with tau = J sigma and Fi = F^-1."""
+    J = np.linalg.det(F)
+    Fi = np.linalg.inv(F)
+    tau = J[:, None, None] * sigma
+    d = _I3
+    dtau = (
+        J[:, None, None, None, None] * np.einsum("vipkm,vlm->vipkl", Cab, Fi)
+        + 0.5 * np.einsum("ik,vlm,vmp->vipkl", d, Fi, tau)
+        - 0.5 * np.einsum("vli,vkp->vipkl", Fi, tau)
+        + 0.5 * np.einsum("pk,vlm,vim->vipkl", d, Fi, tau)
+        - 0.5 * np.einsum("vlp,vik->vipkl", Fi, tau)
+    )
+    K = np.einsum("vipkl,vjp->vijkl", dtau, Fi) - np.einsum("vip,vlp,vjk->vijkl", tau, Fi, Fi)
+    P = np.einsum("vip,vjp->vij", tau, Fi)
+    return P, K
+
+
+def neo_hookean_umat(F, lam, mu):
+    """Compressible neo-Hookean solid in umat form: Kirchhoff stress
+    tau = mu (b - I) + lam ln(J) I (b = F F^T), returned as the Cauchy stress
+    sigma = tau / J and the Jaumann-rate tangent of Eq. ABAtang, for which
+    J C^ab : d = mu (d b + b d) + lam tr(d) I, i.e.
+    J C^ab_ijkl = mu/2 (delta_ik b_jl + delta_il b_jk + b_ik delta_jl + b_il delta_jk) + lam delta_ij delta_kl."""
+    J = np.linalg.det(F)
+    b = F @ _T(F)
+    tau = mu * (b - _I3) + lam * np.log(J)[:, None, None] * _I3
+    d = _I3
+    JC = 0.5 * mu * (np.einsum("ik,vjl->vijkl", d, b) + np.einsum("il,vjk->vijkl", d, b)
+                     + np.einsum("vik,jl->vijkl", b, d) + np.einsum("vil,jk->vijkl", b, d)) \
+        + lam * np.einsum("ij,kl->ijkl", d, d)[None]
+    return tau / J[:, None, None], JC / J[:, None, None, None, None]

@@ -29,6 +29,7 @@ from . import fips
 SVK_CUBIC = 0
 SVK_ISO = 1
 CP_FCC = 2
+NEO_HOOKE = 3  # compressible neo-Hookean, evaluated through the umat conversion of Appendix A
 
 
 class Material:
@@ -100,7 +101,7 @@ class OracleRVE:
         s, m = mat.fcc_slip_systems()
         for g in range(self.ngrains):
             M = materials[int(self.phase[g])]
-            if M.kind == SVK_ISO:
+            if M.kind in (SVK_ISO, NEO_HOOKE):
                 C = mat.isotropic_stiffness(M.E, M.nu)
             else:
                 C = mat.rotate4(mat.cubic_stiffness(M.C11, M.C12, M.C44), R[g])
@@ -140,6 +141,11 @@ class OracleRVE:
                 trial["dg"][idx] = out["dg"]
                 trial["tau"][idx] = out["tau"]
                 trial["ok"] = trial["ok"] and bool(out["conv"].all())
+            elif M.kind == NEO_HOOKE:
+                lam = M.E * M.nu / ((1 + M.nu) * (1 - 2 * M.nu))
+                mu = M.E / (2 * (1 + M.nu))
+                sig, Cab = mat.neo_hookean_umat(Fv[idx], lam, mu)
+                P[idx], K[idx] = mat.umat_to_PK(Fv[idx], sig, Cab)
             else:
                 P[idx], K[idx] = mat.svk(Fv[idx], g["C"])
         Pf = voxels_to_field(P, self.shape)
@@ -211,6 +217,12 @@ class OracleRVE:
             if on_step:
                 on_step(k, rep)
         return out
+
+    def band_fips(self, width):
+        """Band-averaged W_cyc per grain (Eq. Wmax), bands of `width` along each slip plane."""
+        cp = np.array([self.materials[int(self.phase[g])].kind == CP_FCC for g in range(self.ngrains)])
+        normals = np.stack([g["normals"][0::3] for g in self.grains])
+        return fips.band_fips(self.acc["w"], self.gid.reshape(self.shape), normals, cp, self.L, width)
 
     def grain_fips(self):
         cp = np.array([self.materials[int(self.phase[g])].kind == CP_FCC for g in range(self.ngrains)])

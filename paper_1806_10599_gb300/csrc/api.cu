@@ -8,6 +8,7 @@
 #include <cstring>
 #include <vector>
 
+#include "bulk_copy.cuh"
 #include "gff_internal.cuh"
 
 using namespace gff;
@@ -128,7 +129,7 @@ void stiffness(const gff_material& m, const double* R, double* Cout) {
             for (int k = 0; k < 3; ++k)
                 for (int l = 0; l < 3; ++l) {
                     double v;
-                    if (m.kind == GFF_MAT_SVK_ISO) {
+                    if (m.kind == GFF_MAT_SVK_ISO || m.kind == GFF_MAT_NEOHOOKE) {
                         const double lam = m.E * m.nu / ((1 + m.nu) * (1 - 2 * m.nu));
                         const double mu = m.E / (2 * (1 + m.nu));
                         v = lam * kd(i, j) * kd(k, l) + mu * (kd(i, k) * kd(j, l) + kd(i, l) * kd(j, k));
@@ -138,7 +139,7 @@ void stiffness(const gff_material& m, const double* R, double* Cout) {
                     }
                     C[27 * i + 9 * j + 3 * k + l] = v;
                 }
-    if (m.kind == GFF_MAT_SVK_ISO) {
+    if (m.kind == GFF_MAT_SVK_ISO || m.kind == GFF_MAT_NEOHOOKE) {  // isotropic: no rotation
         std::memcpy(Cout, C, sizeof C);
         return;
     }
@@ -411,6 +412,7 @@ GFF_EXPORT gff_status gff_create(const gff_grid* grid, const gff_options* opt, g
     h->g.nz = grid->nz;
     h->g.nxh = h->nxh;
     h->g.N = h->N;
+    h->g.wait_cycles = BULK_WAIT_CYCLES;
     *out = h;
     if ((st = build_tables(h)) != GFF_OK) return st;
     const long long N = h->N;
@@ -524,7 +526,9 @@ GFF_EXPORT gff_status gff_set_microstructure(gff_handle* h, const int32_t* grain
 
 GFF_EXPORT gff_status gff_set_material(gff_handle* h, int phase, const gff_material* m) {
     if (!h || !m || phase < 0 || phase >= 8) return fail(h, GFF_ERR_ARG, "bad material args");
-    if (m->kind < GFF_MAT_SVK_CUBIC || m->kind > GFF_MAT_CP_FCC) return fail(h, GFF_ERR_ARG, "material kind %d", m->kind);
+    if (m->kind < GFF_MAT_SVK_CUBIC || m->kind > GFF_MAT_NEOHOOKE) return fail(h, GFF_ERR_ARG, "material kind %d", m->kind);
+    if ((m->kind == GFF_MAT_SVK_ISO || m->kind == GFF_MAT_NEOHOOKE) && !(m->E > 0 && m->nu > -1 && m->nu < 0.5))
+        return fail(h, GFF_ERR_ARG, "isotropic constants out of range");
     if (m->kind == GFF_MAT_CP_FCC) {
         const double p = m->p_exp;
         if (!(p >= 1 && p <= 64 && p == std::floor(p)) || !(m->tau0 > 0) || !(m->gdot0 > 0) || m->d_af < 0)
@@ -660,9 +664,80 @@ GFF_EXPORT gff_status gff_apply_operator_timed(gff_handle* h, int precision, con
     for (int i = 0; i < 4; ++i)
         if (ev[i]) cudaEventDestroy(ev[i]);
     if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "timed apply: %s", cudaGetErrorString(e));
+    return gff_sync(h);
+}
+
+GFF_EXPORT gff_status gff_apply_operator_host(gff_handle* h, int precision, const uint8_t* mask9, const void* x_host,
+                                              void* y_host) {
+    if (!h || !x_host || !y_host) return fail(h, GFF_ERR_ARG, "bad apply args");
+    if (precision != GFF_PREC_FP64 && precision != GFF_PREC_MIXED) return fail(h, GFF_ERR_ARG, "precision %d", precision);
+    const size_t bytes = 9 * (size_t)h->N * (precision == GFF_PREC_FP64 ? sizeof(double) : sizeof(float));
+    void* xd = precision == GFF_PREC_FP64 ? (void*)h->d_x : (void*)h->d_x32;
+    void* yd = precision == GFF_PREC_FP64 ? (void*)h->d_Ap : (void*)h->d_Ap32;
+    GFF_TRY(cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, h->stream));
+    gff_status st = gff_apply_operator(h, precision, mask9, xd, yd);
+    if (st != GFF_OK) return st;
+    GFF_TRY(cudaMemcpyAsync(y_host, yd, bytes, cudaMemcpyDeviceToHost, h->stream));
+    return gff_sync(h);
+}
+
+GFF_EXPORT gff_status gff_cg_kernels_timed(gff_handle* h, int precision, int reps, float* ms_out) {
+    if (!h || !ms_out || reps < 1) return fail(h, GFF_ERR_ARG, "bad args");
+    double* cg = h->d_scal + 32;
+    int* flag = reinterpret_cast<int*>(h->d_scal + 48);
+    cudaError_t e;
+    if (precision == GFF_PREC_FP64)
+        e = time_cg_kernels<double>(h->d_x, h->d_r, h->d_p, h->d_Ap, 9 * h->N, h->d_red, cg, flag, h->stream, reps,
+                                    ms_out);
+    else if (precision == GFF_PREC_MIXED)
+        e = time_cg_kernels<float>(h->d_x32, h->d_r32, h->d_p32, h->d_Ap32, 9 * h->N, h->d_red, cg, flag, h->stream,
+                                   reps, ms_out);
+    else
+        return fail(h, GFF_ERR_ARG, "precision %d", precision);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "timed CG kernels: %s", cudaGetErrorString(e));
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_measure_fp64_peak(double* gflops_out, double* ms_out) {
+    if (!gflops_out) return GFF_ERR_ARG;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GFF_ERR_CUDA;
+    const int blocks = 4 * nsm;
+    double* out = nullptr;
+    if (cudaMalloc(&out, (size_t)blocks * 256 * sizeof(double)) != cudaSuccess) return GFF_ERR_OOM;
+    float ms = 0.f;
+    cudaError_t e = measure_fp64_fma(out, blocks, 8192, 5, nullptr, gflops_out, &ms);
+    cudaFree(out);
+    if (e != cudaSuccess) return GFF_ERR_CUDA;
+    if (ms_out) *ms_out = ms;
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_sync(gff_handle* h) {
+    if (!h) return GFF_ERR_ARG;
     int tmo = 0;
-    GFF_TRY(cudaMemcpy(&tmo, h->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost));
-    if (tmo) return fail(h, GFF_ERR_TIMEOUT, "a bulk-copy wait in an FFT pass timed out");
+    GFF_TRY(cudaMemcpyAsync(h->h_scal, h->d_flag + 2, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    GFF_TRY(cudaStreamSynchronize(h->stream));
+    std::memcpy(&tmo, h->h_scal, sizeof(int));
+    if (tmo) {
+        GFF_TRY(cudaMemsetAsync(h->d_flag + 2, 0, sizeof(int), h->stream));
+        GFF_TRY(cudaStreamSynchronize(h->stream));
+        return fail(h, GFF_ERR_TIMEOUT, "a bounded bulk-copy wait in an FFT pass gave up (%d)", tmo);
+    }
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_set_wait_limit(gff_handle* h, long long cycles) {
+    if (!h) return GFF_ERR_ARG;
+    h->g.wait_cycles = cycles < 0 ? BULK_WAIT_CYCLES : cycles;
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_set_return_map(gff_handle* h, int mode) {
+    if (!h || (mode != GFF_RETURN_MAP_DEFAULT && mode != GFF_RETURN_MAP_EXACT))
+        return fail(h, GFF_ERR_ARG, "return-map mode must be 0 or 1");
+    h->cp_exact_only = mode == GFF_RETURN_MAP_EXACT ? 1 : 0;
     return GFF_OK;
 }
 
@@ -775,6 +850,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     const long long N = h->N;
     const long long n = 9 * N;
     gff_status st;
+    GFF_TRY(cudaMemsetAsync(h->d_flag + 2, 0, sizeof(int), h->stream));  // timeouts are counted per increment
     // zero-fluctuation start: F = F_{k-1} + dFbar on strain-controlled components
     double Fsum[9];
     GFF_TRY(launch_sum9(h->d_F, N, h->d_red, h->d_scal, h->stream));
@@ -1122,6 +1198,40 @@ GFF_EXPORT gff_status gff_get_fips(gff_handle* h, double* pcyc_g, double* wcyc_g
     if (pcyc_g) std::memcpy(pcyc_g, host.data(), ng * sizeof(double));
     if (wcyc_g) std::memcpy(wcyc_g, host.data() + ng, 12 * (size_t)ng * sizeof(double));
     if (fs_g) std::memcpy(fs_g, host.data() + 13 * (size_t)ng, ng * sizeof(double));
+    return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_umat_tangent(long long n, const double* F_dev, const double* sigma_dev, const double* Cab_dev,
+                                       double* P_dev, double* K_dev, void* stream) {
+    if (n < 0 || (n > 0 && (!F_dev || !sigma_dev || !Cab_dev || !P_dev || !K_dev))) return GFF_ERR_ARG;
+    if (n == 0) return GFF_OK;
+    cudaError_t e = launch_umat_convert(n, F_dev, sigma_dev, Cab_dev, P_dev, K_dev, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GFF_OK : GFF_ERR_CUDA;
+}
+
+GFF_EXPORT gff_status gff_get_band_fips(gff_handle* h, double width, double* wb_g, double* wb_max) {
+    if (!h || !(width > 0)) return fail(h, GFF_ERR_ARG, "band width must be positive");
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    const int ng = h->ngrains;
+    const double smax = 0.5 * std::sqrt(h->grid.L[0] * h->grid.L[0] + h->grid.L[1] * h->grid.L[1] +
+                                        h->grid.L[2] * h->grid.L[2]);
+    const double nbd = 2.0 * (std::floor(smax / width) + 2.0);
+    if (nbd * ng * 16.0 * sizeof(double) > 2e9)
+        return fail(h, GFF_ERR_ARG, "band width %.3e too small for %d grains (more than 2 GB of band sums)", width, ng);
+    const int NB = (int)nbd;
+    void* scratch = nullptr;
+    const size_t bytes = band_scratch_bytes(ng, NB) + (size_t)ng * sizeof(double);
+    if ((st = dalloc(h, &scratch, bytes, "band sums")) != GFF_OK) return st;
+    double* out = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + band_scratch_bytes(ng, NB));
+    std::vector<double> host(ng);
+    cudaError_t e = launch_band_fips(h, width, NB, scratch, out);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), out, ng * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(scratch);
+    if (e != cudaSuccess) return fail(h, GFF_ERR_CUDA, "band fips: %s", cudaGetErrorString(e));
+    if (wb_g) std::memcpy(wb_g, host.data(), ng * sizeof(double));
+    if (wb_max) *wb_max = *std::max_element(host.begin(), host.end());
     return GFF_OK;
 }
 

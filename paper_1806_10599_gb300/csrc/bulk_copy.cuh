@@ -55,15 +55,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Waits until the phase with the given parity has completed, for at most
-// `cycles` SM clock cycles.  Returns false on timeout.
+// `cycles` SM clock cycles.  Returns false on timeout; a budget of zero or
+// less gives up at once, without looking at the barrier (the error path can
+// then be exercised deterministically).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long cycles) {
+    if (cycles <= 0) return false;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > cycles) return false;
     return true;
 }
 
-// about two seconds at the GB300 clock: far beyond any copy of this library
+// about two seconds at the GB300 clock: far beyond any copy of this library.
+// The first wait on each load takes GridDev::wait_cycles (this value unless a
+// caller lowers it); the waits that drain copies after a timeout always take this.
 constexpr long long BULK_WAIT_CYCLES = 4000000000LL;
 
 }  // namespace gff

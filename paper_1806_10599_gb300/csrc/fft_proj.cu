@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(512) k_zproj_tma(const __grid_constant__ CUten
             tma_load_3d(buf[cur ^ 1], &tm, (nxt / 3) * W * K, 0, 3 * (nxt % 3), &bar[cur ^ 1], bytes);
         }
         zproj_columns<T, W>(g, (s / 3) * W, tb);
-        const bool ok = mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+        const bool ok = mbar_wait(&bar[cur], phase[cur], g.wait_cycles);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicExch(err, 1);
@@ -872,6 +872,15 @@ __device__ __forceinline__ void plane_inv_compute(typename C2<T>::t* s, T* __res
     }
 }
 
+// Plane (c, z) of the output set to NaN: what an inverse pass leaves where a
+// bounded wait gave up, so that the failure shows in y as well as in the flag.
+template <typename T>
+__device__ __noinline__ void plane_fill_nan(T* y, const GridDev& g, int c, int z) {
+    T* yc = y + (long long)c * g.N + (long long)z * g.ny * g.nx;
+    const T nanv = (T)__int_as_float(0x7fc00000);
+    for (int e = threadIdx.x; e < g.ny * g.nx; e += blockDim.x) yc[e] = nanv;
+}
+
 template <typename T>
 __device__ __forceinline__ void plane_tables(const GridDev& g, typename C2<T>::t* twx, typename C2<T>::t* twy,
                                              int* posx) {
@@ -932,12 +941,13 @@ __global__ void __launch_bounds__(512) k_plane_inv(const typename C2<T>::t* __re
     if (threadIdx.x == 0)  // plane * sizeof(C) is a multiple of 16 (ny even), the plane start too
         bulk_load(s, spec + ((long long)c * g.nz + z) * plane, (uint32_t)(plane * sizeof(C)), bar);
     plane_tables<T>(g, twx, twy, posx);
-    const bool ok = mbar_wait(bar, 0u, BULK_WAIT_CYCLES);
+    const bool ok = mbar_wait(bar, 0u, g.wait_cycles);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
             if (err) atomicExch(err, 1);
             mbar_wait(bar, 0u, BULK_WAIT_CYCLES);  // let the copy land (bounded) before leaving
         }
+        plane_fill_nan<T>(y, g, c, z);  // the plane is not computed: make that visible in y
         __syncthreads();
         return;
     }
@@ -988,14 +998,16 @@ __global__ void __launch_bounds__(inv_stream_max_threads<T>()) k_plane_inv_strea
             fence_proxy_async_smem();  // the other buffer's last readers finished at the barrier below
             bulk_load(buf[cur ^ 1], spec + (long long)nextp * plane, bytes, &bar[cur ^ 1]);
         }
-        const bool ok = mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+        const bool ok = mbar_wait(&bar[cur], phase[cur], g.wait_cycles);
         if (__syncthreads_or(!ok)) {
-            // record, let the copies in flight land (bounded), leave
+            // record, let the copies in flight land (bounded), mark the planes this
+            // block still owns as not computed (NaN), leave
             if (threadIdx.x == 0) {
                 atomicExch(err, 1);
                 mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
                 if (nextp < total) mbar_wait(&bar[cur ^ 1], phase[cur ^ 1], BULK_WAIT_CYCLES);
             }
+            for (int q = p; q < total; q += gridDim.x) plane_fill_nan<T>(y, g, q / g.nz, q % g.nz);
             __syncthreads();
             return;
         }
@@ -1372,6 +1384,9 @@ bool set_tiles(gff_handle* h, const Tune& t64, const Tune& t32) {
 }
 
 cudaError_t autotune_galerkin(gff_handle* h) {
+    // timings are taken at the default wait budget, whatever the handle's is
+    const long long wait = h->g.wait_cycles;
+    h->g.wait_cycles = BULK_WAIT_CYCLES;
     // the kernels' cost does not depend on the values: the handle's vectors serve as inputs
     cudaError_t e = cudaMemsetAsync(h->d_x, 0, 9 * h->N * sizeof(double), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_x32, 0, 9 * h->N * sizeof(float), h->stream);
@@ -1383,6 +1398,7 @@ cudaError_t autotune_galerkin(gff_handle* h) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) h->tuned = true;
     h->K32_valid = false;  // the FP32 tangent buffer was used as scratch
+    h->g.wait_cycles = wait;
     return e;
 }
 
@@ -1570,22 +1586,72 @@ cudaError_t noalloc_scratch(void** out) {
 
 bool noalloc_plan(int n, AxisPlan& p) { return make_axis_plan(n, p); }
 
-// frequency at position pos after the in-place forward transform of plan p
-int noalloc_freq(int pos, const AxisPlan& p) { return axis_freq_of_pos(pos, p); }
+// Frequency at position pos after the in-place forward transform of plan p
+// (the digits of pos in the plan's mixed radix, read in reverse order).
+__device__ int noalloc_freq_dev(int pos, const AxisPlan& p) {
+    int f = 0, mult = 1, len = p.n;
+    for (int i = 0; i < p.nst; ++i) {
+        const int m = len / p.radix[i];
+        const int d = pos / m;
+        pos -= d * m;
+        f += d * mult;
+        mult *= p.radix[i];
+        len = m;
+    }
+    return f;
+}
+
+// The grid tables, written on the device by one block from the plans and box
+// lengths passed by value: twiddles exp(-2 pi i k / n), wave-vector tables
+// (continuous 2 pi kappa / L, discrete tan(pi kappa / n) n / L, 0 at Nyquist)
+// and the position/frequency maps of the in-place transforms.
+__global__ void k_noalloc_tables(NoallocTables* t, AxisPlan ax, AxisPlan ay, AxisPlan az, double Lx, double Ly,
+                                 double Lz) {
+    const AxisPlan* pl[3] = {&ax, &ay, &az};
+    const double L[3] = {Lx, Ly, Lz};
+    for (int a = 0; a < 3; ++a) {
+        const int n = pl[a]->n;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double sn, cs;
+            sincospi(2.0 * k / n, &sn, &cs);
+            t->tw64[a][k] = make_double2(cs, -sn);
+            t->tw32[a][k] = make_float2((float)cs, (float)-sn);
+            const int kappa = (2 * k < n) ? k : k - n;
+            const double qc = 2.0 * 3.141592653589793238462643383279502884 * kappa / L[a];
+            const double qd = (2 * k == n) ? 0.0 : sinpi((double)kappa / n) / cospi((double)kappa / n) * n / L[a];
+            t->qt64[0][a][k] = qc;
+            t->qt64[1][a][k] = qd;
+            t->qt32[0][a][k] = (float)qc;
+            t->qt32[1][a][k] = (float)qd;
+        }
+    }
+    for (int p = threadIdx.x; p < ax.n; p += blockDim.x) t->posx[noalloc_freq_dev(p, ax)] = p;
+    for (int p = threadIdx.x; p < ay.n; p += blockDim.x) t->fqy[p] = noalloc_freq_dev(p, ay);
+    for (int p = threadIdx.x; p < az.n; p += blockDim.x) t->fqz[p] = noalloc_freq_dev(p, az);
+}
+
+// Every CUDA call is checked where it is made, so that an error is reported
+// by the call that caused it.
+template <typename K> cudaError_t noalloc_smem(K kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 template <typename T>
 cudaError_t noalloc_launch(const GridDev& g, const T* x, T* y, const ProjArgs& pa, const OutArgs& oa,
                            typename C2<T>::t* spec, cudaStream_t st) {
-    using C = typename C2<T>::t;
-    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(C));
+    const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
     const size_t smB = zproj_smem<T>(g);
     constexpr int W = zproj_width<T>();
     const dim3 gridA(9, g.nz);
-    allow_smem(k_plane_fwd<T, false, false>, smA);
+    cudaError_t e = noalloc_smem(k_plane_fwd<T, false, false>, smA);
+    if (e != cudaSuccess) return e;
     k_plane_fwd<T, false, false><<<gridA, 512, smA, st>>>(x, nullptr, spec, g, nullptr);
-    allow_smem(k_zproj<T, W>, smB);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = noalloc_smem(k_zproj<T, W>, smB)) != cudaSuccess) return e;
     k_zproj<T, W><<<zproj_blocks(g, W), 256, smB, st>>>(spec, g, pa, nullptr);
-    allow_smem(k_plane_inv<T, false>, smA);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = noalloc_smem(k_plane_inv<T, false>, smA)) != cudaSuccess) return e;
+    // no status word: a bounded wait that gives up leaves its plane of y as NaN
     k_plane_inv<T, false><<<gridA, 512, smA, st>>>(spec, y, g, oa, nullptr, nullptr);
     return cudaGetLastError();
 }
@@ -1610,43 +1676,24 @@ __attribute__((visibility("default"))) gff_status gff_project_noalloc(const gff_
     }
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > NOALLOC_MAX_VOXELS) return GFF_ERR_ARG;  // larger grids need gff_create + gff_project
+
+    // a CUDA error left pending by an earlier call belongs to that call: report it, do not clear it
+    if (cudaPeekAtLastError() != cudaSuccess) return GFF_ERR_CUDA;
     void* base = nullptr;
     if (noalloc_scratch(&base) != cudaSuccess) return GFF_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-
-    // grid tables, built on the host stack and copied into the scratch
-    NoallocTables t;
-    std::memset(&t, 0, sizeof t);
-    const double twopi = 6.283185307179586476925286766559;
-    for (int a = 0; a < 3; ++a) {
-        const int n = n3[a];
-        for (int k = 0; k < n; ++k) {
-            const double th = twopi * k / n;
-            t.tw64[a][k] = make_double2(std::cos(th), -std::sin(th));
-            t.tw32[a][k] = make_float2((float)std::cos(th), (float)-std::sin(th));
-            const int kappa = (2 * k < n) ? k : k - n;
-            const double q = twopi * kappa / n;
-            const double qc = q * n / grid->L[a];
-            const double qd = (2 * k == n) ? 0.0 : std::tan(0.5 * q) * n / grid->L[a];
-            t.qt64[0][a][k] = qc;
-            t.qt64[1][a][k] = qd;
-            t.qt32[0][a][k] = (float)qc;
-            t.qt32[1][a][k] = (float)qd;
-        }
-    }
-    for (int p = 0; p < grid->nx; ++p) t.posx[noalloc_freq(p, g.ax)] = p;
-    for (int p = 0; p < grid->ny; ++p) t.fqy[p] = noalloc_freq(p, g.ay);
-    for (int p = 0; p < grid->nz; ++p) t.fqz[p] = noalloc_freq(p, g.az);
     unsigned char* d = static_cast<unsigned char*>(base);
     NoallocTables* dt = reinterpret_cast<NoallocTables*>(d + NOALLOC_TABLE_OFFSET);
-    // pageable source: the call returns once the data is staged, so the stack buffer may go
-    if (cudaMemcpyAsync(dt, &t, sizeof t, cudaMemcpyHostToDevice, st) != cudaSuccess) return GFF_ERR_CUDA;
+    // grid tables, written on the device in stream order (no host buffer is involved)
+    k_noalloc_tables<<<1, 128, 0, st>>>(dt, g.ax, g.ay, g.az, grid->L[0], grid->L[1], grid->L[2]);
+    if (cudaGetLastError() != cudaSuccess) return GFF_ERR_CUDA;
 
     g.nx = grid->nx;
     g.ny = grid->ny;
     g.nz = grid->nz;
     g.nxh = grid->nx / 2 + 1;
     g.N = N;
+    g.wait_cycles = BULK_WAIT_CYCLES;
     for (int a = 0; a < 3; ++a) {
         g.tw64[a] = dt->tw64[a];
         g.tw32[a] = dt->tw32[a];

@@ -42,6 +42,7 @@ struct GridDev {
     const int* fqz;          // [nz]
     const double* qt64[2][3];  // [kind][axis][k]: q~ (continuous) or q~' (discrete) per FFT index
     const float* qt32[2][3];
+    long long wait_cycles;     // budget of the first wait on each bulk load (BULK_WAIT_CYCLES by default)
 };
 
 // Projection parameters of one call.
@@ -178,6 +179,7 @@ struct gff_handle {
     double* d_dg = nullptr;    // [12][N] slip increments of the trial
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
+    int cp_exact_only = 0;     // 1: every return map runs the exact Newton from dg = 0 (gff_set_return_map)
     int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out bulk-copy waits,
                                // [4] return-map fallbacks, [5] local Newton iterations
     // reductions
@@ -294,6 +296,13 @@ cudaError_t launch_cg_step(T* x, T* r, T* p, const T* Ap, long long n, double* p
 template <typename T>
 cudaError_t launch_zero(T* y, long long n, cudaStream_t s);
 
+// measurement helpers (vec.cu): FP64 FMA throughput; durations of the CG vector kernels
+cudaError_t measure_fp64_fma(double* out, int blocks, int iters, int reps, cudaStream_t s, double* gflops,
+                             float* ms_best);
+template <typename T>
+cudaError_t time_cg_kernels(T* x, T* r, T* p, T* Ap, long long n, double* partial, double* cg, int* flag,
+                            cudaStream_t s, int reps, float* ms);
+
 // batched CG (per-RVE scalars cg[r * 8 + CG_*], flags[2 r], flags[2 r + 1])
 cudaError_t launch_cg_init_batch(int n, double* cg, int* flag, const double* rr0_stop2_dev, cudaStream_t s);
 template <typename T>
@@ -324,6 +333,12 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
                                       int part = CONST_ALL);
 size_t constitutive_batch_scratch_bytes();
 cudaError_t launch_fip_reset(gff_handle* h);
+// Appendix A: (F, Cauchy stress, Jaumann-rate tangent C^ab) -> (P, K) for n voxels, SoA [9][n] / [81][n]
+cudaError_t launch_umat_convert(long long n, const double* F, const double* sigma, const double* Cab, double* P,
+                                double* K, cudaStream_t st);
+// band-averaged W_cyc (Eq. Wmax) per grain into out[ngrains] (device), NB bands per plane
+size_t band_scratch_bytes(int ngrains, int NB);
+cudaError_t launch_band_fips(gff_handle* h, double width, int NB, void* scratch, double* out);
 cudaError_t launch_grain_fips(gff_handle* h, double* pc, double* w, double* fs);
 
 }  // namespace gff

@@ -9,14 +9,17 @@
 //   S = C : (Ce - I)/2, tau_a = (Ce S) : S0_a,
 //   chi_a = (chi_n,a + c dg_a) / (1 + d |dg_a|),
 //   r_a = dg_a - dt gdot0 h((tau_a - chi_a)/tau0),  h(x) = |x|^p sign(x),
-// solved for dg by Newton (12x12 LU with partial pivoting), then
+// solved for dg by Newton, then
 //   P = Fe S Fp^-T and K by implicit differentiation of r(dg, F) = 0.
 // The local Newton starts from the slip increments of the previous global
 // Newton iterate when there is one (else from 0) and takes its steps with the
-// per-grain small-strain Jacobian (see cp_jacobian_approx); the residual is
-// always exact, so it converges to the same root.  The exact Jacobian is
-// assembled once, at the root, for the tangent.  If the fast iteration fails
-// it restarts with the exact Jacobian from dg = 0.
+// per-grain small-elastic-strain Jacobian, solved as a 5x5 system on the
+// deviatoric strains (cp_correction_lowrank); the residual is always exact,
+// so it converges to the same root.  The exact 12x12 Jacobian is assembled
+// once, at the root, for the tangent (LU with partial pivoting).  If the fast
+// iteration fails, the return map restarts from dg = 0 with exact Newton
+// steps (12x12 LU with partial pivoting) -- the fallback; a handle can also
+// ask for that exact iteration alone (gff_set_return_map).
 // Everything is FP64.  One thread per voxel.
 #include <cmath>
 
@@ -513,7 +516,8 @@ template <typename T>
 __device__ void cp_update(const double* F, const double* A, const double* chin, double dt,
                           const double* __restrict__ S0, const double* __restrict__ C, const double* __restrict__ H,
                           const T* __restrict__ S0t, const T* __restrict__ Ct, const CPParamsDev& pr,
-                          const double* dg0 /* 12 or null */, T* K /* 81 or null */, CPOut& out) {
+                          const double* dg0 /* 12 or null */, T* K /* 81 or null */, CPOut& out,
+                          bool exact_only = false) {
     const double coef = dt * pr.gdot0;
     const int p = (int)pr.p;
     double dg[NSLIP], dh[NSLIP], chi[NSLIP];
@@ -522,7 +526,8 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
     // FP64 corrections: J is ill-conditioned (cond ~ 1e8 and more) once slip
     // systems are active, beyond what an FP32 solve can steer
     int it1 = 0, it2 = 0;
-    bool conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh, &it1);
+    bool conv = false;
+    if (!exact_only) conv = cp_local_solve<double>(F, A, chin, S0, C, H, pr, coef, p, true, 60, dg, st, chi, dh, &it1);
     out.fallback = !conv;
     if (!conv) {  // fall back: exact Newton from dg = 0
         for (int a = 0; a < NSLIP; ++a) dg[a] = 0.0;
@@ -573,6 +578,102 @@ __device__ void svk_update(const double* F, const double* __restrict__ C, double
         }
 }
 
+// ---- Appendix A: umat outputs (Cauchy stress sigma, Jaumann-rate tangent C^ab)
+// to P = J sigma F^-T (Eq. fPK) and K = dP/dF:
+//   d tau_ip/d F_kl = J C_ipkm Fi_lm + 1/2 delta_ik (Fi tau)_lp - 1/2 Fi_li tau_kp
+//                     + 1/2 delta_pk (tau Fi^T)_il - 1/2 Fi_lp tau_ik,
+//   K_ijkl = d tau_ip/d F_kl Fi_jp - (tau Fi^T)_il Fi_jk,
+// tau = J sigma, Fi = F^-1.  Cab(q) returns C^ab at index q = 9 (3i+j) + 3k + l;
+// K is written column by column through Kout(q, value).
+__device__ __forceinline__ double det3(const double* F) {
+    return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) + F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+__device__ __forceinline__ void inv3(const double* F, double J, double* Fi) {
+    const double r = 1.0 / J;
+    Fi[0] = (F[4] * F[8] - F[5] * F[7]) * r;
+    Fi[1] = (F[2] * F[7] - F[1] * F[8]) * r;
+    Fi[2] = (F[1] * F[5] - F[2] * F[4]) * r;
+    Fi[3] = (F[5] * F[6] - F[3] * F[8]) * r;
+    Fi[4] = (F[0] * F[8] - F[2] * F[6]) * r;
+    Fi[5] = (F[2] * F[3] - F[0] * F[5]) * r;
+    Fi[6] = (F[3] * F[7] - F[4] * F[6]) * r;
+    Fi[7] = (F[1] * F[6] - F[0] * F[7]) * r;
+    Fi[8] = (F[0] * F[4] - F[1] * F[3]) * r;
+}
+
+template <typename CA, typename KO>
+__device__ __forceinline__ void umat_to_PK(const double* F, const double* sig, CA Cab, double* P, KO Kout) {
+    const double J = det3(F);
+    double Fi[9], tau[9], A[9], B[9];
+    inv3(F, J, Fi);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) tau[q] = J * sig[q];
+    mm(Fi, tau, A);   // A_lp = Fi_lm tau_mp
+    mmt(tau, Fi, B);  // B_il = tau_im Fi_lm
+    mmt(tau, Fi, P);  // P_ij = tau_ip Fi_jp
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            double dt[9];  // d tau_ip / d F_kl
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    double c = 0.0;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) c = fma(Cab(9 * (3 * i + p) + 3 * k + m), Fi[3 * l + m], c);
+                    double v = J * c - 0.5 * Fi[3 * l + i] * tau[3 * k + p] - 0.5 * Fi[3 * l + p] * tau[3 * i + k];
+                    if (i == k) v += 0.5 * A[3 * l + p];
+                    if (p == k) v += 0.5 * B[3 * i + l];
+                    dt[3 * i + p] = v;
+                }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const double v = dt[3 * i] * Fi[3 * j] + dt[3 * i + 1] * Fi[3 * j + 1] + dt[3 * i + 2] * Fi[3 * j + 2] -
+                                     B[3 * i + l] * Fi[3 * j + k];
+                    Kout(9 * (3 * i + j) + 3 * k + l, v);
+                }
+        }
+}
+
+// Compressible neo-Hookean solid in umat form: tau = mu (b - I) + lam ln(J) I,
+// sigma = tau / J and J C^ab_ijkl = mu/2 (d_ik b_jl + d_il b_jk + b_ik d_jl + b_il d_jk) + lam d_ij d_kl.
+__device__ __forceinline__ void neohooke_umat(const double* F, double lam, double mu, double* sig, double* b, double& J) {
+    J = det3(F);
+    mmt(F, F, b);  // b = F F^T
+    const double lnJ = log(J), iJ = 1.0 / J;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sig[q] = (mu * (b[q] - ((q % 4) == 0 ? 1.0 : 0.0)) + ((q % 4) == 0 ? lam * lnJ : 0.0)) * iJ;
+}
+__device__ __forceinline__ double neohooke_Cab(int q, const double* b, double lam, double mu, double iJ) {
+    const int i = q / 27, j = (q / 9) % 3, k = (q / 3) % 3, l = q % 3;
+    double v = 0.0;
+    if (i == k) v += b[3 * j + l];
+    if (i == l) v += b[3 * j + k];
+    if (j == l) v += b[3 * i + k];
+    if (j == k) v += b[3 * i + l];
+    v *= 0.5 * mu;
+    if (i == j && k == l) v += lam;
+    return v * iJ;
+}
+
+__global__ void __launch_bounds__(TPB) k_umat_convert(long long n, const double* __restrict__ F,
+                                                      const double* __restrict__ sig, const double* __restrict__ Cab,
+                                                      double* __restrict__ P, double* __restrict__ K) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    double f[9], s9[9], p9[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        f[q] = F[q * n + v];
+        s9[q] = sig[q * n + v];
+    }
+    umat_to_PK(f, s9, [&](int q) { return __ldg(Cab + q * n + v); }, p9, [&](int q, double x) { K[q * n + v] = x; });
+#pragma unroll
+    for (int q = 0; q < 9; ++q) P[q * n + v] = p9[q];
+}
+
 struct ConstArgs {
     const double* F;
     const int* gid;
@@ -581,6 +682,7 @@ struct ConstArgs {
     const float* G32;  // [ngrains][G32_STRIDE]: S0 and C in FP32 for the FP32 tangent
     const double* H;  // [ngrains][144]: P [5][12], C5^-1 [5][5] of the small-strain Jacobian (cp_correction_lowrank)
     int warm;         // 1: start the local Newton from dg (previous iterate)
+    int exact;        // 1: skip the small-strain iteration, exact Newton from dg = 0 only
     double rtol;      // return-map tolerance (return_map_tol)
     const int* gkind;
     const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
@@ -677,17 +779,17 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         CPOut o;
         if (PART == PART_P) {
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
-                              (double*)nullptr, o);
+                              (double*)nullptr, o, a.exact != 0);
         } else if (F32T) {
             float K[81];
             cp_update<float>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, g32 + G32_S0, g32 + G32_C, pr,
-                             a.warm ? dg0 : nullptr, K, o);
+                             a.warm ? dg0 : nullptr, K, o, a.exact != 0);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
             double K[81];
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
-                              K, o);
+                              K, o, a.exact != 0);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
             if (a.K32) {
@@ -710,7 +812,16 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         }
     } else {
         double P[9], K[81];
-        svk_update(F, C, P, K);
+        if (kind == GFF_MAT_NEOHOOKE) {  // through the umat interface (Appendix A)
+            const double lam = __ldg(C + 4), mu = __ldg(C + 10);  // C_1122, C_1212 of the isotropic C
+            double sg[9], b[9], J;
+            neohooke_umat(F, lam, mu, sg, b, J);
+            const double iJ = 1.0 / J;
+            umat_to_PK(F, sg, [&](int q) { return neohooke_Cab(q, b, lam, mu, iJ); }, P,
+                       [&](int q, double x) { K[q] = x; });
+        } else {
+            svk_update(F, C, P, K);
+        }
         if (PART != PART_K) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) a.P[k * N + v] = P[k];
@@ -876,7 +987,116 @@ __global__ void k_grain_final(const double* sums, int ngrains, double fs_k, doub
     fs[gi] = best;
 }
 
+// ---- band-averaged dissipated energy (Eq. Wmax).  Bands of width w parallel to
+// each of a grain's four slip planes: the band index of a voxel for plane p is
+// floor(s / w + 1/2), s = (x - x_ref) . m_p with the minimum-image offset of the
+// voxel centre from the grain's reference voxel (its lowest voxel index), which
+// sits in the middle of band 0.
+__global__ void __launch_bounds__(TPB) k_band_ref(const int* __restrict__ gid, long long N, int* __restrict__ ref) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= N) return;
+    atomicMin(ref + gid[v], (int)v);
+}
+
+__device__ __forceinline__ int min_image(int i, int r, int n) {
+    int d = i - r;
+    if (d < 0) d += n;
+    return 2 * d >= n ? d - n : d;
+}
+
+struct BandArgs {
+    const int* gid;
+    const int* gkind;
+    const double* nrm;  // [ngrains][12][3] sample-frame normals; plane p is system 3p's
+    const double* w;    // [12][N] W_cyc per system
+    const int* ref;
+    int nx, ny, nz, NB;
+    double hx, hy, hz, width;
+    long long N;
+    double* sums;  // [ngrains][4][NB][4]: voxel count, then the three systems' W sums
+};
+
+__global__ void __launch_bounds__(TPB) k_band_sums(BandArgs a) {
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.N) return;
+    const int gi = a.gid[v];
+    if (a.gkind[gi] != GFF_MAT_CP_FCC) return;
+    const int ix = (int)(v % a.nx), iy = (int)((v / a.nx) % a.ny), iz = (int)(v / ((long long)a.nx * a.ny));
+    const int r = a.ref[gi];
+    const int rx = r % a.nx, ry = (r / a.nx) % a.ny, rz = r / (a.nx * a.ny);
+    const double dx = min_image(ix, rx, a.nx) * a.hx, dy = min_image(iy, ry, a.ny) * a.hy,
+                 dz = min_image(iz, rz, a.nz) * a.hz;
+    const double* nr = a.nrm + 36LL * gi;
+    for (int p = 0; p < 4; ++p) {
+        const double* m = nr + 9 * p;  // system 3p
+        const double sc = dx * m[0] + dy * m[1] + dz * m[2];
+        const int jo = (int)floor(sc / a.width + 0.5) + a.NB / 2;
+        if (jo < 0 || jo >= a.NB) continue;  // the host sizes NB so that this never happens
+        double* o = a.sums + 4 * ((4LL * gi + p) * a.NB + jo);
+        atomicAdd(o, 1.0);
+        for (int k = 0; k < 3; ++k) atomicAdd(o + 1 + k, a.w[(3 * p + k) * a.N + v]);
+    }
+}
+
+// out[g] = the largest band average over the grain's planes, bands and systems (0 without bands)
+__global__ void k_band_final(const double* __restrict__ sums, int ngrains, int NB, double* __restrict__ out) {
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= ngrains) return;
+    double best = -INFINITY;
+    bool any = false;
+    for (long long b = 4LL * gi * NB; b < 4LL * (gi + 1) * NB; ++b) {
+        const double* o = sums + 4 * b;
+        if (o[0] <= 0.0) continue;
+        any = true;
+        for (int k = 0; k < 3; ++k) best = fmax(best, o[1 + k] / o[0]);
+    }
+    out[gi] = any ? best : 0.0;
+}
+
 }  // namespace
+
+cudaError_t launch_umat_convert(long long n, const double* F, const double* sigma, const double* Cab, double* P,
+                                double* K, cudaStream_t st) {
+    k_umat_convert<<<(unsigned)((n + TPB - 1) / TPB), TPB, 0, st>>>(n, F, sigma, Cab, P, K);
+    return cudaGetLastError();
+}
+
+// Band-averaged W_cyc per grain into out[ngrains] (device); scratch holds
+// ngrains ints + 16 NB ngrains doubles (band_scratch_bytes).
+size_t band_scratch_bytes(int ngrains, int NB) {
+    return ((size_t)ngrains * sizeof(int) + 255) / 256 * 256 + (size_t)ngrains * 16 * NB * sizeof(double);
+}
+
+cudaError_t launch_band_fips(gff_handle* h, double width, int NB, void* scratch, double* out) {
+    const int ng = h->ngrains;
+    int* ref = static_cast<int*>(scratch);
+    double* sums = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) +
+                                             ((size_t)ng * sizeof(int) + 255) / 256 * 256);
+    cudaError_t e = cudaMemsetAsync(ref, 0x7f, (size_t)ng * sizeof(int), h->stream);  // large positive ints
+    if (e == cudaSuccess) e = cudaMemsetAsync(sums, 0, (size_t)ng * 16 * NB * sizeof(double), h->stream);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)((h->N + TPB - 1) / TPB);
+    k_band_ref<<<blocks, TPB, 0, h->stream>>>(h->d_gid, h->N, ref);
+    BandArgs a;
+    a.gid = h->d_gid;
+    a.gkind = h->d_gkind;
+    a.nrm = h->d_nrm;
+    a.w = h->d_acc + h->N;
+    a.ref = ref;
+    a.nx = h->grid.nx;
+    a.ny = h->grid.ny;
+    a.nz = h->grid.nz;
+    a.NB = NB;
+    a.hx = h->grid.L[0] / h->grid.nx;
+    a.hy = h->grid.L[1] / h->grid.ny;
+    a.hz = h->grid.L[2] / h->grid.nz;
+    a.width = width;
+    a.N = h->N;
+    a.sums = sums;
+    k_band_sums<<<blocks, TPB, 0, h->stream>>>(a);
+    k_band_final<<<(ng + 127) / 128, 128, 0, h->stream>>>(sums, ng, NB, out);
+    return cudaGetLastError();
+}
 
 // Loads every constitutive kernel now (with lazy module loading the first launch of
 // each would otherwise pay for it inside the caller's first increment).
@@ -904,6 +1124,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.G32 = h->d_geo32;
     a.H = h->d_nrm + 41LL * h->ngrains;
     a.warm = warm ? 1 : 0;
+    a.exact = h->cp_exact_only;
     a.rtol = return_map_tol(h->opt.newton_tol);
     a.gkind = h->d_gkind;
     a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
@@ -955,6 +1176,7 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.G32 = h->d_geo32;
         a.H = h->d_nrm + 41LL * h->ngrains;
         a.warm = warm[r] ? 1 : 0;
+        a.exact = h->cp_exact_only;
         a.rtol = return_map_tol(h->opt.newton_tol);
         a.gkind = h->d_gkind;
         a.gprm = h->d_nrm + 36LL * h->ngrains;

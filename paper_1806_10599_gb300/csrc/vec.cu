@@ -414,6 +414,110 @@ cudaError_t launch_cg_step(T* x, T* r, T* p, const T* Ap, long long n, double* p
     return cudaGetLastError();
 }
 
+// ---- measurement helpers
+
+namespace {
+// Independent FP64 FMA chains: 8 per thread, `iters` rounds each.  The
+// constants keep every chain bounded (x -> b / (1 - a)); the final store keeps
+// the work alive.
+__global__ void __launch_bounds__(256) k_fma64_chains(double* __restrict__ out, int iters, double a, double b) {
+    double x0 = threadIdx.x * 1e-6, x1 = x0 + 1e-3, x2 = x0 + 2e-3, x3 = x0 + 3e-3;
+    double x4 = x0 + 4e-3, x5 = x0 + 5e-3, x6 = x0 + 6e-3, x7 = x0 + 7e-3;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_fill_ramp(T* __restrict__ y, long long n, double base) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = (T)(base + 1e-3 * (double)(i & 1023));
+}
+}  // namespace
+
+// FP64 FMA throughput of this GPU: blocks x 256 threads x 8 chains x iters
+// FMAs (2 flops each), timed with CUDA events on stream s.  out holds blocks x
+// 256 doubles.  The best of `reps` launches is returned.
+cudaError_t measure_fp64_fma(double* out, int blocks, int iters, int reps, cudaStream_t s, double* gflops,
+                             float* ms_best) {
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return e;
+    }
+    float best = 1e30f;
+    k_fma64_chains<<<blocks, 256, 0, s>>>(out, iters, 0.999999, 1e-6);  // warm-up
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) k_fma64_chains<<<blocks, 256, 0, s>>>(out, iters, 0.999999, 1e-6);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    *ms_best = best;
+    *gflops = 2.0 * 8.0 * (double)blocks * 256.0 * (double)iters / (best * 1e-3) / 1e9;
+    return cudaSuccess;
+}
+
+// Times the CG vector kernels of one iteration on the vectors x, r, p, Ap
+// (n elements, overwritten with a ramp first): ms[0] p.Ap (partial sums and
+// alpha), ms[1] x += alpha p, r -= alpha Ap with r.r (and beta), ms[2]
+// p = r + beta p; averages over `reps` iterations.
+template <typename T>
+cudaError_t time_cg_kernels(T* x, T* r, T* p, T* Ap, long long n, double* partial, double* cg, int* flag,
+                            cudaStream_t s, int reps, float* ms) {
+    const int gb = grid_for(n);
+    k_fill_ramp<T><<<gb, TPB, 0, s>>>(x, n, 0.0);
+    k_fill_ramp<T><<<gb, TPB, 0, s>>>(r, n, 1.0);
+    k_fill_ramp<T><<<gb, TPB, 0, s>>>(p, n, 1.0);
+    k_fill_ramp<T><<<gb, TPB, 0, s>>>(Ap, n, 2.0);
+    k_cg_init<<<1, 1, 0, s>>>(cg, flag, 1.0, 0.0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cudaEvent_t ev[4];
+    for (int i = 0; i < 4; ++i)
+        if ((e = cudaEventCreate(&ev[i])) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ev[j]);
+            return e;
+        }
+    double acc[3] = {0, 0, 0};
+    for (int it = 0; it < reps && e == cudaSuccess; ++it) {
+        cudaEventRecord(ev[0], s);
+        k_dot_partial_skip<T><<<RED_BLOCKS, TPB, 0, s>>>(p, Ap, n, partial, flag);
+        k_final_alpha<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+        cudaEventRecord(ev[1], s);
+        k_cg_update_dev<T><<<RED_BLOCKS, TPB, 0, s>>>(x, r, p, Ap, n, partial, cg, flag);
+        k_final_beta<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+        cudaEventRecord(ev[2], s);
+        k_xpby_dev<T><<<grid_for(n), TPB, 0, s>>>(p, r, n, cg, flag);
+        cudaEventRecord(ev[3], s);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            acc[k] += t;
+        }
+    }
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    for (int k = 0; k < 3; ++k) ms[k] = (float)(acc[k] / (reps > 0 ? reps : 1));
+    return e;
+}
+template cudaError_t time_cg_kernels<double>(double*, double*, double*, double*, long long, double*, double*, int*,
+                                             cudaStream_t, int, float*);
+template cudaError_t time_cg_kernels<float>(float*, float*, float*, float*, long long, double*, double*, int*,
+                                            cudaStream_t, int, float*);
+
 template cudaError_t launch_cg_alpha<double>(const double*, const double*, long long, double*, double*, int*,
                                              cudaStream_t);
 template cudaError_t launch_cg_alpha<float>(const float*, const float*, long long, double*, double*, int*,

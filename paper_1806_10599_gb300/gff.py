@@ -28,7 +28,8 @@ GFF_PROJ_CONTINUOUS, GFF_PROJ_DISCRETE = 0, 1
 GFF_WARM_OFF, GFF_WARM_NET_IF_BETTER, GFF_WARM_NET, GFF_WARM_EXTRAPOLATE = 0, 1, 2, 3
 UNET_IN = 32  # input channels of the warm-start network
 GFF_PREC_FP64, GFF_PREC_MIXED = 0, 1
-GFF_MAT_SVK_CUBIC, GFF_MAT_SVK_ISO, GFF_MAT_CP_FCC = 0, 1, 2
+GFF_RETURN_MAP_DEFAULT, GFF_RETURN_MAP_EXACT = 0, 1
+GFF_MAT_SVK_CUBIC, GFF_MAT_SVK_ISO, GFF_MAT_CP_FCC, GFF_MAT_NEOHOOKE = 0, 1, 2, 3
 (GFF_FIELD_F, GFF_FIELD_P, GFF_FIELD_K, GFF_FIELD_FP_INV, GFF_FIELD_CHI,
  GFF_FIELD_GAMMA, GFF_FIELD_PCYC, GFF_FIELD_WCYC) = range(8)
 FIELD_COMPONENTS = {0: 9, 1: 9, 2: 81, 3: 9, 4: 12, 5: 12, 6: 1, 7: 12}
@@ -105,6 +106,12 @@ _SIGS = {
     "gff_autotune": (c_int, [c_void_p, c_void_p]),
     "gff_set_tiles": (c_int, [c_void_p, c_void_p]),
     "gff_project_noalloc": (c_int, [_P(gff_grid), c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_sync": (c_int, [c_void_p]),
+    "gff_apply_operator_host": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "gff_cg_kernels_timed": (c_int, [c_void_p, c_int, c_int, c_void_p]),
+    "gff_measure_fp64_peak": (c_int, [c_void_p, c_void_p]),
+    "gff_set_wait_limit": (c_int, [c_void_p, ctypes.c_longlong]),
+    "gff_set_return_map": (c_int, [c_void_p, c_int]),
     "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
     "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
@@ -127,6 +134,8 @@ _SIGS = {
     "gff_set_warm_start": (c_int, [c_void_p, c_void_p, c_int]),
     "gff_reset_fips": (c_int, [c_void_p]),
     "gff_get_fips": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "gff_get_band_fips": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
+    "gff_umat_tangent": (c_int, [ctypes.c_longlong, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "gff_save_state": (c_int, [c_void_p, ctypes.c_char_p]),
     "gff_load_state": (c_int, [c_void_p, ctypes.c_char_p]),
 }
@@ -274,6 +283,47 @@ def gff_project_noalloc(grid, projection, precision, mask9, x_dev, y_dev, stream
     if st != GFF_OK:
         raise GffError(st, "gff_project_noalloc failed")
     return st
+
+
+def gff_apply_operator_host(h, precision, mask9, x_host, y_host):
+    """x_host, y_host: host tensors/arrays (pinned torch tensors give asynchronous copies)."""
+    m, mp = _mask(mask9)
+    return _check(h, _lib.gff_apply_operator_host(h, int(precision), mp, _hostptr(x_host), _hostptr(y_host)))
+
+
+def _hostptr(a):
+    if hasattr(a, "data_ptr"):
+        return c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(c_void_p)
+    return c_void_p(int(a))
+
+
+def gff_cg_kernels_timed(h, precision, reps=10):
+    ms = (ctypes.c_float * 3)()
+    _check(h, _lib.gff_cg_kernels_timed(h, int(precision), int(reps), ctypes.cast(ms, c_void_p)))
+    return [ms[0], ms[1], ms[2]]
+
+
+def gff_measure_fp64_peak():
+    """Returns (GFLOP/s, ms of the best launch)."""
+    gf, ms = c_double(), c_double()
+    st = _lib.gff_measure_fp64_peak(ctypes.byref(gf), ctypes.byref(ms))
+    if st != GFF_OK:
+        raise GffError(st, "gff_measure_fp64_peak failed")
+    return gf.value, ms.value
+
+
+def gff_sync(h):
+    return _check(h, _lib.gff_sync(h))
+
+
+def gff_set_wait_limit(h, cycles):
+    return _check(h, _lib.gff_set_wait_limit(h, int(cycles)))
+
+
+def gff_set_return_map(h, mode):
+    return _check(h, _lib.gff_set_return_map(h, int(mode)))
 
 
 def gff_step(h, dt, Fbar, mask, Pbar):
@@ -426,6 +476,23 @@ def gff_get_fips(h, ngrains):
     _check(h, _lib.gff_get_fips(h, pc.ctypes.data_as(c_void_p), w.ctypes.data_as(c_void_p),
                                 fs.ctypes.data_as(c_void_p)))
     return pc, w, fs
+
+
+def gff_umat_tangent(n, F_dev, sigma_dev, Cab_dev, P_dev, K_dev, stream=0):
+    s = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", 0)
+    st = _lib.gff_umat_tangent(int(n), _dev(F_dev), _dev(sigma_dev), _dev(Cab_dev), _dev(P_dev), _dev(K_dev),
+                               c_void_p(s))
+    if st != GFF_OK:
+        raise GffError(st, "gff_umat_tangent failed")
+    return st
+
+
+def gff_get_band_fips(h, width, ngrains):
+    """Band-averaged W_cyc per grain and its maximum over the RVE."""
+    wb = np.zeros(ngrains)
+    mx = c_double()
+    _check(h, _lib.gff_get_band_fips(h, float(width), wb.ctypes.data_as(c_void_p), ctypes.byref(mx)))
+    return wb, mx.value
 
 
 def gff_save_state(h, path):

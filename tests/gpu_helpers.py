@@ -4,7 +4,7 @@ CPU oracle on the same seeded inputs)."""
 import numpy as np
 
 from oracle import materials as omat
-from oracle.solver import Material as OMaterial, SVK_CUBIC, SVK_ISO, CP_FCC
+from oracle.solver import Material as OMaterial, SVK_CUBIC, SVK_ISO, CP_FCC, NEO_HOOKE
 
 C11, C12, C44 = 168.4e9, 121.4e9, 75.4e9
 
@@ -33,12 +33,12 @@ def gpu_materials(kinds):
     out = {}
     for ph, kind in kinds.items():
         out[ph] = g.make_material({SVK_CUBIC: g.GFF_MAT_SVK_CUBIC, SVK_ISO: g.GFF_MAT_SVK_ISO,
-                                   CP_FCC: g.GFF_MAT_CP_FCC}[kind])
+                                   CP_FCC: g.GFF_MAT_CP_FCC, NEO_HOOKE: g.GFF_MAT_NEOHOOKE}[kind])
     return out
 
 
-def oracle_materials(kinds):
-    return {ph: OMaterial(kind) for ph, kind in kinds.items()}
+def oracle_materials(kinds, **kw):
+    return {ph: OMaterial(kind, **kw) for ph, kind in kinds.items()}
 
 
 def voxel_K_oracle(ms, F):

@@ -13,7 +13,9 @@ from rve_inputs import polycrystal, standard_normal
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(16, 16, 16), (6, 10, 12), (12, 48, 20), (40, 8, 30), (32, 32, 32)]  # (nz, ny, nx)
+# (nz, ny, nx): radix plans 16, 4x3 / 2x5 / 4x3, 4x3 / 16x3 / 4x5, 8x5 / 8 / 2x5x3, 8x4, and the
+# batch sizes 80 (16x5) and 96 (16x2x3, generic stages) with 48 (16x3)
+SHAPES = [(16, 16, 16), (6, 10, 12), (12, 48, 20), (40, 8, 30), (32, 32, 32), (96, 80, 48), (80, 80, 80)]
 MASKS = [None, np.array([0, 1, 1, 1, 1, 1, 1, 0, 1], dtype=np.uint8)]
 
 
@@ -55,7 +57,7 @@ def _svk_handle(shape, ngrains, seed, kind=sp.KIND_CONTINUOUS):
     return g, ms, h
 
 
-@pytest.mark.parametrize("shape", [(16, 16, 16), (6, 10, 12), (40, 8, 30)])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (6, 10, 12), (40, 8, 30), (48, 96, 80)])
 @pytest.mark.parametrize("kind", [sp.KIND_CONTINUOUS, sp.KIND_DISCRETE])
 def test_apply_matches_oracle(shape, kind):
     torch = torch_cuda()
@@ -178,5 +180,65 @@ def test_launch_shapes_give_identical_results(prec):
         assert rel_l2(outs[0], ref.reshape(9, -1)) <= (1e-12 if prec == 0 else 2e-6)
         with pytest.raises(g.GffError):
             g.gff_set_tiles(h, (512, 4, 256, 512, 0, 5), (512, 4, 256, 512, 0, 5))  # no TMA at W = 4
+    finally:
+        g.gff_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_bounded_wait_timeout_is_reported_and_recoverable(prec):
+    """The inverse FFT pass waits on an asynchronous (TMA) copy with a bounded
+    budget.  With the budget set to 0 every such wait gives up at once: the
+    pass records it, lets its copies land and leaves its planes of y as NaN;
+    gff_sync reports GFF_ERR_TIMEOUT once and clears the record.  With the
+    default budget restored the same handle computes the oracle's result."""
+    torch = torch_cuda()
+    shape = (16, 16, 16)
+    g, ms, h = _svk_handle(shape, 5, 3)
+    try:
+        g.gff_autotune(h)
+        g.gff_constitutive(h, 1.0)
+        x = _field(12, shape)
+        X = torch.from_numpy(x.reshape(9, -1).copy()).cuda()
+        if prec == 1:
+            X = X.float()
+        Y = torch.zeros_like(X)
+        g.gff_set_wait_limit(h, 0)
+        g.gff_apply_operator(h, prec, None, X, Y)  # queued: the device reports through gff_sync
+        with pytest.raises(g.GffError) as e:
+            g.gff_sync(h)
+        assert e.value.status == g.GFF_ERR_TIMEOUT
+        assert torch.isnan(Y).all()
+        g.gff_sync(h)  # the record was cleared
+        g.gff_set_wait_limit(h, -1)
+        g.gff_apply_operator(h, prec, None, X, Y)
+        g.gff_sync(h)
+        F = np.tile(np.eye(3).reshape(3, 3, 1, 1, 1), (1, 1) + shape)
+        _, K = voxel_K_oracle(ms, F)
+        ref = sp.GK(K, x, ms.L, sp.KIND_CONTINUOUS)
+        assert rel_l2(Y.double().cpu().numpy(), ref) <= (1e-12 if prec == 0 else 2e-6)
+    finally:
+        g.gff_destroy(h)
+
+
+def test_timeout_fails_the_increment_and_keeps_the_state():
+    """A load increment whose residual evaluation meets a timed-out wait
+    returns GFF_ERR_TIMEOUT (no cut-back: it is not a convergence failure)
+    and commits nothing; the next increment at the default budget runs."""
+    torch_cuda()
+    g, ms, h = _svk_handle((8, 8, 8), 3, 4)
+    try:
+        g.gff_autotune(h)
+        N = ms.n_voxels
+        Fbar = np.eye(3).ravel() + np.array([0.004, 0, 0, 0, -0.002, 0, 0, 0, -0.002])
+        zero9 = np.zeros(9)
+        g.gff_set_wait_limit(h, 0)
+        with pytest.raises(g.GffError) as e:
+            g.gff_step(h, 1.0, Fbar, np.zeros(9, np.uint8), zero9)
+        assert e.value.status == g.GFF_ERR_TIMEOUT
+        F = g.gff_get_field(h, g.GFF_FIELD_F, N)
+        assert np.array_equal(F, np.tile(np.eye(3).reshape(9, 1), (1, N)).ravel())
+        g.gff_set_wait_limit(h, -1)
+        rep = g.gff_step(h, 1.0, Fbar, np.zeros(9, np.uint8), zero9)
+        assert rep.residual <= 1e-8 and np.allclose(rep.Fmacro, Fbar, rtol=0, atol=1e-14)
     finally:
         g.gff_destroy(h)

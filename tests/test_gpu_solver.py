@@ -86,7 +86,7 @@ def test_homogeneous_medium_converges_without_newton_correction():
         g.gff_destroy(h)
 
 
-CP_HIST = cyclic_history(0.01, 1).head(14)  # through yield and past the first peak
+CP_HIST = cyclic_history(0.01, 1).head(14)  # through yield, 14 of the 20 increments up to the first peak
 
 
 @pytest.mark.parametrize("kind", [sp.KIND_CONTINUOUS, sp.KIND_DISCRETE])

@@ -16,7 +16,10 @@ from rve_inputs import standard_normal
 
 pytestmark = pytest.mark.gpu
 
-CASES = [((16, 16, 16), 0, 0), ((8, 12, 20), 1, 0), ((32, 32, 32), 0, 1), ((4, 64, 120), 1, 1)]  # (nz, ny, nx)
+# (nz, ny, nx).  The half spectrum takes 9 nz ny (nx/2 + 1) of the 9 * 32768 * 3/4 complex
+# values the scratch holds; with nx = 4 and 32768 voxels it fills them exactly.
+CASES = [((16, 16, 16), 0, 0), ((8, 12, 20), 1, 0), ((32, 32, 32), 0, 1), ((4, 64, 120), 1, 1),
+         ((64, 128, 4), 0, 0), ((64, 128, 4), 1, 1)]
 
 
 @pytest.mark.parametrize("shape,kind,prec", CASES)
