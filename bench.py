@@ -61,8 +61,10 @@ def parse():
     p.add_argument("--unet-train-rves", type=int, default=2, help="64^3 RVEs whose increments train the U-Net")
     p.add_argument("--cpu-applies", type=int, default=3, help="oracle applies in the CPU baseline sample")
     p.add_argument("--cpu-increments", type=int, default=1, help="1: time the oracle per load increment too")
-    p.add_argument("--batch-increments", type=int, default=2,
-                   help="increments of the 32-RVE batch, batched and one by one (0: skip)")
+    p.add_argument("--batch-cycle", type=int, default=80,
+                   help="increments of the 32-RVE batch run (80 = one cycle; 0: skip)")
+    p.add_argument("--batch-increments", type=int, default=8,
+                   help="increments of the 32-RVE batch compared with one handle after the other (0: skip)")
     p.add_argument("--grid", type=int, default=N_GRID, help="grid size (smaller grids only for profiling runs)")
     a = p.parse_args()
     return a
@@ -508,39 +510,68 @@ def cyclic_increments(g, torch, args, clock_index):
     return out
 
 
-def time_batch(g, torch, nsteps, precision):
+def time_batch(g, torch, cycle_increments, compare_increments, precision):
     """32 RVEs of 32^3 ... 96^3 voxels (10,956,800 in all), crystal plasticity,
-    first `nsteps` increments of a +-1 % cycle: gff_batch_run against running
-    the same RVEs one handle after the other."""
+    +-1 % strain cycle, mixed precision, extrapolated warm start: one full
+    cycle through gff_batch_run (one graph launch per increment) with the
+    per-grain Fatemi-Socie parameter at its end, and the first
+    `compare_increments` increments batched against running the same RVEs one
+    handle after the other."""
     try:
         from rve_inputs import batch_rves, cyclic_history, polycrystal
 
         specs = batch_rves()
-        hist = cyclic_history(0.01, 1).head(nsteps)
-        opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3)
-        out = {"rves": len(specs), "voxels": int(sum(n ** 3 for n, _, _ in specs)), "increments": nsteps}
-        for mode in ("batched", "one_by_one"):
+        full = cyclic_history(0.01, 1).head(cycle_increments)
+        opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3,
+                              warm_start=g.GFF_WARM_EXTRAPOLATE)
+        out = {"rves": len(specs), "voxels": int(sum(n ** 3 for n, _, _ in specs))}
+
+        def make():
             hs = [g.create_rve(polycrystal(n, ng, seed), {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts)
                   for n, ng, seed in specs]
+            for h in hs:
+                g.gff_set_warm_start(h, None, g.GFF_WARM_EXTRAPOLATE)
+                g.gff_autotune(h)
+            torch.cuda.synchronize()
+            return hs
+
+        if cycle_increments > 0:
+            hs = make()
             try:
-                for h in hs:
-                    g.gff_autotune(h)
-                torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                if mode == "batched":
-                    Pm, reps, stat = g.gff_batch_run(hs, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
-                    newton = [r[-1].newton_iters for r in reps]
-                else:
-                    newton = []
-                    for h in hs:
-                        _, rp = g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
-                        newton.append(rp[-1].newton_iters)
+                Pm, reps, stat = g.gff_batch_run(hs, full.dt, full.Fbar, full.mask, full.Pbar, full.cycle_start,
+                                                 raise_on_error=False)
                 torch.cuda.synchronize()
-                out["s_per_increment_" + mode] = (time.perf_counter() - t0) / nsteps
-                out["newton_last_" + mode] = newton
+                secs = time.perf_counter() - t0
+                fs_max = [float(max(g.gff_get_fips(h, ng)[2])) for h, (n, ng, seed) in zip(hs, specs)]
             finally:
                 for h in hs:
                     g.gff_destroy(h)
+            out["cycle"] = {"increments": full.nsteps, "s_per_increment_batched": secs / full.nsteps,
+                            "status": [int(x) for x in stat],
+                            "newton_mean": float(sum(r.newton_iters for rr in reps for r in rr) / (len(reps) * full.nsteps)),
+                            "cuts": int(sum(r.cuts for rr in reps for r in rr)),
+                            "fatemi_socie_max_per_rve": fs_max}
+        if compare_increments > 0:
+            part = full.head(compare_increments)
+            for mode in ("batched", "one_by_one"):
+                hs = make()
+                try:
+                    t0 = time.perf_counter()
+                    if mode == "batched":
+                        g.gff_batch_run(hs, part.dt, part.Fbar, part.mask, part.Pbar, part.cycle_start)
+                    else:
+                        for h in hs:
+                            g.gff_run_history(h, part.dt, part.Fbar, part.mask, part.Pbar, part.cycle_start)
+                    torch.cuda.synchronize()
+                    out["s_per_increment_%s_first_%d" % (mode, part.nsteps)] = (time.perf_counter() - t0) / part.nsteps
+                finally:
+                    for h in hs:
+                        g.gff_destroy(h)
+            a1 = out.get("s_per_increment_batched_first_%d" % part.nsteps)
+            a2 = out.get("s_per_increment_one_by_one_first_%d" % part.nsteps)
+            if a1 and a2:
+                out["batched_speedup_first_%d" % part.nsteps] = a2 / a1
         return out
     except Exception as e:  # report, do not lose the apply measurement
         return {"error": str(e)}
@@ -609,10 +640,11 @@ def run_gpu(args, world, rank, local):
     if args.increments > 0 and rank == 0:
         inc = cyclic_increments(g, torch, args, clock_index)
     batch = None
-    if args.batch_increments > 0 and rank == 0:
+    if (args.batch_cycle > 0 or args.batch_increments > 0) and rank == 0:
         batch = {"workload": "32 RVEs (7x32^3, 7x48^3, 6x64^3, 6x80^3, 6x96^3; 50-300 grains, seeds 4000+i), FCC "
-                             "crystal plasticity, +-1 pct cycle, mixed precision, Newton tol 1e-6",
-                 "mixed": time_batch(g, torch, args.batch_increments, 1)}
+                             "crystal plasticity, +-1 pct cycle, mixed precision, Newton tol 1e-6, extrapolated "
+                             "warm start",
+                 "mixed": time_batch(g, torch, args.batch_cycle, args.batch_increments, 1)}
 
     if rank != 0:
         return

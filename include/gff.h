@@ -234,6 +234,20 @@ gff_status gff_sync(gff_handle* h);
  * tests of that path; the default is the only sensible value otherwise. */
 gff_status gff_set_wait_limit(gff_handle* h, long long cycles);
 
+/* Small-strain variant of the variational method (the paper's solver runs at
+ * small and finite strains, Sect. 2.3).  GFF_STRAIN_SMALL: the unknown field
+ * is the infinitesimal strain eps (stored, read and set as GFF_FIELD_F,
+ * starting at 0); the phases must be linear elastic (GFF_MAT_SVK_CUBIC /
+ * GFF_MAT_SVK_ISO read as sigma = C : eps, tangent C), GFF_FIELD_P is the
+ * Cauchy stress; gff_step's Fbar is the prescribed average strain and Pbar
+ * the prescribed average stress; the projection onto compatible fields is the
+ * symmetric one, y = n (x) a + a (x) n - (n . a) n (x) n with a = sym(x^) n
+ * and n the unit continuous or discrete (GFF_PROJ_*) wave vector, and the
+ * zero frequency takes the mask as in the finite-strain case.  Switching
+ * resets the state.  gff_batch_run rejects small-strain handles. */
+enum { GFF_STRAIN_FINITE = 0, GFF_STRAIN_SMALL = 1 };
+gff_status gff_set_strain_measure(gff_handle* h, int mode);
+
 /* How the crystal-plasticity return maps are iterated (the paper leaves it
  * open; the root of the backward-Euler residual of Eq. gamma_dot is the same):
  * GFF_RETURN_MAP_DEFAULT: Newton steps with the small-elastic-strain Jacobian
@@ -300,17 +314,55 @@ gff_status gff_run_history(gff_handle* h, int nsteps, const double* dt, const do
  * hs: n distinct handles (1 <= n <= 64) on one device with identical
  * precision, projection, tolerances and caps, each with microstructure and
  * materials set.  dt, Fbar, mask, Pbar, cycle_start: as in gff_run_history
- * (one history for all).  Every Newton/CG step of all RVEs runs as one launch
- * per kernel; the CG iterations are replayed from a captured CUDA graph.
- * Each RVE's results are bitwise those of gff_run_history on its own handle.
+ * (one history for all).  Each increment of all RVEs is one launch of a CUDA
+ * graph (captured once per stress-control mask) whose Newton and CG loops run
+ * on the device as conditional WHILE nodes, bounded by newton_max + 1 and
+ * cg_max iterations, with per-RVE status words; RVEs of one grid size run the
+ * apply kernels with the launch shapes tuned for that size, each size class
+ * on its own stream inside the graph.  RVEs whose handle has warm-start mode
+ * GFF_WARM_EXTRAPOLATE start from the extrapolated guess (other modes start
+ * from the zero-fluctuation start).  An RVE whose increment fails in the batch
+ * is redone by gff_step on its own handle, cut-backs included; if that fails
+ * too, the RVE keeps its last committed state, gets the status in per_rve and
+ * leaves the batch while the others go on.  An RVE that converges in the
+ * batch gets bitwise the result of gff_run_history on its own handle.
  * Pmacro_out (n x nsteps x 9), reports (n x nsteps), per_rve (n): may be NULL.
- * An RVE whose increment fails keeps its last committed state, gets its
- * status in per_rve and leaves the batch; the others go on.  Returns GFF_OK
- * when all RVEs finished, else the first failing RVE's status.  The handles'
- * streams are synchronised before and after the call. */
+ * Returns GFF_OK when all RVEs finished, else the first failing RVE's status.
+ * The handles' streams are synchronised before and after the call. */
 gff_status gff_batch_run(int n, gff_handle* const* hs, int nsteps, const double* dt, const double* Fbar,
                          const uint8_t* mask, const double* Pbar, const uint8_t* cycle_start,
                          double* Pmacro_out, gff_step_report* reports, gff_status* per_rve);
+
+/* Automatic time incrementation (Sect. 2.3 names an automatic time
+ * incrementation algorithm without stating it; this is the FE-style rule).
+ * The macroscopic path is piecewise linear between nknots knots: at time
+ * t_knots[k] the targets are Fbar_knots[9k..] (strain-controlled components)
+ * and Pbar_knots[9k..] (stress-controlled ones, mask[9] for the whole path);
+ * t_knots[0] is the time of the committed state.  Increments never step
+ * across a knot.  The first increment takes dt_initial; after each accepted
+ * increment the next size is
+ *   the size that worked, if gff_step had to cut the increment;
+ *   dt * grow, if it converged in at most easy_newton Newton corrections
+ *     (and was not shortened by a knot);
+ *   dt * shrink, if it needed hard_newton corrections or more;
+ *   dt otherwise;
+ * clamped to [dt_min, dt_max].  cycle_start (nknots, may be NULL) restarts
+ * the FIP accumulators when the path reaches a flagged knot.  Outputs (host,
+ * up to max_increments entries each; t_out, Pmacro_out, reports may be NULL):
+ * *n_out increments, their end times, average P (x 9) and reports.  Stops at
+ * the first failing increment (its status), or with GFF_ERR_NO_CONVERGENCE
+ * if max_increments do not reach the end of the path. */
+typedef struct {
+    double dt_initial, dt_min, dt_max;
+    double grow, shrink;
+    int easy_newton, hard_newton;
+} gff_auto_options;
+/* dt_initial 0.05, dt_min 1e-6, dt_max 1, grow 1.5, shrink 0.75, easy 3, hard 8 */
+void gff_auto_options_default(gff_auto_options* a);
+gff_status gff_run_auto(gff_handle* h, int nknots, const double* t_knots, const double* Fbar_knots,
+                        const uint8_t* mask, const double* Pbar_knots, const uint8_t* cycle_start,
+                        const gff_auto_options* ao, int max_increments, int* n_out, double* t_out,
+                        double* Pmacro_out, gff_step_report* reports);
 
 /* ------------------------------------------------------------------------
  * Warm starts (not in the paper; Sect. 2.1 leaves the Newton initial guess

@@ -42,8 +42,11 @@ class Material:
 
 class Options:
     def __init__(self, projection=sp.KIND_CONTINUOUS, newton_tol=1e-8, cg_tol=1e-8,
-                 newton_max=30, cg_max=2000, fs_k=0.5, fs_sigma_y=153e6):
+                 newton_max=30, cg_max=2000, fs_k=0.5, fs_sigma_y=153e6, small_strain=False):
         self.projection = projection
+        # small-strain variant (Sect. 2.3): the field is the strain eps, linear
+        # elastic phases sigma = C : eps, symmetric projection G^s
+        self.small_strain = small_strain
         self.newton_tol = newton_tol
         self.cg_tol = cg_tol
         self.newton_max = newton_max
@@ -114,7 +117,8 @@ class OracleRVE:
                     "mat": M,
                 }
             )
-        self.F = voxels_to_field(np.broadcast_to(np.eye(3), (self.V, 3, 3)).copy(), self.shape)
+        F0 = np.zeros((3, 3)) if self.opt.small_strain else np.eye(3)
+        self.F = voxels_to_field(np.broadcast_to(F0, (self.V, 3, 3)).copy(), self.shape)
         self.Fpi = np.broadcast_to(np.eye(3), (self.V, 3, 3)).copy()
         self.chi = np.zeros((self.V, 12))
         self.acc = fips.new_accumulators(self.V)
@@ -133,7 +137,12 @@ class OracleRVE:
             if idx.size == 0:
                 continue
             M = g["mat"]
-            if M.kind == CP_FCC:
+            if self.opt.small_strain:
+                if M.kind not in (SVK_CUBIC, SVK_ISO):
+                    raise ValueError("the small-strain variant takes linear elastic phases only")
+                P[idx] = np.einsum("ijkl,vkl->vij", g["C"], Fv[idx])  # Cauchy stress C : eps
+                K[idx] = g["C"][None]
+            elif M.kind == CP_FCC:
                 out = mat.cp_return_map(Fv[idx], self.Fpi[idx], self.chi[idx], dt, g["S0"], g["C"], M.cp)
                 P[idx], K[idx] = out["P"], out["K"]
                 trial["Fpi"][idx] = out["Fpi"]
@@ -154,6 +163,8 @@ class OracleRVE:
 
     # ------------------------------------------------------------------ operators
     def G_M(self, A, mask9):
+        if self.opt.small_strain:
+            return sp.G_sym(A, self.L, self.opt.projection, mask9)
         return sp.G(A, self.L, self.opt.projection, mask9)
 
     def residual(self, P, mask9, Pbar):
@@ -184,7 +195,7 @@ class OracleRVE:
                 break
 
             def apply(x):
-                return sp.GK(K, x, self.L, self.opt.projection, mask9)
+                return self.G_M(sp.ddot42(K, x), mask9)
 
             dFx, ncg, _ = cg(apply, b, self.opt.cg_tol, self.opt.cg_max, 0.1 * self.opt.newton_tol * nP)
             rep["cg"].append(ncg)

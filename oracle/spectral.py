@@ -115,3 +115,35 @@ def ddot42(K, A):
 def GK(K, A, L=(1.0, 1.0, 1.0), kind=KIND_CONTINUOUS, mask9=None):
     """Tangent operator G_K(A) = G(K : A) (Eq. newlinop)."""
     return G(ddot42(K, A), L, kind, mask9)
+
+
+# --------------------------------------------------------------------------- small-strain variant
+def project_hat_sym(xh, shape, L=(1.0, 1.0, 1.0), kind=KIND_CONTINUOUS, mask9=None):
+    """Orthogonal projection onto compatible symmetric (small) strains,
+    sym(q (x) u), at every frequency: with n the unit scaled wave vector and
+    a = sym(x^) n,  y^ = n (x) a + a (x) n - (n . a) n (x) n.  Zero where the
+    finite-strain operator is zero; the zero frequency takes the mask."""
+    qt, zero, vanish = wavevectors(shape, L, kind)
+    qq = np.einsum("m...,m...->...", qt, qt)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        n = np.where(vanish[None], 0.0, qt / np.sqrt(np.where(vanish, 1.0, qq))[None])
+    xs = 0.5 * (xh + np.swapaxes(xh, 0, 1))
+    a = np.einsum("jk...,k...->j...", xs, n)
+    na = np.einsum("j...,j...->...", n, a)
+    yh = np.einsum("i...,j...->ij...", n, a) + np.einsum("i...,j...->ij...", a, n) - na * np.einsum(
+        "i...,j...->ij...", n, n)
+    if mask9 is not None:
+        m = np.asarray(mask9, dtype=np.float64).reshape(3, 3)
+        yh[:, :, 0, 0, 0] = m * xh[:, :, 0, 0, 0]
+    return yh
+
+
+def G_sym(A, L=(1.0, 1.0, 1.0), kind=KIND_CONTINUOUS, mask9=None):
+    """Small-strain equilibrium operator F^-1{ G^s : F(A) } of a real field A (3, 3, nz, ny, nx)."""
+    shape = A.shape[2:]
+    return np.real(ifft3(project_hat_sym(fft3(A), shape, L, kind, mask9)))
+
+
+def GK_sym(K, A, L=(1.0, 1.0, 1.0), kind=KIND_CONTINUOUS, mask9=None):
+    """Small-strain tangent operator G^s(K : A)."""
+    return G_sym(ddot42(K, A), L, kind, mask9)

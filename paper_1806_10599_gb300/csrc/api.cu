@@ -254,6 +254,8 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
         const int ph = phase[g];
         if (ph < 0 || ph >= 8 || !h->mat_set[ph]) return fail(h, GFF_ERR_STATE, "grain %d: phase %d has no material", g, ph);
         const gff_material& mt = h->mat[ph];
+        if (h->small_strain && mt.kind != GFF_MAT_SVK_CUBIC && mt.kind != GFF_MAT_SVK_ISO)
+            return fail(h, GFF_ERR_ARG, "grain %d: the small-strain variant takes linear elastic phases only", g);
         double R[9];
         quat_rot(&quat[4 * (size_t)g], R);
         stiffness(mt, R, &C[81 * (size_t)g]);
@@ -340,6 +342,7 @@ gff_status fetch(gff_handle* h, const double* d, int n, double* out) {
 ProjArgs proj_args(const gff_handle* h, const uint8_t* mask9) {
     ProjArgs pa;
     pa.kind = h->opt.projection;
+    pa.sym = h->small_strain;
     for (int c = 0; c < 9; ++c) pa.mask[c] = (mask9 && mask9[c]) ? 1.0f : 0.0f;
     return pa;
 }
@@ -476,8 +479,14 @@ static gff_status reset_state(gff_handle* h) {
     std::vector<double> eye(9 * N);
     for (int c = 0; c < 9; ++c)
         for (long long v = 0; v < N; ++v) eye[c * N + v] = (c % 4 == 0) ? 1.0 : 0.0;
-    GFF_TRY(cudaMemcpy(h->d_F, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
-    GFF_TRY(cudaMemcpy(h->d_Fk, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
+    // finite strain starts at F = I, the small-strain variant at eps = 0
+    if (h->small_strain) {
+        GFF_TRY(cudaMemset(h->d_F, 0, 9 * N * sizeof(double)));
+        GFF_TRY(cudaMemset(h->d_Fk, 0, 9 * N * sizeof(double)));
+    } else {
+        GFF_TRY(cudaMemcpy(h->d_F, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
+        GFF_TRY(cudaMemcpy(h->d_Fk, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
+    }
     GFF_TRY(cudaMemcpy(h->d_Fpi, eye.data(), 9 * N * sizeof(double), cudaMemcpyHostToDevice));
     GFF_TRY(cudaMemset(h->d_chi, 0, 12 * N * sizeof(double)));
     GFF_TRY(cudaMemset(h->d_P, 0, 9 * N * sizeof(double)));
@@ -732,6 +741,14 @@ GFF_EXPORT gff_status gff_set_wait_limit(gff_handle* h, long long cycles) {
     if (!h) return GFF_ERR_ARG;
     h->g.wait_cycles = cycles < 0 ? BULK_WAIT_CYCLES : cycles;
     return GFF_OK;
+}
+
+GFF_EXPORT gff_status gff_set_strain_measure(gff_handle* h, int mode) {
+    if (!h || (mode != GFF_STRAIN_FINITE && mode != GFF_STRAIN_SMALL))
+        return fail(h, GFF_ERR_ARG, "strain measure must be 0 or 1");
+    h->small_strain = mode == GFF_STRAIN_SMALL ? 1 : 0;
+    h->grains_ready = false;  // phases are checked against the variant again
+    return h->have_ms ? reset_state(h) : GFF_OK;
 }
 
 GFF_EXPORT gff_status gff_set_return_map(gff_handle* h, int mode) {
@@ -1171,6 +1188,74 @@ GFF_EXPORT gff_status gff_run_history(gff_handle* h, int nsteps, const double* d
         if (reports) reports[k] = rep;
         if (st != GFF_OK) return st;
         if (Pmacro_out) std::memcpy(Pmacro_out + 9 * k, rep.Pmacro, 9 * sizeof(double));
+    }
+    return GFF_OK;
+}
+
+GFF_EXPORT void gff_auto_options_default(gff_auto_options* a) {
+    if (!a) return;
+    a->dt_initial = 0.05;
+    a->dt_min = 1e-6;
+    a->dt_max = 1.0;
+    a->grow = 1.5;
+    a->shrink = 0.75;
+    a->easy_newton = 3;
+    a->hard_newton = 8;
+}
+
+// Automatic time incrementation along a piecewise-linear macroscopic path.
+GFF_EXPORT gff_status gff_run_auto(gff_handle* h, int nknots, const double* t_knots, const double* Fbar_knots,
+                                   const uint8_t* mask, const double* Pbar_knots, const uint8_t* cycle_start,
+                                   const gff_auto_options* ao, int max_increments, int* n_out, double* t_out,
+                                   double* Pmacro_out, gff_step_report* reports) {
+    if (!h || nknots < 2 || !t_knots || !Fbar_knots || !mask || !Pbar_knots || !ao || max_increments < 1 || !n_out)
+        return fail(h, GFF_ERR_ARG, "bad automatic-incrementation args");
+    for (int k = 1; k < nknots; ++k)
+        if (!(t_knots[k] > t_knots[k - 1])) return fail(h, GFF_ERR_ARG, "knot times must increase");
+    if (!(ao->dt_min > 0) || !(ao->dt_initial >= ao->dt_min) || !(ao->dt_max >= ao->dt_initial) || !(ao->grow >= 1) ||
+        !(ao->shrink > 0 && ao->shrink <= 1) || ao->easy_newton < 0 || ao->hard_newton <= ao->easy_newton)
+        return fail(h, GFF_ERR_ARG, "automatic-incrementation options out of range");
+    *n_out = 0;
+    gff_status st = ensure_grains(h);
+    if (st != GFF_OK) return st;
+    double t = t_knots[0], dt = ao->dt_initial;
+    int seg = 0;  // current knot interval [t_knots[seg], t_knots[seg + 1]]
+    const double tend = t_knots[nknots - 1];
+    const double eps_t = 1e-12 * (tend - t_knots[0]);
+    while (t < tend - eps_t) {
+        if (*n_out >= max_increments) return fail(h, GFF_ERR_NO_CONVERGENCE, "more than %d increments needed", max_increments);
+        while (seg + 1 < nknots - 1 && t >= t_knots[seg + 1] - eps_t) ++seg;
+        // a knot flagged as a cycle start restarts the FIP accumulators when the path reaches it
+        if (cycle_start && std::fabs(t - t_knots[seg]) <= eps_t && cycle_start[seg]) {
+            if ((st = gff_reset_fips(h)) != GFF_OK) return st;
+        }
+        double t1 = t + dt;
+        if (t1 > t_knots[seg + 1] - eps_t) t1 = t_knots[seg + 1];  // never step across a knot
+        const double w = (t1 - t_knots[seg]) / (t_knots[seg + 1] - t_knots[seg]);
+        double Fb[9], Pb[9];
+        for (int c = 0; c < 9; ++c) {
+            Fb[c] = (1 - w) * Fbar_knots[9 * seg + c] + w * Fbar_knots[9 * (seg + 1) + c];
+            Pb[c] = (1 - w) * Pbar_knots[9 * seg + c] + w * Pbar_knots[9 * (seg + 1) + c];
+        }
+        gff_step_report rep;
+        st = gff_step(h, t1 - t, Fb, mask, Pb, &rep);
+        if (reports) reports[*n_out] = rep;
+        if (st != GFF_OK) return st;
+        if (t_out) t_out[*n_out] = t1;
+        if (Pmacro_out) std::memcpy(Pmacro_out + 9 * *n_out, rep.Pmacro, 9 * sizeof(double));
+        ++*n_out;
+        const double taken = t1 - t;
+        t = t1;
+        // the next step: the size that worked after cut-backs, grown after an easy
+        // increment, shrunk after a hard one; within [dt_min, dt_max]
+        double nd = dt;
+        if (rep.cuts > 0)
+            nd = taken * std::ldexp(1.0, -rep.cuts);
+        else if (rep.newton_iters <= ao->easy_newton && taken >= 0.999 * dt)
+            nd = dt * ao->grow;
+        else if (rep.newton_iters >= ao->hard_newton)
+            nd = dt * ao->shrink;
+        dt = std::min(std::max(nd, ao->dt_min), ao->dt_max);
     }
     return GFF_OK;
 }

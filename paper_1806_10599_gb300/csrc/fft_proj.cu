@@ -700,6 +700,90 @@ __global__ void __launch_bounds__(256) k_zproj(typename C2<T>::t* __restrict__ s
     zproj_body<T, W>(spec, g, pa, blockIdx.x, sm_raw);
 }
 
+// ---------------------------------------------------------------- small-strain variant: symmetric projection
+// Compatible small strains are sym(q (x) u).  The orthogonal projection of a
+// tensor A onto them at a frequency with unit (scaled) wave vector n is
+//   y = n (x) a + a (x) n - (n . a) n (x) n,   a = sym(A) n,
+// which couples all nine components: a block takes the 9 components of W
+// consecutive (ky, kx) columns, [9][nz][W] in shared memory.
+template <typename T> constexpr int zsym_width() { return sizeof(T) == 8 ? 4 : 8; }
+template <typename T> size_t zsym_smem(const GridDev& g) {
+    constexpr int W = zsym_width<T>();
+    return (size_t)9 * g.nz * W * sizeof(typename C2<T>::t) + ztables_bytes<T>(g.nz, g.ny, g.nxh, W) + 16;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_zproj_sym(typename C2<T>::t* __restrict__ spec, GridDev g, ProjArgs pa,
+                                                  const int* __restrict__ skip) {
+    using C = typename C2<T>::t;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int nz = g.nz, nx = g.nx, ny = g.ny;
+    C* s = reinterpret_cast<C*>(sm_raw);  // [9][nz][W]
+    const ZTables<T> tb = ztables_at<T>(reinterpret_cast<unsigned char*>(s + 9 * nz * W), g);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int nF = ny * g.nxh;
+    const int f0 = blockIdx.x * W;
+    zproj_tables<T>(g, pa, tb);
+    zproj_columns<T, W>(g, f0, tb);
+    for (int e = tid; e < 9 * nz * W; e += nthr) {
+        const int w = e % W, cz = e / W;  // cz = component * nz + z
+        const int f = f0 + w;
+        s[e] = f < nF ? spec[(long long)cz * nF + f] : mk<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    fft_lines<T, false>(s, tb.twz, g.az, W, 1, 9, nz * W, W, tid, nthr);
+    for (int e = tid; e < nz * W; e += nthr) {
+        const int w = e % W, pz = e / W;
+        const int ck = tb.colk[w];
+        if (ck < 0) continue;
+        const int kx = ck & 0xffff, ky = ck >> 16, kz = tb.fqz[pz];
+        C* p0 = s + pz * W + w;
+        C v[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) v[c] = p0[c * nz * W];
+        if (kx == 0 && ky == 0 && kz == 0) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = cscale(v[c], (T)pa.mask[c]);
+        } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
+#pragma unroll
+            for (int c = 0; c < 9; ++c) v[c] = mk<C>((T)0, (T)0);
+        } else {
+            const T qa = tb.qx[kx], qb = tb.qy[ky], qd = tb.qz[kz];
+            const T inv = rnorm3(qa, qb, qd);
+            const T n[3] = {qa * inv, qb * inv, qd * inv};
+            C a[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {  // a_j = sym(A)_jk n_k
+                T re = (T)0, im = (T)0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    re += (T)0.5 * (v[3 * j + k].x + v[3 * k + j].x) * n[k];
+                    im += (T)0.5 * (v[3 * j + k].y + v[3 * k + j].y) * n[k];
+                }
+                a[j] = mk<C>(re, im);
+            }
+            const C na = mk<C>(n[0] * a[0].x + n[1] * a[1].x + n[2] * a[2].x,
+                               n[0] * a[0].y + n[1] * a[1].y + n[2] * a[2].y);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    v[3 * i + j] = mk<C>(n[i] * a[j].x + a[i].x * n[j] - na.x * n[i] * n[j],
+                                         n[i] * a[j].y + a[i].y * n[j] - na.y * n[i] * n[j]);
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) p0[c * nz * W] = v[c];
+    }
+    __syncthreads();
+    fft_lines<T, true>(s, tb.twz, g.az, W, 1, 9, nz * W, W, tid, nthr);
+    for (int e = tid; e < 9 * nz * W; e += nthr) {
+        const int w = e % W, cz = e / W;
+        const int f = f0 + w;
+        if (f < nF) spec[(long long)cz * nF + f] = s[e];
+    }
+}
+
 // Persistent z pass on the tensor-memory accelerator: the half spectrum seen as
 // a 3-D tensor [9 components][nz][ny nxh columns] (64-bit elements), a strip
 // (3 components of one tensor row, all z, W columns) is one TMA box whose
@@ -1133,6 +1217,16 @@ cudaError_t launch_z(const GridDev& g, int W, int threads, typename C2<T>::t* sp
 
 template <typename T> int tune_index() { return sizeof(T) == 8 ? 0 : 1; }
 
+template <typename T>
+cudaError_t launch_zsym(const GridDev& g, typename C2<T>::t* spec, const ProjArgs& pa, const int* skip,
+                        cudaStream_t st) {
+    constexpr int W = zsym_width<T>();
+    const size_t sm = zsym_smem<T>(g);
+    allow_smem(k_zproj_sym<T, W>, sm);
+    k_zproj_sym<T, W><<<(g.ny * g.nxh + W - 1) / W, 256, sm, st>>>(spec, g, pa, skip);
+    return cudaGetLastError();
+}
+
 // ---- TMA z pass: tensor maps and launch
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -1516,7 +1610,9 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], h->stream);
     // the TMA pass addresses the handle's own spectrum through its tensor map
-    if (tn.z_blocks > 0 && static_cast<const void*>(spec) == h->d_spec)
+    if (pa.sym)
+        e = launch_zsym<T>(g, spec, pa, skip, h->stream);
+    else if (tn.z_blocks > 0 && static_cast<const void*>(spec) == h->d_spec)
         e = launch_z_tma<T>(const_cast<gff_handle*>(h), tn.wz, tn.t_z, tn.z_blocks, pa, skip, h->stream);
     else
         e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, skip, h->stream);

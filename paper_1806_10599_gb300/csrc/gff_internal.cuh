@@ -49,6 +49,7 @@ struct GridDev {
 struct ProjArgs {
     int kind;        // GFF_PROJ_*
     float mask[9];   // 1 = stress-controlled component (zero frequency keeps it)
+    int sym = 0;     // 1: small-strain variant, projection onto compatible symmetric fields
 };
 
 // Output epilogue of the inverse plane pass: out = scale * y + add[c].
@@ -180,6 +181,7 @@ struct gff_handle {
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
     int cp_exact_only = 0;     // 1: every return map runs the exact Newton from dg = 0 (gff_set_return_map)
+    int small_strain = 0;      // 1: small-strain variant: d_F holds the strain, sigma = C : eps, symmetric projection
     int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out bulk-copy waits,
                                // [4] return-map fallbacks, [5] local Newton iterations
     // reductions
@@ -326,11 +328,16 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
                                 int part = CONST_ALL);
 cudaError_t launch_fip_accumulate(gff_handle* h);
 cudaError_t preload_constitutive();
-// Batched constitutive update of the RVEs hs[0..n) (skip[r] != 0: RVE r is left alone);
-// cpflag[r] counts return-map failures of RVE r.
-cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
-                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st,
-                                      int part = CONST_ALL);
+// Batched constitutive update of the RVEs hs[0..n): the per-RVE arguments are
+// uploaded once (skip_dev[2 r] != 0: RVE r is left alone; cpflag_dev[r] counts
+// its return-map failures; warm[r] or, when warm_dev is set, warm_dev[r] != 0
+// at run time starts its return maps from the stored slips), then launched as
+// often as needed -- also inside a captured graph.
+cudaError_t upload_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
+                                      const int* warm_dev, const int* skip_dev, int* cpflag_dev, void* scratch_dev,
+                                      int* blocks_out, cudaStream_t st);
+cudaError_t launch_constitutive_batch_uploaded(const void* scratch_dev, int n, int blocks, int tangent, int part,
+                                               cudaStream_t st);
 size_t constitutive_batch_scratch_bytes();
 cudaError_t launch_fip_reset(gff_handle* h);
 // Appendix A: (F, Cauchy stress, Jaumann-rate tangent C^ab) -> (P, K) for n voxels, SoA [9][n] / [81][n]

@@ -682,7 +682,9 @@ struct ConstArgs {
     const float* G32;  // [ngrains][G32_STRIDE]: S0 and C in FP32 for the FP32 tangent
     const double* H;  // [ngrains][144]: P [5][12], C5^-1 [5][5] of the small-strain Jacobian (cp_correction_lowrank)
     int warm;         // 1: start the local Newton from dg (previous iterate)
+    const int* warm_dev;  // device flag (may be null): when set, start warm as well
     int exact;        // 1: skip the small-strain iteration, exact Newton from dg = 0 only
+    int small;        // 1: small-strain variant, F holds the strain: P = C : F (Cauchy stress), K = C
     double rtol;      // return-map tolerance (return_map_tol)
     const int* gkind;
     const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
@@ -774,21 +776,22 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
             return;
         }
         double dg0[12];
-        if (a.warm)
+        const bool warm = a.warm || (a.warm_dev && *a.warm_dev);
+        if (warm)
             for (int s2 = 0; s2 < NSLIP; ++s2) dg0[s2] = a.dg[s2 * N + v];
         CPOut o;
         if (PART == PART_P) {
-            cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
+            cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
                               (double*)nullptr, o, a.exact != 0);
         } else if (F32T) {
             float K[81];
             cp_update<float>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, g32 + G32_S0, g32 + G32_C, pr,
-                             a.warm ? dg0 : nullptr, K, o, a.exact != 0);
+                             warm ? dg0 : nullptr, K, o, a.exact != 0);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
             double K[81];
-            cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, a.warm ? dg0 : nullptr,
+            cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
                               K, o, a.exact != 0);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
@@ -812,7 +815,11 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         }
     } else {
         double P[9], K[81];
-        if (kind == GFF_MAT_NEOHOOKE) {  // through the umat interface (Appendix A)
+        if (a.small) {  // linear elasticity at small strain: sigma = C : eps, tangent C
+            c_ddot(C, F, P);
+#pragma unroll
+            for (int q = 0; q < 81; ++q) K[q] = __ldg(C + q);
+        } else if (kind == GFF_MAT_NEOHOOKE) {  // through the umat interface (Appendix A)
             const double lam = __ldg(C + 4), mu = __ldg(C + 10);  // C_1122, C_1212 of the isotropic C
             double sg[9], b[9], J;
             neohooke_umat(F, lam, mu, sg, b, J);
@@ -1124,7 +1131,9 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.G32 = h->d_geo32;
     a.H = h->d_nrm + 41LL * h->ngrains;
     a.warm = warm ? 1 : 0;
+    a.warm_dev = nullptr;
     a.exact = h->cp_exact_only;
+    a.small = h->small_strain;
     a.rtol = return_map_tol(h->opt.newton_tol);
     a.gkind = h->d_gkind;
     a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
@@ -1160,9 +1169,9 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     return cudaGetLastError();
 }
 
-cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
-                                      const int* skip_dev, int* cpflag_dev, void* scratch_dev, cudaStream_t st,
-                                      int part) {
+cudaError_t upload_constitutive_batch(gff_handle* const* hs, int n, double dt, int tangent, const bool* warm,
+                                      const int* warm_dev, const int* skip_dev, int* cpflag_dev, void* scratch_dev,
+                                      int* blocks_out, cudaStream_t st) {
     ConstArgs args[MAX_BATCH];
     int start[MAX_BATCH + 1];
     start[0] = 0;
@@ -1176,7 +1185,9 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.G32 = h->d_geo32;
         a.H = h->d_nrm + 41LL * h->ngrains;
         a.warm = warm[r] ? 1 : 0;
+        a.warm_dev = warm_dev ? warm_dev + r : nullptr;
         a.exact = h->cp_exact_only;
+        a.small = h->small_strain;
         a.rtol = return_map_tol(h->opt.newton_tol);
         a.gkind = h->d_gkind;
         a.gprm = h->d_nrm + 36LL * h->ngrains;
@@ -1197,24 +1208,32 @@ cudaError_t launch_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         start[r + 1] = start[r] + (int)((h->N + TPB - 1) / TPB);
     }
     unsigned char* d = static_cast<unsigned char*>(scratch_dev);
-    ConstArgs* dargs = reinterpret_cast<ConstArgs*>(d);
-    int* dstart = reinterpret_cast<int*>(d + sizeof(ConstArgs) * MAX_BATCH);
-    cudaError_t e = cudaMemcpyAsync(dargs, args, sizeof(ConstArgs) * n, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dstart, start, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaMemcpyAsync(d, args, sizeof(ConstArgs) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d + sizeof(ConstArgs) * MAX_BATCH, start, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host arrays above go out of scope
+    *blocks_out = start[n];
+    return e;
+}
+
+cudaError_t launch_constitutive_batch_uploaded(const void* scratch_dev, int n, int blocks, int tangent, int part,
+                                               cudaStream_t st) {
+    const unsigned char* d = static_cast<const unsigned char*>(scratch_dev);
+    const ConstArgs* dargs = reinterpret_cast<const ConstArgs*>(d);
+    const int* dstart = reinterpret_cast<const int*>(d + sizeof(ConstArgs) * MAX_BATCH);
     const bool f32 = tangent == TANGENT_F32;
     switch (part) {
         case CONST_P:
-            if (f32) k_constitutive_batch<true, PART_P><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
-            else k_constitutive_batch<false, PART_P><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            if (f32) k_constitutive_batch<true, PART_P><<<blocks, TPB, 0, st>>>(dargs, dstart, n);
+            else k_constitutive_batch<false, PART_P><<<blocks, TPB, 0, st>>>(dargs, dstart, n);
             break;
         case CONST_K:
-            if (f32) k_constitutive_batch<true, PART_K><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
-            else k_constitutive_batch<false, PART_K><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            if (f32) k_constitutive_batch<true, PART_K><<<blocks, TPB, 0, st>>>(dargs, dstart, n);
+            else k_constitutive_batch<false, PART_K><<<blocks, TPB, 0, st>>>(dargs, dstart, n);
             break;
         default:
-            if (f32) k_constitutive_batch<true, PART_ALL><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
-            else k_constitutive_batch<false, PART_ALL><<<start[n], TPB, 0, st>>>(dargs, dstart, n);
+            if (f32) k_constitutive_batch<true, PART_ALL><<<blocks, TPB, 0, st>>>(dargs, dstart, n);
+            else k_constitutive_batch<false, PART_ALL><<<blocks, TPB, 0, st>>>(dargs, dstart, n);
     }
     return cudaGetLastError();
 }

@@ -386,6 +386,7 @@ cudaError_t warm_guess(gff_unet* u, gff_handle* h, const double* d9, int* applie
     if (e != cudaSuccess) return e;
     ProjArgs pa;
     pa.kind = h->opt.projection;
+    pa.sym = h->small_strain;
     for (int c = 0; c < 9; ++c) pa.mask[c] = 0.f;  // compatible, zero mean
     OutArgs oa;
     oa.scale = 1.0 / (double)h->N;

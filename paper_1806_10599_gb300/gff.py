@@ -29,6 +29,7 @@ GFF_WARM_OFF, GFF_WARM_NET_IF_BETTER, GFF_WARM_NET, GFF_WARM_EXTRAPOLATE = 0, 1,
 UNET_IN = 32  # input channels of the warm-start network
 GFF_PREC_FP64, GFF_PREC_MIXED = 0, 1
 GFF_RETURN_MAP_DEFAULT, GFF_RETURN_MAP_EXACT = 0, 1
+GFF_STRAIN_FINITE, GFF_STRAIN_SMALL = 0, 1
 GFF_MAT_SVK_CUBIC, GFF_MAT_SVK_ISO, GFF_MAT_CP_FCC, GFF_MAT_NEOHOOKE = 0, 1, 2, 3
 (GFF_FIELD_F, GFF_FIELD_P, GFF_FIELD_K, GFF_FIELD_FP_INV, GFF_FIELD_CHI,
  GFF_FIELD_GAMMA, GFF_FIELD_PCYC, GFF_FIELD_WCYC) = range(8)
@@ -81,6 +82,11 @@ class gff_step_report(ctypes.Structure):
     ]
 
 
+class gff_auto_options(ctypes.Structure):
+    _fields_ = [("dt_initial", c_double), ("dt_min", c_double), ("dt_max", c_double), ("grow", c_double),
+                ("shrink", c_double), ("easy_newton", c_int), ("hard_newton", c_int)]
+
+
 class GffError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("gff status %d: %s" % (status, msg))
@@ -112,11 +118,15 @@ _SIGS = {
     "gff_measure_fp64_peak": (c_int, [c_void_p, c_void_p]),
     "gff_set_wait_limit": (c_int, [c_void_p, ctypes.c_longlong]),
     "gff_set_return_map": (c_int, [c_void_p, c_int]),
+    "gff_set_strain_measure": (c_int, [c_void_p, c_int]),
     "gff_step": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_void_p, _P(gff_step_report)]),
     "gff_run_history": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                 c_void_p]),
     "gff_batch_run": (c_int, [c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_void_p]),
+    "gff_auto_options_default": (None, [_P(gff_auto_options)]),
+    "gff_run_auto": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                             _P(gff_auto_options), c_int, _P(c_int), c_void_p, c_void_p, c_void_p]),
     "gff_unet_create": (c_int, [ctypes.c_uint64, _P(c_void_p)]),
     "gff_unet_destroy": (None, [c_void_p]),
     "gff_unet_last_error": (ctypes.c_char_p, [c_void_p]),
@@ -322,6 +332,10 @@ def gff_set_wait_limit(h, cycles):
     return _check(h, _lib.gff_set_wait_limit(h, int(cycles)))
 
 
+def gff_set_strain_measure(h, mode):
+    return _check(h, _lib.gff_set_strain_measure(h, int(mode)))
+
+
 def gff_set_return_map(h, mode):
     return _check(h, _lib.gff_set_return_map(h, int(mode)))
 
@@ -347,6 +361,34 @@ def gff_run_history(h, dt, Fbar, mask, Pbar, cycle_start=None):
     _check(h, _lib.gff_run_history(h, n, dp, fp, mp, pp, csp, Pm.ctypes.data_as(c_void_p),
                                    ctypes.cast(reps, c_void_p)))
     return Pm, [reps[k] for k in range(n)]
+
+
+def gff_auto_options_default(**kw):
+    a = gff_auto_options()
+    _lib.gff_auto_options_default(ctypes.byref(a))
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return a
+
+
+def gff_run_auto(h, t_knots, Fbar_knots, mask, Pbar_knots, cycle_start=None, options=None, max_increments=10000):
+    """Automatic time incrementation along a piecewise-linear path.  Returns
+    (end times [n], Pmacro [n][9], reports [n])."""
+    nk = int(np.asarray(t_knots).shape[0])
+    t, tp = _host(t_knots, np.float64)
+    f, fp = _host(Fbar_knots, np.float64)
+    m, mp = _host(mask, np.uint8)
+    p, pp = _host(Pbar_knots, np.float64)
+    cs, csp = _host(cycle_start, np.uint8) if cycle_start is not None else (None, None)
+    ao = options if options is not None else gff_auto_options_default()
+    n = c_int(0)
+    tout = np.zeros(max_increments)
+    Pm = np.zeros((max_increments, 9))
+    reps = (gff_step_report * max_increments)()
+    _check(h, _lib.gff_run_auto(h, nk, tp, fp, mp, pp, csp, ctypes.byref(ao), int(max_increments), ctypes.byref(n),
+                                tout.ctypes.data_as(c_void_p), Pm.ctypes.data_as(c_void_p), ctypes.cast(reps, c_void_p)))
+    k = n.value
+    return tout[:k].copy(), Pm[:k].copy(), [reps[i] for i in range(k)]
 
 
 def gff_batch_run(handles, dt, Fbar, mask, Pbar, cycle_start=None, raise_on_error=True):
@@ -527,10 +569,12 @@ def make_material(kind, C11=168.4e9, C12=121.4e9, C44=75.4e9, E=400e9, nu=0.2, g
     return m
 
 
-def create_rve(ms, materials, options=None):
+def create_rve(ms, materials, options=None, small_strain=False):
     """Handle for a rve_inputs.Microstructure with {phase: gff_material}."""
     h = gff_create(make_grid(ms.nx, ms.ny, ms.nz, ms.L), options)
     try:
+        if small_strain:
+            gff_set_strain_measure(h, GFF_STRAIN_SMALL)
         for ph, m in materials.items():
             gff_set_material(h, ph, m)
         gff_set_microstructure(h, ms.grain_id.reshape(-1), ms.ngrains, ms.quat, ms.phase)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from gpu_helpers import gff, gpu_materials, torch_cuda
-from oracle.solver import CP_FCC, SVK_ISO
+from oracle.solver import CP_FCC, SVK_CUBIC, SVK_ISO
 from rve_inputs import cyclic_history, polycrystal, polycrystal_with_particles
 
 pytestmark = pytest.mark.gpu
@@ -98,3 +98,66 @@ def test_batch_rejects_mismatched_options():
     finally:
         g.gff_destroy(a)
         g.gff_destroy(b)
+
+
+def test_batch_with_extrapolated_warm_start_equals_one_by_one():
+    """Warm-start mode 3 (extrapolated last increment) applied per RVE inside
+    the batch gives each RVE the bits of its own gff_run_history."""
+    torch_cuda()
+    g = gff()
+    hist = cyclic_history(0.01, 1).head(6)
+    opts = dict(precision=1, newton_tol=1e-7, cg_tol=1e-6)
+    rves = _rves()
+    singles, batch = [], []
+    try:
+        for ms, kinds in rves:
+            for lst in (singles, batch):
+                h = g.create_rve(ms, gpu_materials(kinds), g.make_options(**opts))
+                g.gff_set_warm_start(h, None, g.GFF_WARM_EXTRAPOLATE)
+                lst.append(h)
+        ref = [g.gff_run_history(h, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start) for h in singles]
+        Pm, reps, stat = g.gff_batch_run(batch, hist.dt, hist.Fbar, hist.mask, hist.Pbar, hist.cycle_start)
+        assert (stat == 0).all()
+        for r, (ms, kinds) in enumerate(rves):
+            assert np.array_equal(Pm[r], ref[r][0]), r
+            assert [x.warm_start_used for x in reps[r]] == [x.warm_start_used for x in ref[r][1]]
+            assert sum(x.warm_start_used for x in reps[r]) >= 4
+            for w in (g.GFF_FIELD_F, g.GFF_FIELD_FP_INV):
+                assert np.array_equal(g.gff_get_field(batch[r], w, ms.n_voxels),
+                                      g.gff_get_field(singles[r], w, ms.n_voxels)), (r, w)
+    finally:
+        for h in singles + batch:
+            g.gff_destroy(h)
+
+
+def test_failed_batch_increments_are_cut_back_per_rve():
+    """A hyperelastic increment too large for the Newton budget fails inside the
+    batched graph; each RVE is then redone on its own handle with cut-backs and
+    ends exactly where gff_step with cut-backs ends."""
+    torch_cuda()
+    g = gff()
+    shapes = [(8, 8, 8), (12, 8, 16), (16, 16, 16)]
+    Fbar = np.eye(3).ravel().copy()
+    Fbar[0] += 0.08
+    Fbar[4] -= 0.03
+    dt, F1, mk, P0 = np.ones(1), Fbar[None, :], np.zeros((1, 9), np.uint8), np.zeros((1, 9))
+    opts = dict(newton_tol=1e-10, cg_tol=1e-4, newton_max=3, max_cuts=4)
+    singles, batch = [], []
+    try:
+        for i, sh in enumerate(shapes):
+            ms = polycrystal(sh, 4, 50 + i)
+            singles.append(g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(**opts)))
+            batch.append(g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(**opts)))
+        ref = [g.gff_run_history(h, dt, F1, mk, P0) for h in singles]
+        assert all(r[1][0].cuts >= 1 for r in ref)  # the increment does need cutting
+        Pm, reps, stat = g.gff_batch_run(batch, dt, F1, mk, P0)
+        assert (stat == 0).all()
+        for r, sh in enumerate(shapes):
+            assert reps[r][0].cuts == ref[r][1][0].cuts
+            assert np.array_equal(Pm[r], ref[r][0])
+            N = int(np.prod(sh))
+            assert np.array_equal(g.gff_get_field(batch[r], g.GFF_FIELD_F, N),
+                                  g.gff_get_field(singles[r], g.GFF_FIELD_F, N))
+    finally:
+        for h in singles + batch:
+            g.gff_destroy(h)
