@@ -215,7 +215,7 @@ struct gff_handle {
 namespace gff {
 
 constexpr int NACC = 1 + 12 * 5;  // pcyc, W[12], gamma[12], gmin[12], gmax[12], sn[12]
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_BLOCKS = 608;   // 4 x 152 SMs: blocks of the reductions and CG vector updates
 
 // ---- warm starts (unet.cu): add G^(|d| y~) to h->d_Fk for the prescribed increment d9,
 // y~ = s y_{k-1} (+ the network's correction when u is given).  *applied = 0 when there

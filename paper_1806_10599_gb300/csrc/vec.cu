@@ -21,13 +21,100 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return v;
 }
 
+// 16-byte vectors of the CG kernels: every vector length here is a multiple of
+// 4 (9 N with nx, ny even) and every base 16-byte aligned (cudaMalloc'd), so the
+// streams are read and written as float4 / double2.  A thread takes whole
+// vectors in a grid-stride loop and accumulates their elements in order; the
+// single-RVE and the batched kernels share this mapping, so their reductions
+// are bitwise equal.
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    using t = float4;
+    static constexpr int n = 4;
+};
+template <> struct Vec<double> {
+    using t = double2;
+    static constexpr int n = 2;
+};
+template <typename T> __device__ __forceinline__ T& at(typename Vec<T>::t& v, int j) {
+    return reinterpret_cast<T*>(&v)[j];
+}
+template <typename T> __device__ __forceinline__ T get(const typename Vec<T>::t& v, int j) {
+    return reinterpret_cast<const T*>(&v)[j];
+}
+
+template <typename T>
+__device__ __forceinline__ double dot_thread(const T* __restrict__ a, const T* __restrict__ b, long long n) {
+    using V = typename Vec<T>::t;
+    constexpr int W = Vec<T>::n;
+    const V* a4 = reinterpret_cast<const V*>(a);
+    const V* b4 = reinterpret_cast<const V*>(b);
+    const long long nv = n / W, gs = (long long)gridDim.x * blockDim.x;
+    double acc = 0.0;
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + gs < nv; i += 2 * gs) {  // two vectors in flight per thread
+        const V x0 = a4[i], y0 = b4[i], x1 = a4[i + gs], y1 = b4[i + gs];
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc = fma((double)get<T>(x0, j), (double)get<T>(y0, j), acc);
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc = fma((double)get<T>(x1, j), (double)get<T>(y1, j), acc);
+    }
+    if (i < nv) {
+        const V x = a4[i], y = b4[i];
+#pragma unroll
+        for (int j = 0; j < W; ++j) acc = fma((double)get<T>(x, j), (double)get<T>(y, j), acc);
+    }
+    return acc;
+}
+
+// x += alpha p, r -= alpha Ap; returns this thread's part of r.r
+template <typename T>
+__device__ __forceinline__ double update_thread(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                                                const T* __restrict__ Ap, T alpha, long long n) {
+    using V = typename Vec<T>::t;
+    constexpr int W = Vec<T>::n;
+    V* x4 = reinterpret_cast<V*>(x);
+    V* r4 = reinterpret_cast<V*>(r);
+    const V* p4 = reinterpret_cast<const V*>(p);
+    const V* a4 = reinterpret_cast<const V*>(Ap);
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n / W; i += (long long)gridDim.x * blockDim.x) {
+        V xv = x4[i], rv = r4[i];
+        const V pv = p4[i], av = a4[i];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            at<T>(xv, j) = fma(alpha, get<T>(pv, j), get<T>(xv, j));
+            const T ri = fma(-alpha, get<T>(av, j), get<T>(rv, j));
+            at<T>(rv, j) = ri;
+            acc = fma((double)ri, (double)ri, acc);
+        }
+        x4[i] = xv;
+        r4[i] = rv;
+    }
+    return acc;
+}
+
+// p = r + beta p
+template <typename T>
+__device__ __forceinline__ void xpby_thread(T* __restrict__ p, const T* __restrict__ r, T beta, long long n) {
+    using V = typename Vec<T>::t;
+    constexpr int W = Vec<T>::n;
+    V* p4 = reinterpret_cast<V*>(p);
+    const V* r4 = reinterpret_cast<const V*>(r);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n / W; i += (long long)gridDim.x * blockDim.x) {
+        V pv = p4[i];
+        const V rv = r4[i];
+#pragma unroll
+        for (int j = 0; j < W; ++j) at<T>(pv, j) = fma(beta, get<T>(pv, j), get<T>(rv, j));
+        p4[i] = pv;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_dot_partial(const T* __restrict__ a, const T* __restrict__ b, long long n,
                                                      double* __restrict__ partial) {
     __shared__ double sh[32];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        acc = fma((double)a[i], (double)b[i], acc);
+    double acc = dot_thread<T>(a, b, n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -45,10 +132,13 @@ __global__ void __launch_bounds__(TPB) k_final(const double* __restrict__ partia
 __global__ void __launch_bounds__(TPB) k_sum9_partial(const double* __restrict__ a, long long N,
                                                       double* __restrict__ partial) {
     __shared__ double sh[32];
-    const double* ac = a + (long long)blockIdx.y * N;
+    const double2* ac = reinterpret_cast<const double2*>(a + (long long)blockIdx.y * N);  // N is a multiple of 4
     double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-        acc += ac[i];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N / 2; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = ac[i];
+        acc += v.x;
+        acc += v.y;
+    }
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = acc;
 }
@@ -58,21 +148,14 @@ __global__ void __launch_bounds__(TPB) k_cg_update(T* __restrict__ x, T* __restr
                                                    const T* __restrict__ Ap, T alpha, long long n,
                                                    double* __restrict__ partial) {
     __shared__ double sh[32];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const T ri = fma(-alpha, Ap[i], r[i]);
-        r[i] = ri;
-        acc = fma((double)ri, (double)ri, acc);
-    }
+    double acc = update_thread<T>(x, r, p, Ap, alpha, n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_xpby(T* __restrict__ p, const T* __restrict__ r, T beta, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], r[i]);
+    xpby_thread<T>(p, r, beta, n);
 }
 
 struct Nine {
@@ -125,9 +208,7 @@ __global__ void __launch_bounds__(TPB) k_dot_partial_skip(const T* __restrict__ 
                                                           double* __restrict__ partial, const int* __restrict__ flag) {
     if (*flag) return;
     __shared__ double sh[32];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        acc = fma((double)a[i], (double)b[i], acc);
+    double acc = dot_thread<T>(a, b, n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -156,14 +237,7 @@ __global__ void __launch_bounds__(TPB) k_cg_update_dev(T* __restrict__ x, T* __r
                                                        const double* __restrict__ cg, const int* __restrict__ flag) {
     if (*flag) return;
     __shared__ double sh[32];
-    const T alpha = (T)cg[CG_ALPHA];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const T ri = fma(-alpha, Ap[i], r[i]);
-        r[i] = ri;
-        acc = fma((double)ri, (double)ri, acc);
-    }
+    double acc = update_thread<T>(x, r, p, Ap, (T)cg[CG_ALPHA], n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
@@ -193,9 +267,7 @@ template <typename T>
 __global__ void __launch_bounds__(TPB) k_xpby_dev(T* __restrict__ p, const T* __restrict__ r, long long n,
                                                   const double* __restrict__ cg, int* __restrict__ flag) {
     if (*flag == 1) return;
-    const T beta = (T)cg[CG_BETA];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], r[i]);
+    xpby_thread<T>(p, r, (T)cg[CG_BETA], n);
 }
 
 __global__ void k_promote_stop(int* flag) {
@@ -212,10 +284,7 @@ __global__ void __launch_bounds__(TPB) k_dot_partial_batch(const RveVec* __restr
     __shared__ double sh[32];
     const T* a = static_cast<const T*>(which == 0 ? v[r].p : v[r].x);
     const T* b = static_cast<const T*>(which == 0 ? v[r].Ap : v[r].r);
-    const long long n = v[r].n;
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        acc = fma((double)a[i], (double)b[i], acc);
+    double acc = dot_thread<T>(a, b, v[r].n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = acc;
 }
@@ -246,19 +315,8 @@ __global__ void __launch_bounds__(TPB) k_cg_update_batch(const RveVec* __restric
     const int r = blockIdx.y;
     if (flag[2 * r]) return;
     __shared__ double sh[32];
-    T* x = static_cast<T*>(v[r].x);
-    T* rr = static_cast<T*>(v[r].r);
-    const T* p = static_cast<const T*>(v[r].p);
-    const T* Ap = static_cast<const T*>(v[r].Ap);
-    const long long n = v[r].n;
-    const T alpha = (T)cg[8 * r + CG_ALPHA];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const T ri = fma(-alpha, Ap[i], rr[i]);
-        rr[i] = ri;
-        acc = fma((double)ri, (double)ri, acc);
-    }
+    double acc = update_thread<T>(static_cast<T*>(v[r].x), static_cast<T*>(v[r].r), static_cast<const T*>(v[r].p),
+                                  static_cast<const T*>(v[r].Ap), (T)cg[8 * r + CG_ALPHA], v[r].n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[(long long)r * gridDim.x + blockIdx.x] = acc;
 }
@@ -290,12 +348,7 @@ __global__ void __launch_bounds__(TPB) k_xpby_batch(const RveVec* __restrict__ v
                                                     const int* __restrict__ flag) {
     const int r = blockIdx.y;
     if (flag[2 * r] == 1) return;
-    T* p = static_cast<T*>(v[r].p);
-    const T* rr = static_cast<const T*>(v[r].r);
-    const long long n = v[r].n;
-    const T beta = (T)cg[8 * r + CG_BETA];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        p[i] = fma(beta, p[i], rr[i]);
+    xpby_thread<T>(static_cast<T*>(v[r].p), static_cast<const T*>(v[r].r), (T)cg[8 * r + CG_BETA], v[r].n);
 }
 
 __global__ void k_promote_stop_batch(int* flag, int n) {
