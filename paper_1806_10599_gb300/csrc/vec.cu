@@ -1,7 +1,8 @@
 // Conjugate-gradient vector updates and reductions (Sect. 2.1, the Krylov
 // solver of Eq. linequil2).  Reductions are two-stage and deterministic: a
 // fixed grid of RED_BLOCKS blocks writes partial sums, one block adds them in
-// a fixed order.  Sums are accumulated in FP64 for both precisions.
+// a fixed order.  Sums are accumulated in FP64 for both precisions (FP32 data:
+// each 4-element vector's part in FP32 first, see vdot_acc).
 #include "gff_internal.cuh"
 
 namespace gff {
@@ -24,9 +25,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // 16-byte vectors of the CG kernels: every vector length here is a multiple of
 // 4 (9 N with nx, ny even) and every base 16-byte aligned (cudaMalloc'd), so the
 // streams are read and written as float4 / double2.  A thread takes whole
-// vectors in a grid-stride loop and accumulates their elements in order; the
-// single-RVE and the batched kernels share this mapping, so their reductions
-// are bitwise equal.
+// vectors in a grid-stride loop and adds each vector's contribution to its FP64
+// sum in order; the single-RVE and the batched kernels share this mapping, so
+// their reductions are bitwise equal.
 template <typename T> struct Vec;
 template <> struct Vec<float> {
     using t = float4;
@@ -43,6 +44,17 @@ template <typename T> __device__ __forceinline__ T get(const typename Vec<T>::t&
     return reinterpret_cast<const T*>(&v)[j];
 }
 
+// a . b of one vector, added to the FP64 sum: FP64 products for double data; for
+// float data the vector's products are summed in FP32 first (one conversion and
+// one FP64 add per four elements -- conversions and FP64 FMAs per element would
+// make the FP32 kernels FP64-pipe bound)
+__device__ __forceinline__ double vdot_acc(const double2& x, const double2& y, double acc) {
+    return fma(x.y, y.y, fma(x.x, y.x, acc));
+}
+__device__ __forceinline__ double vdot_acc(const float4& x, const float4& y, double acc) {
+    return acc + (double)fmaf(x.w, y.w, fmaf(x.z, y.z, fmaf(x.y, y.y, x.x * y.x)));
+}
+
 template <typename T>
 __device__ __forceinline__ double dot_thread(const T* __restrict__ a, const T* __restrict__ b, long long n) {
     using V = typename Vec<T>::t;
@@ -54,16 +66,10 @@ __device__ __forceinline__ double dot_thread(const T* __restrict__ a, const T* _
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + gs < nv; i += 2 * gs) {  // two vectors in flight per thread
         const V x0 = a4[i], y0 = b4[i], x1 = a4[i + gs], y1 = b4[i + gs];
-#pragma unroll
-        for (int j = 0; j < W; ++j) acc = fma((double)get<T>(x0, j), (double)get<T>(y0, j), acc);
-#pragma unroll
-        for (int j = 0; j < W; ++j) acc = fma((double)get<T>(x1, j), (double)get<T>(y1, j), acc);
+        acc = vdot_acc(x0, y0, acc);
+        acc = vdot_acc(x1, y1, acc);
     }
-    if (i < nv) {
-        const V x = a4[i], y = b4[i];
-#pragma unroll
-        for (int j = 0; j < W; ++j) acc = fma((double)get<T>(x, j), (double)get<T>(y, j), acc);
-    }
+    if (i < nv) acc = vdot_acc(a4[i], b4[i], acc);
     return acc;
 }
 
@@ -84,10 +90,9 @@ __device__ __forceinline__ double update_thread(T* __restrict__ x, T* __restrict
 #pragma unroll
         for (int j = 0; j < W; ++j) {
             at<T>(xv, j) = fma(alpha, get<T>(pv, j), get<T>(xv, j));
-            const T ri = fma(-alpha, get<T>(av, j), get<T>(rv, j));
-            at<T>(rv, j) = ri;
-            acc = fma((double)ri, (double)ri, acc);
+            at<T>(rv, j) = fma(-alpha, get<T>(av, j), get<T>(rv, j));
         }
+        acc = vdot_acc(rv, rv, acc);
         x4[i] = xv;
         r4[i] = rv;
     }

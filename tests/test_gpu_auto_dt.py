@@ -35,7 +35,9 @@ def test_controller_follows_its_rule_on_an_elastic_path():
     torch_cuda()
     g = gff()
     ms = polycrystal(8, 4, 7)
-    tk, Fk = _path([0.0, 0.004, 0.0])
+    # (an elastic path ending back at F = I would end at P = 0, where the relative residual
+    # ||b|| / ||P|| of the stopping test has no meaning; this one ends at 0.2 %)
+    tk, Fk = _path([0.0, 0.004, 0.002])
     h = g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(newton_tol=1e-10, cg_tol=1e-8))
     try:
         ao = g.gff_auto_options_default(dt_initial=0.05, dt_max=0.4, grow=1.5, easy_newton=3, hard_newton=8)

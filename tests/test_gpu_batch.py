@@ -141,11 +141,22 @@ def test_failed_batch_increments_are_cut_back_per_rve():
     Fbar[0] += 0.08
     Fbar[4] -= 0.03
     dt, F1, mk, P0 = np.ones(1), Fbar[None, :], np.zeros((1, 9), np.uint8), np.zeros((1, 9))
-    opts = dict(newton_tol=1e-10, cg_tol=1e-4, newton_max=3, max_cuts=4)
+    mss = [polycrystal(sh, 4, 50 + i) for i, sh in enumerate(shapes)]
+    # the Newton corrections each RVE needs for the whole increment; a budget below the
+    # smallest of them makes every RVE fail in the graph
+    need = []
+    for ms in mss:
+        h = g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(newton_tol=1e-10, cg_tol=1e-4,
+                                                                           newton_max=60, max_cuts=0))
+        try:
+            need.append(g.gff_step(h, 1.0, Fbar, mk[0], P0[0]).newton_iters)
+        finally:
+            g.gff_destroy(h)
+    assert min(need) >= 2, need
+    opts = dict(newton_tol=1e-10, cg_tol=1e-4, newton_max=min(need) - 1, max_cuts=4)
     singles, batch = [], []
     try:
-        for i, sh in enumerate(shapes):
-            ms = polycrystal(sh, 4, 50 + i)
+        for ms in mss:
             singles.append(g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(**opts)))
             batch.append(g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(**opts)))
         ref = [g.gff_run_history(h, dt, F1, mk, P0) for h in singles]

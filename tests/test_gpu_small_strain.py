@@ -80,7 +80,8 @@ def test_polycrystal_uniaxial_stress_matches_oracle(kind, precision):
     assert rel_l2(sig, o.P.reshape(9, -1)) <= ftol
     assert np.abs(Pm[-1][1:7]).max() <= 1e-6 * abs(Pm[-1][0])  # stress-controlled averages vanish
     e = eps.reshape(3, 3, -1)
-    assert np.abs(e - e.transpose(1, 0, 2)).max() <= 1e-12 * np.abs(e).max()  # strains stay symmetric
+    # strains stay symmetric (to rounding: FP32 corrections in mixed precision)
+    assert np.abs(e - e.transpose(1, 0, 2)).max() <= (1e-12 if precision == 0 else 1e-5) * np.abs(e).max()
 
 
 def test_laminate_closed_form_on_the_gpu():
