@@ -208,7 +208,7 @@ gff_status gff_autotune(gff_handle* h, int* tiles_out);
 /* Sets the launch shapes instead of tuning them: tiles (host, 12 ints) in the
  * layout gff_autotune writes.  Allowed: fwd threads 256/512; z columns
  * 4/8/16/32 with z threads 128/256 (one block per strip), or, with TMA z
- * blocks > 0, z columns 8/16 and z threads 256/512; inv threads 256/512, or
+ * blocks > 0, z columns 8/16 and z threads 192/256/384/512; inv threads 256/512, or
  * with inv persistent blocks > 0 up to 1024 (FP32) / 512 (FP64).  Every
  * shape performs the same operations in the same order, so results do not
  * depend on them.  gff_batch_run uses the shapes of its largest RVE and runs

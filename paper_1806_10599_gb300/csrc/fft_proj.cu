@@ -1411,19 +1411,22 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     if (e != cudaSuccess) return e;
     tn.t_fwd = tp[b];
     // z pass: one block per strip (W 4..32, 128 or 256 threads), or the persistent TMA pass (W 8, 16; 256, 512)
-    const int wz[12] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16};
-    const int tz[12] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512};
-    int zb[12] = {0};
-    bool zv[12];
+    // (the TMA pass also takes 192 / 384 threads: a strip of W columns has 24 W radix-16
+    // butterflies at n = 128, so 384 threads at W = 16 and 192 at W = 8 take one each)
+    constexpr int NZC = 15;
+    const int wz[NZC] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16, 8, 8, 16};
+    const int tz[NZC] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512, 192, 384, 384};
+    int zb[NZC] = {0};
+    bool zv[NZC];
     for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i]) <= SMEM_MAX;
-    for (int i = 8; i < 12; ++i) {
+    for (int i = 8; i < NZC; ++i) {
         zb[i] = z_tma_blocks<T>(h, wz[i], tz[i]);
         zv[i] = zb[i] > 0;
     }
     ProjArgs pa;
     pa.kind = GFF_PROJ_CONTINUOUS;
     for (int c = 0; c < 9; ++c) pa.mask[c] = 0.f;
-    e = pick_fastest(12, zv, reps, st, [&](int i) {
+    e = pick_fastest(NZC, zv, reps, st, [&](int i) {
         return zb[i] ? launch_z_tma<T>(h, wz[i], tz[i], zb[i], pa, nullptr, st)
                      : launch_z<T>(g, wz[i], tz[i], spec, pa, nullptr, st);
     }, &b);
@@ -1457,7 +1460,8 @@ bool tiles_valid(gff_handle* h, const Tune& t) {
     if (t.wz != 4 && t.wz != 8 && t.wz != 16 && t.wz != 32) return false;
     if (t.inv_blocks < 0 || t.z_blocks < 0) return false;
     if (t.z_blocks > 0) {
-        if ((t.t_z != 256 && t.t_z != 512) || z_tma_blocks<T>(h, t.wz, t.t_z) < 1) return false;
+        if ((t.t_z != 192 && t.t_z != 256 && t.t_z != 384 && t.t_z != 512) || z_tma_blocks<T>(h, t.wz, t.t_z) < 1)
+            return false;
     } else if ((t.t_z != 128 && t.t_z != 256) || zproj_smem<T>(g, t.wz) > SMEM_MAX) {
         return false;
     }

@@ -175,10 +175,18 @@ def test_training_lowers_the_loss_and_warm_start_keeps_the_solution(tmp_path):
         h0, (P0, r0) = _solve(g, ms, hist)
         h2, (P2, r2) = _solve(g, ms, hist, u, mode=2)
         h1, (P1, r1) = _solve(g, ms, hist, u, mode=1)
-        hs += [h0, h2, h1]
+        h3, (P3, r3) = _solve(g, ms, hist, None, mode=g.GFF_WARM_EXTRAPOLATE)
+        hs += [h0, h2, h1, h3]
         assert all(r.warm_start_used == 1 for r in r2)
-        # the trained network proposes a non-trivial (non-constant) fluctuation: the first residual moves
-        assert all(a.residual_first != b.residual_first for a, b in zip(r2, r0))
+        # The measured relation (the same one the 128^3 benchmark shows over a full cycle): the
+        # network's guess keeps the extrapolation's gain over the zero start, and its trained
+        # correction moves the first residual by little either way -- it does not beat the
+        # extrapolation it is added to.
+        f0 = np.mean([r.residual_first for r in r0[1:]])
+        f2 = np.mean([r.residual_first for r in r2[1:]])
+        f3 = np.mean([r.residual_first for r in r3[1:]])
+        assert f2 <= 0.6 * f0, (f2, f0)
+        assert 0.8 <= f2 / f3 <= 1.25, (f2, f3)
         # same increments solved to tolerance: same solution
         for k in range(hist.nsteps):
             assert np.linalg.norm(P2[k] - P0[k]) <= 1e-7 * np.linalg.norm(P0[k])
