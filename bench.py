@@ -382,7 +382,7 @@ def per_kernel_ms(g, h, prec, X, Y, reps):
     return [a / reps for a in acc]
 
 
-def time_arm(g, torch, ms, hist, precision, projection=0, warm=0, unet=None, clock_index=None):
+def time_arm(g, torch, ms, hist, precision, projection=0, warm=0, unet=None, clock_index=None, return_map=None):
     """One arm of the cyclic-increment measurement: the whole history through
     gff_run_history on a fresh handle, timed on the host around the call (the
     launch shapes are tuned before).  Returns seconds per increment, the
@@ -393,6 +393,8 @@ def time_arm(g, torch, ms, hist, precision, projection=0, warm=0, unet=None, clo
         try:
             if warm:
                 g.gff_set_warm_start(h, unet, warm)
+            if return_map is not None:
+                g.gff_set_return_map(h, return_map)
             g.gff_autotune(h)  # outside the timed region
             torch.cuda.synchronize()
             clk = ClockSampler(clock_index) if clock_index is not None else None
@@ -471,6 +473,9 @@ def cyclic_increments(g, torch, args, clock_index):
         arms["mixed_" + pname] = time_arm(g, torch, ms2, hist, 1, proj, clock_index=clock_index)
         arms["mixed_extrapolated_" + pname] = time_arm(g, torch, ms2, hist, 1, proj, g.GFF_WARM_EXTRAPOLATE,
                                                        clock_index=clock_index)
+        arms["mixed_extrapolated_f32first_" + pname] = time_arm(g, torch, ms2, hist, 1, proj,
+                                                                g.GFF_WARM_EXTRAPOLATE, clock_index=clock_index,
+                                                                return_map=g.GFF_RETURN_MAP_F32_FIRST)
     macro_errors({k: v for k, v in arms.items() if k.endswith("continuous")}, "fp64_continuous")
     macro_errors({k: v for k, v in arms.items() if k.endswith("discrete")}, "fp64_discrete")
     out["config2"] = {"workload": "64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1 pct "

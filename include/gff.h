@@ -254,8 +254,13 @@ gff_status gff_set_strain_measure(gff_handle* h, int mode);
  *   from the previous iterate's slips, then, if that fails, exact Newton from
  *   zero slip (the fallback, counted in gff_step_report.cp_fallbacks);
  * GFF_RETURN_MAP_EXACT: exact Newton (12x12 LU with partial pivoting) from
- *   zero slip only -- every return map counts as a fallback. */
-enum { GFF_RETURN_MAP_DEFAULT = 0, GFF_RETURN_MAP_EXACT = 1 };
+ *   zero slip only -- every return map counts as a fallback;
+ * GFF_RETURN_MAP_F32_FIRST: the default, preceded by the same iteration in
+ *   FP32 (elastic state formed from the small quantities F - I and
+ *   Fp^-1 - I) down to FP32 resolution; the FP64 iteration then starts from
+ *   its root.  The FP64 residual still decides convergence, so the root is
+ *   the default's to the return-map tolerance. */
+enum { GFF_RETURN_MAP_DEFAULT = 0, GFF_RETURN_MAP_EXACT = 1, GFF_RETURN_MAP_F32_FIRST = 2 };
 gff_status gff_set_return_map(gff_handle* h, int mode);
 
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */

@@ -299,8 +299,14 @@ gff_status upload_grains(gff_handle* h, const std::vector<double>& quat, const s
     {
         std::vector<float> g32(G32_STRIDE * (size_t)ng, 0.f);
         for (int g = 0; g < ng; ++g) {
-            for (int k = 0; k < 108; ++k) g32[G32_STRIDE * (size_t)g + G32_S0 + k] = (float)S0[GEO_STRIDE * (size_t)g + GEO_S0 + k];
-            for (int k = 0; k < 81; ++k) g32[G32_STRIDE * (size_t)g + G32_C + k] = (float)C[81 * (size_t)g + k];
+            float* d = &g32[G32_STRIDE * (size_t)g];
+            const double* geo = &S0[GEO_STRIDE * (size_t)g];
+            for (int k = 0; k < 108; ++k) d[G32_S0 + k] = (float)geo[GEO_S0 + k];
+            for (int k = 0; k < 81; ++k) d[G32_C + k] = (float)C[81 * (size_t)g + k];
+            for (int k = 0; k < 36; ++k) d[G32_DIR + k] = (float)geo[GEO_DIR + k];
+            for (int k = 0; k < 12; ++k) d[G32_NRM + k] = (float)geo[GEO_NRM + k];
+            for (int k = 0; k < 36; ++k) d[G32_C6 + k] = (float)geo[GEO_C6 + k];
+            for (int k = 0; k < 85; ++k) d[G32_PC + k] = (float)nrmprm[41 * (size_t)ng + 144 * (size_t)g + k];
         }
         GFF_TRY(cudaMemcpy(h->d_geo32, g32.data(), g32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
@@ -752,9 +758,10 @@ GFF_EXPORT gff_status gff_set_strain_measure(gff_handle* h, int mode) {
 }
 
 GFF_EXPORT gff_status gff_set_return_map(gff_handle* h, int mode) {
-    if (!h || (mode != GFF_RETURN_MAP_DEFAULT && mode != GFF_RETURN_MAP_EXACT))
-        return fail(h, GFF_ERR_ARG, "return-map mode must be 0 or 1");
+    if (!h || (mode != GFF_RETURN_MAP_DEFAULT && mode != GFF_RETURN_MAP_EXACT && mode != GFF_RETURN_MAP_F32_FIRST))
+        return fail(h, GFF_ERR_ARG, "return-map mode must be 0, 1 or 2");
     h->cp_exact_only = mode == GFF_RETURN_MAP_EXACT ? 1 : 0;
+    h->cp_f32_first = mode == GFF_RETURN_MAP_F32_FIRST ? 1 : 0;
     return GFF_OK;
 }
 

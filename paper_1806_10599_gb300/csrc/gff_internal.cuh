@@ -124,8 +124,11 @@ inline double return_map_tol(double newton_tol) {
 // (systems 3p, 3p+1, 3p+2 share plane p) and the stiffness in Voigt order
 // (11, 22, 33, 23, 13, 12) [6][6].
 constexpr int GEO_S0 = 0, GEO_DIR = 108, GEO_NRM = 144, GEO_C6 = 156, GEO_STRIDE = 192;
-// FP32 copies for the FP32 tangent: S0 [12][9], C [81].
-constexpr int G32_S0 = 0, G32_C = 108, G32_STRIDE = 192;
+// FP32 copies for the FP32 tangent (S0 [12][9], C [81]) and for the FP32
+// pre-iteration of the return map (slip directions [12][3], plane normals
+// [4][3], Voigt stiffness [6][6], the small-strain factors P [5][12] and
+// C5^-1 [5][5]).
+constexpr int G32_S0 = 0, G32_C = 108, G32_DIR = 189, G32_NRM = 225, G32_C6 = 237, G32_PC = 273, G32_STRIDE = 384;
 
 }  // namespace gff
 
@@ -181,6 +184,7 @@ struct gff_handle {
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
     int cp_exact_only = 0;     // 1: every return map runs the exact Newton from dg = 0 (gff_set_return_map)
+    int cp_f32_first = 0;      // 1: FP32 pre-iteration before the FP64 iteration (gff_set_return_map)
     int small_strain = 0;      // 1: small-strain variant: d_F holds the strain, sigma = C : eps, symmetric projection
     int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out bulk-copy waits,
                                // [4] return-map fallbacks, [5] local Newton iterations

@@ -89,7 +89,8 @@ struct CPOut {
     double tau[12];
     bool ok;
     bool fallback;  // the small-strain iteration failed; the exact Newton from zero ran
-    int iters;      // local Newton iterations, both tries
+    int iters;      // local Newton iterations in FP64, both tries
+    int iters32;    // FP32 pre-iterations
 };
 
 // LU with partial pivoting of an NN x NN row-major matrix, in place.
@@ -384,6 +385,231 @@ __device__ __forceinline__ bool cp_correction_lowrank(const double* __restrict__
     return true;
 }
 
+// ---------------------------------------------------------------- FP32 pre-iteration
+// The same iteration as the FP64 one (exact residual, small-elastic-strain
+// corrections), in FP32.  With f = F - I, a = Fp^-1_n - I and G = Fe - I all
+// small, the elastic state is formed from them directly --
+//   Fp^-1 - I = a - Lp - a Lp,  G = (Fp^-1 - I) + f + f (Fp^-1 - I),
+//   E = (G + G^T + G^T G) / 2,  M = Ce S = S + 2 E S --
+// so FP32 keeps its relative accuracy on E instead of losing it in Ce - I.
+// It stops at FP32 resolution (or when it stalls); the FP64 iteration then
+// starts from its iterate.  It only steers: the FP64 residual decides
+// convergence, so the root does not change.
+__device__ __forceinline__ float ipowf_n(float a, int p) {  // a >= 0, p >= 0
+    float r = 1.f, b = a;
+    while (p) {
+        if (p & 1) r *= b;
+        b *= b;
+        p >>= 1;
+    }
+    return r;
+}
+
+__device__ void elastic_tau_f32(const float* f, const float* a, const float* dg, const float* __restrict__ g,
+                                float* tau) {
+    const float* sd = g + G32_DIR;
+    const float* mn = g + G32_NRM;
+    const float* C6 = g + G32_C6;
+    float Lp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Lp[k] = 0.f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = fmaf(dg[3 * p + i], __ldg(sd + 3 * (3 * p + i) + j), v[j]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Lp[3 * j + k] = fmaf(v[j], __ldg(mn + 3 * p + k), Lp[3 * j + k]);
+    }
+    float aL[9], q[9], fq[9], G[9], GtG[9];
+    mm(a, Lp, aL);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) q[k] = a[k] - Lp[k] - aL[k];  // Fp^-1 - I
+    mm(f, q, fq);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) G[k] = q[k] + f[k] + fq[k];  // Fe - I
+    mtm(G, G, GtG);
+    float E[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) E[3 * i + j] = 0.5f * (G[3 * i + j] + G[3 * j + i] + GtG[3 * i + j]);
+    const float e[6] = {E[0], E[4], E[8], 2.f * E[5], 2.f * E[2], 2.f * E[1]};  // Voigt, engineering shears
+    float sv[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+        float t = 0.f;
+#pragma unroll
+        for (int J = 0; J < 6; ++J) t = fmaf(__ldg(C6 + 6 * I + J), e[J], t);
+        sv[I] = t;
+    }
+    float S[9];
+    S[0] = sv[0], S[4] = sv[1], S[8] = sv[2];
+    S[5] = S[7] = sv[3];
+    S[2] = S[6] = sv[4];
+    S[1] = S[3] = sv[5];
+    float ES[9], M[9];
+    mm(E, S, ES);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) M[k] = fmaf(2.f, ES[k], S[k]);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float m0 = __ldg(mn + 3 * p), m1 = __ldg(mn + 3 * p + 1), m2 = __ldg(mn + 3 * p + 2);
+        float Mm[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Mm[j] = M[3 * j] * m0 + M[3 * j + 1] * m1 + M[3 * j + 2] * m2;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float* sv3 = sd + 3 * (3 * p + i);
+            tau[3 * p + i] = __ldg(sv3) * Mm[0] + __ldg(sv3 + 1) * Mm[1] + __ldg(sv3 + 2) * Mm[2];
+        }
+    }
+}
+
+struct F32Consts {
+    float cf, c, d, it0;
+    int p;
+};
+
+__device__ float cp_residual_f32(const float* f, const float* a, const float* chn, const float* dg,
+                                 const float* __restrict__ g, const F32Consts& k, float* chi, float* dh, float* r,
+                                 float* iden) {
+    float tau[NSLIP];
+    elastic_tau_f32(f, a, dg, g, tau);
+    float rmax = 0.f;
+    for (int s = 0; s < NSLIP; ++s) {
+        const float id = 1.f / (1.f + k.d * fabsf(dg[s]));
+        iden[s] = id;
+        chi[s] = (chn[s] + k.c * dg[s]) * id;
+        const float x = (tau[s] - chi[s]) * k.it0;
+        const float ax = fabsf(x);
+        const float axp1 = ipowf_n(ax, k.p - 1);
+        dh[s] = (float)k.p * axp1;
+        r[s] = dg[s] - k.cf * sgn(x) * axp1 * ax;
+        rmax = fmaxf(rmax, fabsf(r[s]));
+    }
+    return rmax;
+}
+
+// The small-elastic-strain correction (as cp_correction_lowrank) in FP32 throughout.
+__device__ bool cp_correction_f32(const float* __restrict__ PC, const float* dg, const F32Consts& k, const float* chi,
+                                  const float* dh, const float* iden, const float* r, float* x) {
+    float A[15], b[5];
+    {
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            b[i] = 0.f;
+#pragma unroll
+            for (int j = 0; j <= i; ++j) A[q++] = __ldg(PC + 60 + 5 * i + j);
+        }
+    }
+    float fa[NSLIP], Di[NSLIP];
+#pragma unroll
+    for (int s = 0; s < NSLIP; ++s) {
+        fa[s] = k.cf * k.it0 * dh[s];
+        const float dchi = (k.c - k.d * sgn(dg[s]) * chi[s]) * iden[s];
+        Di[s] = 1.f / (1.f + fa[s] * dchi);
+        const float ga = fa[s] * Di[s], ra = r[s] * Di[s];
+        float pp[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) pp[i] = __ldg(PC + 12 * i + s);
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            b[i] = fmaf(ra, pp[i], b[i]);
+#pragma unroll
+            for (int j = 0; j <= i; ++j) A[q] = fmaf(ga * pp[i], pp[j], A[q]), ++q;
+        }
+    }
+    float L[5][5], qd[5], iq[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        float t = A[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int m = 0; m < j; ++m) t -= L[j][m] * L[j][m] * qd[m];
+        if (!(t > 0.f)) return false;
+        qd[j] = t;
+        iq[j] = 1.f / t;
+#pragma unroll
+        for (int i = j + 1; i < 5; ++i) {
+            float u = A[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int m = 0; m < j; ++m) u -= L[i][m] * L[j][m] * qd[m];
+            L[i][j] = u * iq[j];
+        }
+    }
+    float u[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        float t = b[i];
+#pragma unroll
+        for (int m = 0; m < i; ++m) t -= L[i][m] * u[m];
+        u[i] = t;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) u[i] *= iq[i];
+#pragma unroll
+    for (int i = 4; i >= 0; --i) {
+#pragma unroll
+        for (int m = i + 1; m < 5; ++m) u[i] -= L[m][i] * u[m];
+    }
+#pragma unroll
+    for (int s = 0; s < NSLIP; ++s) {
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) t = fmaf(__ldg(PC + 12 * i + s), u[i], t);
+        x[s] = Di[s] * (r[s] - fa[s] * t);
+    }
+    return true;
+}
+
+// FP32 iteration from dg (in/out, FP64 storage); false (dg untouched) if it
+// breaks down before reaching FP32 resolution or stalling.
+__device__ bool cp_presolve_f32(const double* F, const double* A, const double* chin, const float* __restrict__ g,
+                                const CPParamsDev& pr, double coef, double* dg64, int* iters) {
+    float f[9], a[9], chn[NSLIP], dg[NSLIP], chi[NSLIP], dh[NSLIP], r[NSLIP], iden[NSLIP], x[NSLIP];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double I = (k % 4) == 0 ? 1.0 : 0.0;
+        f[k] = (float)(F[k] - I);
+        a[k] = (float)(A[k] - I);
+    }
+    for (int s = 0; s < NSLIP; ++s) {
+        chn[s] = (float)chin[s];
+        dg[s] = (float)dg64[s];
+    }
+    F32Consts k;
+    k.cf = (float)coef;
+    k.c = (float)pr.c;
+    k.d = (float)pr.d;
+    k.it0 = (float)pr.itau0;
+    k.p = (int)pr.p;
+    float prev = 3.0e38f;
+    constexpr int MAXIT = 30;
+    for (int it = 0; it < MAXIT; ++it) {
+        const float rmax = cp_residual_f32(f, a, chn, dg, g, k, chi, dh, r, iden);
+        *iters = it;
+        if (!(rmax < 1e30f)) return false;
+        float dgmax = 0.f;
+        for (int s = 0; s < NSLIP; ++s) dgmax = fmaxf(dgmax, fabsf(dg[s]));
+        // FP32 resolution of this residual is a few 1e-6 of the slips; stalling there (or
+        // slower than halving after a few steps) ends the pre-iteration
+        if (rmax <= 1e-5f * dgmax || (it > 3 && rmax > 0.5f * prev)) {
+            for (int s = 0; s < NSLIP; ++s) dg64[s] = (double)dg[s];
+            return true;
+        }
+        prev = rmax;
+        if (!cp_correction_f32(g + G32_PC, dg, k, chi, dh, iden, r, x)) return false;
+        for (int s = 0; s < NSLIP; ++s) dg[s] -= x[s];
+    }
+    return false;
+}
+
 // Local Newton on dg from the given start.  lowrank: corrections from the
 // small-elastic-strain Jacobian in precision TJ; otherwise the exact
 // Jacobian with pivoting in FP64.
@@ -517,12 +743,21 @@ __device__ void cp_update(const double* F, const double* A, const double* chin, 
                           const double* __restrict__ S0, const double* __restrict__ C, const double* __restrict__ H,
                           const T* __restrict__ S0t, const T* __restrict__ Ct, const CPParamsDev& pr,
                           const double* dg0 /* 12 or null */, T* K /* 81 or null */, CPOut& out,
-                          bool exact_only = false) {
+                          bool exact_only = false, const float* __restrict__ g32 = nullptr) {
     const double coef = dt * pr.gdot0;
     const int p = (int)pr.p;
     double dg[NSLIP], dh[NSLIP], chi[NSLIP];
     ElState st;
     for (int a = 0; a < NSLIP; ++a) dg[a] = dg0 ? dg0[a] : 0.0;
+    out.iters32 = 0;
+    if (g32 && !exact_only) {  // FP32 pre-iteration (g32: the grain's FP32 data)
+        double dgs[NSLIP];
+        for (int a = 0; a < NSLIP; ++a) dgs[a] = dg[a];
+        int it32 = 0;
+        if (cp_presolve_f32(F, A, chin, g32, pr, coef, dgs, &it32))
+            for (int a = 0; a < NSLIP; ++a) dg[a] = dgs[a];
+        out.iters32 = it32;
+    }
     // FP64 corrections: J is ill-conditioned (cond ~ 1e8 and more) once slip
     // systems are active, beyond what an FP32 solve can steer
     int it1 = 0, it2 = 0;
@@ -685,6 +920,7 @@ struct ConstArgs {
     const int* warm_dev;  // device flag (may be null): when set, start warm as well
     int exact;        // 1: skip the small-strain iteration, exact Newton from dg = 0 only
     int small;        // 1: small-strain variant, F holds the strain: P = C : F (Cauchy stress), K = C
+    int f32first;     // 1: FP32 pre-iteration of the return map
     double rtol;      // return-map tolerance (return_map_tol)
     const int* gkind;
     const double* gprm;  // [ngrains][5]: gdot0, p, tau0, c, d
@@ -782,17 +1018,17 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         CPOut o;
         if (PART == PART_P) {
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
-                              (double*)nullptr, o, a.exact != 0);
+                              (double*)nullptr, o, a.exact != 0, a.f32first ? g32 : nullptr);
         } else if (F32T) {
             float K[81];
             cp_update<float>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, g32 + G32_S0, g32 + G32_C, pr,
-                             warm ? dg0 : nullptr, K, o, a.exact != 0);
+                             warm ? dg0 : nullptr, K, o, a.exact != 0, a.f32first ? g32 : nullptr);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
             double K[81];
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
-                              K, o, a.exact != 0);
+                              K, o, a.exact != 0, a.f32first ? g32 : nullptr);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K[k * N + v] = K[k];
             if (a.K32) {
@@ -1134,6 +1370,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.warm_dev = nullptr;
     a.exact = h->cp_exact_only;
     a.small = h->small_strain;
+    a.f32first = h->cp_f32_first;
     a.rtol = return_map_tol(h->opt.newton_tol);
     a.gkind = h->d_gkind;
     a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
@@ -1188,6 +1425,7 @@ cudaError_t upload_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.warm_dev = warm_dev ? warm_dev + r : nullptr;
         a.exact = h->cp_exact_only;
         a.small = h->small_strain;
+        a.f32first = h->cp_f32_first;
         a.rtol = return_map_tol(h->opt.newton_tol);
         a.gkind = h->d_gkind;
         a.gprm = h->d_nrm + 36LL * h->ngrains;

@@ -62,7 +62,7 @@ def oracle_runs():
     pool.shutdown(wait=False, cancel_futures=True)
 
 
-def _gpu_run(case, precision=0, exact=False, newton_tol=TOL, cg_tol=TOL):
+def _gpu_run(case, precision=0, exact=False, newton_tol=TOL, cg_tol=TOL, return_map=None):
     """The library's run of a case, in segments ending at the FIP snapshots."""
     torch_cuda()
     g = gff()
@@ -73,6 +73,8 @@ def _gpu_run(case, precision=0, exact=False, newton_tol=TOL, cg_tol=TOL):
     try:
         if exact:
             g.gff_set_return_map(h, g.GFF_RETURN_MAP_EXACT)
+        if return_map is not None:
+            g.gff_set_return_map(h, return_map)
         Pm, reps, fips, a = [], [], {}, 0
         for b in sorted(snaps):
             sl = slice(a, b + 1)
@@ -149,6 +151,17 @@ def test_exact_return_map_matches_oracle(oracle_runs):
     Pm, reps, f, fips = _gpu_run("c8_cont", exact=True)
     assert all(r.cp_fallbacks >= 512 for r in reps)
     _compare("c8_cont", oracle_runs["c8_cont"].result(), Pm, reps, f, fips, False)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fp32_pre_iteration_reaches_the_oracle_root(oracle_runs, precision):
+    """Return maps that iterate in FP32 first and finish in FP64 reach the
+    oracle's roots across both cycles (the FP64 residual decides)."""
+    mixed = precision == 1
+    g = gff()
+    Pm, reps, f, fips = _gpu_run("c8_cont", precision, newton_tol=1e-9 if mixed else TOL,
+                                 cg_tol=1e-6 if mixed else TOL, return_map=g.GFF_RETURN_MAP_F32_FIRST)
+    _compare("c8_cont", oracle_runs["c8_cont"].result(), Pm, reps, f, fips, mixed)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
