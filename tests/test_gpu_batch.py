@@ -138,22 +138,45 @@ def test_failed_batch_increments_are_cut_back_per_rve():
     g = gff()
     shapes = [(8, 8, 8), (12, 8, 16), (16, 16, 16)]
     Fbar = np.eye(3).ravel().copy()
-    Fbar[0] += 0.08
-    Fbar[4] -= 0.03
+    Fbar[0] += 0.12
+    Fbar[4] -= 0.04
     dt, F1, mk, P0 = np.ones(1), Fbar[None, :], np.zeros((1, 9), np.uint8), np.zeros((1, 9))
     mss = [polycrystal(sh, 4, 50 + i) for i, sh in enumerate(shapes)]
+    # Tight CG: the Newton iteration count is then set by the nonlinearity, and a
+    # smaller increment needs fewer corrections.  (With a loose CG tolerance the
+    # relative residual of a first increment from F = I is limited by the CG
+    # tolerance whatever the increment's size, and no cut-back helps.)
+    base = dict(newton_tol=1e-10, cg_tol=1e-11)
     # the Newton corrections each RVE needs for the whole increment; a budget below the
     # smallest of them makes every RVE fail in the graph
     need = []
     for ms in mss:
-        h = g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(newton_tol=1e-10, cg_tol=1e-4,
-                                                                           newton_max=60, max_cuts=0))
+        h = g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(newton_max=60, max_cuts=0, **base))
         try:
             need.append(g.gff_step(h, 1.0, Fbar, mk[0], P0[0]).newton_iters)
         finally:
             g.gff_destroy(h)
     assert min(need) >= 2, need
-    opts = dict(newton_tol=1e-10, cg_tol=1e-4, newton_max=min(need) - 1, max_cuts=4)
+    # the smallest such budget at which the one-by-one runs succeed through cut-backs
+    opts = None
+    for nm in range(1, min(need)):
+        o = dict(newton_max=nm, max_cuts=6, **base)
+        hs = [g.create_rve(ms, gpu_materials({0: SVK_CUBIC}), g.make_options(**o)) for ms in mss]
+        ok = True
+        try:
+            for h in hs:
+                try:
+                    g.gff_run_history(h, dt, F1, mk, P0)
+                except g.GffError:
+                    ok = False
+                    break
+        finally:
+            for h in hs:
+                g.gff_destroy(h)
+        if ok:
+            opts = o
+            break
+    assert opts is not None, need
     singles, batch = [], []
     try:
         for ms in mss:
