@@ -200,22 +200,25 @@ gff_status gff_measure_fp64_peak(double* gflops_out, double* ms_out);
  * gff_step runs it once per handle if it has not been run.  Uses the handle's
  * work buffers (call it before setting up an apply by hand, or call
  * gff_constitutive again afterwards).  tiles_out (host, 12 ints, may be NULL):
- * {fwd threads, z columns, z threads, inv threads, inv persistent blocks
- * (0: one block per plane)} for FP64 then FP32, then the persistent TMA z
- * pass's blocks for FP64 and FP32 (0: one block per strip). */
+ * {fwd threads, z columns, z threads, inv threads, inv blocks} for FP64 then
+ * FP32, then the persistent TMA z pass's blocks for FP64 and FP32 (0: one
+ * block per strip).  inv blocks: 0 one block per plane; > 0 the persistent
+ * streamed inverse pass with that many blocks; -1 the register-staged
+ * inverse pass (one block per plane) of grids with nx = ny = 64 or 128. */
 gff_status gff_autotune(gff_handle* h, int* tiles_out);
 
 /* Sets the launch shapes instead of tuning them: tiles (host, 12 ints) in the
  * layout gff_autotune writes.  Allowed: fwd threads 256/512; z columns
  * 4/8/16/32 with z threads 128/256 (one block per strip), or, with TMA z
  * blocks > 0, z columns 8/16 and z threads 192/256/384/512; inv threads 256/512, or
- * with inv persistent blocks > 0 up to 1024 (FP32) / 512 (FP64).  Every
- * shape performs the same operations in the same order, so results do not
- * depend on them.  gff_batch_run uses the shapes of its largest RVE and runs
- * one-block-per-strip / one-block-per-plane kernels: persistent shapes are
+ * with inv blocks > 0 up to 1024 (FP32) / 512 (FP64), or with inv blocks -1
+ * (nx = ny = 64 or 128 only) 256/512.  Every shape performs the same
+ * operations in the same order, so results do not depend on them.
+ * gff_batch_run gives each size class the shapes of its first RVE and runs
+ * one-block-per-strip / one-block-per-plane kernels: the other shapes are
  * mapped onto them (z threads at most 256, inv threads at most 512).  Returns
  * GFF_ERR_ARG, changing nothing, for a shape the grid cannot use (shared
- * memory, or no tensor-map support for TMA). */
+ * memory, no tensor-map support for TMA, no register-staged pass). */
 gff_status gff_set_tiles(gff_handle* h, const int* tiles);
 
 /* gff_apply_operator and gff_project return once their kernels are queued on

@@ -622,6 +622,33 @@ __device__ __forceinline__ void zproj_columns(const GridDev& g, int f0, const ZT
     }
 }
 
+// Projection of the three components (v0, v1, v2) of one tensor row at the
+// frequency (kx, ky, kz): the zero frequency keeps the stress-controlled
+// components (mask m), Nyquist planes are zeroed, else y_ij = (x_il n_l) n_j
+// with n the unit (continuous or discrete) wave vector.
+template <typename T>
+__device__ __forceinline__ void proj_point(typename C2<T>::t& v0, typename C2<T>::t& v1, typename C2<T>::t& v2,
+                                           int kx, int ky, int kz, int nx, int ny, int nz, T m0, T m1, T m2,
+                                           const ZTables<T>& tb) {
+    using C = typename C2<T>::t;
+    if (kx == 0 && ky == 0 && kz == 0) {
+        v0 = cscale(v0, m0);
+        v1 = cscale(v1, m1);
+        v2 = cscale(v2, m2);
+    } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
+        v0 = v1 = v2 = mk<C>((T)0, (T)0);
+    } else {
+        const T a = tb.qx[kx], b = tb.qy[ky], d = tb.qz[kz];
+        const T inv = rnorm3(a, b, d);
+        const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
+        // t = sum_l x_il n_l ; y_ij = t n_j
+        const C t = mk<C>(v0.x * n0 + v1.x * n1 + v2.x * n2, v0.y * n0 + v1.y * n1 + v2.y * n2);
+        v0 = cscale(t, n0);
+        v1 = cscale(t, n1);
+        v2 = cscale(t, n2);
+    }
+}
+
 // Forward z transform, projection and inverse z transform of one loaded strip
 // s = [3][nz][W] (tensor row `row`); ends with a barrier.
 template <typename T, int W>
@@ -639,28 +666,94 @@ __device__ __forceinline__ void zproj_strip(typename C2<T>::t* s, const GridDev&
         const int kx = ck & 0xffff, ky = ck >> 16, kz = tb.fqz[pz];
         C* p0 = s + pz * W + w;
         C v0 = p0[0], v1 = p0[nz * W], v2 = p0[2 * nz * W];
-        if (kx == 0 && ky == 0 && kz == 0) {
-            v0 = cscale(v0, m0);
-            v1 = cscale(v1, m1);
-            v2 = cscale(v2, m2);
-        } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
-            v0 = v1 = v2 = mk<C>((T)0, (T)0);
-        } else {
-            const T a = tb.qx[kx], b = tb.qy[ky], d = tb.qz[kz];
-            const T inv = rnorm3(a, b, d);
-            const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
-            // t = sum_l x_il n_l ; y_ij = t n_j
-            const C t = mk<C>(v0.x * n0 + v1.x * n1 + v2.x * n2, v0.y * n0 + v1.y * n1 + v2.y * n2);
-            v0 = cscale(t, n0);
-            v1 = cscale(t, n1);
-            v2 = cscale(t, n2);
-        }
+        proj_point<T>(v0, v1, v2, kx, ky, kz, nx, ny, nz, m0, m1, m2, tb);
         p0[0] = v0;
         p0[nz * W] = v1;
         p0[2 * nz * W] = v2;
     }
     __syncthreads();
     fft_lines<T, true>(s, tb.twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+}
+
+// z transform, projection and inverse z transform of one strip for the
+// two-stage plans nz = 16 x 8 and 8 x 8, with one butterfly's values held in
+// registers across a stage: the forward radix-R1 stage; then per (column,
+// sub) the forward radix-8 stage of the three components, the projection of
+// the eight frequencies sub + R1 q it produced, and the inverse radix-8 stage,
+// without leaving registers; then the inverse radix-R1 stage.  The same
+// operations in the same order as zproj_strip (bit-identical), with two
+// passes over shared memory and two barriers fewer.  Ends with a barrier.
+template <typename T, int R1, int W>
+__device__ __forceinline__ void zstrip2(typename C2<T>::t* s, const GridDev& g, const ProjArgs& pa, int row,
+                                        const ZTables<T>& tb) {
+    using C = typename C2<T>::t;
+    constexpr int R2 = 8, nz = R1 * R2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    // forward radix R1 over positions j + R2 n1 of each (component, column), twiddles after
+    for (int t = tid; t < 3 * R2 * W; t += nthr) {
+        const int w = t % W, jc = t / W, j = jc % R2, comp = jc / R2;
+        C* b = s + (comp * nz + j) * W + w;
+        C v[R1];
+#pragma unroll
+        for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * W];
+        Bfly<R1, false, C>::run(v);
+        if (j) {
+#pragma unroll
+            for (int p = 1; p < R1; ++p) v[p] = cmul(v[p], tb.twz[p * j]);
+        }
+#pragma unroll
+        for (int q = 0; q < R1; ++q) b[q * R2 * W] = v[q];
+    }
+    __syncthreads();
+    const int nx = g.nx, ny = g.ny;
+    const T m0 = (T)pa.mask[3 * row], m1 = (T)pa.mask[3 * row + 1], m2 = (T)pa.mask[3 * row + 2];
+    for (int t = tid; t < R1 * W; t += nthr) {
+        const int w = t % W, sub = t / W;
+        const int ck = tb.colk[w];
+        C* b = s + sub * R2 * W + w;
+        C v0[R2], v1[R2], v2[R2];
+#pragma unroll
+        for (int q = 0; q < R2; ++q) {
+            v0[q] = b[q * W];
+            v1[q] = b[(nz + q) * W];
+            v2[q] = b[(2 * nz + q) * W];
+        }
+        Bfly<R2, false, C>::run(v0);
+        Bfly<R2, false, C>::run(v1);
+        Bfly<R2, false, C>::run(v2);
+        if (ck >= 0) {
+            const int kx = ck & 0xffff, ky = ck >> 16;
+#pragma unroll
+            for (int q = 0; q < R2; ++q)
+                proj_point<T>(v0[q], v1[q], v2[q], kx, ky, tb.fqz[sub * R2 + q], nx, ny, nz, m0, m1, m2, tb);
+        }
+        Bfly<R2, true, C>::run(v0);
+        Bfly<R2, true, C>::run(v1);
+        Bfly<R2, true, C>::run(v2);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) {
+            b[q * W] = v0[q];
+            b[(nz + q) * W] = v1[q];
+            b[(2 * nz + q) * W] = v2[q];
+        }
+    }
+    __syncthreads();
+    // inverse radix R1, conjugate twiddles before
+    for (int t = tid; t < 3 * R2 * W; t += nthr) {
+        const int w = t % W, jc = t / W, j = jc % R2, comp = jc / R2;
+        C* b = s + (comp * nz + j) * W + w;
+        C v[R1];
+#pragma unroll
+        for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * W];
+        if (j) {
+#pragma unroll
+            for (int p = 1; p < R1; ++p) v[p] = cmulc(v[p], tb.twz[p * j]);
+        }
+        Bfly<R1, true, C>::run(v);
+#pragma unroll
+        for (int q = 0; q < R1; ++q) b[q * R2 * W] = v[q];
+    }
+    __syncthreads();
 }
 
 template <typename T, int W>
@@ -799,9 +892,16 @@ template <typename T, int W> size_t ztma_smem(const GridDev& g) {
     return 2 * zstrip_bytes<T, W>(g.nz) + ztables_bytes<T>(g.nz, g.ny, g.nxh, W) + 160;
 }
 
-template <typename T, int W>
-__global__ void __launch_bounds__(512) k_zproj_tma(const __grid_constant__ CUtensorMap tm, GridDev g, ProjArgs pa,
-                                                  const int* __restrict__ skip, int* __restrict__ err) {
+// R1 = 0: any nz (zproj_strip); R1 = 16 / 8: nz = 128 / 64 with the register-staged
+// strip (zstrip2), 256 threads whose register budget holds the 24 complex values of
+// the fused middle stage: two blocks per SM in FP32, one in FP64
+template <typename T, int R1> constexpr int ztma_max_threads() { return R1 ? 256 : 512; }
+template <typename T, int R1> constexpr int ztma_min_blocks() { return (R1 && sizeof(T) == 4) ? 2 : 1; }
+
+template <typename T, int W, int R1>
+__global__ void __launch_bounds__(ztma_max_threads<T, R1>(), ztma_min_blocks<T, R1>())
+    k_zproj_tma(const __grid_constant__ CUtensorMap tm, GridDev g, ProjArgs pa, const int* __restrict__ skip,
+                int* __restrict__ err) {
     using C = typename C2<T>::t;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -844,7 +944,10 @@ __global__ void __launch_bounds__(512) k_zproj_tma(const __grid_constant__ CUten
             return;
         }
         phase[cur] ^= 1u;
-        zproj_strip<T, W>(buf[cur], g, pa, s % 3, tb);
+        if constexpr (R1 > 0)
+            zstrip2<T, R1, W>(buf[cur], g, pa, s % 3, tb);
+        else
+            zproj_strip<T, W>(buf[cur], g, pa, s % 3, tb);
         fence_proxy_async_smem();  // the transforms' writes, before the asynchronous store reads them
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -1102,6 +1205,212 @@ __global__ void __launch_bounds__(inv_stream_max_threads<T>()) k_plane_inv_strea
     }
 }
 
+// ---------------------------------------------------------------- pass 3 for two-stage plans, register-staged
+// For planes with nx = ny = n = R1 R2 and the two-stage plans 16 x 8 (n = 128)
+// and 8 x 8 (n = 64): the operations of plane_inv_compute in the same order
+// (bit-identical results) with half its passes over shared memory.  Each
+// thread keeps one butterfly's values in registers across a stage:
+//   Y1  radix R2 of the inverse y transform over contiguous positions (columns
+//       kx < n/2; column 0 takes X_0 + i X_h, the DC and Nyquist columns);
+//   Y2  radix R1 with twiddles over stride R2, natural y order;
+//   X1  merge and radix R2 of the x transform: a thread takes the butterflies
+//       sub and R1 - sub (0 and R1/2) of one packed row r, whose inputs
+//       Z_k = A_k + i B_k and Z_{n-k} = conj(A_k) + i conj(B_k) (A, B the half
+//       spectra of rows 2r, 2r+1) come from the same stored columns; the
+//       result overwrites rows 2r, 2r+1, XOR-swizzled inside each run of 8;
+//   X2  radix R1 with twiddles, epilogue, stores straight to y.
+// A warp's row pairs in X1 / X2 are 2 apart: with the row stride n/2 + 1 every
+// shared-memory access of the four phases is free of bank conflicts.  The
+// half-spectrum plane arrives by one bulk asynchronous copy with a bounded
+// wait, as in k_plane_inv.
+template <int R1, int R2> struct Inv2Plan {
+    static_assert(R2 == 8 && (R1 == 8 || R1 == 16), "two-stage plans 8 x 8 and 16 x 8");
+    static constexpr int n = R1 * R2, h = n / 2, nxh = h + 1;
+    static constexpr int L1 = R1 / 2, G1 = 32 / L1;  // X1: lanes per row pair, row pairs per warp
+    static constexpr int L2 = R2, G2 = 32 / R2;      // X2
+    static constexpr bool SAMEWARP = (G1 == G2);     // X1 and X2 give a warp the same row pairs
+};
+
+__device__ __forceinline__ int swz8(int p) { return (p & ~7) | ((p ^ (p >> 3)) & 7); }
+__device__ __forceinline__ int inv2_pair(int wg, int k, int G) { return (wg & 1) + 2 * k + (wg >> 1) * 2 * G; }
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void inv2_x1(typename C2<T>::t* s, int wg, int lane) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, R2>;
+    constexpr int HQ = R2 / 2;
+    const int k = lane / P::L1, u = lane % P::L1;
+    const int r = inv2_pair(wg, k, P::G1);
+    C* A = s + 2 * r * P::nxh;
+    const C* B = A + P::nxh;
+    const int c1 = u, c2 = u ? R1 - u : R1 / 2;
+    const bool u0 = (u == 0);
+    C p1[HQ], m1[HQ], p2[HQ], m2[HQ];
+    C z0, zh;
+#pragma unroll
+    for (int q = 0; q < HQ; ++q) {
+        const C a = A[c1 + R1 * q], b = B[c1 + R1 * q];
+        p1[q] = mk<C>(a.x - b.y, a.y + b.x);
+        m1[q] = mk<C>(a.x + b.y, b.x - a.y);
+        if (q == 0) {  // u = 0: column 0 holds (DC, Nyquist) of both rows
+            z0 = mk<C>(a.x, b.x);
+            zh = mk<C>(a.y, b.y);
+        }
+        const C a2 = A[c2 + R1 * q], b2 = B[c2 + R1 * q];
+        p2[q] = mk<C>(a2.x - b2.y, a2.y + b2.x);
+        m2[q] = mk<C>(a2.x + b2.y, b2.x - a2.y);
+    }
+    // position sub R2 + q holds frequency k = sub + R1 q; k > n/2 reads the
+    // stored column n - k: (c2 + R1 (R2-1-q)) for sub = c1 != 0, (R1 (R2-q)) for sub = 0
+    C za[R2], zb[R2];
+#pragma unroll
+    for (int q = 0; q < HQ; ++q) {
+        za[q] = (q == 0 && u0) ? z0 : p1[q];
+        zb[q] = p2[q];
+    }
+    za[HQ] = u0 ? zh : m2[HQ - 1];
+#pragma unroll
+    for (int q = HQ + 1; q < R2; ++q) za[q] = u0 ? m1[R2 - q] : m2[R2 - 1 - q];
+#pragma unroll
+    for (int q = HQ; q < R2; ++q) zb[q] = u0 ? m2[R2 - 1 - q] : m1[R2 - 1 - q];
+    Bfly<R2, true, C>::run(za);
+    Bfly<R2, true, C>::run(zb);
+    __syncwarp();  // every lane of the warp has read its rows before any is overwritten
+#pragma unroll
+    for (int q = 0; q < R2; ++q) {
+        A[swz8(c1 * R2 + q)] = za[q];
+        A[swz8(c2 * R2 + q)] = zb[q];
+    }
+}
+
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void inv2_x2(const typename C2<T>::t* s, const typename C2<T>::t* twx, T* __restrict__ yp,
+                                        T sc, T ad, int wg, int lane) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, R2>;
+    const int k = lane / P::L2, j = lane % P::L2;
+    const int r = inv2_pair(wg, k, P::G2);
+    const C* Z = s + 2 * r * P::nxh;
+    C v[R1];
+#pragma unroll
+    for (int q = 0; q < R1; ++q) v[q] = Z[swz8(j + R2 * q)];
+    if (j) {
+#pragma unroll
+        for (int p = 1; p < R1; ++p) v[p] = cmulc(v[p], twx[p * j]);
+    }
+    Bfly<R1, true, C>::run(v);
+    T* y0 = yp + (long long)(2 * r) * P::n;
+#pragma unroll
+    for (int q = 0; q < R1; ++q) {
+        y0[j + R2 * q] = fma(sc, v[q].x, ad);
+        y0[P::n + j + R2 * q] = fma(sc, v[q].y, ad);
+    }
+}
+
+// blocks per SM the register budget is set for: FP32 planes of 68 KB fit three
+// to an SM (256 threads at <= 85 registers) or two (512 threads at <= 64)
+template <typename T, int BT> constexpr int inv2_min_blocks() { return sizeof(T) == 4 ? (BT == 256 ? 3 : 2) : 1; }
+
+template <typename T, int R1, int R2, int BT>
+__global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(const typename C2<T>::t* __restrict__ spec,
+                                                                      T* __restrict__ y, GridDev g, OutArgs oa,
+                                                                      const int* __restrict__ skip,
+                                                                      int* __restrict__ err) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, R2>;
+    constexpr int n = P::n, h = P::h, nxh = P::nxh;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* s = reinterpret_cast<C*>(sm_raw);  // [n][nxh]
+    C* twx = s + n * nxh;
+    C* twy = twx + n;
+    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(twy + n) + 7) & ~uintptr_t(7));
+    const int c = blockIdx.x, z = blockIdx.y;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0)  // n nxh sizeof(C) is a multiple of 16 (n even), the plane start too
+        bulk_load(s, spec + ((long long)c * g.nz + z) * (n * nxh), (uint32_t)(n * nxh * sizeof(C)), bar);
+    for (int i = tid; i < n; i += nthr) {
+        twx[i] = twp<T>(g, 0)[i];
+        twy[i] = twp<T>(g, 1)[i];
+    }
+    const bool ok = mbar_wait(bar, 0u, g.wait_cycles);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            if (err) atomicExch(err, 1);
+            mbar_wait(bar, 0u, BULK_WAIT_CYCLES);  // let the copy land (bounded) before leaving
+        }
+        plane_fill_nan<T>(y, g, c, z);
+        __syncthreads();
+        return;
+    }
+    // Y1: radix R2 over positions sub R2 + q of column col
+    for (int t = tid; t < h * R1; t += nthr) {
+        const int col = t % h, sub = t / h;
+        C* b = s + sub * R2 * nxh + col;
+        C v[R2];
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[q] = b[q * nxh];
+        if (col == 0) {
+#pragma unroll
+            for (int q = 0; q < R2; ++q) {
+                const C w = b[q * nxh + h];
+                v[q] = mk<C>(v[q].x - w.y, v[q].y + w.x);
+            }
+        }
+        Bfly<R2, true, C>::run(v);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) b[q * nxh] = v[q];
+    }
+    __syncthreads();
+    // Y2: twiddles, radix R1 over positions j + R2 q
+    for (int t = tid; t < h * R2; t += nthr) {
+        const int col = t % h, j = t / h;
+        C* b = s + j * nxh + col;
+        C v[R1];
+#pragma unroll
+        for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * nxh];
+        if (j) {
+#pragma unroll
+            for (int p = 1; p < R1; ++p) v[p] = cmulc(v[p], twy[p * j]);
+        }
+        Bfly<R1, true, C>::run(v);
+#pragma unroll
+        for (int q = 0; q < R1; ++q) b[q * R2 * nxh] = v[q];
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    const T sc = (T)oa.scale, ad = (T)oa.add[c];
+    T* yp = y + c * g.N + (long long)z * n * n;
+    if (P::SAMEWARP) {
+        for (int wg = warp; wg < h / P::G1; wg += nw) {  // warp-uniform
+            inv2_x1<T, R1, R2>(s, wg, lane);
+            __syncwarp();
+            inv2_x2<T, R1, R2>(s, twx, yp, sc, ad, wg, lane);
+        }
+    } else {
+        for (int wg = warp; wg < h / P::G1; wg += nw) inv2_x1<T, R1, R2>(s, wg, lane);
+        __syncthreads();
+        for (int wg = warp; wg < h / P::G2; wg += nw) inv2_x2<T, R1, R2>(s, twx, yp, sc, ad, wg, lane);
+    }
+}
+
+template <typename T> size_t inv2_smem(const GridDev& g) {
+    using C = typename C2<T>::t;
+    return ((size_t)g.nx * (g.nx / 2 + 1) + 2 * (size_t)g.nx) * sizeof(C) + 16;
+}
+
+// 16 x 8 -> 16, 8 x 8 -> 8; 0 if the grid has no register-staged inverse pass
+int inv2_radix(const GridDev& g) {
+    if (g.nx != g.ny || g.ax.nst != 2 || g.ay.nst != 2 || g.ax.radix[1] != 8 || g.ay.radix[1] != 8) return 0;
+    if (g.ax.radix[0] != g.ay.radix[0]) return 0;
+    return (g.ax.radix[0] == 16 || g.ax.radix[0] == 8) ? g.ax.radix[0] : 0;
+}
+
 template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 16; }
 
 template <typename T> size_t zproj_smem(const GridDev& g, int W = zproj_width<T>()) {
@@ -1274,15 +1583,34 @@ const CUtensorMap* zmap(gff_handle* h, int W) {
     return &h->zmap[pi][wi];
 }
 
-template <typename T, int W>
-cudaError_t launch_z_tma_w(gff_handle* h, int threads, int blocks, const ProjArgs& pa, const int* skip,
+// 16 x 8 -> 16, 8 x 8 -> 8: the z plans with a register-staged strip; else 0
+int z2_radix(const GridDev& g) {
+    if (g.az.nst != 2 || g.az.radix[1] != 8) return 0;
+    return (g.az.radix[0] == 16 || g.az.radix[0] == 8) ? g.az.radix[0] : 0;
+}
+
+template <typename T, int W, int R1>
+cudaError_t launch_z_tma_k(gff_handle* h, int threads, int blocks, const ProjArgs& pa, const int* skip,
                            cudaStream_t st) {
     const CUtensorMap* tm = zmap<T>(h, W);
     if (!tm) return cudaErrorNotSupported;
+    if (threads > ztma_max_threads<T, R1>()) return cudaErrorInvalidValue;
     const size_t sm = ztma_smem<T, W>(h->g);
-    allow_smem(k_zproj_tma<T, W>, sm);
-    k_zproj_tma<T, W><<<blocks, threads, sm, st>>>(*tm, h->g, pa, skip, h->d_flag + 2);
+    allow_smem(k_zproj_tma<T, W, R1>, sm);
+    k_zproj_tma<T, W, R1><<<blocks, threads, sm, st>>>(*tm, h->g, pa, skip, h->d_flag + 2);
     return cudaGetLastError();
+}
+
+// blocks > 0: the TMA z pass with the generic strip; < 0: with the register-staged strip, -blocks blocks
+template <typename T, int W>
+cudaError_t launch_z_tma_w(gff_handle* h, int threads, int blocks, const ProjArgs& pa, const int* skip,
+                           cudaStream_t st) {
+    if (blocks > 0) return launch_z_tma_k<T, W, 0>(h, threads, blocks, pa, skip, st);
+    switch (z2_radix(h->g)) {
+        case 16: return launch_z_tma_k<T, W, 16>(h, threads, -blocks, pa, skip, st);
+        case 8: return launch_z_tma_k<T, W, 8>(h, threads, -blocks, pa, skip, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
@@ -1295,29 +1623,56 @@ cudaError_t launch_z_tma(gff_handle* h, int W, int threads, int blocks, const Pr
     }
 }
 
-// blocks of the TMA z pass: all that fit at once, at most one per strip; 0 if it cannot run
-template <typename T, int W>
-int z_tma_blocks_w(gff_handle* h, int threads) {
+// blocks of a TMA z pass: all that fit at once, at most one per strip; 0 if it cannot run
+template <typename T, int W, int R1>
+int z_tma_blocks_k(gff_handle* h, int threads) {
     const size_t sm = ztma_smem<T, W>(h->g);
-    if (sm > SMEM_MAX || !zmap<T>(h, W)) return 0;
+    if (sm > SMEM_MAX || !zmap<T>(h, W) || threads > ztma_max_threads<T, R1>()) return 0;
     int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    allow_smem(k_zproj_tma<T, W>, sm);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zproj_tma<T, W>, threads, sm) != cudaSuccess ||
+    allow_smem(k_zproj_tma<T, W, R1>, sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zproj_tma<T, W, R1>, threads, sm) != cudaSuccess ||
         per < 1)
         return 0;
     const int total = zproj_blocks(h->g, W);
     return nsm * per < total ? nsm * per : total;
 }
+template <typename T, int W>
+int z_tma_blocks_w(gff_handle* h, int threads, bool reg) {
+    if (!reg) return z_tma_blocks_k<T, W, 0>(h, threads);
+    switch (z2_radix(h->g)) {
+        case 16: return z_tma_blocks_k<T, W, 16>(h, threads);
+        case 8: return z_tma_blocks_k<T, W, 8>(h, threads);
+        default: return 0;
+    }
+}
+// > 0 blocks of the generic TMA z pass (reg false) or of the register-staged one (reg true); 0 if it cannot run
 template <typename T>
-int z_tma_blocks(gff_handle* h, int W, int threads) {
-    return W == 8 ? z_tma_blocks_w<T, 8>(h, threads) : (W == 16 ? z_tma_blocks_w<T, 16>(h, threads) : 0);
+int z_tma_blocks(gff_handle* h, int W, int threads, bool reg = false) {
+    return W == 8 ? z_tma_blocks_w<T, 8>(h, threads, reg) : (W == 16 ? z_tma_blocks_w<T, 16>(h, threads, reg) : 0);
 }
 
 template <typename T>
 cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename C2<T>::t* spec, T* y,
                        const OutArgs& oa, const int* skip, cudaStream_t st, bool vout, int* err) {
+    if (blocks < 0) {  // register-staged pass of the two-stage plans, one block per plane
+        const size_t sm = inv2_smem<T>(g);
+        const dim3 grid(9, g.nz);
+        const int r1 = inv2_radix(g);
+#define GFF_INV2(R, BT)                                                              \
+    if (r1 == R && threads == BT) {                                                  \
+        allow_smem(k_plane_inv2<T, R, 8, BT>, sm);                                   \
+        k_plane_inv2<T, R, 8, BT><<<grid, BT, sm, st>>>(spec, y, g, oa, skip, err);  \
+        return cudaGetLastError();                                                   \
+    }
+        GFF_INV2(16, 256)
+        GFF_INV2(16, 512)
+        GFF_INV2(8, 256)
+        GFF_INV2(8, 512)
+#undef GFF_INV2
+        return cudaErrorInvalidValue;
+    }
     if (blocks > 0) {
         const size_t sm = plane_stream_smem<T>(g);
         if (vout) {
@@ -1413,21 +1768,26 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     // z pass: one block per strip (W 4..32, 128 or 256 threads), or the persistent TMA pass (W 8, 16; 256, 512)
     // (the TMA pass also takes 192 / 384 threads: a strip of W columns has 24 W radix-16
     // butterflies at n = 128, so 384 threads at W = 16 and 192 at W = 8 take one each)
-    constexpr int NZC = 15;
-    const int wz[NZC] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16, 8, 8, 16};
-    const int tz[NZC] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512, 192, 384, 384};
+    // and (nz = 64 or 128) the TMA pass with the register-staged strip (W 8, 16; 256 threads)
+    constexpr int NZC = 17;
+    const int wz[NZC] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16, 8, 8, 16, 8, 16};
+    const int tz[NZC] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512, 192, 384, 384, 256, 256};
     int zb[NZC] = {0};
     bool zv[NZC];
     for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i]) <= SMEM_MAX;
-    for (int i = 8; i < NZC; ++i) {
+    for (int i = 8; i < 15; ++i) {
         zb[i] = z_tma_blocks<T>(h, wz[i], tz[i]);
         zv[i] = zb[i] > 0;
+    }
+    for (int i = 15; i < NZC; ++i) {  // negative: register-staged strip
+        zb[i] = -z_tma_blocks<T>(h, wz[i], tz[i], true);
+        zv[i] = zb[i] < 0;
     }
     ProjArgs pa;
     pa.kind = GFF_PROJ_CONTINUOUS;
     for (int c = 0; c < 9; ++c) pa.mask[c] = 0.f;
     e = pick_fastest(NZC, zv, reps, st, [&](int i) {
-        return zb[i] ? launch_z_tma<T>(h, wz[i], tz[i], zb[i], pa, nullptr, st)
+        return zb[i] != 0 ? launch_z_tma<T>(h, wz[i], tz[i], zb[i], pa, nullptr, st)
                      : launch_z<T>(g, wz[i], tz[i], spec, pa, nullptr, st);
     }, &b);
     if (e != cudaSuccess) return e;
@@ -1437,13 +1797,15 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     OutArgs oa;
     oa.scale = 1.0;
     for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
-    // one block per plane with 256 or 512 threads, or the persistent streamed pass with 512 or 1024
+    // one block per plane with 256 or 512 threads, the persistent streamed pass with 512 or 1024,
+    // or (two-stage plans, nx = ny) the register-staged pass with 256 or 512
     const bool vout = vec_ok<T>(g, y);
-    const int ti[4] = {256, 512, inv_stream_max_threads<T>() / 2, inv_stream_max_threads<T>()};
-    int ib[4] = {0, 0, inv_stream_blocks<T>(g, 512, vout), inv_stream_blocks<T>(g, 1024, vout)};
-    const bool iv[4] = {true, true, ib[2] > 0, ib[3] > 0};
+    const int ti[6] = {256, 512, inv_stream_max_threads<T>() / 2, inv_stream_max_threads<T>(), 256, 512};
+    int ib[6] = {0, 0, inv_stream_blocks<T>(g, 512, vout), inv_stream_blocks<T>(g, 1024, vout), -1, -1};
+    const bool r2 = inv2_radix(g) > 0 && inv2_smem<T>(g) <= SMEM_MAX;
+    const bool iv[6] = {true, true, ib[2] > 0, ib[3] > 0, r2, r2};
     int* err = h->d_flag + 2;
-    e = pick_fastest(4, iv, reps, st, [&](int i) { return launch_inv<T>(g, ti[i], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
+    e = pick_fastest(6, iv, reps, st, [&](int i) { return launch_inv<T>(g, ti[i], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
     if (e != cudaSuccess) return e;
     tn.t_inv = ti[b];
     tn.inv_blocks = ib[b];
@@ -1458,10 +1820,15 @@ bool tiles_valid(gff_handle* h, const Tune& t) {
     const GridDev& g = h->g;
     if ((t.t_fwd != 256 && t.t_fwd != 512) || (t.t_inv != 256 && t.t_inv != 512 && t.t_inv != 1024)) return false;
     if (t.wz != 4 && t.wz != 8 && t.wz != 16 && t.wz != 32) return false;
-    if (t.inv_blocks < 0 || t.z_blocks < 0) return false;
+    if (t.inv_blocks < -1) return false;
+    if (t.inv_blocks == -1 && (inv2_radix(g) == 0 || inv2_smem<T>(g) > SMEM_MAX || (t.t_inv != 256 && t.t_inv != 512)))
+        return false;
     if (t.z_blocks > 0) {
         if ((t.t_z != 192 && t.t_z != 256 && t.t_z != 384 && t.t_z != 512) || z_tma_blocks<T>(h, t.wz, t.t_z) < 1)
             return false;
+    } else if (t.z_blocks < 0) {  // register-staged strip: -z_blocks blocks, at most the resident count
+        const int mx = z_tma_blocks<T>(h, t.wz, t.t_z, true);
+        if (t.t_z != 256 || mx < 1 || -t.z_blocks > mx) return false;
     } else if ((t.t_z != 128 && t.t_z != 256) || zproj_smem<T>(g, t.wz) > SMEM_MAX) {
         return false;
     }
@@ -1616,7 +1983,7 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     // the TMA pass addresses the handle's own spectrum through its tensor map
     if (pa.sym)
         e = launch_zsym<T>(g, spec, pa, skip, h->stream);
-    else if (tn.z_blocks > 0 && static_cast<const void*>(spec) == h->d_spec)
+    else if (tn.z_blocks != 0 && static_cast<const void*>(spec) == h->d_spec)
         e = launch_z_tma<T>(const_cast<gff_handle*>(h), tn.wz, tn.t_z, tn.z_blocks, pa, skip, h->stream);
     else
         e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, skip, h->stream);

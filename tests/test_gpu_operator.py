@@ -184,6 +184,60 @@ def test_launch_shapes_give_identical_results(prec):
         g.gff_destroy(h)
 
 
+@pytest.mark.parametrize("shape", [(64, 64, 64), (12, 128, 128), (128, 16, 32)])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_register_staged_passes_are_bit_identical(shape, prec):
+    """The register-staged passes of the two-stage plans -- the inverse plane
+    pass for nx = ny = 64 (8 x 8) or 128 (16 x 8), tiles inv blocks = -1 with
+    256 or 512 threads, and the TMA z pass's strip for nz = 64 or 128, TMA z
+    blocks < 0 -- perform the operations of the generic passes in the same
+    order: y equal bit for bit, with and without the mixed-control mask, and
+    the oracle's."""
+    torch = torch_cuda()
+    nz, ny, nx = shape
+    g, ms, h = _svk_handle(shape, 12, 21)
+    inv2 = nx == ny and nx in (64, 128)
+    z2 = nz in (64, 128)
+    shapes = [(512, 8, 256, 512, 0, 0)]
+    if inv2:
+        shapes += [(512, 8, 256, 256, -1, 0), (512, 8, 256, 512, -1, 0), (256, 16, 256, 512, -1, 7)]
+    if z2:
+        shapes += [(512, 16, 256, 512, 0, -5), (256, 8, 256, 256, 0, -3)]
+    if inv2 and z2:
+        shapes += [(512, 16, 256, 512, -1, -11)]
+    try:
+        g.gff_constitutive(h, 1.0)
+        x = _field(13, shape).reshape(9, -1)
+        X = torch.from_numpy(x.copy()).cuda()
+        if prec == 1:
+            X = X.float()
+        outs = []
+        for s in shapes:
+            g.gff_set_tiles(h, s, s)
+            for mask in (None, MASKS[1]):
+                Y = torch.empty_like(X)
+                g.gff_apply_operator(h, prec, mask, X, Y)
+                g.gff_sync(h)
+                outs.append(Y.double().cpu().numpy())
+        for i in range(2, len(outs)):
+            assert np.array_equal(outs[i], outs[i % 2])
+        F = np.tile(np.eye(3).reshape(3, 3, 1, 1, 1), (1, 1) + shape)
+        _, K = voxel_K_oracle(ms, F)
+        ref = sp.GK(K, x.reshape(3, 3, nz, ny, nx), ms.L, sp.KIND_CONTINUOUS)
+        assert rel_l2(outs[0], ref.reshape(9, -1)) <= (1e-12 if prec == 0 else 2e-6)
+        refused = [(512, 8, 256, 1024, -1, 0)]  # 1024 threads is not a shape of the inverse pass
+        if not inv2:
+            refused.append((512, 8, 256, 512, -1, 0))
+        if not z2:
+            refused.append((512, 16, 256, 512, 0, -5))
+        refused.append((512, 16, 384, 512, 0, -5))  # the register-staged strip runs 256 threads
+        for s in refused:
+            with pytest.raises(g.GffError):
+                g.gff_set_tiles(h, s, s)
+    finally:
+        g.gff_destroy(h)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_bounded_wait_timeout_is_reported_and_recoverable(prec):
     """The inverse FFT pass waits on an asynchronous (TMA) copy with a bounded
