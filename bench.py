@@ -484,9 +484,11 @@ def cyclic_increments(g, torch, args, clock_index):
         arms["mixed_" + pname] = time_arm(g, torch, ms2, hist, 1, proj, clock_index=clock_index)
         arms["mixed_extrapolated_" + pname] = time_arm(g, torch, ms2, hist, 1, proj, g.GFF_WARM_EXTRAPOLATE,
                                                        clock_index=clock_index)
-        arms["mixed_extrapolated_f32first_" + pname] = time_arm(g, torch, ms2, hist, 1, proj,
-                                                                g.GFF_WARM_EXTRAPOLATE, clock_index=clock_index,
-                                                                return_map=g.GFF_RETURN_MAP_F32_FIRST)
+        # the mixed arms run the default return map (FP32 pre-iteration, then FP64); this one the FP64
+        # iteration alone, which shows what the pre-iteration saves
+        arms["mixed_extrapolated_fp64map_" + pname] = time_arm(g, torch, ms2, hist, 1, proj,
+                                                               g.GFF_WARM_EXTRAPOLATE, clock_index=clock_index,
+                                                               return_map=g.GFF_RETURN_MAP_FP64)
     macro_errors({k: v for k, v in arms.items() if k.endswith("continuous")}, "fp64_continuous")
     macro_errors({k: v for k, v in arms.items() if k.endswith("discrete")}, "fp64_discrete")
     out["config2"] = {"workload": "64^3, 200-grain periodic Voronoi (seed 2), FCC crystal plasticity, R=-1 +-1 pct "

@@ -253,17 +253,26 @@ gff_status gff_set_strain_measure(gff_handle* h, int mode);
 
 /* How the crystal-plasticity return maps are iterated (the paper leaves it
  * open; the root of the backward-Euler residual of Eq. gamma_dot is the same):
- * GFF_RETURN_MAP_DEFAULT: Newton steps with the small-elastic-strain Jacobian
- *   from the previous iterate's slips, then, if that fails, exact Newton from
- *   zero slip (the fallback, counted in gff_step_report.cp_fallbacks);
+ * GFF_RETURN_MAP_FP64: Newton steps with the small-elastic-strain Jacobian
+ *   from the previous iterate's slips, in FP64, then, if that fails, exact
+ *   Newton from zero slip (the fallback, counted in
+ *   gff_step_report.cp_fallbacks);
+ * GFF_RETURN_MAP_F32_FIRST: the same FP64 iteration preceded by that
+ *   iteration in FP32 (elastic state formed from the small quantities F - I
+ *   and Fp^-1 - I) down to FP32 resolution; the FP64 iteration then starts
+ *   from its root.  The FP64 residual still decides convergence, so the root
+ *   is GFF_RETURN_MAP_FP64's to the return-map tolerance;
+ * GFF_RETURN_MAP_DEFAULT (a new handle's mode): GFF_RETURN_MAP_F32_FIRST when
+ *   the handle's precision is GFF_PREC_MIXED, GFF_RETURN_MAP_FP64 in
+ *   GFF_PREC_FP64;
  * GFF_RETURN_MAP_EXACT: exact Newton (12x12 LU with partial pivoting) from
- *   zero slip only -- every return map counts as a fallback;
- * GFF_RETURN_MAP_F32_FIRST: the default, preceded by the same iteration in
- *   FP32 (elastic state formed from the small quantities F - I and
- *   Fp^-1 - I) down to FP32 resolution; the FP64 iteration then starts from
- *   its root.  The FP64 residual still decides convergence, so the root is
- *   the default's to the return-map tolerance. */
-enum { GFF_RETURN_MAP_DEFAULT = 0, GFF_RETURN_MAP_EXACT = 1, GFF_RETURN_MAP_F32_FIRST = 2 };
+ *   zero slip only -- every return map counts as a fallback. */
+enum {
+    GFF_RETURN_MAP_DEFAULT = 0,
+    GFF_RETURN_MAP_EXACT = 1,
+    GFF_RETURN_MAP_F32_FIRST = 2,
+    GFF_RETURN_MAP_FP64 = 3
+};
 gff_status gff_set_return_map(gff_handle* h, int mode);
 
 /* y = G_M(x) = F^-1{ G^ : F(x) }  (Eq. eql_discrete3), same conventions. */

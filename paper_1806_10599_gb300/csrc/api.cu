@@ -758,10 +758,10 @@ GFF_EXPORT gff_status gff_set_strain_measure(gff_handle* h, int mode) {
 }
 
 GFF_EXPORT gff_status gff_set_return_map(gff_handle* h, int mode) {
-    if (!h || (mode != GFF_RETURN_MAP_DEFAULT && mode != GFF_RETURN_MAP_EXACT && mode != GFF_RETURN_MAP_F32_FIRST))
-        return fail(h, GFF_ERR_ARG, "return-map mode must be 0, 1 or 2");
+    if (!h || mode < GFF_RETURN_MAP_DEFAULT || mode > GFF_RETURN_MAP_FP64)
+        return fail(h, GFF_ERR_ARG, "return-map mode must be 0, 1, 2 or 3");
     h->cp_exact_only = mode == GFF_RETURN_MAP_EXACT ? 1 : 0;
-    h->cp_f32_first = mode == GFF_RETURN_MAP_F32_FIRST ? 1 : 0;
+    h->cp_f32_first = mode == GFF_RETURN_MAP_F32_FIRST ? 1 : (mode == GFF_RETURN_MAP_DEFAULT ? 2 : 0);
     return GFF_OK;
 }
 

@@ -184,7 +184,7 @@ struct gff_handle {
     double* d_tau = nullptr;   // [12][N]
     double* d_acc = nullptr;   // [NACC][N]
     int cp_exact_only = 0;     // 1: every return map runs the exact Newton from dg = 0 (gff_set_return_map)
-    int cp_f32_first = 0;      // 1: FP32 pre-iteration before the FP64 iteration (gff_set_return_map)
+    int cp_f32_first = 2;      // FP32 pre-iteration before the FP64 iteration: 1 always, 2 in mixed precision, 0 never
     int small_strain = 0;      // 1: small-strain variant: d_F holds the strain, sigma = C : eps, symmetric projection
     int* d_flag = nullptr;     // device status words: [0] CP failures, [2] timed-out bulk-copy waits,
                                // [4] return-map fallbacks, [5] local Newton iterations

@@ -1358,6 +1358,11 @@ cudaError_t preload_constitutive() {
     return e;
 }
 
+// the return-map mode's FP32 pre-iteration for this handle (gff_set_return_map)
+int f32_first(const gff_handle* h) {
+    return h->cp_f32_first == 1 || (h->cp_f32_first == 2 && h->opt.precision == GFF_PREC_MIXED) ? 1 : 0;
+}
+
 cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int tangent, bool warm, int part) {
     ConstArgs a;
     a.F = F;
@@ -1370,7 +1375,7 @@ cudaError_t launch_constitutive(gff_handle* h, const double* F, double dt, int t
     a.warm_dev = nullptr;
     a.exact = h->cp_exact_only;
     a.small = h->small_strain;
-    a.f32first = h->cp_f32_first;
+    a.f32first = f32_first(h);
     a.rtol = return_map_tol(h->opt.newton_tol);
     a.gkind = h->d_gkind;
     a.gprm = h->d_nrm + 36LL * h->ngrains;  // parameters stored after the normals
@@ -1425,7 +1430,7 @@ cudaError_t upload_constitutive_batch(gff_handle* const* hs, int n, double dt, i
         a.warm_dev = warm_dev ? warm_dev + r : nullptr;
         a.exact = h->cp_exact_only;
         a.small = h->small_strain;
-        a.f32first = h->cp_f32_first;
+        a.f32first = f32_first(h);
         a.rtol = return_map_tol(h->opt.newton_tol);
         a.gkind = h->d_gkind;
         a.gprm = h->d_nrm + 36LL * h->ngrains;

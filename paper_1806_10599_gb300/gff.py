@@ -28,7 +28,7 @@ GFF_PROJ_CONTINUOUS, GFF_PROJ_DISCRETE = 0, 1
 GFF_WARM_OFF, GFF_WARM_NET_IF_BETTER, GFF_WARM_NET, GFF_WARM_EXTRAPOLATE = 0, 1, 2, 3
 UNET_IN = 32  # input channels of the warm-start network
 GFF_PREC_FP64, GFF_PREC_MIXED = 0, 1
-GFF_RETURN_MAP_DEFAULT, GFF_RETURN_MAP_EXACT, GFF_RETURN_MAP_F32_FIRST = 0, 1, 2
+GFF_RETURN_MAP_DEFAULT, GFF_RETURN_MAP_EXACT, GFF_RETURN_MAP_F32_FIRST, GFF_RETURN_MAP_FP64 = 0, 1, 2, 3
 GFF_STRAIN_FINITE, GFF_STRAIN_SMALL = 0, 1
 GFF_MAT_SVK_CUBIC, GFF_MAT_SVK_ISO, GFF_MAT_CP_FCC, GFF_MAT_NEOHOOKE = 0, 1, 2, 3
 (GFF_FIELD_F, GFF_FIELD_P, GFF_FIELD_K, GFF_FIELD_FP_INV, GFF_FIELD_CHI,

@@ -165,6 +165,26 @@ def test_fp32_pre_iteration_reaches_the_oracle_root(oracle_runs, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
+def test_default_return_map_is_f32_first_in_mixed_and_fp64_in_fp64(precision):
+    """GFF_RETURN_MAP_DEFAULT runs the FP32 pre-iteration in mixed precision and
+    the FP64 iteration alone in FP64: bit for bit the explicit modes."""
+    g = gff()
+    mixed = precision == 1
+    kw = dict(newton_tol=1e-9 if mixed else TOL, cg_tol=1e-6 if mixed else TOL)
+    a = _gpu_run("c8_cont", precision, **kw)
+    b = _gpu_run("c8_cont", precision, return_map=g.GFF_RETURN_MAP_F32_FIRST if mixed else g.GFF_RETURN_MAP_FP64,
+                 **kw)
+    c = _gpu_run("c8_cont", precision, return_map=g.GFF_RETURN_MAP_FP64 if mixed else g.GFF_RETURN_MAP_F32_FIRST,
+                 **kw)
+    F, FPI = g.GFF_FIELD_F, g.GFF_FIELD_FP_INV
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[2][F], b[2][F]) and np.array_equal(a[2][FPI], b[2][FPI])
+    # the other mode iterates differently: the same root to the tolerances, not the same bits
+    assert not np.array_equal(a[2][FPI], c[2][FPI])
+    assert np.abs(a[0] - c[0]).max() <= 1e-6 * np.abs(a[0]).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
 def test_cycle_and_restart_16cube(oracle_runs, precision):
     mixed = precision == 1
     Pm, reps, f, fips = _gpu_run("c16", precision, newton_tol=1e-9 if mixed else TOL, cg_tol=1e-6 if mixed else TOL)
