@@ -309,6 +309,7 @@ BatchLaunch class_launch(const std::vector<RveApply>& rv, RveApply* d_rv, int* d
     // the batched passes run the one-block-per-strip z kernel (at most 256 threads) and
     // the one-block-per-plane inverse (at most 512): persistent shapes map onto them,
     // and every shape gives the same bits
+    bl.tn.t_fwd = std::abs(bl.tn.t_fwd);  // (negative: the register-staged pass of one handle)
     bl.tn.t_z = std::min(bl.tn.t_z, 256);
     bl.tn.t_inv = std::min(bl.tn.t_inv, 512);
     bl.withK = withK;

@@ -381,30 +381,16 @@ template <typename T> constexpr int SPLIT_ROWS = sizeof(T) == 4 ? 4 : 1;
 template <typename T> constexpr int SPLIT_G = 32 / SPLIT_ROWS<T>;
 template <typename T> constexpr int SPLIT_K = (MAXN / 2 + SPLIT_G<T>) / SPLIT_G<T>;  // covers k = 0 .. MAXN/2
 
+// (K:x)_c (or x_c alone) of plane z written as ny/2 packed complex rows: row pair r
+// (real part row 2r, imaginary part row 2r+1) at s + 2 r ls.
 template <typename T, bool WITH_K, bool VEC>
-__device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T* __restrict__ K,
-                                               typename C2<T>::t* __restrict__ spec, const GridDev& g, const int c,
-                                               const int z, unsigned char* sm_raw) {
+__device__ __forceinline__ void plane_contract(typename C2<T>::t* s, const T* __restrict__ x, const T* __restrict__ K,
+                                               const GridDev& g, const int c, const int z, const int ls) {
     using C = typename C2<T>::t;
-    const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
-    C* s = reinterpret_cast<C*>(sm_raw);
-    C* twx = s + ny * ls;
-    C* twy = twx + nx;
-    int* posx = reinterpret_cast<int*>(twy + ny);
-    int* posy = posx + nx;  // position of each y frequency after the forward y transform
+    const int nx = g.nx, ny = g.ny, half = ny / 2;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const long long N = g.N;
     const long long pl = (long long)z * ny * nx;
-
-    for (int i = tid; i < nx; i += nthr) {
-        twx[i] = twp<T>(g, 0)[i];
-        posx[i] = g.posx[i];
-    }
-    for (int i = tid; i < ny; i += nthr) {
-        twy[i] = twp<T>(g, 1)[i];
-        posy[g.fqy[i]] = i;
-    }
-
     if (VEC) {
         // 16-byte loads of VW consecutive voxels of one row; K row c is read
         // once, the 9 components of x are shared by the 9 CTAs of this plane.
@@ -480,6 +466,31 @@ __device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T*
             s[r * 2 * ls + xi] = mk<C>(a, b);
         }
     }
+}
+
+template <typename T, bool WITH_K, bool VEC>
+__device__ __forceinline__ void plane_fwd_body(const T* __restrict__ x, const T* __restrict__ K,
+                                               typename C2<T>::t* __restrict__ spec, const GridDev& g, const int c,
+                                               const int z, unsigned char* sm_raw) {
+    using C = typename C2<T>::t;
+    const int nx = g.nx, ny = g.ny, nxh = g.nxh, ls = nxh, half = ny / 2;
+    C* s = reinterpret_cast<C*>(sm_raw);
+    C* twx = s + ny * ls;
+    C* twy = twx + nx;
+    int* posx = reinterpret_cast<int*>(twy + ny);
+    int* posy = posx + nx;  // position of each y frequency after the forward y transform
+    const int tid = threadIdx.x, nthr = blockDim.x;
+
+    for (int i = tid; i < nx; i += nthr) {
+        twx[i] = twp<T>(g, 0)[i];
+        posx[i] = g.posx[i];
+    }
+    for (int i = tid; i < ny; i += nthr) {
+        twy[i] = twp<T>(g, 1)[i];
+        posy[g.fqy[i]] = i;
+    }
+
+    plane_contract<T, WITH_K, VEC>(s, x, K, g, c, z, ls);
     __syncthreads();
     // x transform of the ny/2 packed rows (row pair r at offset 2 r ls); rows are the
     // fast thread index, so that neighbouring lanes read neighbouring rows rather than
@@ -892,14 +903,17 @@ template <typename T, int W> size_t ztma_smem(const GridDev& g) {
     return 2 * zstrip_bytes<T, W>(g.nz) + ztables_bytes<T>(g.nz, g.ny, g.nxh, W) + 160;
 }
 
-// R1 = 0: any nz (zproj_strip); R1 = 16 / 8: nz = 128 / 64 with the register-staged
-// strip (zstrip2), 256 threads whose register budget holds the 24 complex values of
-// the fused middle stage: two blocks per SM in FP32, one in FP64
-template <typename T, int R1> constexpr int ztma_max_threads() { return R1 ? 256 : 512; }
-template <typename T, int R1> constexpr int ztma_min_blocks() { return (R1 && sizeof(T) == 4) ? 2 : 1; }
+// R1 = 0: any nz (zproj_strip), up to BT = 512 threads; R1 = 16 / 8: nz = 128 / 64 with
+// the register-staged strip (zstrip2), whose register budget holds the 24 complex values
+// of the fused middle stage: BT = 256 threads, two blocks per SM in FP32 and one in FP64,
+// or (FP32) BT = 384, one block per SM, where the 384 radix-16 tasks of a W = 16 strip
+// take one round instead of two
+template <typename T, int R1, int BT> constexpr int ztma_min_blocks() {
+    return (R1 && sizeof(T) == 4 && BT == 256) ? 2 : 1;
+}
 
-template <typename T, int W, int R1>
-__global__ void __launch_bounds__(ztma_max_threads<T, R1>(), ztma_min_blocks<T, R1>())
+template <typename T, int W, int R1, int BT>
+__global__ void __launch_bounds__(BT, ztma_min_blocks<T, R1, BT>())
     k_zproj_tma(const __grid_constant__ CUtensorMap tm, GridDev g, ProjArgs pa, const int* __restrict__ skip,
                 int* __restrict__ err) {
     using C = typename C2<T>::t;
@@ -1218,21 +1232,25 @@ __global__ void __launch_bounds__(inv_stream_max_threads<T>()) k_plane_inv_strea
 //       Z_k = A_k + i B_k and Z_{n-k} = conj(A_k) + i conj(B_k) (A, B the half
 //       spectra of rows 2r, 2r+1) come from the same stored columns; the
 //       result overwrites rows 2r, 2r+1, XOR-swizzled inside each run of 8;
-//   X2  radix R1 with twiddles, epilogue, stores straight to y.
-// A warp's row pairs in X1 / X2 are 2 apart: with the row stride n/2 + 1 every
-// shared-memory access of the four phases is free of bank conflicts.  The
-// half-spectrum plane arrives by one bulk asynchronous copy with a bounded
-// wait, as in k_plane_inv.
+//   X2  radix R1 with twiddles (from a [j][p] table padded to R1 + 1 per row),
+//       epilogue, stores straight to y.
+// Shared memory serves 8-byte accesses a half-warp and 16-byte ones a quarter-
+// warp at a time; the row pairs that share such a phase in X1 / X2 are S = L/2
+// apart (L lanes per row pair), which with the row stride n/2 + 1 puts every
+// access of the four phases in distinct banks.  The half-spectrum plane
+// arrives by one bulk asynchronous copy with a bounded wait, as in k_plane_inv.
 template <int R1, int R2> struct Inv2Plan {
     static_assert(R2 == 8 && (R1 == 8 || R1 == 16), "two-stage plans 8 x 8 and 16 x 8");
     static constexpr int n = R1 * R2, h = n / 2, nxh = h + 1;
-    static constexpr int L1 = R1 / 2, G1 = 32 / L1;  // X1: lanes per row pair, row pairs per warp
-    static constexpr int L2 = R2, G2 = 32 / R2;      // X2
-    static constexpr bool SAMEWARP = (G1 == G2);     // X1 and X2 give a warp the same row pairs
+    static constexpr int L1 = R1 / 2, G1 = 32 / L1, S1 = L1 / 2;  // X1: lanes per row pair, pairs per warp, spacing
+    static constexpr int L2 = R2, G2 = 32 / R2, S2 = L2 / 2;      // X2
+    static constexpr bool SAMEWARP = (G1 == G2 && S1 == S2);      // X1 and X2 give a warp the same row pairs
+    static constexpr int TWS = R1 + 1;                            // row stride of the X2 twiddle table
 };
 
 __device__ __forceinline__ int swz8(int p) { return (p & ~7) | ((p ^ (p >> 3)) & 7); }
-__device__ __forceinline__ int inv2_pair(int wg, int k, int G) { return (wg & 1) + 2 * k + (wg >> 1) * 2 * G; }
+// row pair of lane group k of warp group wg: groups S apart, S G consecutive pairs per S warp groups
+__device__ __forceinline__ int inv2_pair(int wg, int k, int G, int S) { return wg % S + S * k + (wg / S) * S * G; }
 
 template <typename T, int R1, int R2>
 __device__ __forceinline__ void inv2_x1(typename C2<T>::t* s, int wg, int lane) {
@@ -1240,7 +1258,7 @@ __device__ __forceinline__ void inv2_x1(typename C2<T>::t* s, int wg, int lane) 
     using P = Inv2Plan<R1, R2>;
     constexpr int HQ = R2 / 2;
     const int k = lane / P::L1, u = lane % P::L1;
-    const int r = inv2_pair(wg, k, P::G1);
+    const int r = inv2_pair(wg, k, P::G1, P::S1);
     C* A = s + 2 * r * P::nxh;
     const C* B = A + P::nxh;
     const int c1 = u, c2 = u ? R1 - u : R1 / 2;
@@ -1284,19 +1302,20 @@ __device__ __forceinline__ void inv2_x1(typename C2<T>::t* s, int wg, int lane) 
 }
 
 template <typename T, int R1, int R2>
-__device__ __forceinline__ void inv2_x2(const typename C2<T>::t* s, const typename C2<T>::t* twx, T* __restrict__ yp,
+__device__ __forceinline__ void inv2_x2(const typename C2<T>::t* s, const typename C2<T>::t* twx2, T* __restrict__ yp,
                                         T sc, T ad, int wg, int lane) {
     using C = typename C2<T>::t;
     using P = Inv2Plan<R1, R2>;
     const int k = lane / P::L2, j = lane % P::L2;
-    const int r = inv2_pair(wg, k, P::G2);
+    const int r = inv2_pair(wg, k, P::G2, P::S2);
     const C* Z = s + 2 * r * P::nxh;
+    const C* tw = twx2 + j * P::TWS;  // tw[p] = W_n^(p j)
     C v[R1];
 #pragma unroll
     for (int q = 0; q < R1; ++q) v[q] = Z[swz8(j + R2 * q)];
     if (j) {
 #pragma unroll
-        for (int p = 1; p < R1; ++p) v[p] = cmulc(v[p], twx[p * j]);
+        for (int p = 1; p < R1; ++p) v[p] = cmulc(v[p], tw[p]);
     }
     Bfly<R1, true, C>::run(v);
     T* y0 = yp + (long long)(2 * r) * P::n;
@@ -1322,9 +1341,10 @@ __global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(con
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     C* s = reinterpret_cast<C*>(sm_raw);  // [n][nxh]
-    C* twx = s + n * nxh;
-    C* twy = twx + n;
-    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(twy + n) + 7) & ~uintptr_t(7));
+    C* twy = s + n * nxh;                  // [n]: W_n^k of the y axis
+    C* twx2 = twy + n;                     // [R2][R1 + 1]: W_n^(p j) of the x axis
+    uint64_t* bar =
+        reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(twx2 + R2 * P::TWS) + 7) & ~uintptr_t(7));
     const int c = blockIdx.x, z = blockIdx.y;
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) {
@@ -1334,9 +1354,10 @@ __global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(con
     __syncthreads();
     if (tid == 0)  // n nxh sizeof(C) is a multiple of 16 (n even), the plane start too
         bulk_load(s, spec + ((long long)c * g.nz + z) * (n * nxh), (uint32_t)(n * nxh * sizeof(C)), bar);
-    for (int i = tid; i < n; i += nthr) {
-        twx[i] = twp<T>(g, 0)[i];
-        twy[i] = twp<T>(g, 1)[i];
+    for (int i = tid; i < n; i += nthr) twy[i] = twp<T>(g, 1)[i];
+    for (int i = tid; i < R2 * P::TWS; i += nthr) {
+        const int j = i / P::TWS, p = i - j * P::TWS;
+        twx2[i] = p < R1 ? twp<T>(g, 0)[p * j] : mk<C>((T)0, (T)0);
     }
     const bool ok = mbar_wait(bar, 0u, g.wait_cycles);
     if (__syncthreads_or(!ok)) {
@@ -1390,18 +1411,19 @@ __global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(con
         for (int wg = warp; wg < h / P::G1; wg += nw) {  // warp-uniform
             inv2_x1<T, R1, R2>(s, wg, lane);
             __syncwarp();
-            inv2_x2<T, R1, R2>(s, twx, yp, sc, ad, wg, lane);
+            inv2_x2<T, R1, R2>(s, twx2, yp, sc, ad, wg, lane);
         }
     } else {
         for (int wg = warp; wg < h / P::G1; wg += nw) inv2_x1<T, R1, R2>(s, wg, lane);
         __syncthreads();
-        for (int wg = warp; wg < h / P::G2; wg += nw) inv2_x2<T, R1, R2>(s, twx, yp, sc, ad, wg, lane);
+        for (int wg = warp; wg < h / P::G2; wg += nw) inv2_x2<T, R1, R2>(s, twx2, yp, sc, ad, wg, lane);
     }
 }
 
 template <typename T> size_t inv2_smem(const GridDev& g) {
     using C = typename C2<T>::t;
-    return ((size_t)g.nx * (g.nx / 2 + 1) + 2 * (size_t)g.nx) * sizeof(C) + 16;
+    // plane, y twiddles, x twiddle table [8][R1 + 1] (R1 <= 16), barrier
+    return ((size_t)g.nx * (g.nx / 2 + 1) + (size_t)g.nx + 8 * 17) * sizeof(C) + 16;
 }
 
 // 16 x 8 -> 16, 8 x 8 -> 8; 0 if the grid has no register-staged inverse pass
@@ -1409,6 +1431,176 @@ int inv2_radix(const GridDev& g) {
     if (g.nx != g.ny || g.ax.nst != 2 || g.ay.nst != 2 || g.ax.radix[1] != 8 || g.ay.radix[1] != 8) return 0;
     if (g.ax.radix[0] != g.ay.radix[0]) return 0;
     return (g.ax.radix[0] == 16 || g.ax.radix[0] == 8) ? g.ax.radix[0] : 0;
+}
+
+// ---------------------------------------------------------------- pass 1 for two-stage plans, register-staged
+// The mirror of k_plane_inv2 for the forward pass of planes with nx = ny = n =
+// R1 8 (16 x 8, 8 x 8) with K: the operations of plane_fwd_body in the same
+// order (bit-identical), with 8 passes over shared memory instead of 12:
+//   C   (K:x)_c into packed rows, as in plane_fwd_body (16-byte loads);
+//   X1  the thread of (packed row r, j) runs the x transform's radix-R1 stage
+//       with twiddles over positions j + 8 n1 and writes positions j + 8 p
+//       (XOR-swizzled inside each run of 8) in place;
+//   X2  radix 8 over the runs sub and R1 - sub (0 and R1/2) of one packed row,
+//       whose outputs are the mirror frequencies k and n - k, so the split into
+//       the half spectra A_k, B_k of rows 2r, 2r+1 (and the packing of X_h into
+//       column 0) happens in registers; written in place as rows 2r, 2r+1;
+//   Y1  radix R1 of the y transform with twiddles over columns kx < n/2;
+//   Y2  radix 8, stored straight to the half spectrum, except column 0, whose
+//       DC and Nyquist parts are separated after one more barrier.
+// (Forming K:x in registers at the X1 positions, scalar loads 8 voxels apart,
+// measured 1.3x slower in FP32 at 128^3 than these 16-byte loads.)
+template <typename T, int R1>
+__device__ __forceinline__ void fwd2_x1(typename C2<T>::t* s, const typename C2<T>::t* twx2, int wg, int lane) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, 8>;
+    const int k = lane / P::L2, j = lane % P::L2;
+    const int r = inv2_pair(wg, k, P::G2, P::S2);
+    C* Z = s + 2 * r * P::nxh;
+    C v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = Z[j + 8 * n1];
+    Bfly<R1, false, C>::run(v);
+    if (j) {
+        const C* tw = twx2 + j * P::TWS;
+#pragma unroll
+        for (int p = 1; p < R1; ++p) v[p] = cmul(v[p], tw[p]);
+    }
+    __syncwarp();  // every lane of the warp has read its packed row before it is overwritten
+#pragma unroll
+    for (int p = 0; p < R1; ++p) Z[swz8(j + 8 * p)] = v[p];
+}
+
+template <typename T, int R1>
+__device__ __forceinline__ void fwd2_x2(typename C2<T>::t* s, int wg, int lane) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, 8>;
+    constexpr int R2 = 8, HQ = 4, n = P::n;
+    const int k = lane / P::L1, u = lane % P::L1;
+    const int r = inv2_pair(wg, k, P::G1, P::S1);
+    C* A = s + 2 * r * P::nxh;  // row 2r; row 2r + 1 follows at A + nxh
+    const int c1 = u, c2 = u ? R1 - u : R1 / 2;
+    C za[R2], zb[R2];
+#pragma unroll
+    for (int q = 0; q < R2; ++q) {
+        za[q] = A[swz8(c1 * R2 + q)];
+        zb[q] = A[swz8(c2 * R2 + q)];
+    }
+    Bfly<R2, false, C>::run(za);
+    Bfly<R2, false, C>::run(zb);
+    // za[q] holds frequency c1 + R1 q, zb[q] frequency c2 + R1 q; the mirror n - k of
+    // c1 + R1 q is c2 + R1 (R2-1-q) for c1 != 0 and R1 (R2 - q) for c1 = 0
+    __syncwarp();  // every lane of the warp has read its packed row before the rows are written
+    const T hf = (T)0.5;
+    auto split = [&](const C zk, const C zm, int kk) {
+        A[kk] = mk<C>((zk.x + zm.x) * hf, (zk.y - zm.y) * hf);
+        A[P::nxh + kk] = mk<C>((zk.y + zm.y) * hf, (zm.x - zk.x) * hf);
+    };
+    if (u) {
+#pragma unroll
+        for (int q = 0; q < HQ; ++q) {
+            split(za[q], zb[R2 - 1 - q], c1 + R1 * q);
+            split(zb[q], za[R2 - 1 - q], c2 + R1 * q);
+        }
+    } else {
+        // k = 0 and n/2 (za[0], za[HQ]) are their own mirrors: A_0, B_0, A_h, B_h are real,
+        // and column 0 carries X_0 + i X_h of both rows
+        const C z0 = za[0], zh = za[HQ];
+        A[0] = mk<C>((z0.x + z0.x) * hf, (zh.x + zh.x) * hf);
+        A[P::nxh] = mk<C>((z0.y + z0.y) * hf, (zh.y + zh.y) * hf);
+#pragma unroll
+        for (int q = 1; q < HQ; ++q) split(za[q], za[R2 - q], R1 * q);
+#pragma unroll
+        for (int q = 0; q < HQ; ++q) split(zb[q], zb[R2 - 1 - q], c2 + R1 * q);
+    }
+    (void)n;
+}
+
+template <typename T, int BT> constexpr int fwd2_min_blocks() { return sizeof(T) == 4 ? (BT == 256 ? 3 : 2) : 1; }
+
+template <typename T, int R1, int BT>
+__global__ void __launch_bounds__(BT, fwd2_min_blocks<T, BT>()) k_plane_fwd2(const T* __restrict__ x,
+                                                                           const T* __restrict__ K,
+                                                                           typename C2<T>::t* __restrict__ spec,
+                                                                           GridDev g, const int* __restrict__ skip) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, 8>;
+    constexpr int n = P::n, h = P::h, nxh = P::nxh, R2 = 8;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* s = reinterpret_cast<C*>(sm_raw);  // [n][nxh]
+    C* twy = s + n * nxh;                  // [n]: W_n^k of the y axis
+    C* twx2 = twy + n;                     // [8][R1 + 1]: W_n^(p j) of the x axis
+    const int c = blockIdx.x, z = blockIdx.y;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int i = tid; i < n; i += nthr) twy[i] = twp<T>(g, 1)[i];
+    for (int i = tid; i < R2 * P::TWS; i += nthr) {
+        const int j = i / P::TWS, p = i - j * P::TWS;
+        twx2[i] = p < R1 ? twp<T>(g, 0)[p * j] : mk<C>((T)0, (T)0);
+    }
+    plane_contract<T, true, true>(s, x, K, g, c, z, nxh);
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    if (P::SAMEWARP) {
+        for (int wg = warp; wg < h / P::G2; wg += nw) {  // warp-uniform
+            fwd2_x1<T, R1>(s, twx2, wg, lane);
+            __syncwarp();
+            fwd2_x2<T, R1>(s, wg, lane);
+        }
+    } else {
+        for (int wg = warp; wg < h / P::G2; wg += nw) fwd2_x1<T, R1>(s, twx2, wg, lane);
+        __syncthreads();
+        for (int wg = warp; wg < h / P::G1; wg += nw) fwd2_x2<T, R1>(s, wg, lane);
+    }
+    __syncthreads();
+    // Y1: radix R1 over positions j + 8 n1 of column col, twiddles after
+    for (int t = tid; t < h * R2; t += nthr) {
+        const int col = t % h, j = t / h;
+        C* b = s + j * nxh + col;
+        C v[R1];
+#pragma unroll
+        for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * nxh];
+        Bfly<R1, false, C>::run(v);
+        if (j) {
+#pragma unroll
+            for (int p = 1; p < R1; ++p) v[p] = cmul(v[p], twy[p * j]);
+        }
+#pragma unroll
+        for (int q = 0; q < R1; ++q) b[q * R2 * nxh] = v[q];
+    }
+    __syncthreads();
+    // Y2: radix 8 over positions sub 8 + q; position sub 8 + q holds y frequency sub + R1 q
+    C* out = spec + ((long long)c * g.nz + z) * (long long)n * nxh;
+    for (int t = tid; t < h * R1; t += nthr) {
+        const int col = t % h, sub = t / h;
+        C* b = s + sub * R2 * nxh + col;
+        C v[R2];
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[q] = b[q * nxh];
+        Bfly<R2, false, C>::run(v);
+        if (col == 0) {
+#pragma unroll
+            for (int q = 0; q < R2; ++q) b[q * nxh] = v[q];
+        } else {
+            C* o = out + sub * R2 * nxh + col;
+#pragma unroll
+            for (int q = 0; q < R2; ++q) o[q * nxh] = v[q];
+        }
+    }
+    __syncthreads();
+    // column 0 carries Z = X_0 + i X_h: X_0(k) = (Z(k) + conj Z(-k)) / 2, X_h(k) = (Z(k) - conj Z(-k)) / 2i
+    for (int p = tid; p < n; p += nthr) {
+        const int kk = p / R2 + R1 * (p % R2);
+        const int km = kk == 0 ? 0 : n - kk;
+        const C zp = s[p * nxh], zq = s[((km % R1) * R2 + km / R1) * nxh];
+        out[p * nxh] = mk<C>((zp.x + zq.x) * (T)0.5, (zp.y - zq.y) * (T)0.5);
+        out[p * nxh + h] = mk<C>((zp.y + zq.y) * (T)0.5, (zq.x - zp.x) * (T)0.5);
+    }
+}
+
+template <typename T> size_t fwd2_smem(const GridDev& g) {
+    using C = typename C2<T>::t;
+    return ((size_t)g.nx * (g.nx / 2 + 1) + (size_t)g.nx + 8 * 17) * sizeof(C);
 }
 
 template <typename T> constexpr int zproj_width() { return sizeof(T) == 8 ? 8 : 16; }
@@ -1481,6 +1673,24 @@ namespace {
 template <typename T>
 cudaError_t launch_fwd(const GridDev& g, int threads, const T* x, const T* K, typename C2<T>::t* spec,
                        const int* skip, cudaStream_t st, bool vin) {
+    if (threads < 0 && !(K && vin)) threads = -threads;  // projection alone, unaligned: the generic pass
+    if (threads < 0) {  // register-staged pass of the two-stage plans (nx = ny = 64 or 128), -threads threads
+        const size_t sm = fwd2_smem<T>(g);
+        const dim3 grid(9, g.nz);
+        const int r1 = inv2_radix(g);
+#define GFF_FWD2(R, BT)                                                             \
+    if (r1 == R && threads == -BT) {                                                \
+        allow_smem(k_plane_fwd2<T, R, BT>, sm);                                     \
+        k_plane_fwd2<T, R, BT><<<grid, BT, sm, st>>>(x, K, spec, g, skip);          \
+        return cudaGetLastError();                                                  \
+    }
+        GFF_FWD2(16, 256)
+        GFF_FWD2(16, 512)
+        GFF_FWD2(8, 256)
+        GFF_FWD2(8, 512)
+#undef GFF_FWD2
+        return cudaErrorInvalidValue;
+    }
     const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
     const dim3 gridA(9, g.nz);
     if (K) {
@@ -1589,16 +1799,33 @@ int z2_radix(const GridDev& g) {
     return (g.az.radix[0] == 16 || g.az.radix[0] == 8) ? g.az.radix[0] : 0;
 }
 
+// block threads of the TMA z pass: any up to 512 for the generic strip; 256, or 384 in FP32, for zstrip2
+template <typename T> bool ztma_threads_ok(int R1, int threads) {
+    if (!R1) return threads > 0 && threads <= 512;
+    return threads == 256 || (sizeof(T) == 4 && threads == 384);
+}
+
+template <typename T, int W, int R1, int BT>
+cudaError_t launch_z_tma_kb(gff_handle* h, int threads, int blocks, const ProjArgs& pa, const int* skip,
+                            cudaStream_t st) {
+    const CUtensorMap* tm = zmap<T>(h, W);
+    if (!tm) return cudaErrorNotSupported;
+    const size_t sm = ztma_smem<T, W>(h->g);
+    allow_smem(k_zproj_tma<T, W, R1, BT>, sm);
+    k_zproj_tma<T, W, R1, BT><<<blocks, threads, sm, st>>>(*tm, h->g, pa, skip, h->d_flag + 2);
+    return cudaGetLastError();
+}
 template <typename T, int W, int R1>
 cudaError_t launch_z_tma_k(gff_handle* h, int threads, int blocks, const ProjArgs& pa, const int* skip,
                            cudaStream_t st) {
-    const CUtensorMap* tm = zmap<T>(h, W);
-    if (!tm) return cudaErrorNotSupported;
-    if (threads > ztma_max_threads<T, R1>()) return cudaErrorInvalidValue;
-    const size_t sm = ztma_smem<T, W>(h->g);
-    allow_smem(k_zproj_tma<T, W, R1>, sm);
-    k_zproj_tma<T, W, R1><<<blocks, threads, sm, st>>>(*tm, h->g, pa, skip, h->d_flag + 2);
-    return cudaGetLastError();
+    if (!ztma_threads_ok<T>(R1, threads)) return cudaErrorInvalidValue;
+    if constexpr (R1 == 0) {
+        return launch_z_tma_kb<T, W, 0, 512>(h, threads, blocks, pa, skip, st);
+    } else {
+        if constexpr (sizeof(T) == 4)
+            if (threads == 384) return launch_z_tma_kb<T, W, R1, 384>(h, threads, blocks, pa, skip, st);
+        return launch_z_tma_kb<T, W, R1, 256>(h, threads, blocks, pa, skip, st);
+    }
 }
 
 // blocks > 0: the TMA z pass with the generic strip; < 0: with the register-staged strip, -blocks blocks
@@ -1624,19 +1851,31 @@ cudaError_t launch_z_tma(gff_handle* h, int W, int threads, int blocks, const Pr
 }
 
 // blocks of a TMA z pass: all that fit at once, at most one per strip; 0 if it cannot run
-template <typename T, int W, int R1>
-int z_tma_blocks_k(gff_handle* h, int threads) {
+template <typename T, int W, int R1, int BT>
+int z_tma_blocks_kb(gff_handle* h, int threads) {
     const size_t sm = ztma_smem<T, W>(h->g);
-    if (sm > SMEM_MAX || !zmap<T>(h, W) || threads > ztma_max_threads<T, R1>()) return 0;
+    if (sm > SMEM_MAX || !zmap<T>(h, W)) return 0;
     int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    allow_smem(k_zproj_tma<T, W, R1>, sm);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zproj_tma<T, W, R1>, threads, sm) != cudaSuccess ||
+    allow_smem(k_zproj_tma<T, W, R1, BT>, sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_zproj_tma<T, W, R1, BT>, threads, sm) !=
+            cudaSuccess ||
         per < 1)
         return 0;
     const int total = zproj_blocks(h->g, W);
     return nsm * per < total ? nsm * per : total;
+}
+template <typename T, int W, int R1>
+int z_tma_blocks_k(gff_handle* h, int threads) {
+    if (!ztma_threads_ok<T>(R1, threads)) return 0;
+    if constexpr (R1 == 0) {
+        return z_tma_blocks_kb<T, W, 0, 512>(h, threads);
+    } else {
+        if constexpr (sizeof(T) == 4)
+            if (threads == 384) return z_tma_blocks_kb<T, W, R1, 384>(h, threads);
+        return z_tma_blocks_kb<T, W, R1, 256>(h, threads);
+    }
 }
 template <typename T, int W>
 int z_tma_blocks_w(gff_handle* h, int threads, bool reg) {
@@ -1759,19 +1998,21 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     const int reps = 3;
     Tune& tn = h->tune[tune_index<T>()];
     const bool vin = vec_ok<T>(g, x) && vec_ok<T>(g, K);
-    const int tp[2] = {256, 512};
-    const bool tv[2] = {true, true};
+    // forward pass: 256 or 512 threads, or (two-stage plans, nx = ny) the register-staged pass (-256, -512)
+    const bool f2 = inv2_radix(g) > 0 && fwd2_smem<T>(g) <= SMEM_MAX;
+    const int tp[4] = {256, 512, -256, -512};
+    const bool tv[4] = {true, true, f2, f2};
     int b = -1;
-    cudaError_t e = pick_fastest(2, tv, reps, st, [&](int i) { return launch_fwd<T>(g, tp[i], x, K, spec, nullptr, st, vin); }, &b);
+    cudaError_t e = pick_fastest(4, tv, reps, st, [&](int i) { return launch_fwd<T>(g, tp[i], x, K, spec, nullptr, st, vin); }, &b);
     if (e != cudaSuccess) return e;
     tn.t_fwd = tp[b];
     // z pass: one block per strip (W 4..32, 128 or 256 threads), or the persistent TMA pass (W 8, 16; 256, 512)
     // (the TMA pass also takes 192 / 384 threads: a strip of W columns has 24 W radix-16
     // butterflies at n = 128, so 384 threads at W = 16 and 192 at W = 8 take one each)
-    // and (nz = 64 or 128) the TMA pass with the register-staged strip (W 8, 16; 256 threads)
-    constexpr int NZC = 17;
-    const int wz[NZC] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16, 8, 8, 16, 8, 16};
-    const int tz[NZC] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512, 192, 384, 384, 256, 256};
+    // and (nz = 64 or 128) the TMA pass with the register-staged strip (W 8, 16; 256 threads, or 384 in FP32)
+    constexpr int NZC = 18;
+    const int wz[NZC] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16, 8, 8, 16, 8, 16, 16};
+    const int tz[NZC] = {128, 256, 128, 256, 128, 256, 128, 256, 256, 512, 256, 512, 192, 384, 384, 256, 256, 384};
     int zb[NZC] = {0};
     bool zv[NZC];
     for (int i = 0; i < 8; ++i) zv[i] = zproj_smem<T>(g, wz[i]) <= SMEM_MAX;
@@ -1818,7 +2059,9 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
 template <typename T>
 bool tiles_valid(gff_handle* h, const Tune& t) {
     const GridDev& g = h->g;
-    if ((t.t_fwd != 256 && t.t_fwd != 512) || (t.t_inv != 256 && t.t_inv != 512 && t.t_inv != 1024)) return false;
+    const bool f2 = inv2_radix(g) > 0 && fwd2_smem<T>(g) <= SMEM_MAX;
+    if (t.t_fwd != 256 && t.t_fwd != 512 && !(f2 && (t.t_fwd == -256 || t.t_fwd == -512))) return false;
+    if (t.t_inv != 256 && t.t_inv != 512 && t.t_inv != 1024) return false;
     if (t.wz != 4 && t.wz != 8 && t.wz != 16 && t.wz != 32) return false;
     if (t.inv_blocks < -1) return false;
     if (t.inv_blocks == -1 && (inv2_radix(g) == 0 || inv2_smem<T>(g) > SMEM_MAX || (t.t_inv != 256 && t.t_inv != 512)))
@@ -1828,7 +2071,7 @@ bool tiles_valid(gff_handle* h, const Tune& t) {
             return false;
     } else if (t.z_blocks < 0) {  // register-staged strip: -z_blocks blocks, at most the resident count
         const int mx = z_tma_blocks<T>(h, t.wz, t.t_z, true);
-        if (t.t_z != 256 || mx < 1 || -t.z_blocks > mx) return false;
+        if (mx < 1 || -t.z_blocks > mx) return false;  // (mx is 0 for thread counts zstrip2 does not take)
     } else if ((t.t_z != 128 && t.t_z != 256) || zproj_smem<T>(g, t.wz) > SMEM_MAX) {
         return false;
     }

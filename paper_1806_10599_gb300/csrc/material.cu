@@ -569,8 +569,12 @@ __device__ bool cp_correction_f32(const float* __restrict__ PC, const float* dg,
 }
 
 // FP32 iteration from dg (in/out, FP64 storage); false (dg untouched) if it
-// breaks down before reaching FP32 resolution or stalling.
-__device__ bool cp_presolve_f32(const double* F, const double* A, const double* chin, const float* __restrict__ g,
+// breaks down before reaching FP32 resolution or stalling.  Not inlined: the
+// compiler contracts FP32 multiply-adds per inlined copy, and the one-handle
+// and the batched constitutive kernels must iterate to the same bits (the
+// FP64 iteration that follows stops at its tolerance, so a last-bit change of
+// its start would show up at that tolerance).
+__device__ __noinline__ bool cp_presolve_f32(const double* F, const double* A, const double* chin, const float* __restrict__ g,
                                 const CPParamsDev& pr, double coef, double* dg64, int* iters) {
     float f[9], a[9], chn[NSLIP], dg[NSLIP], chi[NSLIP], dh[NSLIP], r[NSLIP], iden[NSLIP], x[NSLIP];
 #pragma unroll

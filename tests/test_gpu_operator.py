@@ -187,12 +187,12 @@ def test_launch_shapes_give_identical_results(prec):
 @pytest.mark.parametrize("shape", [(64, 64, 64), (12, 128, 128), (128, 16, 32)])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_register_staged_passes_are_bit_identical(shape, prec):
-    """The register-staged passes of the two-stage plans -- the inverse plane
-    pass for nx = ny = 64 (8 x 8) or 128 (16 x 8), tiles inv blocks = -1 with
-    256 or 512 threads, and the TMA z pass's strip for nz = 64 or 128, TMA z
-    blocks < 0 -- perform the operations of the generic passes in the same
-    order: y equal bit for bit, with and without the mixed-control mask, and
-    the oracle's."""
+    """The register-staged passes of the two-stage plans -- the forward and the
+    inverse plane passes for nx = ny = 64 (8 x 8) or 128 (16 x 8), tiles fwd
+    threads -256 / -512 and inv blocks = -1 with 256 or 512 threads, and the TMA
+    z pass's strip for nz = 64 or 128, TMA z blocks < 0 -- perform the
+    operations of the generic passes in the same order: y equal bit for bit,
+    with and without the mixed-control mask, and the oracle's."""
     torch = torch_cuda()
     nz, ny, nx = shape
     g, ms, h = _svk_handle(shape, 12, 21)
@@ -200,11 +200,14 @@ def test_register_staged_passes_are_bit_identical(shape, prec):
     z2 = nz in (64, 128)
     shapes = [(512, 8, 256, 512, 0, 0)]
     if inv2:
-        shapes += [(512, 8, 256, 256, -1, 0), (512, 8, 256, 512, -1, 0), (256, 16, 256, 512, -1, 7)]
+        shapes += [(512, 8, 256, 256, -1, 0), (512, 8, 256, 512, -1, 0), (256, 16, 256, 512, -1, 7),
+                   (-256, 8, 256, 512, 0, 0), (-512, 8, 256, 256, -1, 0)]
     if z2:
         shapes += [(512, 16, 256, 512, 0, -5), (256, 8, 256, 256, 0, -3)]
+        if prec == 1:  # 384 threads: FP32 only
+            shapes += [(512, 16, 384, 512, 0, -4)]
     if inv2 and z2:
-        shapes += [(512, 16, 256, 512, -1, -11)]
+        shapes += [(512, 16, 256, 512, -1, -11), (-256, 16, 256, 256, -1, -7)]
     try:
         g.gff_constitutive(h, 1.0)
         x = _field(13, shape).reshape(9, -1)
@@ -212,25 +215,32 @@ def test_register_staged_passes_are_bit_identical(shape, prec):
         if prec == 1:
             X = X.float()
         outs = []
+        base = (512, 8, 256, 512, 0, 0)
         for s in shapes:
-            g.gff_set_tiles(h, s, s)
+            g.gff_set_tiles(h, s if prec == 0 else base, s if prec == 1 else base)
             for mask in (None, MASKS[1]):
                 Y = torch.empty_like(X)
                 g.gff_apply_operator(h, prec, mask, X, Y)
                 g.gff_sync(h)
                 outs.append(Y.double().cpu().numpy())
-        for i in range(2, len(outs)):
-            assert np.array_equal(outs[i], outs[i % 2])
+            Y = torch.empty_like(X)  # projection alone (the forward pass without K)
+            g.gff_project(h, prec, MASKS[1], X, Y)
+            g.gff_sync(h)
+            outs.append(Y.double().cpu().numpy())
+        for i in range(3, len(outs)):
+            assert np.array_equal(outs[i], outs[i % 3]), (i // 3, i % 3)
+        refG = sp.G(x.reshape(3, 3, nz, ny, nx), ms.L, sp.KIND_CONTINUOUS, MASKS[1].astype(np.float64))
+        assert rel_l2(outs[2], refG.reshape(9, -1)) <= (1e-12 if prec == 0 else 2e-6)
         F = np.tile(np.eye(3).reshape(3, 3, 1, 1, 1), (1, 1) + shape)
         _, K = voxel_K_oracle(ms, F)
         ref = sp.GK(K, x.reshape(3, 3, nz, ny, nx), ms.L, sp.KIND_CONTINUOUS)
         assert rel_l2(outs[0], ref.reshape(9, -1)) <= (1e-12 if prec == 0 else 2e-6)
-        refused = [(512, 8, 256, 1024, -1, 0)]  # 1024 threads is not a shape of the inverse pass
+        refused = [(512, 8, 256, 1024, -1, 0), (-384, 8, 256, 512, 0, 0)]  # not shapes of the two passes
         if not inv2:
-            refused.append((512, 8, 256, 512, -1, 0))
+            refused += [(512, 8, 256, 512, -1, 0), (-256, 8, 256, 512, 0, 0)]
         if not z2:
             refused.append((512, 16, 256, 512, 0, -5))
-        refused.append((512, 16, 384, 512, 0, -5))  # the register-staged strip runs 256 threads
+        refused.append((512, 16, 192, 512, 0, -5))  # the register-staged strip runs 256 (or 384 in FP32) threads
         for s in refused:
             with pytest.raises(g.GffError):
                 g.gff_set_tiles(h, s, s)
