@@ -338,31 +338,61 @@ def workload_config(n=N_GRID):
 
 
 PASS1_END = b"// ---------------------------------------------------------------- pass 2:"
+STAGED_START = b"// ---------------------------------------------------------------- pass 3 for two-stage plans, register-staged"
+STAGED_END = b"template <typename T> constexpr int zproj_width()"
+# the parts of fft_proj.cu each profiled forward kernel is built from: everything before the pass-2
+# marker (complex arithmetic, butterflies, radix stages, line transforms, the contraction, pass 1),
+# and for the register-staged pass also the register-staged section (plan constants, swizzle, its kernels)
+SOURCE_REGIONS = {"k_plane_fwd": [(None, PASS1_END)],
+                  "k_plane_fwd2": [(None, PASS1_END), (STAGED_START, STAGED_END)]}
+PROFILE_FILES = {"k_plane_fwd": "k_plane_fwd_fp64_64cube.md", "k_plane_fwd2": "k_plane_fwd2_fp64_64cube.md"}
+
+
+def kernel_source_sha1(kernel):
+    """sha1 of the source regions of fft_proj.cu that `kernel` is built from."""
+    src = open(os.path.join(ROOT, "paper_1806_10599_gb300", "csrc", "fft_proj.cu"), "rb").read()
+    parts = []
+    for a, b in SOURCE_REGIONS[kernel]:
+        i = 0 if a is None else src.find(a)
+        j = src.find(b, max(i, 0))
+        if i < 0 or j < 0:
+            return None
+        parts.append(src[i:j])
+    return hashlib.sha1(b"".join(parts)).hexdigest()
 
 
 def pass1_source_sha1():
-    """sha1 of the part of fft_proj.cu that k_plane_fwd is built from: everything before the pass-2 marker
-    (complex arithmetic, butterflies, radix stages, the line transforms and pass 1 itself)."""
-    src = open(os.path.join(ROOT, "paper_1806_10599_gb300", "csrc", "fft_proj.cu"), "rb").read()
-    cut = src.find(PASS1_END)
-    return hashlib.sha1(src[:cut] if cut > 0 else src).hexdigest()
+    return kernel_source_sha1("k_plane_fwd")
 
 
-def measured_traffic(n):
-    """DRAM bytes per launch of the FP64 k_plane_fwd at 128^3 from the committed ncu summary, or None when
-    the grid differs or the kernel source changed since the counters were taken."""
-    if n != 128:
+def measured_traffic(n, kernel="k_plane_fwd"):
+    """DRAM bytes per launch of the FP64 forward kernel at 128^3 from its committed ncu summary, or None when
+    the grid differs, no summary exists, or the kernel source changed since the counters were taken."""
+    if n != 128 or kernel not in PROFILE_FILES:
         return None
     try:
-        txt = open(os.path.join(ROOT, "profiles", "k_plane_fwd_fp64_64cube.md")).read()
-        src_sha = pass1_source_sha1()
+        txt = open(os.path.join(ROOT, "profiles", PROFILE_FILES[kernel])).read()
+        src_sha = kernel_source_sha1(kernel)
     except OSError:
         return None
-    sha = re.search(r"pass-1 source sha1 ([0-9a-f]{40})", txt)
+    sha = re.search(r"source sha1 ([0-9a-f]{40})", txt)
     val = re.search(r"traffic_bytes_per_launch_128: ([0-9.eE+]+)", txt)
     if not sha or not val or sha.group(1) != src_sha:
         return None
     return float(val.group(1))
+
+
+def pass_names(tiles):
+    """Names of the three apply kernels the tuned launch shapes select (fwd threads < 0, inv blocks -1 and
+    TMA z blocks < 0 are the register-staged variants)."""
+    fwd, _, _, _, invb, zb = tiles if tiles else (1, 0, 0, 0, 0, 0)
+    f = ("k_plane_fwd2 (K:x + register-staged forward x/y transforms)" if fwd < 0
+         else "k_plane_fwd (K:x + forward x/y transforms)")
+    z = ("k_zproj_tma (register-staged strip: z transforms + projection)" if zb < 0
+         else "k_zproj_tma (z transforms + projection)" if zb > 0 else "k_zproj (z transforms + projection)")
+    i = ("k_plane_inv2 (register-staged inverse y/x transforms)" if invb == -1
+         else "k_plane_inv_stream (inverse y/x transforms)" if invb > 0 else "k_plane_inv (inverse y/x transforms)")
+    return [f, z, i], ("k_plane_fwd2" if fwd < 0 else "k_plane_fwd")
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -716,8 +746,9 @@ def build_line(args, world, raw, peaks, src):
     fp64_peak = raw.get("fp64_peak_gflops")
     fp64_src = "measured here (FP64 FMA chains, gff_measure_fp64_peak)" if fp64_peak else "nominal GB300 FP64 rate"
     fp64_peak = fp64_peak or FP64_PEAK_NOMINAL_GFLOPS
-    names = ["k_plane_fwd (K:x + forward x/y transforms)", "k_zproj (z transforms + projection)",
-             "k_plane_inv (inverse y/x transforms)"]
+    tiles = raw.get("tiles") or {}
+    names, fwd_id = pass_names(tiles.get("fp64"))
+    names32, _ = pass_names(tiles.get("fp32"))
     dom = max(range(3), key=lambda i: k64[i])
     gbs = [b64[i] * nvox / (k64[i] * 1e-3) / 1e9 for i in range(3)]
     gfl = [fl[i] * nvox / (k64[i] * 1e-3) / 1e9 for i in range(3)]
@@ -730,14 +761,14 @@ def build_line(args, world, raw, peaks, src):
     else:
         roof = {"bound": "hbm", "kernel": names[dom], "achieved": gbs[dom], "peak": peak, "unit": "GB/s",
                 "frac": hbm_frac, "peak_source": src}
-    roof["traffic"] = measured_traffic(args.grid) if dom == 0 else None
+    roof["traffic"] = measured_traffic(args.grid, fwd_id) if dom == 0 else None
     roof["algorithmic_bytes_per_launch"] = b64[dom] * nvox
     roof["kernel_ms"] = k64
     roof["all_kernels_gflops"] = gfl
     roof["all_kernels_gbs"] = gbs
     dom32 = max(range(3), key=lambda i: k32[i])
     gbs32 = [b32[i] * nvox / (k32[i] * 1e-3) / 1e9 for i in range(3)]
-    roof32 = {"bound": "hbm", "kernel": names[dom32], "achieved": gbs32[dom32], "peak": peak, "unit": "GB/s",
+    roof32 = {"bound": "hbm", "kernel": names32[dom32], "achieved": gbs32[dom32], "peak": peak, "unit": "GB/s",
               "frac": gbs32[dom32] / peak, "peak_source": src, "kernel_ms": k32, "all_kernels_gbs": gbs32,
               "all_kernels_frac": [v / peak for v in gbs32],
               "apply_gbs": sum(b32) * nvox / (sum(k32) * 1e-3) / 1e9, "traffic": None,
