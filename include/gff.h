@@ -204,7 +204,11 @@ gff_status gff_measure_fp64_peak(double* gflops_out, double* ms_out);
  * FP32, then the persistent TMA z pass's blocks for FP64 and FP32 (0: one
  * block per strip).  inv blocks: 0 one block per plane; > 0 the persistent
  * streamed inverse pass with that many blocks; -1 the register-staged
- * inverse pass (one block per plane) of grids with nx = ny = 64 or 128. */
+ * inverse pass (one block per plane) of grids with nx = ny = 64 or 128;
+ * <= -2 the register-staged persistent pass (two plane buffers) with -inv
+ * blocks blocks.  fwd threads < 0: the register-staged forward pass of those
+ * grids with -fwd threads threads.  TMA z blocks < 0: the TMA z pass with the
+ * register-staged strip (nz = 64 or 128) and -(TMA z blocks) blocks. */
 gff_status gff_autotune(gff_handle* h, int* tiles_out);
 
 /* Sets the launch shapes instead of tuning them: tiles (host, 12 ints) in the
@@ -212,7 +216,10 @@ gff_status gff_autotune(gff_handle* h, int* tiles_out);
  * 4/8/16/32 with z threads 128/256 (one block per strip), or, with TMA z
  * blocks > 0, z columns 8/16 and z threads 192/256/384/512; inv threads 256/512, or
  * with inv blocks > 0 up to 1024 (FP32) / 512 (FP64), or with inv blocks -1
- * (nx = ny = 64 or 128 only) 256/512.  Every shape performs the same
+ * (nx = ny = 64 or 128 only) 256/512, or with inv blocks <= -2 512 (or 1024
+ * in FP32; where two planes fit in shared memory); fwd threads also -256 /
+ * -512 on those grids; with TMA z blocks < 0, z threads 256 (or 384 in
+ * FP32).  Every shape performs the same
  * operations in the same order, so results do not depend on them.
  * gff_batch_run gives each size class the shapes of its first RVE and runs
  * one-block-per-strip / one-block-per-plane kernels: the other shapes are

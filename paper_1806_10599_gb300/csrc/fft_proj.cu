@@ -1330,45 +1330,15 @@ __device__ __forceinline__ void inv2_x2(const typename C2<T>::t* s, const typena
 // to an SM (256 threads at <= 85 registers) or two (512 threads at <= 64)
 template <typename T, int BT> constexpr int inv2_min_blocks() { return sizeof(T) == 4 ? (BT == 256 ? 3 : 2) : 1; }
 
-template <typename T, int R1, int R2, int BT>
-__global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(const typename C2<T>::t* __restrict__ spec,
-                                                                      T* __restrict__ y, GridDev g, OutArgs oa,
-                                                                      const int* __restrict__ skip,
-                                                                      int* __restrict__ err) {
+// Y1 .. X2 of one plane already in shared memory s (twiddle tables loaded); writes plane (c, z) of y.
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void inv2_compute(typename C2<T>::t* s, const typename C2<T>::t* twy,
+                                             const typename C2<T>::t* twx2, T* __restrict__ y, const GridDev& g,
+                                             const OutArgs& oa, const int c, const int z) {
     using C = typename C2<T>::t;
     using P = Inv2Plan<R1, R2>;
     constexpr int n = P::n, h = P::h, nxh = P::nxh;
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char sm_raw[];
-    C* s = reinterpret_cast<C*>(sm_raw);  // [n][nxh]
-    C* twy = s + n * nxh;                  // [n]: W_n^k of the y axis
-    C* twx2 = twy + n;                     // [R2][R1 + 1]: W_n^(p j) of the x axis
-    uint64_t* bar =
-        reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(twx2 + R2 * P::TWS) + 7) & ~uintptr_t(7));
-    const int c = blockIdx.x, z = blockIdx.y;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (tid == 0)  // n nxh sizeof(C) is a multiple of 16 (n even), the plane start too
-        bulk_load(s, spec + ((long long)c * g.nz + z) * (n * nxh), (uint32_t)(n * nxh * sizeof(C)), bar);
-    for (int i = tid; i < n; i += nthr) twy[i] = twp<T>(g, 1)[i];
-    for (int i = tid; i < R2 * P::TWS; i += nthr) {
-        const int j = i / P::TWS, p = i - j * P::TWS;
-        twx2[i] = p < R1 ? twp<T>(g, 0)[p * j] : mk<C>((T)0, (T)0);
-    }
-    const bool ok = mbar_wait(bar, 0u, g.wait_cycles);
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-            if (err) atomicExch(err, 1);
-            mbar_wait(bar, 0u, BULK_WAIT_CYCLES);  // let the copy land (bounded) before leaving
-        }
-        plane_fill_nan<T>(y, g, c, z);
-        __syncthreads();
-        return;
-    }
     // Y1: radix R2 over positions sub R2 + q of column col
     for (int t = tid; t < h * R1; t += nthr) {
         const int col = t % h, sub = t / h;
@@ -1417,7 +1387,112 @@ __global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(con
         for (int wg = warp; wg < h / P::G1; wg += nw) inv2_x1<T, R1, R2>(s, wg, lane);
         __syncthreads();
         for (int wg = warp; wg < h / P::G2; wg += nw) inv2_x2<T, R1, R2>(s, twx2, yp, sc, ad, wg, lane);
+    }}
+
+template <typename T, int R1, int R2, int BT>
+__global__ void __launch_bounds__(BT, inv2_min_blocks<T, BT>()) k_plane_inv2(const typename C2<T>::t* __restrict__ spec,
+                                                                      T* __restrict__ y, GridDev g, OutArgs oa,
+                                                                      const int* __restrict__ skip,
+                                                                      int* __restrict__ err) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, R2>;
+    constexpr int n = P::n, nxh = P::nxh;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* s = reinterpret_cast<C*>(sm_raw);  // [n][nxh]
+    C* twy = s + n * nxh;                  // [n]: W_n^k of the y axis
+    C* twx2 = twy + n;                     // [R2][R1 + 1]: W_n^(p j) of the x axis
+    uint64_t* bar =
+        reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(twx2 + R2 * P::TWS) + 7) & ~uintptr_t(7));
+    const int c = blockIdx.x, z = blockIdx.y;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
     }
+    __syncthreads();
+    if (tid == 0)  // n nxh sizeof(C) is a multiple of 16 (n even), the plane start too
+        bulk_load(s, spec + ((long long)c * g.nz + z) * (n * nxh), (uint32_t)(n * nxh * sizeof(C)), bar);
+    for (int i = tid; i < n; i += nthr) twy[i] = twp<T>(g, 1)[i];
+    for (int i = tid; i < R2 * P::TWS; i += nthr) {
+        const int j = i / P::TWS, p = i - j * P::TWS;
+        twx2[i] = p < R1 ? twp<T>(g, 0)[p * j] : mk<C>((T)0, (T)0);
+    }
+    const bool ok = mbar_wait(bar, 0u, g.wait_cycles);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            if (err) atomicExch(err, 1);
+            mbar_wait(bar, 0u, BULK_WAIT_CYCLES);  // let the copy land (bounded) before leaving
+        }
+        plane_fill_nan<T>(y, g, c, z);
+        __syncthreads();
+        return;
+    }
+    inv2_compute<T, R1, R2>(s, twy, twx2, y, g, oa, c, z);
+}
+
+// Persistent FP32 variant: each block walks the planes p = blockIdx.x + k gridDim.x
+// (p = c nz + z) with two plane buffers; the next plane arrives by a bulk copy
+// while the current one is transformed (two 68.6 KB planes: one block per SM).
+template <typename T, int R1, int BT>
+__global__ void __launch_bounds__(BT, 1) k_plane_inv2s(const typename C2<T>::t* __restrict__ spec,
+                                                       T* __restrict__ y, GridDev g, OutArgs oa,
+                                                       const int* __restrict__ skip, int* __restrict__ err) {
+    using C = typename C2<T>::t;
+    using P = Inv2Plan<R1, 8>;
+    constexpr int n = P::n, nxh = P::nxh, plane = n * nxh;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    C* buf[2] = {reinterpret_cast<C*>(sm_raw), reinterpret_cast<C*>(sm_raw) + plane};
+    C* twy = buf[1] + plane;
+    C* twx2 = twy + n;
+    uint64_t* bar = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(twx2 + 8 * P::TWS) + 7) & ~uintptr_t(7));
+    const uint32_t bytes = (uint32_t)(plane * sizeof(C));  // a multiple of 16 (n even)
+    const int total = 9 * g.nz, tid = threadIdx.x, nthr = blockDim.x;
+    for (int i = tid; i < n; i += nthr) twy[i] = twp<T>(g, 1)[i];
+    for (int i = tid; i < 8 * P::TWS; i += nthr) {
+        const int j = i / P::TWS, q = i - j * P::TWS;
+        twx2[i] = q < R1 ? twp<T>(g, 0)[q * j] : mk<C>((T)0, (T)0);
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    int p = blockIdx.x;
+    if (tid == 0 && p < total) bulk_load(buf[0], spec + (long long)p * plane, bytes, &bar[0]);
+    uint32_t phase[2] = {0u, 0u};
+    int cur = 0;
+    for (; p < total; p += gridDim.x) {
+        const int nextp = p + gridDim.x;
+        if (tid == 0 && nextp < total) {
+            fence_proxy_async_smem();  // the other buffer's last readers and writers finished at the barrier below
+            bulk_load(buf[cur ^ 1], spec + (long long)nextp * plane, bytes, &bar[cur ^ 1]);
+        }
+        const bool ok = mbar_wait(&bar[cur], phase[cur], g.wait_cycles);
+        if (__syncthreads_or(!ok)) {
+            // record, let the copies in flight land (bounded), mark the planes this block
+            // still owns as not computed (NaN), leave
+            if (tid == 0) {
+                atomicExch(err, 1);
+                mbar_wait(&bar[cur], phase[cur], BULK_WAIT_CYCLES);
+                if (nextp < total) mbar_wait(&bar[cur ^ 1], phase[cur ^ 1], BULK_WAIT_CYCLES);
+            }
+            for (int q = p; q < total; q += gridDim.x) plane_fill_nan<T>(y, g, q / g.nz, q % g.nz);
+            __syncthreads();
+            return;
+        }
+        phase[cur] ^= 1u;
+        inv2_compute<T, R1, 8>(buf[cur], twy, twx2, y, g, oa, p / g.nz, p % g.nz);
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
+template <typename T> size_t inv2s_smem(const GridDev& g) {
+    using C = typename C2<T>::t;
+    return (2 * (size_t)g.nx * (g.nx / 2 + 1) + (size_t)g.nx + 8 * 17) * sizeof(C) + 32;
 }
 
 template <typename T> size_t inv2_smem(const GridDev& g) {
@@ -1895,6 +1970,24 @@ int z_tma_blocks(gff_handle* h, int W, int threads, bool reg = false) {
 template <typename T>
 cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename C2<T>::t* spec, T* y,
                        const OutArgs& oa, const int* skip, cudaStream_t st, bool vout, int* err) {
+    if (blocks < -1) {  // register-staged persistent pass, -blocks blocks
+        const size_t sm = inv2s_smem<T>(g);
+        const int r1 = inv2_radix(g);
+#define GFF_INV2S(R, BT)                                                                   \
+    if (r1 == R && threads == BT) {                                                        \
+        allow_smem(k_plane_inv2s<T, R, BT>, sm);                                           \
+        k_plane_inv2s<T, R, BT><<<-blocks, BT, sm, st>>>(spec, y, g, oa, skip, err);       \
+        return cudaGetLastError();                                                         \
+    }
+        GFF_INV2S(16, 512)
+        GFF_INV2S(8, 512)
+        if constexpr (sizeof(T) == 4) {
+            GFF_INV2S(16, 1024)
+            GFF_INV2S(8, 1024)
+        }
+#undef GFF_INV2S
+        return cudaErrorInvalidValue;
+    }
     if (blocks < 0) {  // register-staged pass of the two-stage plans, one block per plane
         const size_t sm = inv2_smem<T>(g);
         const dim3 grid(9, g.nz);
@@ -1989,6 +2082,32 @@ int inv_stream_blocks(const GridDev& g, int threads, bool vout) {
     return nsm * per < total ? nsm * per : total;
 }
 
+// blocks of the persistent register-staged inverse pass: all that fit at once, at most one per plane; 0 if it
+// cannot run on this grid (plan, shared memory) with this many threads
+template <typename T, int R1, int BT>
+int inv2s_blocks_k(const GridDev& g) {
+    const size_t sm = inv2s_smem<T>(g);
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    allow_smem(k_plane_inv2s<T, R1, BT>, sm);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_plane_inv2s<T, R1, BT>, BT, sm) != cudaSuccess ||
+        per < 1)
+        return 0;
+    const int total = 9 * g.nz;
+    return nsm * per < total ? nsm * per : total;
+}
+template <typename T>
+int inv2s_blocks(const GridDev& g, int threads) {
+    if (inv2s_smem<T>(g) > SMEM_MAX) return 0;
+    const int r1 = inv2_radix(g);
+    if (threads == 512) return r1 == 16 ? inv2s_blocks_k<T, 16, 512>(g) : (r1 == 8 ? inv2s_blocks_k<T, 8, 512>(g) : 0);
+    if constexpr (sizeof(T) == 4)
+        if (threads == 1024)
+            return r1 == 16 ? inv2s_blocks_k<T, 16, 1024>(g) : (r1 == 8 ? inv2s_blocks_k<T, 8, 1024>(g) : 0);
+    return 0;
+}
+
 template <typename T>
 cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     using C = typename C2<T>::t;
@@ -2039,14 +2158,16 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     oa.scale = 1.0;
     for (int c = 0; c < 9; ++c) oa.add[c] = 0.0;
     // one block per plane with 256 or 512 threads, the persistent streamed pass with 512 or 1024,
-    // or (two-stage plans, nx = ny) the register-staged pass with 256 or 512
+    // or (two-stage plans, nx = ny) the register-staged pass with 256 or 512, one block per plane, or
+    // persistent with two plane buffers (512, or 1024 in FP32)
     const bool vout = vec_ok<T>(g, y);
-    const int ti[6] = {256, 512, inv_stream_max_threads<T>() / 2, inv_stream_max_threads<T>(), 256, 512};
-    int ib[6] = {0, 0, inv_stream_blocks<T>(g, 512, vout), inv_stream_blocks<T>(g, 1024, vout), -1, -1};
+    const int ti[8] = {256, 512, inv_stream_max_threads<T>() / 2, inv_stream_max_threads<T>(), 256, 512, 512, 1024};
+    int ib[8] = {0, 0, inv_stream_blocks<T>(g, 512, vout), inv_stream_blocks<T>(g, 1024, vout), -1, -1,
+                 -inv2s_blocks<T>(g, 512), -inv2s_blocks<T>(g, 1024)};
     const bool r2 = inv2_radix(g) > 0 && inv2_smem<T>(g) <= SMEM_MAX;
-    const bool iv[6] = {true, true, ib[2] > 0, ib[3] > 0, r2, r2};
+    const bool iv[8] = {true, true, ib[2] > 0, ib[3] > 0, r2, r2, ib[6] < -1, ib[7] < -1};
     int* err = h->d_flag + 2;
-    e = pick_fastest(6, iv, reps, st, [&](int i) { return launch_inv<T>(g, ti[i], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
+    e = pick_fastest(8, iv, reps, st, [&](int i) { return launch_inv<T>(g, ti[i], ib[i], spec, y, oa, nullptr, st, vout, err); }, &b);
     if (e != cudaSuccess) return e;
     tn.t_inv = ti[b];
     tn.inv_blocks = ib[b];
@@ -2063,7 +2184,10 @@ bool tiles_valid(gff_handle* h, const Tune& t) {
     if (t.t_fwd != 256 && t.t_fwd != 512 && !(f2 && (t.t_fwd == -256 || t.t_fwd == -512))) return false;
     if (t.t_inv != 256 && t.t_inv != 512 && t.t_inv != 1024) return false;
     if (t.wz != 4 && t.wz != 8 && t.wz != 16 && t.wz != 32) return false;
-    if (t.inv_blocks < -1) return false;
+    if (t.inv_blocks < -1) {  // persistent register-staged inverse: -inv_blocks blocks, at most the resident count
+        const int mx = inv2s_blocks<T>(g, t.t_inv);
+        if (mx < 2 || -t.inv_blocks > mx) return false;
+    }
     if (t.inv_blocks == -1 && (inv2_radix(g) == 0 || inv2_smem<T>(g) > SMEM_MAX || (t.t_inv != 256 && t.t_inv != 512)))
         return false;
     if (t.z_blocks > 0) {
@@ -2077,7 +2201,7 @@ bool tiles_valid(gff_handle* h, const Tune& t) {
     }
     if (t.inv_blocks > 0) {
         if (plane_stream_smem<T>(g) > SMEM_MAX || t.t_inv > inv_stream_max_threads<T>()) return false;
-    } else if (t.t_inv > 512) {
+    } else if (t.t_inv > 512 && t.inv_blocks >= -1) {
         return false;
     }
     return true;

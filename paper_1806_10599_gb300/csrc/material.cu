@@ -672,24 +672,46 @@ __device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd
     }
     T J[NSLIP * NSLIP];
     int piv[NSLIP];
-    cp_jacobian_exact<T>(F, A, dg, S0, C, pr, coef, st, chi, dh, J);
-    if (!lu_factor<NSLIP>(J, piv)) return false;
     const T cg = (T)(coef / pr.tau0);
     T FeS[9];
     mm(st.Fe, st.S, FeS);
-    // dP/ddg_b  (12 x 9)
+    // column b of the exact Jacobian dr_a/ddg_b (as cp_jacobian_exact) and dP/ddg_b (12 x 9) from
+    // one derivative of the elastic state per slip system
     T dPb[NSLIP * 9];
-    for (int b = 0; b < NSLIP; ++b) {
-        T dFpi[9], dFe[9], dCe[9], dS[9], t1[9], t2[9], t3[9], t4[9];
-        dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
-        mm(dFe, st.S, t1);
-        mmt(t1, st.Fpi, t2);  // dFe S Fpi^T
-        mm(st.Fe, dS, t1);
-        mmt(t1, st.Fpi, t3);  // Fe dS Fpi^T
-        mmt(FeS, dFpi, t4);   // Fe S dFpi^T
+    {
+        const T cc = (T)pr.c, d = (T)pr.d;
+        for (int b = 0; b < NSLIP; ++b) {
+            T dFpi[9], dFe[9], dCe[9], dS[9], t1[9], t2[9], t3[9], t4[9];
+            dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
+            {
+                T dM[9];
+                mm(dCe, st.S, dM);
+                mm(st.Ce, dS, t1);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) dPb[9 * b + k] = t2[k] + t3[k] + t4[k];
+                for (int k = 0; k < 9; ++k) dM[k] += t1[k];
+                for (int a = 0; a < NSLIP; ++a) {
+                    T dtau = (T)0;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) dtau = fma(dM[k], __ldg(S0 + 9 * a + k), dtau);
+                    T v = -cg * dh[a] * dtau;
+                    if (a == b) {
+                        const T den = (T)1 + d * fabs(dg[a]);
+                        const T dchi = (cc - d * sgn(dg[a]) * chi[a]) / den;
+                        v += (T)1 + cg * dh[a] * dchi;
+                    }
+                    J[a * NSLIP + b] = v;
+                }
+            }
+            mm(dFe, st.S, t1);
+            mmt(t1, st.Fpi, t2);  // dFe S Fpi^T
+            mm(st.Fe, dS, t1);
+            mmt(t1, st.Fpi, t3);  // Fe dS Fpi^T
+            mmt(FeS, dFpi, t4);   // Fe S dFpi^T
+#pragma unroll
+            for (int k = 0; k < 9; ++k) dPb[9 * b + k] = t2[k] + t3[k] + t4[k];
+        }
     }
+    if (!lu_factor<NSLIP>(J, piv)) return false;
     T SFt[9];
     mmt(st.S, st.Fpi, SFt);  // S Fpi^T
     for (int kl = 0; kl < 9; ++kl) {
