@@ -458,6 +458,7 @@ def time_arm(g, torch, ms, hist, precision, projection=0, warm=0, unet=None, clo
             "cp_local_iters_per_voxel_mean": sum(r.cp_local_iters for r in reps) / n,
             "cp_fallbacks": sum(r.cp_fallbacks for r in reps),
             "s_constitutive": sum(r.t_constitutive for r in reps) / n,
+            "s_tangent": sum(r.t_tangent for r in reps) / n,
             "s_residual": sum(r.t_residual for r in reps) / n, "s_linear": sum(r.t_linear for r in reps) / n,
             "P11_MPa_peak": max(p[0] for p in Pm) / 1e6, "P11_MPa_min": min(p[0] for p in Pm) / 1e6,
             "clocks": clocks, "_Pm": Pm.tolist()}

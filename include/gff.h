@@ -114,6 +114,8 @@ typedef struct {
     int cp_fallbacks;      /* voxel return maps that needed the exact-Newton fallback */
     double cp_local_iters; /* local Newton iterations per voxel, summed over the
                               increment's constitutive evaluations                  */
+    double t_tangent;      /* the part of t_constitutive spent in tangent-only launches
+                              (the return maps take the rest), s                      */
 } gff_step_report;
 
 typedef struct gff_unet gff_unet;

@@ -892,7 +892,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     int newton = 0, cgsum = 0;
     double res = 0.0, nb = 0.0, nP = 0.0, rr_b = 0.0;
     bool conv = false;
-    double t_const = 0.0, t_res = 0.0, t_lin = 0.0;
+    double t_const = 0.0, t_res = 0.0, t_lin = 0.0, t_tan = 0.0;
     cudaEvent_t ev[4];
     for (int i = 0; i < 4; ++i) GFF_TRY(cudaEventCreate(&ev[i]));
     struct EvGuard {
@@ -907,7 +907,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
     struct RepGuard {
         gff_step_report* r;
         const int &newton, &cgsum, &warm_used, &cp_fb;
-        const double &res, &t_const, &t_res, &t_lin, &res_first, &cp_its;
+        const double &res, &t_const, &t_res, &t_lin, &res_first, &cp_its, &t_tan;
         ~RepGuard() {
             if (!r) return;
             r->newton_iters = newton;
@@ -920,8 +920,9 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             r->residual_first = res_first;
             r->cp_fallbacks = cp_fb;
             r->cp_local_iters = cp_its;
+            r->t_tangent = t_tan;
         }
-    } repg{rep, newton, cgsum, warm_used, cp_fb, res, t_const, t_res, t_lin, res_first, cp_its};
+    } repg{rep, newton, cgsum, warm_used, cp_fb, res, t_const, t_res, t_lin, res_first, cp_its, t_tan};
 
     // P, K at d_Fk and the residual b = -G_M(P) + M : Pbar with its norms
     auto evaluate = [&](bool warm_dg) -> gff_status {
@@ -1011,6 +1012,7 @@ gff_status newton_increment(gff_handle* h, double dt, const double* Fbar, const 
             float ms01 = 0.f;
             GFF_TRY(cudaEventElapsedTime(&ms01, ev[0], ev[1]));
             t_const += 1e-3 * ms01;
+            t_tan += 1e-3 * ms01;
             if (kflag) return fail(h, GFF_ERR_CP_FAIL, "tangent failed in %d voxels", kflag);
         }
         const double stop = std::fmax(h->opt.cg_tol * nb, 0.1 * h->opt.newton_tol * nP);
@@ -1139,6 +1141,7 @@ gff_status step_with_cuts(gff_handle* h, double dt, const double* Fbar, const ui
     acc->t_linear += rep.t_linear;
     acc->cp_fallbacks += rep.cp_fallbacks;
     acc->cp_local_iters += rep.cp_local_iters;
+    acc->t_tangent += rep.t_tangent;
     acc->residual = rep.residual;
     if (depth == 0) {
         acc->warm_start_used = rep.warm_start_used;

@@ -79,6 +79,7 @@ class gff_step_report(ctypes.Structure):
         ("residual_first", c_double),
         ("cp_fallbacks", c_int),
         ("cp_local_iters", c_double),
+        ("t_tangent", c_double),
     ]
 
 
