@@ -649,27 +649,9 @@ __device__ bool cp_local_solve(const double* F, const double* A, const double* c
 // (the grain's S0 and C given in T, so no conversions in the loops):
 //   K = dP/dF|_dg + (dP/ddg) (ddg/dF),  J ddg/dF = (coef/g) h' dtau/dF|_dg.
 template <typename T>
-__device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd, const T* __restrict__ S0,
-                           const T* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& sd,
-                           const double* chid, const double* dhd, T* K) {
-    T F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
-    ElStateT<T> st;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        F[k] = (T)Fd[k];
-        A[k] = (T)Ad[k];
-        st.Fpi[k] = (T)sd.Fpi[k];
-        st.Fe[k] = (T)sd.Fe[k];
-        st.Ce[k] = (T)sd.Ce[k];
-        st.S[k] = (T)sd.S[k];
-        st.M[k] = (T)sd.M[k];
-    }
-    for (int a = 0; a < NSLIP; ++a) {
-        dg[a] = (T)dgd[a];
-        chi[a] = (T)chid[a];
-        dh[a] = (T)dhd[a];
-        st.tau[a] = (T)sd.tau[a];
-    }
+__device__ __forceinline__ bool cp_tangent_core(const T* F, const T* A, const T* dg, const T* __restrict__ S0,
+                                                const T* __restrict__ C, const CPParamsDev& pr, double coef,
+                                                const ElStateT<T>& st, const T* chi, const T* dh, T* K) {
     T J[NSLIP * NSLIP];
     int piv[NSLIP];
     const T cg = (T)(coef / pr.tau0);
@@ -761,6 +743,136 @@ __device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd
         for (int q = 0; q < 9; ++q) K[9 * q + kl] = dP[q];
     }
     return true;
+}
+
+// The tangent from the FP64 state of the converged return map, computed in T.
+template <typename T>
+__device__ bool cp_tangent(const double* Fd, const double* Ad, const double* dgd, const T* __restrict__ S0,
+                           const T* __restrict__ C, const CPParamsDev& pr, double coef, const ElState& sd,
+                           const double* chid, const double* dhd, T* K) {
+    T F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
+    ElStateT<T> st;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        F[k] = (T)Fd[k];
+        A[k] = (T)Ad[k];
+        st.Fpi[k] = (T)sd.Fpi[k];
+        st.Fe[k] = (T)sd.Fe[k];
+        st.Ce[k] = (T)sd.Ce[k];
+        st.S[k] = (T)sd.S[k];
+        st.M[k] = (T)sd.M[k];
+    }
+    for (int a = 0; a < NSLIP; ++a) {
+        dg[a] = (T)dgd[a];
+        chi[a] = (T)chid[a];
+        dh[a] = (T)dhd[a];
+        st.tau[a] = (T)sd.tau[a];
+    }
+    return cp_tangent_core<T>(F, A, dg, S0, C, pr, coef, st, chi, dh, K);
+}
+
+// The elastic state at slips dg in FP32, in the displacement-gradient form of the
+// FP32 pre-iteration (f = F - I, a = Fp^-1_n - I; Fp^-1 - I = a - Lp - a Lp,
+// Fe - I = G = q + f + f q, E = (G + G^T + G^T G)/2, Ce = I + 2E, M = S + 2 E S), so
+// that the small parts of Fe, Ce and the stresses keep FP32 relative precision.
+__device__ void elastic_state_f32(const float* f, const float* a, const float* dg, const float* __restrict__ g,
+                                  ElStateT<float>& st) {
+    const float* sd = g + G32_DIR;
+    const float* mn = g + G32_NRM;
+    const float* C6 = g + G32_C6;
+    float Lp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Lp[k] = 0.f;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = fmaf(dg[3 * p + i], __ldg(sd + 3 * (3 * p + i) + j), v[j]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Lp[3 * j + k] = fmaf(v[j], __ldg(mn + 3 * p + k), Lp[3 * j + k]);
+    }
+    float aL[9], q[9], fq[9], G[9], GtG[9];
+    mm(a, Lp, aL);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) q[k] = a[k] - Lp[k] - aL[k];
+    mm(f, q, fq);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) G[k] = q[k] + f[k] + fq[k];
+    mtm(G, G, GtG);
+    float E[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) E[3 * i + j] = 0.5f * (G[3 * i + j] + G[3 * j + i] + GtG[3 * i + j]);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float I = (k % 4) == 0 ? 1.f : 0.f;
+        st.Fpi[k] = I + q[k];
+        st.Fe[k] = I + G[k];
+        st.Ce[k] = I + 2.f * E[k];
+    }
+    const float e[6] = {E[0], E[4], E[8], 2.f * E[5], 2.f * E[2], 2.f * E[1]};  // Voigt, engineering shears
+    float sv[6];
+#pragma unroll
+    for (int I = 0; I < 6; ++I) {
+        float t = 0.f;
+#pragma unroll
+        for (int J = 0; J < 6; ++J) t = fmaf(__ldg(C6 + 6 * I + J), e[J], t);
+        sv[I] = t;
+    }
+    st.S[0] = sv[0], st.S[4] = sv[1], st.S[8] = sv[2];
+    st.S[5] = st.S[7] = sv[3];
+    st.S[2] = st.S[6] = sv[4];
+    st.S[1] = st.S[3] = sv[5];
+    float ES[9];
+    mm(E, st.S, ES);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) st.M[k] = fmaf(2.f, ES[k], st.S[k]);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const float m0 = __ldg(mn + 3 * p), m1 = __ldg(mn + 3 * p + 1), m2 = __ldg(mn + 3 * p + 2);
+        float Mm[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Mm[j] = st.M[3 * j] * m0 + st.M[3 * j + 1] * m1 + st.M[3 * j + 2] * m2;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float* sv3 = sd + 3 * (3 * p + i);
+            st.tau[3 * p + i] = __ldg(sv3) * Mm[0] + __ldg(sv3 + 1) * Mm[1] + __ldg(sv3 + 2) * Mm[2];
+        }
+    }
+}
+
+// The FP32 tangent of mixed precision at the stored slips: the elastic state, the
+// backstress and the flow-rule derivative at dg formed in FP32 (elastic_state_f32)
+// instead of in FP64 and rounded, then the tangent in FP32.  Not inlined, so that
+// the one-handle and the batched kernels compute the same bits.
+__device__ __noinline__ bool cp_tangent_f32(const double* Fd, const double* Ad, const double* chind, const double* dgd,
+                                            double dt, const float* __restrict__ g, const CPParamsDev& pr,
+                                            float* K) {
+    float f[9], a[9], F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double I = (k % 4) == 0 ? 1.0 : 0.0;
+        f[k] = (float)(Fd[k] - I);
+        a[k] = (float)(Ad[k] - I);
+        F[k] = (float)Fd[k];
+        A[k] = (float)Ad[k];
+    }
+    for (int s = 0; s < NSLIP; ++s) dg[s] = (float)dgd[s];
+    ElStateT<float> st;
+    elastic_state_f32(f, a, dg, g, st);
+    const float c = (float)pr.c, d = (float)pr.d, it0 = (float)pr.itau0;
+    const int p = (int)pr.p;
+    for (int s = 0; s < NSLIP; ++s) {
+        chi[s] = ((float)chind[s] + c * dg[s]) / (1.f + d * fabsf(dg[s]));
+        const float x = (st.tau[s] - chi[s]) * it0;
+        dh[s] = (float)p * ipowf_n(fabsf(x), p - 1);
+    }
+    return cp_tangent_core<float>(F, A, dg, g + G32_S0, g + G32_C, pr, dt * pr.gdot0, st, chi, dh, K);
 }
 
 // Return map (FP64) and, when K is not null, the tangent in precision T.
@@ -1021,7 +1133,7 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
             bool ok;
             if (F32T) {
                 float K[81];
-                ok = cp_tangent_at<float>(F, A, chin, dg, a.dt, geo, g32 + G32_S0, g32 + G32_C, pr, K);
+                ok = cp_tangent_f32(F, A, chin, dg, a.dt, g32, pr, K);
 #pragma unroll
                 for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
             } else {
@@ -1045,10 +1157,11 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
         if (PART == PART_P) {
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
                               (double*)nullptr, o, a.exact != 0, a.f32first ? g32 : nullptr);
-        } else if (F32T) {
+        } else if (F32T) {  // the return map, then the tangent as a tangent-only launch forms it
             float K[81];
             cp_update<float>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, g32 + G32_S0, g32 + G32_C, pr,
-                             warm ? dg0 : nullptr, K, o, a.exact != 0, a.f32first ? g32 : nullptr);
+                             warm ? dg0 : nullptr, (float*)nullptr, o, a.exact != 0, a.f32first ? g32 : nullptr);
+            if (o.ok) o.ok = cp_tangent_f32(F, A, chin, o.dg, a.dt, g32, pr, K);
 #pragma unroll
             for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
         } else {
