@@ -846,33 +846,159 @@ __device__ void elastic_state_f32(const float* f, const float* a, const float* d
     }
 }
 
-// The FP32 tangent of mixed precision at the stored slips: the elastic state, the
-// backstress and the flow-rule derivative at dg formed in FP32 (elastic_state_f32)
-// instead of in FP64 and rounded, then the tangent in FP32.  Not inlined, so that
-// the one-handle and the batched kernels compute the same bits.
+// The FP32 tangent of mixed precision at the stored slips, written to Kg[(9q + kl) ldk]:
+//   K = dP/dF|_dg + (dP/ddg) X,   J X = R,   R_a,kl = (coef/tau0) h'_a dtau_a/dF_kl|_dg,
+// with the elastic state, backstress and flow-rule derivative formed in FP32 from the
+// displacement-gradient form (elastic_state_f32), dP/ddg exact, and J the small-elastic-
+// strain Jacobian D + F P^T C5 P of the return map's corrections, solved for the nine
+// columns through one 5 x 5 LDL^T factorisation (cp_correction_f32 for one right-hand
+// side).  Against the exact Jacobian this drops terms of the order of the elastic strain
+// (~1e-3) from the plastic part of K, below the CG tolerance the tangent serves; it keeps
+// no 12 x 12 matrix, so the tangent stays in registers.  Not inlined, so that the
+// one-handle and the batched kernels compute the same bits.
 __device__ __noinline__ bool cp_tangent_f32(const double* Fd, const double* Ad, const double* chind, const double* dgd,
                                             double dt, const float* __restrict__ g, const CPParamsDev& pr,
-                                            float* K) {
-    float f[9], a[9], F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const double I = (k % 4) == 0 ? 1.0 : 0.0;
-        f[k] = (float)(Fd[k] - I);
-        a[k] = (float)(Ad[k] - I);
-        F[k] = (float)Fd[k];
-        A[k] = (float)Ad[k];
-    }
-    for (int s = 0; s < NSLIP; ++s) dg[s] = (float)dgd[s];
+                                            float* __restrict__ Kg, long long ldk) {
+    float F[9], A[9], dg[NSLIP], chi[NSLIP], dh[NSLIP];
     ElStateT<float> st;
-    elastic_state_f32(f, a, dg, g, st);
-    const float c = (float)pr.c, d = (float)pr.d, it0 = (float)pr.itau0;
+    {
+        float f[9], a[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const double I = (k % 4) == 0 ? 1.0 : 0.0;
+            f[k] = (float)(Fd[k] - I);
+            a[k] = (float)(Ad[k] - I);
+            F[k] = (float)Fd[k];
+            A[k] = (float)Ad[k];
+        }
+        for (int s = 0; s < NSLIP; ++s) dg[s] = (float)dgd[s];
+        elastic_state_f32(f, a, dg, g, st);
+    }
+    const float c = (float)pr.c, d = (float)pr.d, it0 = (float)pr.itau0, cg = (float)(dt * pr.gdot0 / pr.tau0);
     const int p = (int)pr.p;
+    const float* __restrict__ S0 = g + G32_S0;
+    const float* __restrict__ C = g + G32_C;
+    const float* __restrict__ PC = g + G32_PC;  // P [5][12], then C5^-1 [5][5]
+    float fa[NSLIP], Di[NSLIP];
+    float A5[15];
+    {
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) A5[q++] = __ldg(PC + 60 + 5 * i + j);
+    }
     for (int s = 0; s < NSLIP; ++s) {
-        chi[s] = ((float)chind[s] + c * dg[s]) / (1.f + d * fabsf(dg[s]));
+        const float id = 1.f / (1.f + d * fabsf(dg[s]));
+        chi[s] = ((float)chind[s] + c * dg[s]) * id;
         const float x = (st.tau[s] - chi[s]) * it0;
         dh[s] = (float)p * ipowf_n(fabsf(x), p - 1);
+        fa[s] = cg * dh[s];
+        const float dchi = (c - d * sgn(dg[s]) * chi[s]) * id;
+        Di[s] = 1.f / (1.f + fa[s] * dchi);
+        const float ga = fa[s] * Di[s];
+        int q = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float pi = __ldg(PC + 12 * i + s);
+#pragma unroll
+            for (int j = 0; j <= i; ++j) A5[q] = fmaf(ga * pi, __ldg(PC + 12 * j + s), A5[q]), ++q;
+        }
     }
-    return cp_tangent_core<float>(F, A, dg, g + G32_S0, g + G32_C, pr, dt * pr.gdot0, st, chi, dh, K);
+    // A5 = L diag(qd) L^T
+    float L[5][5], iq[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        float t = A5[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int m = 0; m < j; ++m) t -= L[j][m] * L[j][m] / iq[m];
+        if (!(t > 0.f)) return false;
+        iq[j] = 1.f / t;
+#pragma unroll
+        for (int i = j + 1; i < 5; ++i) {
+            float u = A5[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int m = 0; m < j; ++m) u -= L[i][m] * L[j][m] / iq[m];
+            L[i][j] = u * iq[j];
+        }
+    }
+    float FeS[9], SFt[9];
+    mm(st.Fe, st.S, FeS);
+    mmt(st.S, st.Fpi, SFt);  // S Fpi^T
+    // dP/ddg_b (12 x 9)
+    float dPb[NSLIP * 9];
+    for (int b = 0; b < NSLIP; ++b) {
+        float dFpi[9], dFe[9], dCe[9], dS[9], t1[9], t2[9], t3[9], t4[9];
+        dstate_ddg(F, A, S0 + 9 * b, C, st, dFpi, dFe, dCe, dS);
+        mm(dFe, st.S, t1);
+        mmt(t1, st.Fpi, t2);  // dFe S Fpi^T
+        mm(st.Fe, dS, t1);
+        mmt(t1, st.Fpi, t3);  // Fe dS Fpi^T
+        mmt(FeS, dFpi, t4);   // Fe S dFpi^T
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dPb[9 * b + k] = t2[k] + t3[k] + t4[k];
+    }
+    for (int kl = 0; kl < 9; ++kl) {
+        const int k = kl / 3, l = kl % 3;
+        float dFe[9];  // dFe = E_kl Fpi: row k equals row l of Fpi
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dFe[q] = 0.f;
+        dFe[3 * k] = st.Fpi[3 * l];
+        dFe[3 * k + 1] = st.Fpi[3 * l + 1];
+        dFe[3 * k + 2] = st.Fpi[3 * l + 2];
+        float t1[9], t2[9], dCe[9], hE[9], dS[9];
+        mtm(dFe, st.Fe, t1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                dCe[3 * i + j] = t1[3 * i + j] + t1[3 * j + i];
+                hE[3 * i + j] = 0.5f * dCe[3 * i + j];
+            }
+        c_ddot(C, hE, dS);
+        float dP[9], t3[9], dM[9];
+        mm(dFe, SFt, dP);  // dP at fixed dg = dFe S Fpi^T + Fe dS Fpi^T
+        mm(st.Fe, dS, t3);
+        mmt(t3, st.Fpi, t1);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dP[q] += t1[q];
+        mm(dCe, st.S, dM);  // dM = dCe S + Ce dS
+        mm(st.Ce, dS, t2);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dM[q] += t2[q];
+        // J x = R_kl through the 5 x 5 system
+        float r[NSLIP], u[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int a = 0; a < NSLIP; ++a) {
+            float dtau = 0.f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dtau = fmaf(dM[q], __ldg(S0 + 9 * a + q), dtau);
+            r[a] = fa[a] * dtau;
+            const float ra = r[a] * Di[a];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) u[i] = fmaf(ra, __ldg(PC + 12 * i + a), u[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int m = 0; m < i; ++m) u[i] -= L[i][m] * u[m];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) u[i] *= iq[i];
+#pragma unroll
+        for (int i = 4; i >= 0; --i)
+#pragma unroll
+            for (int m = i + 1; m < 5; ++m) u[i] -= L[m][i] * u[m];
+        for (int b = 0; b < NSLIP; ++b) {
+            float t = 0.f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i) t = fmaf(__ldg(PC + 12 * i + b), u[i], t);
+            const float xb = Di[b] * (r[b] - fa[b] * t);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dP[q] = fmaf(dPb[9 * b + q], xb, dP[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Kg[(9 * q + kl) * ldk] = dP[q];
+    }
+    return true;
 }
 
 // Return map (FP64) and, when K is not null, the tangent in precision T.
@@ -1132,10 +1258,7 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
             for (int s = 0; s < NSLIP; ++s) dg[s] = a.dg[s * N + v];
             bool ok;
             if (F32T) {
-                float K[81];
-                ok = cp_tangent_f32(F, A, chin, dg, a.dt, g32, pr, K);
-#pragma unroll
-                for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
+                ok = cp_tangent_f32(F, A, chin, dg, a.dt, g32, pr, a.K32 + v, N);
             } else {
                 double K[81];
                 ok = cp_tangent_at<double>(F, A, chin, dg, a.dt, geo, geo + GEO_S0, C, pr, K);
@@ -1158,12 +1281,9 @@ __device__ __forceinline__ void constitutive_voxel(const ConstArgs& a, const lon
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
                               (double*)nullptr, o, a.exact != 0, a.f32first ? g32 : nullptr);
         } else if (F32T) {  // the return map, then the tangent as a tangent-only launch forms it
-            float K[81];
             cp_update<float>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, g32 + G32_S0, g32 + G32_C, pr,
                              warm ? dg0 : nullptr, (float*)nullptr, o, a.exact != 0, a.f32first ? g32 : nullptr);
-            if (o.ok) o.ok = cp_tangent_f32(F, A, chin, o.dg, a.dt, g32, pr, K);
-#pragma unroll
-            for (int k = 0; k < 81; ++k) a.K32[k * N + v] = K[k];
+            if (o.ok) o.ok = cp_tangent_f32(F, A, chin, o.dg, a.dt, g32, pr, a.K32 + v, N);
         } else {
             double K[81];
             cp_update<double>(F, A, chin, a.dt, geo, C, a.H + 144LL * gi, geo + GEO_S0, C, pr, warm ? dg0 : nullptr,
