@@ -338,13 +338,16 @@ def workload_config(n=N_GRID):
 
 
 PASS1_END = b"// ---------------------------------------------------------------- pass 2:"
-STAGED_START = b"// ---------------------------------------------------------------- pass 3 for two-stage plans, register-staged"
-STAGED_END = b"template <typename T> constexpr int zproj_width()"
+PLAN_START = b"template <int R1, int R2> struct Inv2Plan {"
+PLAN_END = b"template <typename T, int R1, int R2>\n__device__ __forceinline__ void inv2_x1("
+FWD2_START = b"// ---------------------------------------------------------------- pass 1 for two-stage plans, register-staged"
+FWD2_END = b"template <typename T> constexpr int zproj_width()"
 # the parts of fft_proj.cu each profiled forward kernel is built from: everything before the pass-2
 # marker (complex arithmetic, butterflies, radix stages, line transforms, the contraction, pass 1),
-# and for the register-staged pass also the register-staged section (plan constants, swizzle, its kernels)
+# and for the register-staged pass also the plan constants, swizzle and row-pair mapping it shares
+# with the register-staged inverse, and its own section
 SOURCE_REGIONS = {"k_plane_fwd": [(None, PASS1_END)],
-                  "k_plane_fwd2": [(None, PASS1_END), (STAGED_START, STAGED_END)]}
+                  "k_plane_fwd2": [(None, PASS1_END), (PLAN_START, PLAN_END), (FWD2_START, FWD2_END)]}
 PROFILE_FILES = {"k_plane_fwd": "k_plane_fwd_fp64_64cube.md", "k_plane_fwd2": "k_plane_fwd2_fp64_64cube.md"}
 
 
