@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--batch-increments", type=int, default=8,
                    help="increments of the 32-RVE batch compared with one handle after the other (0: skip)")
     p.add_argument("--grid", type=int, default=N_GRID, help="grid size (smaller grids only for profiling runs)")
+    p.add_argument("--tiles", default="", help="12 comma-separated launch-shape ints (FP64 then FP32, the layout "
+                   "gff_autotune returns) to use instead of the tuned ones in the apply measurement")
     a = p.parse_args()
     return a
 
@@ -648,6 +650,11 @@ def run_gpu(args, world, rank, local):
     hd = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options(projection=g.GFF_PROJ_DISCRETE))
     tiles = g.gff_autotune(h)
     g.gff_autotune(hd)
+    if args.tiles:  # pinned launch shapes (profiling runs: timings under a profiler would mislead the tuner)
+        t = [int(v) for v in args.tiles.split(",")]
+        tiles = {"fp64": t[:6], "fp32": t[6:12]}
+        for hh in (h, hd):
+            g.gff_set_tiles(hh, tiles["fp64"], tiles["fp32"])
     g.gff_constitutive(h, 1.0)
     g.gff_constitutive(hd, 1.0)
     x = standard_normal(SEED_X, 9 * N).reshape(9, N)
