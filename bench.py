@@ -13,8 +13,10 @@ value = applies/s over all ranks.  The JSON line also carries:
     host y out, copies inside the call);
   * seconds per cyclic load increment over one full +-1 % strain cycle
     (80 increments, Newton tolerance 1e-6) for the 64^3 / 200-grain RVE
-    (FP64, mixed, mixed + extrapolated start; continuous and discrete
-    projection) and the 128^3 / 500-grain RVE (FP64 zero start, mixed zero
+    (FP64, mixed, mixed + extrapolated start, and the latter with the
+    FP64-only return map; continuous and discrete projection; the
+    constitutive time split into return maps and tangents) and the
+    128^3 / 500-grain RVE (FP64 zero start, mixed zero
     start, mixed + extrapolated start, mixed + learned U-Net start trained
     inside the run), each with its macroscopic-P error against the FP64 arm
     and the SM clocks sampled over the arm;
