@@ -69,7 +69,8 @@ def parse():
                    help="increments of the 32-RVE batch compared with one handle after the other (0: skip)")
     p.add_argument("--grid", type=int, default=N_GRID, help="grid size (smaller grids only for profiling runs)")
     p.add_argument("--tiles", default="", help="12 comma-separated launch-shape ints (FP64 then FP32, the layout "
-                   "gff_autotune returns) to use instead of the tuned ones in the apply measurement")
+                   "gff_autotune returns) to use instead of the tuned ones in the apply measurement; write "
+                   "--tiles=... (the values may be negative)")
     a = p.parse_args()
     return a
 
