@@ -291,6 +291,42 @@ def test_bounded_wait_timeout_is_reported_and_recoverable(prec):
         g.gff_destroy(h)
 
 
+@pytest.mark.parametrize("tiles", [(512, 8, 256, 256, -1, 0), (512, 16, 256, 512, -5, -7)])
+def test_bounded_wait_timeout_of_the_register_staged_passes(tiles):
+    """The same error path in the register-staged passes (64^3, FP32): the
+    inverse pass one block per plane (inv blocks -1, bulk copy) or persistent
+    with two plane buffers (inv blocks -5), with the TMA z pass's register-
+    staged strip (z blocks -7).  A zero budget leaves every plane of y NaN and
+    gff_sync reports GFF_ERR_TIMEOUT once; the default budget then gives the
+    bits of the generic passes."""
+    torch = torch_cuda()
+    shape = (64, 64, 64)
+    g, ms, h = _svk_handle(shape, 12, 21)
+    try:
+        g.gff_constitutive(h, 1.0)
+        X = torch.from_numpy(_field(14, shape).reshape(9, -1).copy()).cuda().float()
+        base = (512, 8, 256, 512, 0, 0)
+        g.gff_set_tiles(h, base, base)
+        Yref = torch.empty_like(X)
+        g.gff_apply_operator(h, 1, None, X, Yref)
+        g.gff_sync(h)
+        g.gff_set_tiles(h, base, tiles)
+        Y = torch.zeros_like(X)
+        g.gff_set_wait_limit(h, 0)
+        g.gff_apply_operator(h, 1, None, X, Y)
+        with pytest.raises(g.GffError) as e:
+            g.gff_sync(h)
+        assert e.value.status == g.GFF_ERR_TIMEOUT
+        assert torch.isnan(Y).all()
+        g.gff_sync(h)
+        g.gff_set_wait_limit(h, -1)
+        g.gff_apply_operator(h, 1, None, X, Y)
+        g.gff_sync(h)
+        assert torch.equal(Y, Yref)
+    finally:
+        g.gff_destroy(h)
+
+
 def test_timeout_fails_the_increment_and_keeps_the_state():
     """A load increment whose residual evaluation meets a timed-out wait
     returns GFF_ERR_TIMEOUT (no cut-back: it is not a convergence failure)
