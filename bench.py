@@ -558,8 +558,9 @@ def cyclic_increments(g, torch, args, clock_index):
             if f64 and v:
                 target[k + "_speedup_vs_fp64_zero"] = f64 / v
         if "mixed_unet_speedup_vs_fp64_zero" in target:
-            target["north_star_met"] = (target["mixed_unet_speedup_vs_fp64_zero"] > 1.0
-                                        and arms5["mixed_unet"].get("residual_max", 1.0) <= 1e-6)
+            # mixed precision with the learned start faster per cyclic increment than FP64 at residual <= 1e-6
+            target["mixed_unet_faster_than_fp64_at_1e-6"] = (target["mixed_unet_speedup_vs_fp64_zero"] > 1.0
+                                                            and arms5["mixed_unet"].get("residual_max", 1.0) <= 1e-6)
         out["config5"] = {"workload": "128^3, 500-grain periodic Voronoi (seed 5), FCC crystal plasticity, R=-1 "
                                       "+-1 pct strain cycle, %d increments, Newton tol 1e-6, CG tol 1e-3; U-Net "
                                       "trained in this run" % hist.nsteps,
