@@ -568,71 +568,100 @@ def cyclic_increments(g, torch, args, clock_index):
     return out
 
 
-def time_batch(g, torch, cycle_increments, compare_increments, precision):
+def time_batch(g, torch, cycle_increments, compare_increments, precision, world=1, rank=0):
     """32 RVEs of 32^3 ... 96^3 voxels (10,956,800 in all), crystal plasticity,
     +-1 % strain cycle, mixed precision, extrapolated warm start: one full
     cycle through gff_batch_run (one graph launch per increment) with the
     per-grain Fatemi-Socie parameter at its end, and the first
     `compare_increments` increments batched against running the same RVEs one
-    handle after the other."""
-    try:
-        from rve_inputs import batch_rves, cyclic_history, polycrystal
+    handle after the other.  With several ranks the RVEs are spread over them
+    (shard.assign; each rank runs its share as one batch, no collective on the
+    data path), the time is the slowest rank's and the per-RVE results are
+    gathered on rank 0 once at the end."""
+    from paper_1806_10599_gb300 import shard
+    from rve_inputs import batch_rves, cyclic_history, polycrystal
 
-        specs = batch_rves()
-        full = cyclic_history(0.01, 1).head(cycle_increments)
-        opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3,
-                              warm_start=g.GFF_WARM_EXTRAPOLATE)
-        out = {"rves": len(specs), "voxels": int(sum(n ** 3 for n, _, _ in specs))}
+    specs = batch_rves()
+    parts = shard.assign([n for n, _, _ in specs], world)
+    mine = parts[rank]
+    full = cyclic_history(0.01, 1).head(cycle_increments)
+    out = {"rves": len(specs), "voxels": int(sum(n ** 3 for n, _, _ in specs))}
+    if world > 1:
+        out["ranks"] = world
+        out["rves_per_rank"] = [len(p) for p in parts]
+    errors = []
 
-        def make():
-            hs = [g.create_rve(polycrystal(n, ng, seed), {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts)
-                  for n, ng, seed in specs]
-            for h in hs:
-                g.gff_set_warm_start(h, None, g.GFF_WARM_EXTRAPOLATE)
-                g.gff_autotune(h)
-            torch.cuda.synchronize()
-            return hs
+    def make():
+        opts = g.make_options(precision=precision, newton_tol=1e-6, cg_tol=1e-3, warm_start=g.GFF_WARM_EXTRAPOLATE)
+        hs = []
+        for i in mine:
+            n, ng, seed = specs[i]
+            hs.append(g.create_rve(polycrystal(n, ng, seed), {0: g.make_material(g.GFF_MAT_CP_FCC)}, opts))
+        for h in hs:
+            g.gff_set_warm_start(h, None, g.GFF_WARM_EXTRAPOLATE)
+            g.gff_autotune(h)
+        torch.cuda.synchronize()
+        return hs
 
-        if cycle_increments > 0:
+    def timed(run):
+        """Local run on this rank's RVEs between barriers; seconds of the slowest rank (collectives always run)."""
+        secs, res = float("nan"), None
+        hs = []
+        try:
             hs = make()
-            try:
-                t0 = time.perf_counter()
-                Pm, reps, stat = g.gff_batch_run(hs, full.dt, full.Fbar, full.mask, full.Pbar, full.cycle_start,
-                                                 raise_on_error=False)
-                torch.cuda.synchronize()
-                secs = time.perf_counter() - t0
-                fs_max = [float(max(g.gff_get_fips(h, ng)[2])) for h, (n, ng, seed) in zip(hs, specs)]
-            finally:
-                for h in hs:
-                    g.gff_destroy(h)
+            barrier(world)
+            t0 = time.perf_counter()
+            res = run(hs)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        except Exception as e:  # report, do not lose the apply measurement (nor hang the other ranks)
+            errors.append(str(e))
+            if world > 1 and not hs:
+                barrier(world)
+        finally:
+            for h in hs:
+                g.gff_destroy(h)
+        return max_over_ranks(secs, world), res
+
+    if cycle_increments > 0:
+        def cycle(hs):
+            Pm, reps, stat = g.gff_batch_run(hs, full.dt, full.Fbar, full.mask, full.Pbar, full.cycle_start,
+                                             raise_on_error=False)
+            torch.cuda.synchronize()
+            return [{"status": int(stat[j]), "fs_max": float(max(g.gff_get_fips(h, specs[i][1])[2])),
+                     "newton": int(sum(r.newton_iters for r in reps[j])), "cuts": int(sum(r.cuts for r in reps[j]))}
+                    for j, (i, h) in enumerate(zip(mine, hs))]
+
+        secs, res = timed(cycle)
+        got = shard.gather_to_rank0(res if res is not None else [None] * len(mine), world)
+        if rank == 0:
+            per = shard.merge(got, parts, len(specs))
+            ok = all(p is not None for p in per)
             out["cycle"] = {"increments": full.nsteps, "s_per_increment_batched": secs / full.nsteps,
-                            "status": [int(x) for x in stat],
-                            "newton_mean": float(sum(r.newton_iters for rr in reps for r in rr) / (len(reps) * full.nsteps)),
-                            "cuts": int(sum(r.cuts for rr in reps for r in rr)),
-                            "fatemi_socie_max_per_rve": fs_max}
-        if compare_increments > 0:
-            part = full.head(compare_increments)
-            for mode in ("batched", "one_by_one"):
-                hs = make()
-                try:
-                    t0 = time.perf_counter()
-                    if mode == "batched":
-                        g.gff_batch_run(hs, part.dt, part.Fbar, part.mask, part.Pbar, part.cycle_start)
-                    else:
-                        for h in hs:
-                            g.gff_run_history(h, part.dt, part.Fbar, part.mask, part.Pbar, part.cycle_start)
-                    torch.cuda.synchronize()
-                    out["s_per_increment_%s_first_%d" % (mode, part.nsteps)] = (time.perf_counter() - t0) / part.nsteps
-                finally:
-                    for h in hs:
-                        g.gff_destroy(h)
-            a1 = out.get("s_per_increment_batched_first_%d" % part.nsteps)
-            a2 = out.get("s_per_increment_one_by_one_first_%d" % part.nsteps)
-            if a1 and a2:
-                out["batched_speedup_first_%d" % part.nsteps] = a2 / a1
-        return out
-    except Exception as e:  # report, do not lose the apply measurement
-        return {"error": str(e)}
+                            "status": [p["status"] if p else None for p in per],
+                            "newton_mean": (sum(p["newton"] for p in per) / (len(per) * full.nsteps)) if ok else None,
+                            "cuts": sum(p["cuts"] for p in per) if ok else None,
+                            "fatemi_socie_max_per_rve": [p["fs_max"] if p else None for p in per]}
+    if compare_increments > 0:
+        part = full.head(compare_increments) if cycle_increments > 0 else \
+            cyclic_history(0.01, 1).head(compare_increments)
+        for mode in ("batched", "one_by_one"):
+            if mode == "batched":
+                def run(hs):
+                    return g.gff_batch_run(hs, part.dt, part.Fbar, part.mask, part.Pbar, part.cycle_start)
+            else:
+                def run(hs):
+                    return [g.gff_run_history(h, part.dt, part.Fbar, part.mask, part.Pbar, part.cycle_start)
+                            for h in hs]
+            secs, _ = timed(run)
+            out["s_per_increment_%s_first_%d" % (mode, part.nsteps)] = secs / part.nsteps
+        a1 = out.get("s_per_increment_batched_first_%d" % part.nsteps)
+        a2 = out.get("s_per_increment_one_by_one_first_%d" % part.nsteps)
+        if a1 and a2 and a1 == a1 and a2 == a2:
+            out["batched_speedup_first_%d" % part.nsteps] = a2 / a1
+    if errors:
+        out["error"] = "; ".join(errors)
+    return out
 
 
 def run_gpu(args, world, rank, local):
@@ -703,11 +732,11 @@ def run_gpu(args, world, rank, local):
     if args.increments > 0 and rank == 0:
         inc = cyclic_increments(g, torch, args, clock_index)
     batch = None
-    if (args.batch_cycle > 0 or args.batch_increments > 0) and rank == 0:
+    if args.batch_cycle > 0 or args.batch_increments > 0:  # every rank: the RVEs are spread over the ranks
         batch = {"workload": "32 RVEs (7x32^3, 7x48^3, 6x64^3, 6x80^3, 6x96^3; 50-300 grains, seeds 4000+i), FCC "
                              "crystal plasticity, +-1 pct cycle, mixed precision, Newton tol 1e-6, extrapolated "
                              "warm start",
-                 "mixed": time_batch(g, torch, args.batch_cycle, args.batch_increments, 1)}
+                 "mixed": time_batch(g, torch, args.batch_cycle, args.batch_increments, 1, world, rank)}
 
     if rank != 0:
         return
