@@ -178,14 +178,15 @@ def kernel_flops_per_voxel(n):
     """Algorithmic floating-point operations per voxel (5 n log2 n per complex
     FFT of length n, the usual convention): forward plane pass = K:x (162) +
     9 x (x real transform 2.5 log2 n + y transform 5 log2 n (n/2+1)/n);
-    z pass = 9 x 2 x 5 log2 n (n/2+1)/n + projection (~56 per frequency);
-    inverse plane pass = 9 x (same transforms)."""
+    z pass = 6 x 2 x 5 log2 n (n/2+1)/n (each tensor row packed into two
+    fields, transformed both ways) + packing, projection and unpacking (~72
+    per frequency); inverse plane pass = 9 x (same transforms)."""
     import math
 
     lg = math.log2(n)
     fr = (n // 2 + 1) / n
     plane = 9 * (2.5 * lg + 5 * lg * fr)
-    return [162 + plane, 9 * 2 * 5 * lg * fr + 56 * fr, plane]
+    return [162 + plane, 6 * 2 * 5 * lg * fr + 72 * fr, plane]
 
 
 def measured_peaks():

@@ -633,42 +633,84 @@ __device__ __forceinline__ void zproj_columns(const GridDev& g, int f0, const ZT
     }
 }
 
-// Projection of the three components (v0, v1, v2) of one tensor row at the
-// frequency (kx, ky, kz): the zero frequency keeps the stress-controlled
-// components (mask m), Nyquist planes are zeroed, else y_ij = (x_il n_l) n_j
-// with n the unit (continuous or discrete) wave vector.
+// The projection reaches a tensor row only through t = x_il q_l
+// (y_ij = t q_j / |q|^2), and q_x, q_y are constant along a z column, so the
+// z pass transforms two fields per row instead of three:
+//   before the forward z transform  u = q_x x_i0 + q_y x_i1,  v = x_i2;
+//   at each frequency               a = (u + q_z v) / |q|^2,  v <- q_z a;
+//   after the inverse z transform   y_i0 = q_x a, y_i1 = q_y a, y_i2 = v.
+// On the zero-frequency column (kx, ky) = (0, 0), where q_x = q_y = 0, the
+// plane sums of x_i0 and x_i1 (real numbers) travel packed as
+// u = x_i0 + i x_i1 instead, so the masked mean (zero frequency: the
+// stress-controlled components kept, mask m) of all three components passes
+// through; Nyquist planes are zeroed.
+template <typename T> struct ZCol {
+    T a, b;   // q_x(kx), q_y(ky)
+    bool dc;  // (kx, ky) = (0, 0)
+};
+template <typename T> __device__ __forceinline__ ZCol<T> zcol(int ck, const ZTables<T>& tb) {
+    ZCol<T> c{(T)0, (T)0, false};
+    if (ck >= 0) {
+        const int kx = ck & 0xffff, ky = ck >> 16;
+        c.a = tb.qx[kx];
+        c.b = tb.qy[ky];
+        c.dc = kx == 0 && ky == 0;
+    }
+    return c;
+}
 template <typename T>
-__device__ __forceinline__ void proj_point(typename C2<T>::t& v0, typename C2<T>::t& v1, typename C2<T>::t& v2,
-                                           int kx, int ky, int kz, int nx, int ny, int nz, T m0, T m1, T m2,
-                                           const ZTables<T>& tb) {
+__device__ __forceinline__ typename C2<T>::t zpack(typename C2<T>::t v0, typename C2<T>::t v1, const ZCol<T>& c) {
     using C = typename C2<T>::t;
-    if (kx == 0 && ky == 0 && kz == 0) {
-        v0 = cscale(v0, m0);
-        v1 = cscale(v1, m1);
-        v2 = cscale(v2, m2);
-    } else if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
-        v0 = v1 = v2 = mk<C>((T)0, (T)0);
+    if (c.dc) return mk<C>(v0.x, v1.x);
+    return mk<C>(fma(c.a, v0.x, c.b * v1.x), fma(c.a, v0.y, c.b * v1.y));
+}
+template <typename T>
+__device__ __forceinline__ void zunpack(typename C2<T>::t a, const ZCol<T>& c, typename C2<T>::t& y0,
+                                        typename C2<T>::t& y1) {
+    using C = typename C2<T>::t;
+    if (c.dc) {
+        y0 = mk<C>(a.x, (T)0);
+        y1 = mk<C>(a.y, (T)0);
+    } else {
+        y0 = cscale(a, c.a);
+        y1 = cscale(a, c.b);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void zrow_proj(typename C2<T>::t& u, typename C2<T>::t& v, int kx, int ky, int kz, int nx,
+                                          int ny, int nz, T m0, T m1, T m2, const ZTables<T>& tb) {
+    using C = typename C2<T>::t;
+    if (kx == nx / 2 || ky == ny / 2 || kz == nz / 2) {
+        u = v = mk<C>((T)0, (T)0);
+    } else if (kx == 0 && ky == 0) {
+        if (kz == 0) {
+            u = mk<C>(u.x * m0, u.y * m1);
+            v = cscale(v, m2);
+        } else {
+            u = mk<C>((T)0, (T)0);  // q along z: y_i2 = x_i2, y_i0 = y_i1 = 0
+        }
     } else {
         const T a = tb.qx[kx], b = tb.qy[ky], d = tb.qz[kz];
-        const T inv = rnorm3(a, b, d);
-        const T n0 = a * inv, n1 = b * inv, n2 = d * inv;
-        // t = sum_l x_il n_l ; y_ij = t n_j
-        const C t = mk<C>(v0.x * n0 + v1.x * n1 + v2.x * n2, v0.y * n0 + v1.y * n1 + v2.y * n2);
-        v0 = cscale(t, n0);
-        v1 = cscale(t, n1);
-        v2 = cscale(t, n2);
+        const T r = (T)1 / fma(a, a, fma(b, b, d * d));
+        const C t = mk<C>(fma(d, v.x, u.x) * r, fma(d, v.y, u.y) * r);
+        u = t;
+        v = cscale(t, d);
     }
 }
 
 // Forward z transform, projection and inverse z transform of one loaded strip
-// s = [3][nz][W] (tensor row `row`); ends with a barrier.
+// s = [3][nz][W] (tensor row `row`): the row packed into u (slot 0) and
+// v (slot 2), both transformed, projected, transformed back and unpacked into
+// the three slots; ends with a barrier.
 template <typename T, int W>
 __device__ __forceinline__ void zproj_strip(typename C2<T>::t* s, const GridDev& g, const ProjArgs& pa, int row,
                                             const ZTables<T>& tb) {
     using C = typename C2<T>::t;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    fft_lines<T, false>(s, tb.twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+    for (int e = tid; e < nz * W; e += nthr) s[e] = zpack<T>(s[e], s[nz * W + e], zcol<T>(tb.colk[e % W], tb));
+    __syncthreads();
+    fft_lines<T, false>(s, tb.twz, g.az, W, 1, 2, 2 * nz * W, W, tid, nthr);
     const T m0 = (T)pa.mask[3 * row], m1 = (T)pa.mask[3 * row + 1], m2 = (T)pa.mask[3 * row + 2];
     for (int e = tid; e < nz * W; e += nthr) {
         const int w = e % W, pz = e / W;
@@ -676,37 +718,45 @@ __device__ __forceinline__ void zproj_strip(typename C2<T>::t* s, const GridDev&
         if (ck < 0) continue;
         const int kx = ck & 0xffff, ky = ck >> 16, kz = tb.fqz[pz];
         C* p0 = s + pz * W + w;
-        C v0 = p0[0], v1 = p0[nz * W], v2 = p0[2 * nz * W];
-        proj_point<T>(v0, v1, v2, kx, ky, kz, nx, ny, nz, m0, m1, m2, tb);
-        p0[0] = v0;
-        p0[nz * W] = v1;
-        p0[2 * nz * W] = v2;
+        C u = p0[0], v = p0[2 * nz * W];
+        zrow_proj<T>(u, v, kx, ky, kz, nx, ny, nz, m0, m1, m2, tb);
+        p0[0] = u;
+        p0[2 * nz * W] = v;
     }
     __syncthreads();
-    fft_lines<T, true>(s, tb.twz, g.az, W, 1, 3, nz * W, W, tid, nthr);
+    fft_lines<T, true>(s, tb.twz, g.az, W, 1, 2, 2 * nz * W, W, tid, nthr);
+    for (int e = tid; e < nz * W; e += nthr) zunpack<T>(s[e], zcol<T>(tb.colk[e % W], tb), s[e], s[nz * W + e]);
+    __syncthreads();
 }
 
 // z transform, projection and inverse z transform of one strip for the
 // two-stage plans nz = 16 x 8 and 8 x 8, with one butterfly's values held in
-// registers across a stage: the forward radix-R1 stage; then per (column,
-// sub) the forward radix-8 stage of the three components, the projection of
-// the eight frequencies sub + R1 q it produced, and the inverse radix-8 stage,
-// without leaving registers; then the inverse radix-R1 stage.  The same
-// operations in the same order as zproj_strip (bit-identical), with two
-// passes over shared memory and two barriers fewer.  Ends with a barrier.
+// registers across a stage: the forward radix-R1 stage (the row packed into
+// u, v on its loads); then per (column, sub) the forward radix-8 stage of u
+// and v, the projection of the eight frequencies sub + R1 q it produced, and
+// the inverse radix-8 stage, without leaving registers; then the inverse
+// radix-R1 stage (unpacked on its stores).  The same operations in the same
+// order as zproj_strip (bit-identical), with four passes over shared memory
+// and four barriers fewer.  Ends with a barrier.
 template <typename T, int R1, int W>
 __device__ __forceinline__ void zstrip2(typename C2<T>::t* s, const GridDev& g, const ProjArgs& pa, int row,
                                         const ZTables<T>& tb) {
     using C = typename C2<T>::t;
     constexpr int R2 = 8, nz = R1 * R2;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // forward radix R1 over positions j + R2 n1 of each (component, column), twiddles after
-    for (int t = tid; t < 3 * R2 * W; t += nthr) {
-        const int w = t % W, jc = t / W, j = jc % R2, comp = jc / R2;
-        C* b = s + (comp * nz + j) * W + w;
+    // forward radix R1 over positions j + R2 n1 of u (slot 0) and v (slot 2), twiddles after
+    for (int t = tid; t < 2 * R2 * W; t += nthr) {
+        const int w = t % W, jc = t / W, j = jc % R2, comp = jc / R2;  // comp warp-uniform (R2 W % 32 == 0)
+        C* b = s + (2 * comp * nz + j) * W + w;
         C v[R1];
+        if (comp == 0) {
+            const ZCol<T> c = zcol<T>(tb.colk[w], tb);
 #pragma unroll
-        for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * W];
+            for (int q = 0; q < R1; ++q) v[q] = zpack<T>(b[q * R2 * W], b[(nz + q * R2) * W], c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * W];
+        }
         Bfly<R1, false, C>::run(v);
         if (j) {
 #pragma unroll
@@ -722,37 +772,33 @@ __device__ __forceinline__ void zstrip2(typename C2<T>::t* s, const GridDev& g, 
         const int w = t % W, sub = t / W;
         const int ck = tb.colk[w];
         C* b = s + sub * R2 * W + w;
-        C v0[R2], v1[R2], v2[R2];
+        C u[R2], v[R2];
 #pragma unroll
         for (int q = 0; q < R2; ++q) {
-            v0[q] = b[q * W];
-            v1[q] = b[(nz + q) * W];
-            v2[q] = b[(2 * nz + q) * W];
+            u[q] = b[q * W];
+            v[q] = b[(2 * nz + q) * W];
         }
-        Bfly<R2, false, C>::run(v0);
-        Bfly<R2, false, C>::run(v1);
-        Bfly<R2, false, C>::run(v2);
+        Bfly<R2, false, C>::run(u);
+        Bfly<R2, false, C>::run(v);
         if (ck >= 0) {
             const int kx = ck & 0xffff, ky = ck >> 16;
 #pragma unroll
             for (int q = 0; q < R2; ++q)
-                proj_point<T>(v0[q], v1[q], v2[q], kx, ky, tb.fqz[sub * R2 + q], nx, ny, nz, m0, m1, m2, tb);
+                zrow_proj<T>(u[q], v[q], kx, ky, tb.fqz[sub * R2 + q], nx, ny, nz, m0, m1, m2, tb);
         }
-        Bfly<R2, true, C>::run(v0);
-        Bfly<R2, true, C>::run(v1);
-        Bfly<R2, true, C>::run(v2);
+        Bfly<R2, true, C>::run(u);
+        Bfly<R2, true, C>::run(v);
 #pragma unroll
         for (int q = 0; q < R2; ++q) {
-            b[q * W] = v0[q];
-            b[(nz + q) * W] = v1[q];
-            b[(2 * nz + q) * W] = v2[q];
+            b[q * W] = u[q];
+            b[(2 * nz + q) * W] = v[q];
         }
     }
     __syncthreads();
-    // inverse radix R1, conjugate twiddles before
-    for (int t = tid; t < 3 * R2 * W; t += nthr) {
+    // inverse radix R1, conjugate twiddles before; u unpacked into slots 0 and 1
+    for (int t = tid; t < 2 * R2 * W; t += nthr) {
         const int w = t % W, jc = t / W, j = jc % R2, comp = jc / R2;
-        C* b = s + (comp * nz + j) * W + w;
+        C* b = s + (2 * comp * nz + j) * W + w;
         C v[R1];
 #pragma unroll
         for (int q = 0; q < R1; ++q) v[q] = b[q * R2 * W];
@@ -761,8 +807,14 @@ __device__ __forceinline__ void zstrip2(typename C2<T>::t* s, const GridDev& g, 
             for (int p = 1; p < R1; ++p) v[p] = cmulc(v[p], tb.twz[p * j]);
         }
         Bfly<R1, true, C>::run(v);
+        if (comp == 0) {
+            const ZCol<T> c = zcol<T>(tb.colk[w], tb);
 #pragma unroll
-        for (int q = 0; q < R1; ++q) b[q * R2 * W] = v[q];
+            for (int q = 0; q < R1; ++q) zunpack<T>(v[q], c, b[q * R2 * W], b[(nz + q * R2) * W]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < R1; ++q) b[q * R2 * W] = v[q];
+        }
     }
     __syncthreads();
 }
@@ -904,16 +956,16 @@ template <typename T, int W> size_t ztma_smem(const GridDev& g) {
 }
 
 // R1 = 0: any nz (zproj_strip), up to BT = 512 threads; R1 = 16 / 8: nz = 128 / 64 with
-// the register-staged strip (zstrip2), whose register budget holds the 24 complex values
-// of the fused middle stage: BT = 256 threads, two blocks per SM in FP32 and one in FP64,
-// or (FP32) BT = 384, one block per SM, where the 384 radix-16 tasks of a W = 16 strip
-// take one round instead of two
-template <typename T, int R1, int BT> constexpr int ztma_min_blocks() {
+// the register-staged strip (zstrip2), whose fused middle stage holds 16 complex values
+// (u and v of one radix-8 butterfly): BT = 256 threads, two blocks per SM in FP32 and one
+// in FP64 (whose pipe, not the warps in flight, sets the pace; a cap of 128 registers
+// spills), or (FP32) BT = 384, one block per SM
+template <typename T, int W, int R1, int BT> constexpr int ztma_min_blocks() {
     return (R1 && sizeof(T) == 4 && BT == 256) ? 2 : 1;
 }
 
 template <typename T, int W, int R1, int BT>
-__global__ void __launch_bounds__(BT, ztma_min_blocks<T, R1, BT>())
+__global__ void __launch_bounds__(BT, ztma_min_blocks<T, W, R1, BT>())
     k_zproj_tma(const __grid_constant__ CUtensorMap tm, GridDev g, ProjArgs pa, const int* __restrict__ skip,
                 int* __restrict__ err) {
     using C = typename C2<T>::t;
@@ -2126,8 +2178,8 @@ cudaError_t autotune_prec(gff_handle* h, T* x, T* y, const T* K) {
     if (e != cudaSuccess) return e;
     tn.t_fwd = tp[b];
     // z pass: one block per strip (W 4..32, 128 or 256 threads), or the persistent TMA pass (W 8, 16; 256, 512)
-    // (the TMA pass also takes 192 / 384 threads: a strip of W columns has 24 W radix-16
-    // butterflies at n = 128, so 384 threads at W = 16 and 192 at W = 8 take one each)
+    // (the TMA pass also takes 192 / 384 threads; a strip of W columns has 16 W radix-16
+    // butterflies at n = 128, its rows packed into two transformed fields)
     // and (nz = 64 or 128) the TMA pass with the register-staged strip (W 8, 16; 256 threads, or 384 in FP32)
     constexpr int NZC = 18;
     const int wz[NZC] = {4, 4, 8, 8, 16, 16, 32, 32, 8, 8, 16, 16, 8, 8, 16, 8, 16, 16};
