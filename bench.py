@@ -830,7 +830,7 @@ def build_line(args, world, raw, peaks, src):
         "config": workload_config(args.grid), "roofline": roof, "cpu_baseline": raw["cpu"],
         "e2e": {"value": world * steps / raw["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": raw["xbytes"],
                 "d2h_bytes_per_step": raw["xbytes"],
-                "how": "gff_apply_operator_host per step: pinned host x -> device, apply, device -> pinned host y"},
+                "how": "gff_apply_operator_host per step: pinned host x -> device in chunks of z-planes that overlap the forward plane pass, z pass, pinned host y <- device in chunks that overlap the inverse plane pass"},
         "gpu_launches": 3 * steps, "clocks": raw["clocks"],
         "fp64_tflops_measured": (raw.get("fp64_peak_gflops") or 0) / 1e3 or None,
         "variants": {

@@ -177,9 +177,14 @@ gff_status gff_apply_operator_timed(gff_handle* h, int precision, const uint8_t*
 /* gff_apply_operator with HOST buffers, for callers without device memory of
  * their own: x_host is copied into the handle's work vector, the operator
  * applied, y copied back to y_host (double[9N] for GFF_PREC_FP64, float[9N]
- * for GFF_PREC_MIXED; pinned host memory makes the copies asynchronous and
- * fast).  Returns when y_host is written, with the status of gff_sync.  It
- * uses the handle's CG work vectors as device buffers. */
+ * for GFF_PREC_MIXED, the layout of gff_apply_operator).  The copies go in
+ * chunks of z-planes on a second stream of the handle (made on first use):
+ * a chunk's forward plane pass waits only for its own copy, a chunk's copy
+ * back only for its own inverse plane pass, so with pinned host memory the
+ * copies overlap the plane passes of the other chunks (pageable memory works,
+ * without the overlap).  The result equals gff_apply_operator's bit for bit.
+ * Returns when y_host is written, with the status of gff_sync.  It uses the
+ * handle's CG work vectors as device buffers. */
 gff_status gff_apply_operator_host(gff_handle* h, int precision, const uint8_t* mask9, const void* x_host,
                                    void* y_host);
 

@@ -462,6 +462,8 @@ GFF_EXPORT void gff_destroy(gff_handle* h) {
     dfree(h->d_chi_t); dfree(h->d_dg); dfree(h->d_tau); dfree(h->d_acc); dfree(h->d_flag); dfree(h->d_red);
     dfree(h->d_scal); dfree(h->d_gq); dfree(h->d_yhist); dfree(h->d_geo32);
     if (h->h_scal) cudaFreeHost(h->h_scal);
+    for (int i = 0; i < h->pipe_nev; ++i) cudaEventDestroy(h->pipe_ev[i]);
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     delete reinterpret_cast<gff_hostdata*>(h->hostdata);
     delete h;
 }
@@ -686,13 +688,20 @@ GFF_EXPORT gff_status gff_apply_operator_host(gff_handle* h, int precision, cons
                                               void* y_host) {
     if (!h || !x_host || !y_host) return fail(h, GFF_ERR_ARG, "bad apply args");
     if (precision != GFF_PREC_FP64 && precision != GFF_PREC_MIXED) return fail(h, GFF_ERR_ARG, "precision %d", precision);
-    const size_t bytes = 9 * (size_t)h->N * (precision == GFF_PREC_FP64 ? sizeof(double) : sizeof(float));
-    void* xd = precision == GFF_PREC_FP64 ? (void*)h->d_x : (void*)h->d_x32;
-    void* yd = precision == GFF_PREC_FP64 ? (void*)h->d_Ap : (void*)h->d_Ap32;
-    GFF_TRY(cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, h->stream));
-    gff_status st = gff_apply_operator(h, precision, mask9, xd, yd);
-    if (st != GFF_OK) return st;
-    GFF_TRY(cudaMemcpyAsync(y_host, yd, bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (!tangent_ready(h, precision)) return fail(h, GFF_ERR_STATE, "no tangent for this precision: call gff_constitutive");
+    const ProjArgs pa = proj_args(h, mask9);
+    const OutArgs oa = out_args(h, 1.0, nullptr);
+    if (precision == GFF_PREC_FP64) {
+        GFF_TRY(launch_galerkin_host<double>(h, (const double*)x_host, (double*)y_host, h->d_x, h->d_Ap, h->d_K, pa, oa,
+                                             h->d_spec));
+    } else {
+        if (!h->K32_valid) {
+            GFF_TRY(launch_cast64to32(h->d_K32, h->d_K, 81 * h->N, h->stream));
+            h->K32_valid = true;
+        }
+        GFF_TRY(launch_galerkin_host<float>(h, (const float*)x_host, (float*)y_host, h->d_x32, h->d_Ap32, h->d_K32, pa,
+                                            oa, reinterpret_cast<float2*>(h->d_spec)));
+    }
     return gff_sync(h);
 }
 

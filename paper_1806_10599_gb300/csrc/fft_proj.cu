@@ -1799,11 +1799,13 @@ namespace {
 
 template <typename T>
 cudaError_t launch_fwd(const GridDev& g, int threads, const T* x, const T* K, typename C2<T>::t* spec,
-                       const int* skip, cudaStream_t st, bool vin) {
+                       const int* skip, cudaStream_t st, bool vin, int planes = 0) {
+    // planes > 0: that many z-planes from the ones x, K and spec point at (a chunk of the grid)
+    const int nzl = planes > 0 ? planes : g.nz;
     if (threads < 0 && !(K && vin)) threads = -threads;  // projection alone, unaligned: the generic pass
     if (threads < 0) {  // register-staged pass of the two-stage plans (nx = ny = 64 or 128), -threads threads
         const size_t sm = fwd2_smem<T>(g);
-        const dim3 grid(9, g.nz);
+        const dim3 grid(9, nzl);
         const int r1 = inv2_radix(g);
 #define GFF_FWD2(R, BT)                                                             \
     if (r1 == R && threads == -BT) {                                                \
@@ -1819,7 +1821,7 @@ cudaError_t launch_fwd(const GridDev& g, int threads, const T* x, const T* K, ty
         return cudaErrorInvalidValue;
     }
     const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
-    const dim3 gridA(9, g.nz);
+    const dim3 gridA(9, nzl);
     if (K) {
         if (vin) {
             allow_smem(k_plane_fwd<T, true, true>, smA);
@@ -2021,7 +2023,10 @@ int z_tma_blocks(gff_handle* h, int W, int threads, bool reg = false) {
 
 template <typename T>
 cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename C2<T>::t* spec, T* y,
-                       const OutArgs& oa, const int* skip, cudaStream_t st, bool vout, int* err) {
+                       const OutArgs& oa, const int* skip, cudaStream_t st, bool vout, int* err, int planes = 0) {
+    // planes > 0 (one block per plane only): that many z-planes from the ones spec and y point at
+    const int nzl = planes > 0 ? planes : g.nz;
+    if (planes > 0 && blocks != 0 && blocks != -1) return cudaErrorInvalidValue;
     if (blocks < -1) {  // register-staged persistent pass, -blocks blocks
         const size_t sm = inv2s_smem<T>(g);
         const int r1 = inv2_radix(g);
@@ -2042,7 +2047,7 @@ cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename
     }
     if (blocks < 0) {  // register-staged pass of the two-stage plans, one block per plane
         const size_t sm = inv2_smem<T>(g);
-        const dim3 grid(9, g.nz);
+        const dim3 grid(9, nzl);
         const int r1 = inv2_radix(g);
 #define GFF_INV2(R, BT)                                                              \
     if (r1 == R && threads == BT) {                                                  \
@@ -2069,7 +2074,7 @@ cudaError_t launch_inv(const GridDev& g, int threads, int blocks, const typename
         return cudaGetLastError();
     }
     const size_t smA = plane_smem_bytes(g.nx, g.ny, sizeof(typename C2<T>::t));
-    const dim3 gridA(9, g.nz);
+    const dim3 gridA(9, nzl);
     if (vout) {
         allow_smem(k_plane_inv<T, true>, smA);
         k_plane_inv<T, true><<<gridA, threads, smA, st>>>(spec, y, g, oa, skip, err);
@@ -2413,10 +2418,97 @@ cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, c
     return e;
 }
 
+// The apply with host buffers, pipelined over chunks of z-planes: the forward
+// plane pass of a chunk waits only for that chunk's host-to-device copy, and
+// a chunk's device-to-host copy waits only for its inverse plane pass, so the
+// copies (on the handle's copy stream) overlap the plane passes of the other
+// chunks; the z pass needs every plane and runs between.  Same kernels on the
+// same planes as launch_galerkin: bitwise the same y.  A persistent inverse
+// pass is replaced by its one-block-per-plane counterpart (bitwise the same).
+static cudaError_t host_pipe_ready(gff_handle* h, int nch) {
+    cudaError_t e = cudaSuccess;
+    if (!h->copy_stream) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    while (e == cudaSuccess && h->pipe_nev < 2 + 2 * nch) {
+        e = cudaEventCreateWithFlags(&h->pipe_ev[h->pipe_nev], cudaEventDisableTiming);
+        if (e == cudaSuccess) ++h->pipe_nev;
+    }
+    return e;
+}
+
+static int host_chunks(int nz, size_t bytes) {
+    if (bytes < ((size_t)4 << 20)) return 1;
+    return nz >= 16 ? 8 : nz / 2;
+}
+
+template <typename T>
+cudaError_t launch_galerkin_host(gff_handle* h, const T* x_host, T* y_host, T* xd, T* yd, const T* K,
+                                 const ProjArgs& pa, const OutArgs& oa, typename C2<T>::t* spec) {
+    const GridDev& g = h->g;
+    const Tune& tn = h->tune[tune_index<T>()];
+    const size_t plane = (size_t)g.ny * g.nx, pspec = (size_t)g.ny * g.nxh;
+    const size_t pitch = (size_t)g.N * sizeof(T);
+    const int nch = host_chunks(g.nz, 9 * pitch);
+    cudaError_t e = host_pipe_ready(h, nch);
+    if (e != cudaSuccess) return e;
+    cudaStream_t st = h->stream, cs = h->copy_stream;
+    cudaEvent_t* ev = h->pipe_ev;  // [0] start, [1] done, [2, 2 + nch) copied in, [2 + nch, 2 + 2 nch) computed
+    const bool vin = vec_ok<T>(g, xd) && vec_ok<T>(g, K);
+    const bool vout = vec_ok<T>(g, yd);
+    int t_inv = tn.t_inv, b_inv = tn.inv_blocks;
+    if (b_inv < -1) {
+        t_inv = 256;
+        b_inv = -1;
+    } else if (b_inv > 0) {
+        t_inv = t_inv > 512 ? 512 : t_inv;
+        b_inv = 0;
+    }
+    // the copies start after the work already queued on the handle's stream (it may still use xd, yd)
+    if ((e = cudaEventRecord(ev[0], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev[0], 0)) != cudaSuccess)
+        return e;
+    for (int c = 0; c < nch; ++c) {
+        const int z0 = c * g.nz / nch, z1 = (c + 1) * g.nz / nch;
+        e = cudaMemcpy2DAsync(xd + z0 * plane, pitch, x_host + z0 * plane, pitch, (z1 - z0) * plane * sizeof(T), 9,
+                              cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + c], cs);
+        if (e != cudaSuccess) return e;
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int z0 = c * g.nz / nch, z1 = (c + 1) * g.nz / nch;
+        if ((e = cudaStreamWaitEvent(st, ev[2 + c], 0)) != cudaSuccess) return e;
+        e = launch_fwd<T>(g, tn.t_fwd, xd + z0 * plane, K + z0 * plane, spec + z0 * pspec, nullptr, st, vin, z1 - z0);
+        if (e != cudaSuccess) return e;
+    }
+    if (pa.sym)
+        e = launch_zsym<T>(g, spec, pa, nullptr, st);
+    else if (tn.z_blocks != 0 && static_cast<const void*>(spec) == h->d_spec)
+        e = launch_z_tma<T>(h, tn.wz, tn.t_z, tn.z_blocks, pa, nullptr, st);
+    else
+        e = launch_z<T>(g, tn.wz, tn.t_z, spec, pa, nullptr, st);
+    if (e != cudaSuccess) return e;
+    for (int c = 0; c < nch; ++c) {
+        const int z0 = c * g.nz / nch, z1 = (c + 1) * g.nz / nch;
+        e = launch_inv<T>(g, t_inv, b_inv, spec + z0 * pspec, yd + z0 * plane, oa, nullptr, st, vout, h->d_flag + 2,
+                          z1 - z0);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + nch + c], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[2 + nch + c], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(y_host + z0 * plane, pitch, yd + z0 * plane, pitch, (z1 - z0) * plane * sizeof(T), 9,
+                                  cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return e;
+    }
+    // the handle's stream resumes after the last copy
+    if ((e = cudaEventRecord(ev[1], cs)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(st, ev[1], 0);
+}
+
 template cudaError_t launch_galerkin<double>(const gff_handle*, const double*, const double*, double*,
                                              const ProjArgs&, const OutArgs&, double2*, cudaEvent_t*, const int*);
 template cudaError_t launch_galerkin<float>(const gff_handle*, const float*, const float*, float*, const ProjArgs&,
                                             const OutArgs&, float2*, cudaEvent_t*, const int*);
+template cudaError_t launch_galerkin_host<double>(gff_handle*, const double*, double*, double*, double*,
+                                                  const double*, const ProjArgs&, const OutArgs&, double2*);
+template cudaError_t launch_galerkin_host<float>(gff_handle*, const float*, float*, float*, float*, const float*,
+                                                 const ProjArgs&, const OutArgs&, float2*);
 
 }  // namespace gff
 

@@ -213,6 +213,10 @@ struct gff_handle {
     double prev_d9[9] = {0};     // d of the last completed increment
     double prev2_d9[9] = {0};    // d of the one before
     struct gff_unet* unet = nullptr;
+    // host-buffer apply: copy stream and its events, made on first use
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t pipe_ev[18] = {};
+    int pipe_nev = 0;
     std::string err;
 };
 
@@ -242,6 +246,11 @@ template <typename T>
 cudaError_t launch_galerkin(const gff_handle* h, const T* x, const T* K, T* y, const ProjArgs& pa,
                             const OutArgs& oa, typename C2<T>::t* spec, cudaEvent_t* ev = nullptr,
                             const int* skip = nullptr);
+// the apply from host x_host to host y_host through the device buffers xd, yd,
+// pipelined over chunks of z-planes (copy stream + events of the handle)
+template <typename T>
+cudaError_t launch_galerkin_host(gff_handle* h, const T* x_host, T* y_host, T* xd, T* yd, const T* K,
+                                 const ProjArgs& pa, const OutArgs& oa, typename C2<T>::t* spec);
 size_t plane_smem_bytes(int nx, int ny, int elem);
 // Mixed-radix plan of one axis (false: n unsupported) and the frequency held
 // at position pos after the forward (decimation in frequency) transform:

@@ -250,16 +250,36 @@ __device__ double cp_residual(const double* F, const double* A, const double* ch
                               const double* __restrict__ geo, const CPParamsDev& pr, double coef, int p, ElState& st,
                               double* chi, double* dh, double* r, double* iden) {
     elastic_state(F, A, dg, geo, st);
-    double rmax = 0.0;
+    // the twelve denominators 1 + d |dg_a| inverted with one FP64 division
+    // (simultaneous inversion: prefix products, one reciprocal of the last,
+    // back-substitution), unless their product leaves the finite range
+    double den[NSLIP], pre[NSLIP];
+#pragma unroll
     for (int a = 0; a < NSLIP; ++a) {
-        const double id = 1.0 / (1.0 + pr.d * fabs(dg[a]));
-        iden[a] = id;
-        chi[a] = (chin[a] + pr.c * dg[a]) * id;
+        den[a] = fma(pr.d, fabs(dg[a]), 1.0);
+        pre[a] = a ? pre[a - 1] * den[a] : den[a];
+    }
+    if (pre[NSLIP - 1] < 1e300) {
+        double inv = 1.0 / pre[NSLIP - 1];
+#pragma unroll
+        for (int a = NSLIP - 1; a > 0; --a) {
+            iden[a] = inv * pre[a - 1];
+            inv *= den[a];
+        }
+        iden[0] = inv;
+    } else {
+        for (int a = 0; a < NSLIP; ++a) iden[a] = 1.0 / den[a];
+    }
+    const double pd = (double)p;
+    double rmax = 0.0;
+#pragma unroll
+    for (int a = 0; a < NSLIP; ++a) {
+        chi[a] = (chin[a] + pr.c * dg[a]) * iden[a];
         const double x = (st.tau[a] - chi[a]) * pr.itau0;
         const double ax = fabs(x);
         const double axp1 = ipow(ax, p - 1);
-        dh[a] = p * axp1;
-        r[a] = dg[a] - coef * sgn(x) * axp1 * ax;
+        dh[a] = pd * axp1;
+        r[a] = dg[a] - coef * copysign(axp1 * ax, x);
         rmax = fmax(rmax, fabs(r[a]));
     }
     return rmax;

@@ -349,3 +349,44 @@ def test_timeout_fails_the_increment_and_keeps_the_state():
         assert rep.residual <= 1e-8 and np.allclose(rep.Fmacro, Fbar, rtol=0, atol=1e-14)
     finally:
         g.gff_destroy(h)
+
+
+# 64^3 takes 8 chunks of 8 planes; 36 planes split 4 / 5 unevenly; the persistent inverse
+# passes (streamed with 5 blocks, register-staged with 4) are replaced per chunk
+HOST_CASES = [((64, 64, 64), None), ((36, 48, 64), None), ((64, 64, 64), (512, 8, 256, 512, 5, 0)),
+              ((64, 64, 64), (-256, 8, 256, 512, -4, 0)), ((8, 16, 16), None)]
+
+
+@pytest.mark.parametrize("shape,tiles", HOST_CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_host_buffer_apply_equals_device_apply(shape, tiles, prec):
+    """gff_apply_operator_host copies x in and y out in chunks of z-planes that
+    overlap the plane passes of the other chunks: the same kernels on the same
+    planes as gff_apply_operator, so y is bitwise the same -- from pageable and
+    from pinned host buffers, on repeated calls."""
+    torch = torch_cuda()
+    g = gff()
+    ms = polycrystal(shape, 6, 9)
+    h = g.create_rve(ms, {0: g.make_material(g.GFF_MAT_SVK_CUBIC)}, g.make_options())
+    try:
+        g.gff_constitutive(h, 1.0)
+        if tiles is not None:
+            g.gff_set_tiles(h, tiles, tiles)
+        dt = np.float64 if prec == 0 else np.float32
+        xh = np.ascontiguousarray(_field(13, shape).reshape(9, -1).astype(dt))
+        X = torch.from_numpy(xh.copy()).cuda()
+        Y = torch.empty_like(X)
+        g.gff_apply_operator(h, prec, MASKS[1], X, Y)
+        torch.cuda.synchronize()
+        ref = Y.cpu().numpy()
+        yh = np.full_like(xh, np.nan)
+        g.gff_apply_operator_host(h, prec, MASKS[1], xh, yh)
+        assert np.array_equal(yh, ref)
+        xp = torch.from_numpy(xh.copy()).pin_memory()
+        yp = torch.empty_like(xp).pin_memory()
+        for _ in range(2):
+            yp.fill_(float("nan"))
+            g.gff_apply_operator_host(h, prec, MASKS[1], xp, yp)
+            assert np.array_equal(yp.numpy(), ref)
+    finally:
+        g.gff_destroy(h)
