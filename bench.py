@@ -771,7 +771,7 @@ def cg_kernel_roofline(ms3, n_elems, elem, peak):
     the update reads x, p, r, Ap and writes x, r; p = r + beta p reads 2 and
     writes 1 (each vector n_elems values of elem bytes)."""
     accesses = [2, 6, 3]
-    names = ["dot p.Ap (k_dot_partial_skip + k_final_alpha)", "x, r update + r.r (k_cg_update_dev + k_final_beta)",
+    names = ["dot p.Ap with alpha (k_cg_alpha)", "x, r update + r.r with beta (k_cg_update_dev)",
              "p = r + beta p (k_xpby_dev)"]
     out = {}
     for nm, a, ms in zip(names, accesses, ms3):

@@ -197,6 +197,12 @@ __global__ void __launch_bounds__(TPB) k_fill(T* __restrict__ y, T v, long long 
 }
 
 // ---- device-resident CG iteration (no host round trip per iteration)
+// Each reduction's partial sums and its final sum share one launch: the block
+// that takes the grid's last ticket (flag[CG_TICKET_*], returned to 0 by that
+// block) adds the RED_BLOCKS partials in the same fixed order as the batched
+// final kernels, so the scalars stay deterministic and bitwise equal to the
+// batched solver's.  Three launches per iteration: p.Ap with alpha; the x, r
+// update with r.r, beta and the convergence test; the direction update.
 __global__ void k_cg_init(double* cg, int* flag, double rr0, double stop2) {
     cg[CG_RR] = rr0;
     cg[CG_PAP] = 0.0;
@@ -206,25 +212,42 @@ __global__ void k_cg_init(double* cg, int* flag, double rr0, double stop2) {
     cg[CG_ITERS] = 0.0;
     flag[0] = rr0 <= stop2 ? 1 : 0;
     flag[1] = 0;
+    flag[CG_TICKET_ALPHA] = flag[CG_TICKET_BETA] = flag[CG_TICKET_DIR] = 0;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(TPB) k_dot_partial_skip(const T* __restrict__ a, const T* __restrict__ b, long long n,
-                                                          double* __restrict__ partial, const int* __restrict__ flag) {
-    if (*flag) return;
-    __shared__ double sh[32];
-    double acc = dot_thread<T>(a, b, n);
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+// True in every thread of the block that finishes last; every other block's
+// partial sum (stored before its ticket, behind a fence) is then visible.
+__device__ __forceinline__ bool last_block(int* ticket) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+        if (last) *ticket = 0;
+    }
+    __syncthreads();
+    return last != 0;
 }
 
-// alpha = r.r / p.Ap ; a zero or non-finite p.Ap stops the solve with the breakdown flag
-__global__ void __launch_bounds__(TPB) k_final_alpha(const double* __restrict__ partial, int nb, double* cg, int* flag) {
-    if (*flag) return;
-    __shared__ double sh[32];
+// the sum of nb partials, in the order of the batched final kernels (L2 reads:
+// the partials were written by other blocks of this launch)
+__device__ __forceinline__ double partial_total(const double* partial, int nb, double* sh) {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
-    acc = block_sum(acc, sh);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += __ldcg(partial + i);
+    return block_sum(acc, sh);
+}
+
+// p.Ap, then (last block) alpha = r.r / p.Ap; a zero or non-finite p.Ap stops
+// the solve with the breakdown flag
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_cg_alpha(const T* __restrict__ p, const T* __restrict__ Ap, long long n,
+                                                 double* __restrict__ partial, double* cg, int* flag) {
+    if (*flag) return;
+    __shared__ double sh[32];
+    double acc = block_sum(dot_thread<T>(p, Ap, n), sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    if (!last_block(flag + CG_TICKET_ALPHA)) return;
+    acc = partial_total(partial, gridDim.x, sh);
     if (threadIdx.x == 0) {
         cg[CG_PAP] = acc;
         if (acc == 0.0 || !isfinite(acc)) {
@@ -236,24 +259,19 @@ __global__ void __launch_bounds__(TPB) k_final_alpha(const double* __restrict__ 
     }
 }
 
+// x += alpha p, r -= alpha Ap with r.r, then (last block) beta = r.r(new) /
+// r.r(old), the iteration count and the convergence test r.r <= stop^2
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_cg_update_dev(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                        const T* __restrict__ Ap, long long n, double* __restrict__ partial,
-                                                       const double* __restrict__ cg, const int* __restrict__ flag) {
+                                                       double* cg, int* flag) {
     if (*flag) return;
     __shared__ double sh[32];
     double acc = update_thread<T>(x, r, p, Ap, (T)cg[CG_ALPHA], n);
     acc = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-}
-
-// beta = r.r(new) / r.r(old), iteration count, convergence test on r.r <= stop^2
-__global__ void __launch_bounds__(TPB) k_final_beta(const double* __restrict__ partial, int nb, double* cg, int* flag) {
-    if (*flag) return;
-    __shared__ double sh[32];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += partial[i];
-    acc = block_sum(acc, sh);
+    if (!last_block(flag + CG_TICKET_BETA)) return;
+    acc = partial_total(partial, gridDim.x, sh);
     if (threadIdx.x == 0) {
         cg[CG_BETA] = acc / cg[CG_RR];
         cg[CG_RR] = acc;
@@ -267,16 +285,14 @@ __global__ void __launch_bounds__(TPB) k_final_beta(const double* __restrict__ p
     }
 }
 
-// p = r + beta p (skipped once the solve has stopped before this iteration)
+// p = r + beta p (skipped once the solve has stopped before this iteration);
+// after the run that follows convergence, the last block makes the stop final
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_xpby_dev(T* __restrict__ p, const T* __restrict__ r, long long n,
                                                   const double* __restrict__ cg, int* __restrict__ flag) {
     if (*flag == 1) return;
     xpby_thread<T>(p, r, (T)cg[CG_BETA], n);
-}
-
-__global__ void k_promote_stop(int* flag) {
-    if (flag[0] == 2) flag[0] = 1;
+    if (last_block(flag + CG_TICKET_DIR) && threadIdx.x == 0 && flag[0] == 2) flag[0] = 1;
 }
 
 // ---- batched CG: blockIdx.y = RVE; each RVE uses the same RED_BLOCKS x TPB
@@ -456,8 +472,7 @@ cudaError_t launch_cg_init(double* cg, int* flag, double rr0, double stop2, cuda
 template <typename T>
 cudaError_t launch_cg_alpha(const T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,
                             cudaStream_t s) {
-    k_dot_partial_skip<T><<<RED_BLOCKS, TPB, 0, s>>>(p, Ap, n, partial, flag);
-    k_final_alpha<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+    k_cg_alpha<T><<<RED_BLOCKS, TPB, 0, s>>>(p, Ap, n, partial, cg, flag);
     return cudaGetLastError();
 }
 
@@ -466,9 +481,7 @@ template <typename T>
 cudaError_t launch_cg_step(T* x, T* r, T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,
                            cudaStream_t s) {
     k_cg_update_dev<T><<<RED_BLOCKS, TPB, 0, s>>>(x, r, p, Ap, n, partial, cg, flag);
-    k_final_beta<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
     k_xpby_dev<T><<<grid_for(n), TPB, 0, s>>>(p, r, n, cg, flag);
-    k_promote_stop<<<1, 1, 0, s>>>(flag);
     return cudaGetLastError();
 }
 
@@ -551,11 +564,9 @@ cudaError_t time_cg_kernels(T* x, T* r, T* p, T* Ap, long long n, double* partia
     double acc[3] = {0, 0, 0};
     for (int it = 0; it < reps && e == cudaSuccess; ++it) {
         cudaEventRecord(ev[0], s);
-        k_dot_partial_skip<T><<<RED_BLOCKS, TPB, 0, s>>>(p, Ap, n, partial, flag);
-        k_final_alpha<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
+        k_cg_alpha<T><<<RED_BLOCKS, TPB, 0, s>>>(p, Ap, n, partial, cg, flag);
         cudaEventRecord(ev[1], s);
         k_cg_update_dev<T><<<RED_BLOCKS, TPB, 0, s>>>(x, r, p, Ap, n, partial, cg, flag);
-        k_final_beta<<<1, TPB, 0, s>>>(partial, RED_BLOCKS, cg, flag);
         cudaEventRecord(ev[2], s);
         k_xpby_dev<T><<<grid_for(n), TPB, 0, s>>>(p, r, n, cg, flag);
         cudaEventRecord(ev[3], s);
