@@ -301,8 +301,8 @@ cudaError_t launch_fill(double* y, double v, long long n, cudaStream_t s);
 // Device-resident CG scalars (see vec.cu): cg[CG_RR] = r.r, cg[CG_PAP], cg[CG_ALPHA],
 // cg[CG_BETA], cg[CG_STOP2] = stop^2, cg[CG_ITERS]; flag[0] = stop, flag[1] = breakdown.
 enum { CG_RR = 0, CG_PAP = 1, CG_ALPHA = 2, CG_BETA = 3, CG_STOP2 = 4, CG_ITERS = 5 };
-// flag[CG_TICKET_*]: the last-block tickets of the three CG launches (0 between launches)
-enum { CG_TICKET_ALPHA = 4, CG_TICKET_BETA = 5, CG_TICKET_DIR = 6 };
+// flag[CG_TICKET_*]: the last-block tickets of the two CG reductions (0 between launches)
+enum { CG_TICKET_ALPHA = 4, CG_TICKET_BETA = 5 };
 cudaError_t launch_cg_init(double* cg, int* flag, double rr0, double stop2, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cg_alpha(const T* p, const T* Ap, long long n, double* partial, double* cg, int* flag,

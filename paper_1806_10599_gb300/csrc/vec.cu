@@ -203,6 +203,9 @@ __global__ void __launch_bounds__(TPB) k_fill(T* __restrict__ y, T v, long long 
 // final kernels, so the scalars stay deterministic and bitwise equal to the
 // batched solver's.  Three launches per iteration: p.Ap with alpha; the x, r
 // update with r.r, beta and the convergence test; the direction update.
+// The two reductions are bounded to RED_BLOCKS / 152 resident blocks per SM
+// (64 registers): with fewer, a second wave of blocks would run their
+// grid-stride loops alone.
 __global__ void k_cg_init(double* cg, int* flag, double rr0, double stop2) {
     cg[CG_RR] = rr0;
     cg[CG_PAP] = 0.0;
@@ -212,7 +215,7 @@ __global__ void k_cg_init(double* cg, int* flag, double rr0, double stop2) {
     cg[CG_ITERS] = 0.0;
     flag[0] = rr0 <= stop2 ? 1 : 0;
     flag[1] = 0;
-    flag[CG_TICKET_ALPHA] = flag[CG_TICKET_BETA] = flag[CG_TICKET_DIR] = 0;
+    flag[CG_TICKET_ALPHA] = flag[CG_TICKET_BETA] = 0;
 }
 
 // True in every thread of the block that finishes last; every other block's
@@ -240,9 +243,13 @@ __device__ __forceinline__ double partial_total(const double* partial, int nb, d
 // p.Ap, then (last block) alpha = r.r / p.Ap; a zero or non-finite p.Ap stops
 // the solve with the breakdown flag
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_cg_alpha(const T* __restrict__ p, const T* __restrict__ Ap, long long n,
+__global__ void __launch_bounds__(TPB, RED_BLOCKS / 152) k_cg_alpha(const T* __restrict__ p, const T* __restrict__ Ap, long long n,
                                                  double* __restrict__ partial, double* cg, int* flag) {
-    if (*flag) return;
+    if (*flag) {
+        // a stop reached in the previous iteration (2: its direction update has run) becomes final
+        if (blockIdx.x == 0 && threadIdx.x == 0 && *flag == 2) *flag = 1;
+        return;
+    }
     __shared__ double sh[32];
     double acc = block_sum(dot_thread<T>(p, Ap, n), sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
@@ -262,7 +269,7 @@ __global__ void __launch_bounds__(TPB) k_cg_alpha(const T* __restrict__ p, const
 // x += alpha p, r -= alpha Ap with r.r, then (last block) beta = r.r(new) /
 // r.r(old), the iteration count and the convergence test r.r <= stop^2
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_cg_update_dev(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+__global__ void __launch_bounds__(TPB, RED_BLOCKS / 152) k_cg_update_dev(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                                                        const T* __restrict__ Ap, long long n, double* __restrict__ partial,
                                                        double* cg, int* flag) {
     if (*flag) return;
@@ -285,14 +292,14 @@ __global__ void __launch_bounds__(TPB) k_cg_update_dev(T* __restrict__ x, T* __r
     }
 }
 
-// p = r + beta p (skipped once the solve has stopped before this iteration);
-// after the run that follows convergence, the last block makes the stop final
+// p = r + beta p (skipped once the solve has stopped before this iteration;
+// flag 2, convergence in this iteration, still runs it -- the next k_cg_alpha
+// makes the stop final)
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_xpby_dev(T* __restrict__ p, const T* __restrict__ r, long long n,
-                                                  const double* __restrict__ cg, int* __restrict__ flag) {
+                                                  const double* __restrict__ cg, const int* __restrict__ flag) {
     if (*flag == 1) return;
     xpby_thread<T>(p, r, (T)cg[CG_BETA], n);
-    if (last_block(flag + CG_TICKET_DIR) && threadIdx.x == 0 && flag[0] == 2) flag[0] = 1;
 }
 
 // ---- batched CG: blockIdx.y = RVE; each RVE uses the same RED_BLOCKS x TPB
