@@ -188,3 +188,60 @@ def test_cp_polycrystal_increment_runs_and_conserves_macro_strain():
     assert np.abs(reps[-1]["Fmacro"] - h.Fbar[11]).max() < 1e-13
     pc, w, fs = rve.grain_fips()
     assert (pc > 0).all() and (fs > 0).all()
+
+
+def _one_voxel_cycles(hist, S0, C, normals, cp, fs_k, fs_sigma_y, reset_each_cycle=True):
+    """The same single crystal as one voxel: its return map driven by the
+    prescribed F history directly (no spectral solve), with its own FIP
+    accumulators (cleared at each cycle start when asked)."""
+    Fpi, chi = np.eye(3)[None].copy(), np.zeros((1, 12))
+    acc = fips.new_accumulators(1)
+    fips.reset(acc)
+    P_hist = []
+    for k in range(hist.nsteps):
+        if reset_each_cycle and hist.cycle_start[k]:
+            fips.reset(acc)
+        F = hist.Fbar[k].reshape(1, 3, 3)
+        out = mat.cp_return_map(F, Fpi, chi, hist.dt[k], S0, C, cp)
+        assert out["conv"].all()
+        Fpi, chi = out["Fpi"], out["chi"]
+        fips.accumulate(acc, np.array([0]), out["dg"], out["tau"], S0, normals, out["P"], F)
+        P_hist.append(out["P"][0].reshape(9))
+    pc, w, fs = fips.grain_fips(acc, np.array([0]), 1, np.array([True]), fs_k=fs_k, fs_sigma_y=fs_sigma_y)
+    return np.array(P_hist), pc[0], w[0], fs[0]
+
+
+def test_single_orientation_polycrystal_is_one_crystal_over_two_cycles():
+    """Grains that all share one orientation make a single crystal: under two
+    full strain cycles (both reversals, the accumulators cleared again at the
+    second cycle start) every increment of the RVE is affine and converged at
+    Newton iteration 0, its macro P is the one-voxel return map's P driven by
+    the same F, and every grain's FIPs are the one-voxel FIPs of the second
+    cycle alone (with the first cycle's kept they differ)."""
+    from rve_inputs import cyclic_history
+
+    rng = np.random.default_rng(5)
+    gid = rng.integers(0, 3, size=(4, 4, 4))
+    q = np.array([0.9, 0.3, -0.2, 0.25])
+    q /= np.linalg.norm(q)
+    ms = _ms(gid, np.tile(q, (3, 1)))
+    opt = Options(newton_tol=1e-9, cg_tol=1e-10)
+    rve = OracleRVE(ms, {0: Material(CP_FCC)}, opt)
+    hist = cyclic_history(0.01, 2, incr_per_quarter=3)
+    reps = rve.run(hist)
+    assert all(r["converged"] and r["newton"] == 0 for r in reps)
+    Fv = rve.F.reshape(9, -1)
+    assert np.abs(Fv - hist.Fbar[-1][:, None]).max() < 1e-13  # uniform: the sum of the increments
+    g = rve.grains[0]
+    P1, pc1, w1, fs1 = _one_voxel_cycles(hist, g["S0"], g["C"], g["normals"], g["mat"].cp, opt.fs_k, opt.fs_sigma_y)
+    Pm = np.array([r["Pmacro"] for r in reps])
+    assert np.abs(Pm - P1).max() <= 1e-9 * np.abs(P1).max()
+    assert np.abs(P1[:, 0]).max() > 1e8  # plastic: well past the elastic range, both signs
+    assert P1[:, 0].min() < -1e8
+    pc, w, fs = rve.grain_fips()
+    assert pc1 > 0 and fs1 > 0
+    assert np.allclose(pc, pc1, rtol=1e-9, atol=0) and np.allclose(fs, fs1, rtol=1e-9, atol=0)
+    assert np.allclose(w, w1, rtol=1e-9, atol=1e-9 * np.abs(w1).max())
+    _, pc2, _, fs2 = _one_voxel_cycles(hist, g["S0"], g["C"], g["normals"], g["mat"].cp, opt.fs_k, opt.fs_sigma_y,
+                                       reset_each_cycle=False)
+    assert pc2 > 1.5 * pc1  # the reset matters: two cycles' plastic strain against one
