@@ -22,6 +22,7 @@ Modules
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, invariants, brute force or finite differences, except the
 crystal-plasticity polycrystal fields and the FIPs, which are "parity
-unpinned" beyond the single-voxel checks of the return map (no value printed
-in the paper can be reproduced without the FEM reference).
+unpinned" beyond the single-voxel checks of the return map and the
+single-crystal reduction of a whole polycrystal run (no value printed in the
+paper can be reproduced without the FEM reference).
 """
