@@ -212,7 +212,9 @@ def _one_voxel_cycles(hist, S0, C, normals, cp, fs_k, fs_sigma_y, reset_each_cyc
 
 
 def test_single_orientation_polycrystal_is_one_crystal_over_two_cycles():
-    """Grains that all share one orientation make a single crystal: under two
+    """Sect. 2.1 (the Newton-CG increment), Sect. 3.2 (Eq. gamma_dot) and
+    Sect. 3.3 (FIPs accumulated over a loading cycle).
+    Grains that all share one orientation make a single crystal: under two
     full strain cycles (both reversals, the accumulators cleared again at the
     second cycle start) every increment of the RVE is affine and converged at
     Newton iteration 0, its macro P is the one-voxel return map's P driven by
