@@ -54,3 +54,17 @@ def test_roofline_bytes_and_bound():
 def test_workload_config_names_the_sizes():
     c = bench.workload_config(64)
     assert c["grid"] == [64, 64, 64] and "64^3" in c["workload"]
+
+
+def test_algorithmic_bytes_and_flops_per_voxel_at_128():
+    """The per-voxel figures the roofline divides by: bytes of each apply
+    kernel (every field read or written once) and the 5 n log2 n FLOP
+    convention, with the z pass transforming two fields per tensor row."""
+    b64, b32 = bench.kernel_bytes_per_voxel(128, 8), bench.kernel_bytes_per_voxel(128, 4)
+    assert abs(b64[0] - 793.125) < 1e-9 and abs(b64[1] - 146.25) < 1e-9 and abs(b64[2] - 145.125) < 1e-9
+    assert abs(sum(b64) - 1084.5) < 1e-9 and abs(sum(b32) - 542.25) < 1e-9
+    fl = bench.kernel_flops_per_voxel(128)
+    fr = 65 / 128
+    assert abs(fl[0] - (162 + 9 * (2.5 * 7 + 5 * 7 * fr))) < 1e-9
+    assert abs(fl[1] - (6 * 2 * 5 * 7 * fr + 72 * fr)) < 1e-9
+    assert abs(fl[2] - 9 * (2.5 * 7 + 5 * 7 * fr)) < 1e-9
